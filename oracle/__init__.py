@@ -1,0 +1,272 @@
+"""CPU FP64 oracle of the GB300 performance-model hot path (arxiv 2605.04178).
+
+TEST INFRASTRUCTURE ONLY: the tests, the package smoke check and the bench's
+CPU-baseline arm import this module; the product library never does, and it
+imports nothing from the product package.  The arithmetic lives in
+oracle.cpp (FP64, plain loops, one function per passage of the paper); this
+file compiles it with g++ and wraps it for numpy arrays.
+
+Parity status of each part (pins are in tests/test_oracle_*.py):
+  gemm_f64            pinned: numpy FP64 matmul, integer matrices, identity/permutation
+  to_bf16/tf32/e4m3   pinned: exhaustive/structural checks against the format definitions
+  triad_f32           pinned: exact rational arithmetic (fractions) on random cases
+  pchase              pinned: single-cycle walk returns to its start after n hops
+  model_batch         pinned: survey golden rows, closed forms, homogeneity, monotonicity
+  model gradient      pinned: central differences and Euler's homogeneity identity
+  autotune            pinned: brute force in plain Python on small spaces
+  grouped model       pinned: reduces to the single-GEMM stage time for one group
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "oracle.cpp")
+_BUILD = os.path.join(_HERE, "_build")
+_SO = os.path.join(_BUILD, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+KIND_GEMM, KIND_COPY, KIND_TRIAD, KIND_TMA2D = 0, 1, 2, 3
+DT_FP32, DT_BF16, DT_FP8 = 0, 1, 2
+N_PARAMS = 16
+
+PARAM_NAMES = ("T_launch", "B_sus", "B_peak", "w0", "L_TMA", "B_TMA", "R_tf32", "R_bf16", "R_fp8",
+               "L_mma", "BW_tmem_rd", "BW_tmem_wr", "L_mbar", "L_tmem_mgmt", "S_2SM", "c_alpha")
+# Time-like parameters (seconds) and rate-like parameters (per second); the
+# rest (w0, S_2SM, c_alpha) are dimensionless or sizes.
+LATENCY_IDX = (0, 4, 9, 12, 13)
+RATE_IDX = (1, 2, 5, 6, 7, 8, 10, 11)
+
+
+def build(force: bool = False) -> str:
+    """Compile oracle.cpp into oracle/_build/liboracle.so (g++, OpenMP, FP64)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
+        tmp = _SO + ".tmp%d" % os.getpid()
+        cmd = ["g++", "-O2", "-std=c++17", "-fopenmp", "-ffp-contract=off", "-shared", "-fPIC",
+               _SRC, "-o", tmp]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, _SO)
+    return _SO
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            lib = ctypes.CDLL(_SO)
+            P = ctypes.c_void_p
+            i64 = ctypes.c_int64
+            lib.orc_gemm_f64.argtypes = [P, P, i64, i64, i64, P]
+            lib.orc_gemm_f64_f64.argtypes = [P, P, i64, i64, i64, P]
+            lib.orc_to_bf16.argtypes = [P, i64, P]
+            lib.orc_tf32_split.argtypes = [P, i64, P, P]
+            lib.orc_to_e4m3.argtypes = [P, i64, P]
+            lib.orc_from_e4m3.argtypes = [P, i64, P]
+            lib.orc_triad_f32.argtypes = [P, P, ctypes.c_float, i64, P]
+            lib.orc_pchase.argtypes = [P, i64, ctypes.c_uint32, i64]
+            lib.orc_pchase.restype = ctypes.c_uint32
+            lib.orc_cfg_valid.argtypes = [ctypes.c_int] * 6
+            lib.orc_cfg_valid.restype = ctypes.c_int
+            lib.orc_model_batch.argtypes = [i64] + [P] * 10 + [P, ctypes.c_int, P, P]
+            lib.orc_model_loss_grad.argtypes = [i64] + [P] * 10 + [P, ctypes.c_int, P, P, P]
+            lib.orc_autotune.argtypes = [i64, P, ctypes.c_int, P, ctypes.c_int, P, P]
+            lib.orc_grouped_predict.argtypes = [ctypes.c_int, P, ctypes.c_int32, ctypes.c_int32, P, P,
+                                                ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                                P, ctypes.c_int]
+            lib.orc_grouped_predict.restype = ctypes.c_double
+            lib.orc_grouped_autotune.argtypes = [ctypes.c_int, P, ctypes.c_int32, ctypes.c_int32,
+                                                 ctypes.c_int, P, ctypes.c_int, P, P, P]
+            lib.orc_grouped_autotune.restype = ctypes.c_double
+            _lib = lib
+    return _lib
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _c(a, dtype):
+    return np.ascontiguousarray(a, dtype=dtype)
+
+
+# ----------------------------------------------------------------------------- GEMM
+def gemm_f64(A: np.ndarray, B: np.ndarray) -> np.ndarray:
+    """FP64 C = A.B of FP32 row-major A [M, K], B [K, N] (the definition, k ascending)."""
+    A = _c(A, np.float32)
+    B = _c(B, np.float32)
+    M, K = A.shape
+    K2, N = B.shape
+    assert K == K2
+    C = np.empty((M, N), dtype=np.float64)
+    _load().orc_gemm_f64(_ptr(A), _ptr(B), M, N, K, _ptr(C))
+    return C
+
+
+def gemm_f64_f64(A: np.ndarray, B: np.ndarray) -> np.ndarray:
+    A = _c(A, np.float64)
+    B = _c(B, np.float64)
+    M, K = A.shape
+    _, N = B.shape
+    C = np.empty((M, N), dtype=np.float64)
+    _load().orc_gemm_f64_f64(_ptr(A), _ptr(B), M, N, K, _ptr(C))
+    return C
+
+
+# ----------------------------------------------------------------------------- formats
+def to_bf16(x: np.ndarray) -> np.ndarray:
+    """FP32 values rounded to bf16 (RNE), returned as FP32."""
+    x = _c(x, np.float32)
+    y = np.empty_like(x)
+    _load().orc_to_bf16(_ptr(x), x.size, _ptr(y))
+    return y
+
+
+def tf32_split(x: np.ndarray):
+    """(hi, lo) with hi = tf32_rn(x), lo = tf32_rn(x - hi), both FP32 with 13 zero low bits."""
+    x = _c(x, np.float32)
+    hi = np.empty_like(x)
+    lo = np.empty_like(x)
+    _load().orc_tf32_split(_ptr(x), x.size, _ptr(hi), _ptr(lo))
+    return hi, lo
+
+
+def to_e4m3(x: np.ndarray) -> np.ndarray:
+    """FP8 e4m3 codes (uint8) of FP32 values, RNE with saturation to +-448."""
+    x = _c(x, np.float32)
+    y = np.empty(x.shape, dtype=np.uint8)
+    _load().orc_to_e4m3(_ptr(x), x.size, _ptr(y))
+    return y
+
+
+def from_e4m3(code: np.ndarray) -> np.ndarray:
+    code = _c(code, np.uint8)
+    y = np.empty(code.shape, dtype=np.float32)
+    _load().orc_from_e4m3(_ptr(code), code.size, _ptr(y))
+    return y
+
+
+def fp8_scale(x: np.ndarray) -> np.float32:
+    """Per-tensor scale 448 / max|x| in FP32 (one IEEE division)."""
+    amax = np.float32(np.max(np.abs(x)))
+    return np.float32(np.float32(448.0) / amax)
+
+
+# ----------------------------------------------------------------------------- probes
+def triad_f32(b: np.ndarray, c: np.ndarray, s: float) -> np.ndarray:
+    b = _c(b, np.float32)
+    c = _c(c, np.float32)
+    a = np.empty_like(b)
+    _load().orc_triad_f32(_ptr(b), _ptr(c), ctypes.c_float(s), b.size, _ptr(a))
+    return a
+
+
+def pchase(buf: np.ndarray, stride_words: int, start: int, hops: int) -> int:
+    buf = _c(buf, np.uint32)
+    return int(_load().orc_pchase(_ptr(buf), stride_words, start, hops))
+
+
+# ----------------------------------------------------------------------------- model
+def cfg_valid(BM, BN, BK, s, g, dtype) -> bool:
+    return bool(_load().orc_cfg_valid(int(BM), int(BN), int(BK), int(s), int(g), int(dtype)))
+
+
+_FIELDS = ("M", "N", "K", "BM", "BN", "BK", "stages", "cta_group", "dtype", "kind")
+
+
+def _soa(cfgs: dict):
+    n = len(cfgs["M"])
+    cols = []
+    for f in _FIELDS:
+        v = cfgs.get(f)
+        if v is None:
+            v = np.zeros(n, dtype=np.int32)
+        cols.append(_c(v, np.int32))
+    return n, cols
+
+
+def model_batch(cfgs: dict, theta, n_sm: int, grad: bool = False):
+    """Stage-model prediction (FP64) per configuration; with grad, also dT/dtheta [n, 16]."""
+    n, cols = _soa(cfgs)
+    th = _c(theta, np.float64)
+    assert th.size == N_PARAMS
+    t = np.empty(n, dtype=np.float64)
+    g = np.empty((n, N_PARAMS), dtype=np.float64) if grad else None
+    _load().orc_model_batch(n, *[_ptr(c) for c in cols], _ptr(th), int(n_sm), _ptr(t),
+                            _ptr(g) if grad else None)
+    return (t, g) if grad else t
+
+
+def model_loss_grad(cfgs: dict, theta, n_sm: int, t_meas):
+    """Mean squared log error and its gradient in theta (FP64)."""
+    n, cols = _soa(cfgs)
+    th = _c(theta, np.float64)
+    tm = _c(t_meas, np.float64)
+    loss = np.zeros(1, dtype=np.float64)
+    grad = np.zeros(N_PARAMS, dtype=np.float64)
+    _load().orc_model_loss_grad(n, *[_ptr(c) for c in cols], _ptr(th), int(n_sm), _ptr(tm),
+                                _ptr(loss), _ptr(grad))
+    return float(loss[0]), grad
+
+
+def autotune(MNK: np.ndarray, dtype: int, theta, n_sm: int):
+    """Model-optimal (BM, BN, BK, stages, cta_group) per shape, first minimum in lexicographic order."""
+    MNK = _c(MNK, np.int32).reshape(-1, 3)
+    n = MNK.shape[0]
+    th = _c(theta, np.float64)
+    pick = np.zeros((n, 5), dtype=np.int32)
+    t = np.zeros(n, dtype=np.float64)
+    _load().orc_autotune(n, _ptr(MNK), int(dtype), _ptr(th), int(n_sm), _ptr(pick), _ptr(t))
+    return pick, t
+
+
+def grouped_predict(Mg, N, K, BMg, BNg, BK, s, g, dtype, theta, n_sm) -> float:
+    Mg = _c(Mg, np.int32)
+    BMg = _c(BMg, np.int32)
+    BNg = _c(BNg, np.int32)
+    th = _c(theta, np.float64)
+    return float(_load().orc_grouped_predict(len(Mg), _ptr(Mg), int(N), int(K), _ptr(BMg), _ptr(BNg),
+                                             int(BK), int(s), int(g), int(dtype), _ptr(th), int(n_sm)))
+
+
+def grouped_autotune(Mg, N, K, dtype, theta, n_sm):
+    """(T_hat, BM per group, BN per group, (BK, stages, cta_group)) of the best grouped launch."""
+    Mg = _c(Mg, np.int32)
+    G = len(Mg)
+    th = _c(theta, np.float64)
+    bm = np.zeros(G, dtype=np.int32)
+    bn = np.zeros(G, dtype=np.int32)
+    launch = np.zeros(3, dtype=np.int32)
+    t = _load().orc_grouped_autotune(G, _ptr(Mg), int(N), int(K), int(dtype), _ptr(th), int(n_sm),
+                                     _ptr(bm), _ptr(bn), _ptr(launch))
+    return float(t), bm, bn, tuple(int(v) for v in launch)
+
+
+def prior_theta(n_sm: int, f_hz: float = 1.9e9) -> np.ndarray:
+    """Prior parameter vector built from the paper's printed values (Table "parameters",
+    Sec. II-A sustained figures); cycles are converted with the clock f_hz."""
+    th = np.zeros(N_PARAMS, dtype=np.float64)
+    th[0] = 5e-6                      # launch overhead, 5-12 us (Sec. V-B, memory-bound class)
+    th[1] = 6.8e12                    # sustained HBM (Sec. II-A)
+    th[2] = 8.0e12                    # HBM peak (Table "arch-params")
+    th[3] = 64.0 * 2 ** 20            # w0, tunable (Eq. 16)
+    th[4] = 420.0 / f_hz              # L_TMA 420 cycles
+    th[5] = th[1] / n_sm              # B_TMA per SM (not printed)
+    th[7] = 8192.0 * f_hz             # dense BF16 FLOP/cycle/SM
+    th[6] = th[7] / 2.0               # TF32 at half the BF16 rate
+    th[8] = 2.0 * th[7]               # FP8 at twice the BF16 rate (2,250 vs 4,500 TFLOPS)
+    th[9] = 12.0 / f_hz               # tcgen05.mma latency 11-14 cycles
+    th[10] = 16e12                    # TMEM read
+    th[11] = 8e12                     # TMEM write
+    th[12] = 45.0 / f_hz              # L_mbar 40-50 cycles
+    th[13] = 100e-9                   # TMEM alloc + dealloc (not printed)
+    th[14] = 1.0                      # S_2SM
+    th[15] = 0.3                      # alpha(2) = 0.85, alpha(6) = 0.95
+    return th
