@@ -1,0 +1,211 @@
+/*
+ * perfmodel.h -- C ABI of libperfmodel.so, the GB300 (sm_103a) hot path of the
+ * stage-centric performance model of arxiv 2605.04178 ("Microbenchmark-Driven
+ * Analytical Performance Modeling Across Modern GPU Architectures").
+ *
+ * Conventions shared by every entry point
+ *  - Pointers named *_dev are CUDA device pointers on the current device; the
+ *    caller allocates and owns them.  Pointers named *_host are host memory.
+ *    The library keeps only a small per-device cache (TMA descriptors of the
+ *    last call, the watchdog word) and never frees caller memory.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  Entry points documented "async" only enqueue work; those
+ *    documented "synchronises" wait for their stream before returning.
+ *  - Matrices are row-major.  Times are seconds.
+ *  - Every entry point returns a pm_status.  On failure nothing is launched
+ *    unless the status is PM_ECUDA/PM_ETIMEOUT (reported after the fact), and
+ *    pm_last_error() gives a message.  No entry point aborts the process.
+ *  - Device-side waits (mbarrier pipelines) are bounded by a watchdog; on
+ *    expiry the kernel records PM_ETIMEOUT in a device word, releases its
+ *    tensor memory and returns.  Synchronising entry points report it;
+ *    asynchronous ones report it through pm_device_status().
+ */
+#ifndef PERFMODEL_H
+#define PERFMODEL_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  PM_OK = 0,
+  PM_EINVAL = -1,        /* bad argument: null pointer, size, alignment */
+  PM_EUNSUPPORTED = -2,  /* configuration outside the valid tile space */
+  PM_ECUDA = -3,         /* a CUDA runtime/driver call failed */
+  PM_ETIMEOUT = -4,      /* a device-side wait hit the watchdog limit */
+  PM_ENOMEM = -5         /* caller-provided workspace too small */
+} pm_status;
+
+/* Operand precisions of the GEMM family (Sec. II: 5th-gen tensor cores take
+ * TF32, BF16 and FP8; FP32 accumulation in TMEM, Sec. III-A.1).  PM_FP32 runs
+ * three TF32 passes (hi*hi + hi*lo + lo*hi) so the product keeps FP32 accuracy. */
+typedef enum { PM_FP32 = 0, PM_BF16 = 1, PM_FP8E4M3 = 2 } pm_dtype;
+
+/* Workload kinds the model predicts: the GEMM family and the calibration
+ * probes of Sec. V-A (memory copy/triad through Eq. 16, TMA tile copy). */
+typedef enum { PM_KIND_GEMM = 0, PM_KIND_COPY = 1, PM_KIND_TRIAD = 2, PM_KIND_TMA2D = 3 } pm_kind;
+
+/* One workload configuration (24 bytes, 8-byte aligned arrays).
+ *  GEMM : C[M,N] = A[M,K] B[K,N]; tile BM x BN x BK per CTA, `stages` deep
+ *         shared-memory ring, cta_group 1 (one SM) or 2 (CTA pair, the pair
+ *         covers 2*BM x BN), dtype a pm_dtype.  These are the model inputs of
+ *         Sec. III-E (b_M, b_N, b_K, K_tiles, bytes per CTA; P = 1).
+ *  COPY/TRIAD: M = FP32 elements.  TMA2D: M x N FP32 matrix in BM x BN tiles.
+ * Valid GEMM tile space: BM, BN in {64,128,256}; BK in {32,64} (FP32) or
+ * {64,128} (BF16, FP8); stages 2..6; cta_group 1..2; stages * stage bytes
+ * <= 227 KiB - 2 KiB where stage bytes = l*e*BK*(BM + BN/cta_group) with e the
+ * element size and l = 2 for FP32 (hi and lo), else 1; ceil(BM/128)*BN <= 512
+ * TMEM columns (the 256 KB TMEM limit of Sec. III-A.1). */
+typedef struct {
+  int32_t M, N, K;
+  int16_t BM, BN, BK;
+  int8_t stages, cta_group, dtype, kind;
+  int16_t reserved;      /* must be 0 */
+} pm_cfg;
+
+/* Model parameters theta, SI units (Sec. III-A and Eq. 16):
+ *  0 T_launch   1 B_sus      2 B_peak     3 w0          4 L_TMA      5 B_TMA/SM
+ *  6 R_TC tf32  7 R_TC bf16  8 R_TC fp8   9 L_mma      10 BW_TMEM_rd 11 BW_TMEM_wr
+ * 12 L_mbar    13 L_alloc+L_dealloc      14 S_2SM      15 c_alpha
+ * with the overlap law alpha(stages) = clamp(1 - c_alpha/stages, 0, 1). */
+typedef struct { float v[16]; } pm_params;
+
+/* ------------------------------------------------------------------ probes */
+/* Calibration microbenchmarks (Sec. V-A; STREAM-style copy and triad for the
+ * memory-bound class; TMA copy latency and bandwidth by tile size; pointer
+ * chase after Mei & Chu as cited in Sec. III-B).
+ *  PM_PROBE_COPY  : buf1[i] = buf0[i], n FP32 elements (16-byte aligned buffers).
+ *  PM_PROBE_TRIAD : buf0[i] = fmaf(scalar, buf2[i], buf1[i]) (one rounding).
+ *  PM_PROBE_TMA2D : buf1 = buf0, an rows x cols FP32 matrix moved in
+ *                   tile_r x tile_c tiles by TMA loads and TMA stores through
+ *                   a shared-memory ring (cols*4 bytes a multiple of 16).
+ *  PM_PROBE_PCHASE: j = buf0[j * 16] for `hops` hops from `start` by one
+ *                   thread (nodes 64 bytes apart, n nodes); the final j is
+ *                   written to ((uint32_t*)buf1)[0]. */
+typedef enum { PM_PROBE_COPY = 1, PM_PROBE_TRIAD = 2, PM_PROBE_TMA2D = 3, PM_PROBE_PCHASE = 4 } pm_probe_kind;
+
+typedef struct {
+  int32_t kind;          /* pm_probe_kind */
+  int32_t tile_r, tile_c;/* TMA2D tile (rows, cols), each in [8, 256] */
+  uint32_t start;        /* PCHASE start node */
+  int64_t n;             /* COPY/TRIAD elements; PCHASE nodes */
+  int64_t rows, cols;    /* TMA2D matrix */
+  int64_t hops;          /* PCHASE hops */
+  float scalar;          /* TRIAD s */
+  int32_t reserved;
+} pm_probe_args;
+
+typedef struct {
+  double median_s, p25_s, p75_s, min_s;   /* per-launch device time */
+  double bytes;                           /* algorithmic bytes per launch */
+  uint32_t final_index;                   /* PCHASE result */
+  uint32_t reserved;
+} pm_probe_result;
+
+/* One probe launch on `stream` (async). */
+pm_status pm_probe_launch(const pm_probe_args* args, void* buf0, void* buf1, void* buf2, void* stream);
+
+/* `warmup` untimed then `reps` timed launches, each bracketed by CUDA events
+ * on `stream`; fills *out with median and quartiles (Sec. V-B protocol:
+ * 10 warm-ups, 100 runs, median).  Synchronises. */
+pm_status pm_probe_run(const pm_probe_args* args, void* buf0, void* buf1, void* buf2, int warmup, int reps,
+                       void* stream, pm_probe_result* out);
+
+/* ---------------------------------------------------------------- GEMM */
+/* Bytes of the operand buffers pm_gemm_prepare writes: A_op holds A as
+ * dtype [M,K] (FP32: hi then lo, 2*M*K floats), B_op holds B transposed to
+ * [N,K] (K-major, FP32: hi then lo), `scales_dev` 4 floats. */
+pm_status pm_gemm_operand_bytes(int32_t dtype, int32_t M, int32_t N, int32_t K, size_t* a_bytes, size_t* b_bytes);
+
+/* Operand preparation (async): casts row-major FP32 A [M,K] and B [K,N]
+ * into the tensor-core operand formats.  BF16: round to nearest even.
+ * FP8 e4m3: per-tensor scale s = 448/max|X| (FP32 division), codes
+ * RNE-saturated from s*X; scales_dev[0] = s_A, scales_dev[1] = s_B.
+ * FP32: hi = tf32_rn(X), lo = tf32_rn(X - hi).  scales_dev (4 floats) is
+ * required for FP8 and ignored otherwise. */
+pm_status pm_gemm_prepare(int32_t dtype, const float* A_dev, const float* B_dev, int32_t M, int32_t N, int32_t K,
+                          void* A_op_dev, void* B_op_dev, float* scales_dev, void* stream);
+
+/* C[M,N] (FP32, row-major, leading dimension N) = A B with the tile
+ * configuration `cfg` (kind PM_KIND_GEMM), from the operands written by
+ * pm_gemm_prepare.  FP8 results are multiplied by 1/(s_A s_B) read from
+ * scales_dev.  The kernel is the paper's pipeline (Fig. "cta-exec-model"):
+ * TMA -> shared-memory ring -> tcgen05.mma -> TMEM -> epilogue, one
+ * persistent CTA (or CTA pair) per SM.  Async.  Requires K*e % 16 == 0. */
+pm_status pm_gemm_run(const pm_cfg* cfg, const void* A_op_dev, const void* B_op_dev, float* C_dev,
+                      const float* scales_dev, void* stream);
+
+/* Grouped BF16 GEMM in one persistent launch: G problems C_g[M_g,N] =
+ * A_g[M_g,K] B_g[K,N].  A_op_dev stacks the A_g as bf16 [sum M_g, K]; B_op_dev
+ * stacks the B_g transposed, bf16 [G*N, K]; C_dev stacks C_g, FP32
+ * [sum M_g, N].  Group g uses tile BM_host[g] x BN_host[g]; BK, stages and
+ * cta_group are per launch.  Tiles are listed group by group and tile t runs
+ * on CTA t mod (number of CTAs).  Async; capturable in a CUDA graph after one
+ * uncaptured call with the same shapes (which builds the descriptors). */
+pm_status pm_grouped_gemm_run(int32_t G, const int32_t* M_host, int32_t N, int32_t K, const int16_t* BM_host,
+                              const int16_t* BN_host, int32_t BK, int32_t stages, int32_t cta_group,
+                              const void* A_op_dev, const void* B_op_dev, float* C_dev, void* stream);
+
+/* --------------------------------------------------------------- model */
+/* Stage-model prediction T_hat (FP32 seconds) for n configurations (any
+ * kind) on the GPU: Eqs. 2-8 for GEMM tiles with persistent-CTA waves and the
+ * naive roofline as a floor; Eq. 16 for copy/triad; the TMA tile model for
+ * TMA2D.  cfgs_dev: n pm_cfg; t_out_dev: n floats.  Async. */
+pm_status pm_model_predict(const pm_cfg* cfgs_dev, int64_t n, const pm_params* theta_host, int32_t n_sm,
+                           float* t_out_dev, void* stream);
+
+/* Scratch the gradient needs: partial sums of 17 doubles per block. */
+pm_status pm_model_grad_workspace(int64_t n, size_t* bytes);
+
+/* Calibration objective of Sec. III-D (parameters fitted to measured times):
+ *   L = (1/n) sum_i (ln T_hat_i - ln T_i)^2 and dL/dtheta (16 values),
+ * from a hand-written adjoint of the model (ties of max() go to the first
+ * argument, the alpha clamp has zero slope outside (0,1)).  Per-block partial
+ * sums go to workspace_dev (pm_model_grad_workspace bytes) and are reduced in
+ * FP64 in a fixed order; out_dev receives 17 doubles {L, dL/dtheta_0..15}.
+ * Async. */
+pm_status pm_model_grad(const pm_cfg* cfgs_dev, int64_t n, const pm_params* theta_host, int32_t n_sm,
+                        const float* t_meas_dev, void* workspace_dev, size_t workspace_bytes, double* out_dev,
+                        void* stream);
+
+/* Autotuner (Sec. III-B adaptive tile selection; Sec. VI autotuning
+ * guidance): for each of n shapes (MNK_dev: n x {M,N,K} int32) evaluates the
+ * model over the 180-point tile space of `dtype` and picks the fastest valid
+ * configuration; ties go to the first in lexicographic (BM, BN, BK, stages,
+ * cta_group) order.  picks_dev: n pm_cfg; t_pred_dev: n floats.  Async. */
+pm_status pm_autotune_pick(const int32_t* MNK_dev, int64_t n, int32_t dtype, const pm_params* theta_host,
+                           int32_t n_sm, pm_cfg* picks_dev, float* t_pred_dev, void* stream);
+
+/* Grouped autotuner: for each launch-level (BK, stages, cta_group), each
+ * group takes the (BM, BN) minimising tiles_g * (K_tiles T_step_g + T_store_g);
+ * the launch whose static schedule has the smallest makespan
+ *   T_launch + max_w sum_{t = w mod n_conc} tau(t)
+ * wins.  Results to host: BM_out_host/BN_out_host (G each), launch_out_host
+ * {BK, stages, cta_group}, *t_pred_host.  Synchronises. */
+pm_status pm_grouped_autotune(int32_t G, const int32_t* M_host, int32_t N, int32_t K, int32_t dtype,
+                              const pm_params* theta_host, int32_t n_sm, int16_t* BM_out_host,
+                              int16_t* BN_out_host, int32_t* launch_out_host, float* t_pred_host, void* stream);
+
+/* ----------------------------------------------------------- diagnostics */
+/* Text of the last error on this host thread (valid until the next call). */
+const char* pm_last_error(void);
+
+/* Reads (and with clear != 0, clears) the device watchdog word of the current
+ * device: PM_OK or PM_ETIMEOUT.  Synchronises the device. */
+pm_status pm_device_status(int clear);
+
+/* Watchdog self-test: one kernel waits on an mbarrier that nothing completes,
+ * gives up after limit_us microseconds, records PM_ETIMEOUT and returns.
+ * Synchronises; returns the status the device recorded (PM_ETIMEOUT). */
+pm_status pm_watchdog_selftest(int32_t limit_us, void* stream);
+
+/* Library version (major*10000 + minor*100 + patch). */
+int32_t pm_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PERFMODEL_H */

@@ -1,0 +1,275 @@
+"""Python binding of libperfmodel.so (include/perfmodel.h), the GB300 hot path of
+the stage-centric GPU performance model of arxiv 2605.04178.
+
+Argument marshalling only: every step runs in the CUDA library.  The
+functions carry the C names (pm_probe_run, pm_gemm_prepare, pm_gemm_run,
+pm_grouped_gemm_run, pm_model_predict, pm_model_grad, pm_autotune_pick,
+pm_grouped_autotune, ...); device buffers are torch CUDA tensors, streams
+default to torch's current stream.  If the compiled library is missing the
+import fails: there is no fallback path.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "lib", "libperfmodel.so")
+
+PM_OK, PM_EINVAL, PM_EUNSUPPORTED, PM_ECUDA, PM_ETIMEOUT, PM_ENOMEM = 0, -1, -2, -3, -4, -5
+PM_FP32, PM_BF16, PM_FP8E4M3 = 0, 1, 2
+PM_KIND_GEMM, PM_KIND_COPY, PM_KIND_TRIAD, PM_KIND_TMA2D = 0, 1, 2, 3
+PM_PROBE_COPY, PM_PROBE_TRIAD, PM_PROBE_TMA2D, PM_PROBE_PCHASE = 1, 2, 3, 4
+
+# numpy view of pm_cfg (24 bytes)
+CFG_DTYPE = np.dtype([("M", "<i4"), ("N", "<i4"), ("K", "<i4"), ("BM", "<i2"), ("BN", "<i2"), ("BK", "<i2"),
+                      ("stages", "i1"), ("cta_group", "i1"), ("dtype", "i1"), ("kind", "i1"),
+                      ("reserved", "<i2")], align=True)
+assert CFG_DTYPE.itemsize == 24
+
+
+class pm_cfg(ctypes.Structure):
+    _fields_ = [("M", ctypes.c_int32), ("N", ctypes.c_int32), ("K", ctypes.c_int32), ("BM", ctypes.c_int16),
+                ("BN", ctypes.c_int16), ("BK", ctypes.c_int16), ("stages", ctypes.c_int8),
+                ("cta_group", ctypes.c_int8), ("dtype", ctypes.c_int8), ("kind", ctypes.c_int8),
+                ("reserved", ctypes.c_int16)]
+
+
+class pm_params(ctypes.Structure):
+    _fields_ = [("v", ctypes.c_float * 16)]
+
+
+class pm_probe_args(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("tile_r", ctypes.c_int32), ("tile_c", ctypes.c_int32),
+                ("start", ctypes.c_uint32), ("n", ctypes.c_int64), ("rows", ctypes.c_int64),
+                ("cols", ctypes.c_int64), ("hops", ctypes.c_int64), ("scalar", ctypes.c_float),
+                ("reserved", ctypes.c_int32)]
+
+
+class pm_probe_result(ctypes.Structure):
+    _fields_ = [("median_s", ctypes.c_double), ("p25_s", ctypes.c_double), ("p75_s", ctypes.c_double),
+                ("min_s", ctypes.c_double), ("bytes", ctypes.c_double), ("final_index", ctypes.c_uint32),
+                ("reserved", ctypes.c_uint32)]
+
+
+assert ctypes.sizeof(pm_cfg) == 24 and ctypes.sizeof(pm_probe_args) == 56 and ctypes.sizeof(pm_probe_result) == 48
+
+# Every exported symbol of include/perfmodel.h
+EXPORTS = ("pm_probe_launch", "pm_probe_run", "pm_gemm_operand_bytes", "pm_gemm_prepare", "pm_gemm_run",
+           "pm_grouped_gemm_run", "pm_model_predict", "pm_model_grad_workspace", "pm_model_grad",
+           "pm_autotune_pick", "pm_grouped_autotune", "pm_last_error", "pm_device_status",
+           "pm_watchdog_selftest", "pm_version")
+
+
+class PMError(RuntimeError):
+    def __init__(self, status: int, where: str, msg: str):
+        super().__init__("%s -> status %d: %s" % (where, status, msg))
+        self.status = status
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError("libperfmodel.so is not built (%s); run paper_2605_04178_gb300.build.build()" % LIB_PATH)
+    lib = ctypes.CDLL(LIB_PATH)
+    P, i32, i64, sz = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_size_t
+    sig = {
+        "pm_probe_launch": [ctypes.POINTER(pm_probe_args), P, P, P, P],
+        "pm_probe_run": [ctypes.POINTER(pm_probe_args), P, P, P, ctypes.c_int, ctypes.c_int, P,
+                         ctypes.POINTER(pm_probe_result)],
+        "pm_gemm_operand_bytes": [i32, i32, i32, i32, ctypes.POINTER(sz), ctypes.POINTER(sz)],
+        "pm_gemm_prepare": [i32, P, P, i32, i32, i32, P, P, P, P],
+        "pm_gemm_run": [ctypes.POINTER(pm_cfg), P, P, P, P, P],
+        "pm_grouped_gemm_run": [i32, P, i32, i32, P, P, i32, i32, i32, P, P, P, P],
+        "pm_model_predict": [P, i64, ctypes.POINTER(pm_params), i32, P, P],
+        "pm_model_grad_workspace": [i64, ctypes.POINTER(sz)],
+        "pm_model_grad": [P, i64, ctypes.POINTER(pm_params), i32, P, P, sz, P, P],
+        "pm_autotune_pick": [P, i64, i32, ctypes.POINTER(pm_params), i32, P, P, P],
+        "pm_grouped_autotune": [i32, P, i32, i32, i32, ctypes.POINTER(pm_params), i32, P, P, P, P, P],
+        "pm_device_status": [ctypes.c_int],
+        "pm_watchdog_selftest": [i32, P],
+        "pm_version": [],
+        "pm_last_error": [],
+    }
+    for name, args in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = ctypes.c_int32
+    lib.pm_last_error.restype = ctypes.c_char_p
+    return lib
+
+
+_lib = _load()
+
+
+def _check(status: int, where: str) -> int:
+    if status != PM_OK:
+        raise PMError(status, where, _lib.pm_last_error().decode(errors="replace"))
+    return status
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if isinstance(t, int):
+        return ctypes.c_void_p(t)
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+
+
+def params(theta) -> pm_params:
+    p = pm_params()
+    th = np.asarray(theta, dtype=np.float32)
+    assert th.size == 16
+    for j in range(16):
+        p.v[j] = float(th[j])
+    return p
+
+
+def cfg(M, N, K, BM=128, BN=128, BK=64, stages=4, cta_group=1, dtype=PM_BF16, kind=PM_KIND_GEMM) -> pm_cfg:
+    return pm_cfg(int(M), int(N), int(K), int(BM), int(BN), int(BK), int(stages), int(cta_group), int(dtype),
+                  int(kind), 0)
+
+
+def cfg_array(fields: dict) -> np.ndarray:
+    """Structured pm_cfg array from a dict of equal-length columns (missing columns are 0)."""
+    n = len(fields["M"])
+    a = np.zeros(n, dtype=CFG_DTYPE)
+    for k, v in fields.items():
+        a[k] = v
+    return a
+
+
+def cfg_tensor(fields: dict, device="cuda"):
+    """pm_cfg records on the device as a uint8 tensor (24 bytes per configuration)."""
+    import torch
+    a = cfg_array(fields)
+    return torch.from_numpy(a.view(np.uint8).copy()).to(device)
+
+
+# --------------------------------------------------------------------- probes
+def probe_args(kind, n=0, rows=0, cols=0, tile_r=0, tile_c=0, hops=0, start=0, scalar=3.0) -> pm_probe_args:
+    return pm_probe_args(int(kind), int(tile_r), int(tile_c), int(start), int(n), int(rows), int(cols), int(hops),
+                         float(scalar), 0)
+
+
+def pm_probe_launch(args: pm_probe_args, buf0, buf1=None, buf2=None, stream=None):
+    _check(_lib.pm_probe_launch(ctypes.byref(args), _ptr(buf0), _ptr(buf1), _ptr(buf2), _stream(stream)),
+           "pm_probe_launch")
+
+
+def pm_probe_run(args: pm_probe_args, buf0, buf1=None, buf2=None, warmup=10, reps=100, stream=None) -> dict:
+    res = pm_probe_result()
+    _check(_lib.pm_probe_run(ctypes.byref(args), _ptr(buf0), _ptr(buf1), _ptr(buf2), int(warmup), int(reps),
+                             _stream(stream), ctypes.byref(res)), "pm_probe_run")
+    return dict(median_s=res.median_s, p25_s=res.p25_s, p75_s=res.p75_s, min_s=res.min_s, bytes=res.bytes,
+                final_index=res.final_index)
+
+
+# ----------------------------------------------------------------------- GEMM
+def pm_gemm_operand_bytes(dtype, M, N, K):
+    a, b = ctypes.c_size_t(), ctypes.c_size_t()
+    _check(_lib.pm_gemm_operand_bytes(int(dtype), int(M), int(N), int(K), ctypes.byref(a), ctypes.byref(b)),
+           "pm_gemm_operand_bytes")
+    return a.value, b.value
+
+
+def pm_gemm_prepare(dtype, A, B, M, N, K, A_op, B_op, scales=None, stream=None):
+    _check(_lib.pm_gemm_prepare(int(dtype), _ptr(A), _ptr(B), int(M), int(N), int(K), _ptr(A_op), _ptr(B_op),
+                                _ptr(scales), _stream(stream)), "pm_gemm_prepare")
+
+
+def pm_gemm_run(c: pm_cfg, A_op, B_op, C, scales=None, stream=None):
+    _check(_lib.pm_gemm_run(ctypes.byref(c), _ptr(A_op), _ptr(B_op), _ptr(C), _ptr(scales), _stream(stream)),
+           "pm_gemm_run")
+
+
+def pm_grouped_gemm_run(M_list, N, K, BM_list, BN_list, BK, stages, cta_group, A_op, B_op, C, stream=None):
+    G = len(M_list)
+    Mh = (ctypes.c_int32 * G)(*[int(m) for m in M_list])
+    BMh = (ctypes.c_int16 * G)(*[int(m) for m in BM_list])
+    BNh = (ctypes.c_int16 * G)(*[int(m) for m in BN_list])
+    _check(_lib.pm_grouped_gemm_run(G, Mh, int(N), int(K), BMh, BNh, int(BK), int(stages), int(cta_group),
+                                    _ptr(A_op), _ptr(B_op), _ptr(C), _stream(stream)), "pm_grouped_gemm_run")
+
+
+class GemmOperands:
+    """Device operand buffers for one (dtype, M, N, K), allocated with torch."""
+
+    def __init__(self, dtype, M, N, K, device="cuda"):
+        import torch
+        a, b = pm_gemm_operand_bytes(dtype, M, N, K)
+        self.dtype, self.M, self.N, self.K = dtype, M, N, K
+        self.A_op = torch.empty(a, dtype=torch.uint8, device=device)
+        self.B_op = torch.empty(b, dtype=torch.uint8, device=device)
+        self.scales = torch.zeros(4, dtype=torch.float32, device=device)
+
+    def prepare(self, A, B, stream=None):
+        pm_gemm_prepare(self.dtype, A, B, self.M, self.N, self.K, self.A_op, self.B_op, self.scales, stream)
+
+    def run(self, c: pm_cfg, C, stream=None):
+        pm_gemm_run(c, self.A_op, self.B_op, C, self.scales, stream)
+
+
+# ---------------------------------------------------------------------- model
+def pm_model_predict(cfgs_dev, n, theta, n_sm, t_out, stream=None):
+    _check(_lib.pm_model_predict(_ptr(cfgs_dev), int(n), ctypes.byref(params(theta)), int(n_sm), _ptr(t_out),
+                                 _stream(stream)), "pm_model_predict")
+
+
+def pm_model_grad_workspace(n) -> int:
+    b = ctypes.c_size_t()
+    _check(_lib.pm_model_grad_workspace(int(n), ctypes.byref(b)), "pm_model_grad_workspace")
+    return b.value
+
+
+def pm_model_grad(cfgs_dev, n, theta, n_sm, t_meas, workspace, out, stream=None):
+    _check(_lib.pm_model_grad(_ptr(cfgs_dev), int(n), ctypes.byref(params(theta)), int(n_sm), _ptr(t_meas),
+                              _ptr(workspace), int(workspace.numel() * workspace.element_size()), _ptr(out),
+                              _stream(stream)), "pm_model_grad")
+
+
+def pm_autotune_pick(MNK_dev, n, dtype, theta, n_sm, picks_dev, t_pred_dev, stream=None):
+    _check(_lib.pm_autotune_pick(_ptr(MNK_dev), int(n), int(dtype), ctypes.byref(params(theta)), int(n_sm),
+                                 _ptr(picks_dev), _ptr(t_pred_dev), _stream(stream)), "pm_autotune_pick")
+
+
+def pm_grouped_autotune(M_list, N, K, dtype, theta, n_sm, stream=None):
+    G = len(M_list)
+    Mh = (ctypes.c_int32 * G)(*[int(m) for m in M_list])
+    bm = (ctypes.c_int16 * G)()
+    bn = (ctypes.c_int16 * G)()
+    launch = (ctypes.c_int32 * 3)()
+    t = ctypes.c_float()
+    _check(_lib.pm_grouped_autotune(G, Mh, int(N), int(K), int(dtype), ctypes.byref(params(theta)), int(n_sm), bm,
+                                    bn, launch, ctypes.byref(t), _stream(stream)), "pm_grouped_autotune")
+    return float(t.value), list(bm), list(bn), tuple(launch)
+
+
+# ---------------------------------------------------------------- diagnostics
+def pm_last_error() -> str:
+    return _lib.pm_last_error().decode(errors="replace")
+
+
+def pm_device_status(clear=True) -> int:
+    return int(_lib.pm_device_status(1 if clear else 0))
+
+
+def pm_watchdog_selftest(limit_us=200000, stream=None) -> int:
+    return int(_lib.pm_watchdog_selftest(int(limit_us), _stream(stream)))
+
+
+def pm_version() -> int:
+    return int(_lib.pm_version())
+
+
+def sm_count(device=None) -> int:
+    import torch
+    return torch.cuda.get_device_properties(device or torch.cuda.current_device()).multi_processor_count

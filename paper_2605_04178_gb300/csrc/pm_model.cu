@@ -1,0 +1,601 @@
+// Batched evaluation of the stage-centric model of arxiv 2605.04178 (Sec. III-A,
+// Eqs. 2-8; Eq. 16 for the memory probes), its hand-written adjoint for
+// calibration (Sec. III-D), and the model-driven autotuner (Sec. III-B
+// adaptive tile selection, Sec. VI autotuning guidance).
+//
+// One thread per configuration, FP32 arithmetic, integer tile counts.  The
+// explicit-configuration kernels stream 24-byte records (HBM-bound at
+// 24-28 B per configuration); the autotuner decodes the configuration from
+// the thread index and reads nothing per configuration (ALU-bound).
+#include <math.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "pm_internal.cuh"
+
+namespace pm {
+
+struct Theta {
+  float v[16];
+};
+
+__device__ __forceinline__ int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+// Element bytes, tensor passes per K-step (three-pass TF32 for FP32) and
+// operand copies loaded per element (FP32: hi and lo).
+__device__ __forceinline__ float dt_bytes(int dt) { return dt == PM_FP32 ? 4.f : (dt == PM_BF16 ? 2.f : 1.f); }
+__device__ __forceinline__ float dt_passes(int dt) { return dt == PM_FP32 ? 3.f : 1.f; }
+__device__ __forceinline__ float dt_loads(int dt) { return dt == PM_FP32 ? 2.f : 1.f; }
+__device__ __forceinline__ int dt_rate(int dt) { return dt == PM_FP32 ? 6 : (dt == PM_BF16 ? 7 : 8); }
+
+__constant__ int16_t kBM[3] = {64, 128, 256};
+__constant__ int16_t kBN[3] = {64, 128, 256};
+__constant__ int16_t kBK[3][2] = {{32, 64}, {64, 128}, {64, 128}};
+
+// Valid tile space: ring of `s` stages within 227 KiB - 2 KiB, FP32
+// accumulator columns ceil(BM/128)*BN within the 512 TMEM columns.
+__host__ __device__ inline bool tile_valid(int BM, int BN, int BK, int s, int g, int dt) {
+  if (!(BM == 64 || BM == 128 || BM == 256) || !(BN == 64 || BN == 128 || BN == 256)) return false;
+  if (dt == PM_FP32) {
+    if (BK != 32 && BK != 64) return false;
+  } else if (dt == PM_BF16 || dt == PM_FP8E4M3) {
+    if (BK != 64 && BK != 128) return false;
+  } else {
+    return false;
+  }
+  if (s < 2 || s > 6 || (g != 1 && g != 2)) return false;
+  const int e = dt == PM_FP32 ? 4 : (dt == PM_BF16 ? 2 : 1);
+  const int l = dt == PM_FP32 ? 2 : 1;
+  const int64_t stage = (int64_t)l * e * BK * (BM + BN / g);
+  if ((int64_t)s * stage > 232448 - 2048) return false;
+  if (((BM + 127) / 128) * BN > 512) return false;
+  return true;
+}
+
+// Intermediate values of one GEMM evaluation, kept for the adjoint.
+struct GemmFwd {
+  float T, T_stage, T_rl, A_rl, B_rl;
+  float T_c, T_io, T_tma, oma, X, R, S, T_step, T_store;
+  float D, bstep, store_bytes;
+  float waves, Kt;
+  int ri;
+  bool oma_free;
+};
+
+// Stage-centric GEMM time:
+//   T_TMEM = D/BW_rd + L_mma + D/BW_wr                          (Eq. 2)
+//   T_c    = n_p 2 BM BN BK / (R S) + T_TMEM + T_mgmt/K_tiles     (Eqs. 3, 6)
+//   T_tma  = L_TMA + b_step / B_TMA, b_step = l e BK (BM + BN/g) (Eq. 4, P = 1)
+//   T_io   = (1 - alpha) T_tma + T_sync, T_sync = 2 L_mbar       (Eq. 7)
+//   T_step = max(T_c, T_io) + T_sync                             (Eq. 8)
+//   T_stage = T_launch + waves (K_tiles T_step + T_store)
+//   T_hat = max(T_stage, T_launch + max(FLOPs/(n_SM R S), bytes_min/B_peak))
+__device__ __forceinline__ void gemm_forward(const pm_cfg& c, const Theta& th, int n_sm, GemmFwd& f) {
+  const int dt = c.dtype, g = c.cta_group;
+  const float e = dt_bytes(dt), np = dt_passes(dt), l = dt_loads(dt);
+  f.ri = dt_rate(dt);
+  f.R = th.v[f.ri];
+  const int64_t Kt = cdiv(c.K, c.BK);
+  const int64_t tiles = (int64_t)g * cdiv(c.M, (int64_t)g * c.BM) * cdiv(c.N, c.BN);
+  const int64_t n_conc = g == 1 ? n_sm : 2 * (n_sm / 2);
+  const int64_t waves = cdiv(tiles, n_conc);
+  f.Kt = (float)Kt;
+  f.waves = (float)waves;
+  f.D = 4.f * c.BM * c.BN;
+  const float T_tmem = f.D / th.v[10] + th.v[9] + f.D / th.v[11];
+  const float T_mgmt = th.v[13] / f.Kt;
+  f.S = g == 1 ? 1.f : th.v[14];
+  f.X = (np * 2.f * c.BM * c.BN * c.BK) / (f.R * f.S);
+  f.T_c = f.X + T_tmem + T_mgmt;
+  f.bstep = l * e * c.BK * ((float)c.BM + (float)c.BN / (float)g);
+  f.T_tma = th.v[4] + f.bstep / th.v[5];
+  const float T_sync = 2.f * th.v[12];
+  // 1 - alpha = clamp(c_alpha / s, 0, 1)
+  const float r = th.v[15] / (float)c.stages;
+  f.oma_free = r > 0.f && r < 1.f;
+  f.oma = r <= 0.f ? 0.f : (r >= 1.f ? 1.f : r);
+  f.T_io = f.oma * f.T_tma + T_sync;
+  f.T_step = fmaxf(f.T_c, f.T_io) + T_sync;
+  f.store_bytes = 4.f * c.BM * c.BN;
+  f.T_store = th.v[4] + f.store_bytes / th.v[5];
+  f.T_stage = th.v[0] + f.waves * (f.Kt * f.T_step + f.T_store);
+  const float flops = np * 2.f * (float)c.M * (float)c.N * (float)c.K;
+  const float bytes_min = l * e * ((float)c.M * c.K + (float)c.N * c.K) + 4.f * (float)c.M * (float)c.N;
+  f.A_rl = flops / ((float)n_sm * f.R * f.S);
+  f.B_rl = bytes_min / th.v[2];
+  f.T_rl = th.v[0] + (f.A_rl >= f.B_rl ? f.A_rl : f.B_rl);
+  f.T = f.T_stage >= f.T_rl ? f.T_stage : f.T_rl;
+}
+
+// Adjoint of gemm_forward: d[j] += w * dT_hat/dtheta_j.  max() passes the
+// gradient to its first argument on ties; the clamp stops it outside (0,1).
+__device__ __forceinline__ void gemm_adjoint(const pm_cfg& c, const Theta& th, const GemmFwd& f, float w,
+                                             float (&d)[16]) {
+  float g_stage = 0.f, g_rl = 0.f;
+  if (f.T_stage >= f.T_rl) g_stage = w; else g_rl = w;
+  float gR = 0.f, gS = 0.f;
+  // roofline branch
+  d[0] += g_rl;
+  if (g_rl != 0.f) {
+    if (f.A_rl >= f.B_rl) {
+      gR -= g_rl * f.A_rl / f.R;
+      gS -= g_rl * f.A_rl / f.S;
+    } else {
+      d[2] -= g_rl * f.B_rl / th.v[2];
+    }
+  }
+  // stage branch
+  d[0] += g_stage;
+  const float g_step = g_stage * f.waves * f.Kt;
+  const float g_store = g_stage * f.waves;
+  d[4] += g_store;
+  d[5] -= g_store * (f.store_bytes / th.v[5]) / th.v[5];
+  float g_sync = g_step;
+  float g_c = 0.f, g_io = 0.f;
+  if (f.T_c >= f.T_io) g_c = g_step; else g_io = g_step;
+  // T_io = oma * T_tma + T_sync
+  g_sync += g_io;
+  const float g_tma = g_io * f.oma;
+  if (f.oma_free) d[15] += g_io * f.T_tma / (float)c.stages;
+  d[4] += g_tma;
+  d[5] -= g_tma * (f.bstep / th.v[5]) / th.v[5];
+  d[12] += 2.f * g_sync;
+  // T_c = X + D/BW_rd + L_mma + D/BW_wr + L_mgmt/K_tiles
+  gR -= g_c * f.X / f.R;
+  gS -= g_c * f.X / f.S;
+  d[10] -= g_c * (f.D / th.v[10]) / th.v[10];
+  d[9] += g_c;
+  d[11] -= g_c * (f.D / th.v[11]) / th.v[11];
+  d[13] += g_c / f.Kt;
+  d[f.ri] += gR;
+  if (c.cta_group == 2) d[14] += gS;
+}
+
+// Memory probes.  Copy/triad through Eq. 16 with W = beta bytes moved;
+// TMA2D: tile latency plus ceil(tiles/SMs) tile round trips (Eq. 4),
+// bounded below by the streaming time of Eq. 16.
+struct ProbeFwd {
+  float T, T1, T2, Bw, E, W, beta, moved_tiles;
+  bool blend;
+};
+
+__device__ __forceinline__ void probe_forward(const pm_cfg& c, const Theta& th, int n_sm, ProbeFwd& f) {
+  float W, t2num;
+  if (c.kind == PM_KIND_COPY || c.kind == PM_KIND_TRIAD) {
+    f.beta = (c.kind == PM_KIND_COPY ? 8.f : 12.f) * (float)c.M;
+    W = f.beta;
+    t2num = f.beta;
+  } else {
+    const float t = 4.f * c.BM * c.BN;
+    const int64_t nt = cdiv(c.M, c.BM) * cdiv(c.N, c.BN);
+    f.moved_tiles = (float)cdiv(nt, n_sm) * 2.f * t;
+    f.beta = 8.f * (float)c.M * (float)c.N;
+    W = f.beta;
+    t2num = f.moved_tiles;
+  }
+  f.W = W;
+  f.blend = th.v[3] > 0.f;
+  f.E = f.blend ? expf(-W / th.v[3]) : 0.f;
+  f.Bw = f.blend ? th.v[1] + (th.v[2] - th.v[1]) * f.E : th.v[1];
+  if (c.kind == PM_KIND_COPY || c.kind == PM_KIND_TRIAD) {
+    f.T1 = th.v[0] + f.beta / f.Bw;
+    f.T2 = th.v[0] + f.beta / th.v[2];
+  } else {
+    f.T1 = th.v[0] + th.v[4] + t2num / th.v[5];
+    f.T2 = th.v[0] + f.beta / f.Bw;
+  }
+  f.T = f.T1 >= f.T2 ? f.T1 : f.T2;
+}
+
+__device__ __forceinline__ void bw_adjoint(const Theta& th, const ProbeFwd& f, float gB, float (&d)[16]) {
+  if (f.blend) {
+    d[1] += gB * (1.f - f.E);
+    d[2] += gB * f.E;
+    const float gE = gB * (th.v[2] - th.v[1]);
+    d[3] += gE * f.E * f.W / (th.v[3] * th.v[3]);
+  } else {
+    d[1] += gB;
+  }
+}
+
+__device__ __forceinline__ void probe_adjoint(const pm_cfg& c, const Theta& th, const ProbeFwd& f, float w,
+                                              float (&d)[16]) {
+  d[0] += w;
+  const bool first = f.T1 >= f.T2;
+  if (c.kind == PM_KIND_COPY || c.kind == PM_KIND_TRIAD) {
+    if (first) bw_adjoint(th, f, -w * f.beta / (f.Bw * f.Bw), d);
+    else d[2] -= w * f.beta / (th.v[2] * th.v[2]);
+  } else {
+    if (first) {
+      d[4] += w;
+      d[5] -= w * f.moved_tiles / (th.v[5] * th.v[5]);
+    } else {
+      bw_adjoint(th, f, -w * f.beta / (f.Bw * f.Bw), d);
+    }
+  }
+}
+
+__device__ __forceinline__ bool cfg_sane(const pm_cfg& c) {
+  if (c.kind == PM_KIND_GEMM)
+    return c.M > 0 && c.N > 0 && c.K > 0 && c.BM > 0 && c.BN > 0 && c.BK > 0 && c.stages > 0 &&
+           (c.cta_group == 1 || c.cta_group == 2) && c.dtype >= 0 && c.dtype <= 2;
+  if (c.kind == PM_KIND_COPY || c.kind == PM_KIND_TRIAD) return c.M > 0;
+  if (c.kind == PM_KIND_TMA2D) return c.M > 0 && c.N > 0 && c.BM > 0 && c.BN > 0;
+  return false;
+}
+
+__device__ __forceinline__ pm_cfg load_cfg(const pm_cfg* p) {
+  // 24-byte record as three 8-byte loads
+  const int2* q = reinterpret_cast<const int2*>(p);
+  int2 a = __ldg(q), b = __ldg(q + 1), cc = __ldg(q + 2);
+  pm_cfg c;
+  int2* o = reinterpret_cast<int2*>(&c);
+  o[0] = a; o[1] = b; o[2] = cc;
+  return c;
+}
+
+__global__ void __launch_bounds__(256) model_predict_kernel(const pm_cfg* __restrict__ cfgs, int64_t n, Theta th,
+                                                            int n_sm, float* __restrict__ out) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const pm_cfg c = load_cfg(cfgs + i);
+    float t;
+    if (!cfg_sane(c)) {
+      t = __int_as_float(0x7fc00000);
+    } else if (c.kind == PM_KIND_GEMM) {
+      GemmFwd f;
+      gemm_forward(c, th, n_sm, f);
+      t = f.T;
+    } else {
+      ProbeFwd f;
+      probe_forward(c, th, n_sm, f);
+      t = f.T;
+    }
+    out[i] = t;
+  }
+}
+
+// Loss and gradient: per-thread FP32 terms, block sums in FP64, one FP64
+// partial record of 17 values per block; a second kernel adds the records
+// in block order (deterministic).
+constexpr int kGradThreads = 256;
+
+__device__ __forceinline__ double warp_sum_d(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__global__ void __launch_bounds__(kGradThreads) model_grad_kernel(const pm_cfg* __restrict__ cfgs, int64_t n,
+                                                                  Theta th, int n_sm,
+                                                                  const float* __restrict__ t_meas,
+                                                                  double* __restrict__ partials) {
+  float acc[17];
+#pragma unroll
+  for (int j = 0; j < 17; ++j) acc[j] = 0.f;
+  double loss = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const pm_cfg c = load_cfg(cfgs + i);
+    float d[16];
+#pragma unroll
+    for (int j = 0; j < 16; ++j) d[j] = 0.f;
+    float T;
+    if (!cfg_sane(c)) {
+      T = __int_as_float(0x7fc00000);
+    } else if (c.kind == PM_KIND_GEMM) {
+      GemmFwd f;
+      gemm_forward(c, th, n_sm, f);
+      T = f.T;
+      gemm_adjoint(c, th, f, 1.f, d);
+    } else {
+      ProbeFwd f;
+      probe_forward(c, th, n_sm, f);
+      T = f.T;
+      probe_adjoint(c, th, f, 1.f, d);
+    }
+    const float r = logf(T) - logf(__ldg(t_meas + i));
+    loss += (double)r * (double)r;
+    const float w = 2.f * r / T;
+#pragma unroll
+    for (int j = 0; j < 16; ++j) acc[j] = fmaf(w, d[j], acc[j]);
+  }
+  __shared__ double red[kGradThreads / 32][17];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  double v = warp_sum_d(loss);
+  if (lane == 0) red[warp][0] = v;
+#pragma unroll
+  for (int j = 0; j < 16; ++j) {
+    v = warp_sum_d((double)acc[j]);
+    if (lane == 0) red[warp][j + 1] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < 17) {
+    double s = 0.0;
+    for (int w = 0; w < kGradThreads / 32; ++w) s += red[w][threadIdx.x];
+    partials[(int64_t)blockIdx.x * 17 + threadIdx.x] = s;
+  }
+}
+
+__global__ void model_grad_finish_kernel(const double* __restrict__ partials, int blocks, int64_t n,
+                                         double* __restrict__ out) {
+  const int j = threadIdx.x;
+  if (j >= 17) return;
+  double s = 0.0;
+  for (int b = 0; b < blocks; ++b) s += partials[(int64_t)b * 17 + j];
+  out[j] = s / (double)n;
+}
+
+static int grad_blocks(int64_t n) {
+  const int64_t want = (n + kGradThreads - 1) / kGradThreads;
+  const int cap = std::max(1, sm_count()) * 8;
+  return (int)std::max<int64_t>(1, std::min<int64_t>(want, cap));
+}
+
+// Autotuner: one block per shape, thread t evaluates tile configuration t of
+// the 180-point space in lexicographic (BM, BN, BK, stages, cta_group) order.
+constexpr int kTuneThreads = 192;
+
+__device__ __forceinline__ void decode_tile(int t, int dt, int& BM, int& BN, int& BK, int& s, int& g) {
+  BM = kBM[t / 60];
+  BN = kBN[(t / 20) % 3];
+  BK = kBK[dt][(t / 10) % 2];
+  s = 2 + (t / 2) % 5;
+  g = 1 + t % 2;
+}
+
+__global__ void __launch_bounds__(kTuneThreads) autotune_kernel(const int32_t* __restrict__ MNK, int64_t n, int dt,
+                                                                Theta th, int n_sm, pm_cfg* __restrict__ picks,
+                                                                float* __restrict__ t_pred) {
+  __shared__ float sv[kTuneThreads / 32];
+  __shared__ int si[kTuneThreads / 32];
+  const int t = threadIdx.x;
+  for (int64_t shape = blockIdx.x; shape < n; shape += gridDim.x) {
+    pm_cfg c;
+    c.M = __ldg(MNK + 3 * shape);
+    c.N = __ldg(MNK + 3 * shape + 1);
+    c.K = __ldg(MNK + 3 * shape + 2);
+    c.dtype = (int8_t)dt;
+    c.kind = PM_KIND_GEMM;
+    c.reserved = 0;
+    float v = INFINITY;
+    int BM = 0, BN = 0, BK = 0, s = 0, g = 0;
+    if (t < 180) {
+      decode_tile(t, dt, BM, BN, BK, s, g);
+      if (tile_valid(BM, BN, BK, s, g, dt) && c.M > 0 && c.N > 0 && c.K > 0) {
+        c.BM = (int16_t)BM; c.BN = (int16_t)BN; c.BK = (int16_t)BK;
+        c.stages = (int8_t)s; c.cta_group = (int8_t)g;
+        GemmFwd f;
+        gemm_forward(c, th, n_sm, f);
+        v = f.T;
+      }
+    }
+    // argmin, ties to the lower index
+    int idx = t;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const float ov = __shfl_xor_sync(0xffffffffu, v, o);
+      const int oi = __shfl_xor_sync(0xffffffffu, idx, o);
+      if (ov < v || (ov == v && oi < idx)) { v = ov; idx = oi; }
+    }
+    if ((t & 31) == 0) { sv[t >> 5] = v; si[t >> 5] = idx; }
+    __syncthreads();
+    if (t == 0) {
+      float bv = sv[0];
+      int bi = si[0];
+      for (int w = 1; w < kTuneThreads / 32; ++w)
+        if (sv[w] < bv || (sv[w] == bv && si[w] < bi)) { bv = sv[w]; bi = si[w]; }
+      pm_cfg p = c;
+      if (bv < INFINITY) {
+        decode_tile(bi, dt, BM, BN, BK, s, g);
+        p.BM = (int16_t)BM; p.BN = (int16_t)BN; p.BK = (int16_t)BK;
+        p.stages = (int8_t)s; p.cta_group = (int8_t)g;
+      } else {
+        p.BM = p.BN = p.BK = 0; p.stages = p.cta_group = 0;
+      }
+      picks[shape] = p;
+      t_pred[shape] = bv;
+    }
+    __syncthreads();
+  }
+}
+
+// Grouped autotuner: block b handles launch-level combination b =
+// (BK index, stages, cta_group) in lexicographic order; threads pick each
+// group's (BM, BN), then each worker's busy time under the static schedule
+// (tile t on worker t mod n_conc) is summed group by group.
+constexpr int kGroupThreads = 256;
+constexpr int kMaxGroups = 1024;
+
+__device__ __forceinline__ int64_t count_congruent(int64_t X, int64_t w, int64_t n) {
+  // number of t in [0, X] with t = w (mod n), for X >= -1
+  return X < w ? 0 : (X - w) / n + 1;
+}
+
+__global__ void __launch_bounds__(kGroupThreads) grouped_tune_kernel(const int32_t* __restrict__ Mg, int G, int N,
+                                                                     int K, int dt, Theta th, int n_sm,
+                                                                     float* __restrict__ out_t,
+                                                                     int16_t* __restrict__ out_bm,
+                                                                     int16_t* __restrict__ out_bn) {
+  __shared__ float tau[kMaxGroups];
+  __shared__ int64_t tiles[kMaxGroups];
+  __shared__ int64_t off[kMaxGroups + 1];
+  __shared__ float red[kGroupThreads / 32];
+  const int combo = blockIdx.x;                 // 0..19
+  const int BK = kBK[dt][combo / 10];
+  const int s = 2 + (combo / 2) % 5;
+  const int g = 1 + combo % 2;
+  bool any_invalid = false;
+  for (int q = threadIdx.x; q < G; q += blockDim.x) {
+    float best = INFINITY;
+    int bm = 0, bn = 0;
+    float btau = 0.f;
+    int64_t btiles = 0;
+    for (int a = 0; a < 3; ++a)
+      for (int b = 0; b < 3; ++b) {
+        const int BM = kBM[a], BN = kBN[b];
+        if (!tile_valid(BM, BN, BK, s, g, dt)) continue;
+        pm_cfg c;
+        c.M = Mg[q]; c.N = N; c.K = K; c.BM = (int16_t)BM; c.BN = (int16_t)BN; c.BK = (int16_t)BK;
+        c.stages = (int8_t)s; c.cta_group = (int8_t)g; c.dtype = (int8_t)dt; c.kind = 0; c.reserved = 0;
+        GemmFwd f;
+        gemm_forward(c, th, n_sm, f);
+        const float tq = f.Kt * f.T_step + f.T_store;   // one tile of this group
+        const int64_t nt = (int64_t)g * cdiv(c.M, (int64_t)g * BM) * cdiv(N, BN);
+        const float cost = (float)nt * tq;
+        if (cost < best) { best = cost; bm = BM; bn = BN; btau = tq; btiles = nt; }
+      }
+    if (best == INFINITY) any_invalid = true;
+    tau[q] = btau;
+    tiles[q] = btiles;
+    out_bm[combo * G + q] = (int16_t)bm;
+    out_bn[combo * G + q] = (int16_t)bn;
+  }
+  any_invalid = __syncthreads_or(any_invalid);
+  if (threadIdx.x == 0) {
+    off[0] = 0;
+    for (int q = 0; q < G; ++q) off[q + 1] = off[q] + tiles[q];
+  }
+  __syncthreads();
+  const int64_t n_conc = g == 1 ? n_sm : 2 * (n_sm / 2);
+  float mx = 0.f;
+  for (int64_t w = threadIdx.x; w < n_conc; w += blockDim.x) {
+    float busy = 0.f;
+    for (int q = 0; q < G; ++q) {
+      const int64_t cnt = count_congruent(off[q + 1] - 1, w, n_conc) - count_congruent(off[q] - 1, w, n_conc);
+      busy += (float)cnt * tau[q];
+    }
+    mx = fmaxf(mx, busy);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float m = red[0];
+    for (int w = 1; w < kGroupThreads / 32; ++w) m = fmaxf(m, red[w]);
+    out_t[combo] = any_invalid ? INFINITY : th.v[0] + m;
+  }
+}
+
+__global__ void grouped_pick_kernel(const float* __restrict__ t, int* __restrict__ best) {
+  int b = 0;
+  for (int i = 1; i < 20; ++i)
+    if (t[i] < t[b]) b = i;
+  *best = b;
+}
+
+static Theta to_theta(const pm_params* p) {
+  Theta t;
+  for (int j = 0; j < 16; ++j) t.v[j] = p->v[j];
+  return t;
+}
+
+}  // namespace pm
+
+using namespace pm;
+
+extern "C" pm_status pm_model_predict(const pm_cfg* cfgs_dev, int64_t n, const pm_params* theta_host, int32_t n_sm,
+                                      float* t_out_dev, void* stream) {
+  PM_REQUIRE(n >= 0, PM_EINVAL, "n < 0");
+  if (n == 0) return PM_OK;
+  PM_REQUIRE(cfgs_dev && theta_host && t_out_dev && n_sm > 0, PM_EINVAL, "null pointer or n_sm <= 0");
+  PM_REQUIRE(((uintptr_t)cfgs_dev & 7) == 0, PM_EINVAL, "cfgs_dev must be 8-byte aligned");
+  const int64_t want = (n + 255) / 256;
+  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)std::max(1, sm_count()) * 16));
+  model_predict_kernel<<<grid, 256, 0, static_cast<cudaStream_t>(stream)>>>(cfgs_dev, n, to_theta(theta_host),
+                                                                            n_sm, t_out_dev);
+  return launch_status("model_predict_kernel");
+}
+
+extern "C" pm_status pm_model_grad_workspace(int64_t n, size_t* bytes) {
+  PM_REQUIRE(bytes != nullptr && n >= 0, PM_EINVAL, "bad arguments");
+  *bytes = (size_t)grad_blocks(std::max<int64_t>(n, 1)) * 17 * sizeof(double);
+  return PM_OK;
+}
+
+extern "C" pm_status pm_model_grad(const pm_cfg* cfgs_dev, int64_t n, const pm_params* theta_host, int32_t n_sm,
+                                   const float* t_meas_dev, void* workspace_dev, size_t workspace_bytes,
+                                   double* out_dev, void* stream) {
+  PM_REQUIRE(n > 0, PM_EINVAL, "n must be positive");
+  PM_REQUIRE(cfgs_dev && theta_host && t_meas_dev && workspace_dev && out_dev && n_sm > 0, PM_EINVAL,
+             "null pointer or n_sm <= 0");
+  PM_REQUIRE(((uintptr_t)cfgs_dev & 7) == 0 && ((uintptr_t)workspace_dev & 7) == 0, PM_EINVAL,
+             "cfgs_dev and workspace_dev must be 8-byte aligned");
+  const int blocks = grad_blocks(n);
+  PM_REQUIRE(workspace_bytes >= (size_t)blocks * 17 * sizeof(double), PM_ENOMEM,
+             "workspace of %zu bytes is smaller than the %zu needed", workspace_bytes,
+             (size_t)blocks * 17 * sizeof(double));
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  model_grad_kernel<<<blocks, kGradThreads, 0, s>>>(cfgs_dev, n, to_theta(theta_host), n_sm, t_meas_dev,
+                                                    static_cast<double*>(workspace_dev));
+  pm_status st = launch_status("model_grad_kernel");
+  if (st != PM_OK) return st;
+  model_grad_finish_kernel<<<1, 32, 0, s>>>(static_cast<const double*>(workspace_dev), blocks, n, out_dev);
+  return launch_status("model_grad_finish_kernel");
+}
+
+extern "C" pm_status pm_autotune_pick(const int32_t* MNK_dev, int64_t n, int32_t dtype, const pm_params* theta_host,
+                                      int32_t n_sm, pm_cfg* picks_dev, float* t_pred_dev, void* stream) {
+  PM_REQUIRE(n >= 0, PM_EINVAL, "n < 0");
+  if (n == 0) return PM_OK;
+  PM_REQUIRE(MNK_dev && theta_host && picks_dev && t_pred_dev && n_sm > 0, PM_EINVAL, "null pointer or n_sm <= 0");
+  PM_REQUIRE(dtype >= 0 && dtype <= 2, PM_EINVAL, "dtype %d is not a pm_dtype", dtype);
+  const int grid = (int)std::min<int64_t>(n, (int64_t)std::max(1, sm_count()) * 16);
+  autotune_kernel<<<grid, kTuneThreads, 0, static_cast<cudaStream_t>(stream)>>>(
+      MNK_dev, n, dtype, to_theta(theta_host), n_sm, picks_dev, t_pred_dev);
+  return launch_status("autotune_kernel");
+}
+
+extern "C" pm_status pm_grouped_autotune(int32_t G, const int32_t* M_host, int32_t N, int32_t K, int32_t dtype,
+                                         const pm_params* theta_host, int32_t n_sm, int16_t* BM_out_host,
+                                         int16_t* BN_out_host, int32_t* launch_out_host, float* t_pred_host,
+                                         void* stream) {
+  PM_REQUIRE(G > 0 && G <= kMaxGroups, PM_EINVAL, "G must be in [1, %d]", kMaxGroups);
+  PM_REQUIRE(M_host && theta_host && BM_out_host && BN_out_host && launch_out_host && t_pred_host && n_sm > 0,
+             PM_EINVAL, "null pointer or n_sm <= 0");
+  PM_REQUIRE(N > 0 && K > 0 && dtype >= 0 && dtype <= 2, PM_EINVAL, "bad N, K or dtype");
+  for (int q = 0; q < G; ++q) PM_REQUIRE(M_host[q] > 0, PM_EINVAL, "M[%d] <= 0", q);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  // device scratch: M (G int32), t (20 floats), bm/bn (20 x G int16 each), best index
+  const size_t bytes = 256 + G * 4 + 20 * 4 + 2 * 20 * (size_t)G * 2 + 16;
+  char* buf = nullptr;
+  PM_CUDA(cudaMallocAsync((void**)&buf, bytes, s));
+  int32_t* dM = (int32_t*)buf;
+  float* dt = (float*)(buf + ((G * 4 + 15) & ~15));
+  int16_t* dbm = (int16_t*)((char*)dt + 96);
+  int16_t* dbn = dbm + 20 * G;
+  int* dbest = (int*)(((uintptr_t)(dbn + 20 * G) + 15) & ~(uintptr_t)15);
+  pm_status st = PM_OK;
+  std::vector<int16_t> hbm(20 * (size_t)G), hbn(20 * (size_t)G);
+  float ht[20];
+  int best = 0;
+  cudaError_t e = cudaMemcpyAsync(dM, M_host, G * 4, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) {
+    grouped_tune_kernel<<<20, kGroupThreads, 0, s>>>(dM, G, N, K, dtype, to_theta(theta_host), n_sm, dt, dbm, dbn);
+    st = launch_status("grouped_tune_kernel");
+    if (st == PM_OK) {
+      grouped_pick_kernel<<<1, 1, 0, s>>>(dt, dbest);
+      st = launch_status("grouped_pick_kernel");
+    }
+    if (st == PM_OK) e = cudaMemcpyAsync(ht, dt, sizeof(ht), cudaMemcpyDeviceToHost, s);
+    if (st == PM_OK && e == cudaSuccess) e = cudaMemcpyAsync(&best, dbest, 4, cudaMemcpyDeviceToHost, s);
+    if (st == PM_OK && e == cudaSuccess)
+      e = cudaMemcpyAsync(hbm.data(), dbm, hbm.size() * 2, cudaMemcpyDeviceToHost, s);
+    if (st == PM_OK && e == cudaSuccess)
+      e = cudaMemcpyAsync(hbn.data(), dbn, hbn.size() * 2, cudaMemcpyDeviceToHost, s);
+  }
+  cudaFreeAsync(buf, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (st != PM_OK) return st;
+  if (e != cudaSuccess) return cuda_fail(e, "grouped autotune copies");
+  PM_REQUIRE(ht[best] < INFINITY, PM_EUNSUPPORTED, "no valid grouped configuration");
+  for (int q = 0; q < G; ++q) {
+    BM_out_host[q] = hbm[(size_t)best * G + q];
+    BN_out_host[q] = hbn[(size_t)best * G + q];
+  }
+  launch_out_host[0] = (int32_t)(dtype == PM_FP32 ? (best / 10 ? 64 : 32) : (best / 10 ? 128 : 64));
+  launch_out_host[1] = 2 + (best / 2) % 5;
+  launch_out_host[2] = 1 + best % 2;
+  *t_pred_host = ht[best];
+  return PM_OK;
+}

@@ -1,0 +1,110 @@
+"""Boundary tests that need no GPU: the library builds, loads, exports every
+symbol include/perfmodel.h declares, its struct layouts match the binding,
+and bad arguments are rejected with the documented status before anything
+is launched."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def pm():
+    from paper_2605_04178_gb300 import build as B
+    B.build()
+    import paper_2605_04178_gb300 as pm
+    return pm
+
+
+def declared_symbols():
+    text = open(os.path.join(ROOT, "include", "perfmodel.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(pm_[a-z0-9_]+)\s*\(", text)))
+
+
+def test_header_declares_the_boundary():
+    syms = declared_symbols()
+    for s in ("pm_probe_run", "pm_gemm_run", "pm_model_predict", "pm_model_grad", "pm_autotune_pick",
+              "pm_grouped_gemm_run", "pm_last_error"):
+        assert s in syms
+
+
+def test_library_exports_every_declared_symbol(pm):
+    lib = ctypes.CDLL(pm.LIB_PATH)
+    missing = [s for s in declared_symbols() if not hasattr(lib, s)]
+    assert not missing, missing
+    assert set(declared_symbols()) == set(pm.EXPORTS)
+
+
+def test_struct_layouts(pm):
+    assert ctypes.sizeof(pm.pm_cfg) == 24 == pm.CFG_DTYPE.itemsize
+    assert ctypes.sizeof(pm.pm_params) == 64
+    assert pm.pm_version() == 10000
+
+
+def test_invalid_tile_rejected_before_launch(pm):
+    bad = [pm.cfg(512, 512, 512, BM=96), pm.cfg(512, 512, 512, BK=48), pm.cfg(512, 512, 512, stages=7),
+           pm.cfg(512, 512, 512, BM=256, BN=256, BK=128, stages=2), pm.cfg(512, 512, 512, cta_group=3),
+           pm.cfg(512, 512, 512, dtype=5)]
+    for c in bad:
+        st = pm._lib.pm_gemm_run(ctypes.byref(c), None, None, None, None, None)
+        assert st == pm.PM_EUNSUPPORTED, (c.BM, c.BK, c.stages, st)
+        assert "valid space" in pm.pm_last_error()
+    c = pm.cfg(512, 512, 512, kind=pm.PM_KIND_COPY)
+    assert pm._lib.pm_gemm_run(ctypes.byref(c), None, None, None, None, None) == pm.PM_EINVAL
+    c = pm.cfg(0, 512, 512)
+    assert pm._lib.pm_gemm_run(ctypes.byref(c), None, None, None, None, None) == pm.PM_EINVAL
+    assert pm._lib.pm_gemm_run(None, None, None, None, None, None) == pm.PM_EINVAL
+
+
+def test_bad_arguments_rejected(pm):
+    L = pm._lib
+    a = pm.probe_args(pm.PM_PROBE_COPY, n=1024)
+    res = pm.pm_probe_result()
+    assert L.pm_probe_run(ctypes.byref(a), None, None, None, 1, 0, None, ctypes.byref(res)) == pm.PM_EINVAL
+    assert L.pm_probe_run(None, None, None, None, 1, 1, None, ctypes.byref(res)) == pm.PM_EINVAL
+    assert L.pm_probe_launch(ctypes.byref(a), None, None, None, None) == pm.PM_EINVAL
+    a = pm.probe_args(99, n=16)
+    assert L.pm_probe_launch(ctypes.byref(a), ctypes.c_void_p(16), ctypes.c_void_p(32), None, None) == pm.PM_EINVAL
+    a = pm.probe_args(pm.PM_PROBE_TMA2D, rows=64, cols=64, tile_r=4, tile_c=64)
+    assert L.pm_probe_launch(ctypes.byref(a), ctypes.c_void_p(16), ctypes.c_void_p(32), None, None) == pm.PM_EINVAL
+    th = pm.params(np.ones(16))
+    assert L.pm_model_predict(None, 10, ctypes.byref(th), 152, None, None) == pm.PM_EINVAL
+    assert L.pm_model_predict(ctypes.c_void_p(8), 10, ctypes.byref(th), 0, ctypes.c_void_p(8), None) == pm.PM_EINVAL
+    assert L.pm_model_predict(None, 0, ctypes.byref(th), 152, None, None) == pm.PM_OK   # empty batch: nothing to do
+    assert L.pm_model_grad(None, 0, ctypes.byref(th), 152, None, None, 0, None, None) == pm.PM_EINVAL
+    sz = ctypes.c_size_t()
+    assert L.pm_model_grad_workspace(1000, ctypes.byref(sz)) == pm.PM_OK and sz.value >= 17 * 8
+    assert L.pm_model_grad(ctypes.c_void_p(8), 1000, ctypes.byref(th), 152, ctypes.c_void_p(8), ctypes.c_void_p(8),
+                           8, ctypes.c_void_p(8), None) in (pm.PM_ENOMEM, pm.PM_ECUDA)
+    assert L.pm_autotune_pick(ctypes.c_void_p(8), 4, 7, ctypes.byref(th), 152, ctypes.c_void_p(8),
+                              ctypes.c_void_p(8), None) == pm.PM_EINVAL
+    a_b, b_b = ctypes.c_size_t(), ctypes.c_size_t()
+    assert L.pm_gemm_operand_bytes(0, 512, 256, 128, ctypes.byref(a_b), ctypes.byref(b_b)) == pm.PM_OK
+    assert a_b.value == 2 * 4 * 512 * 128 and b_b.value == 2 * 4 * 256 * 128
+    assert L.pm_gemm_operand_bytes(3, 512, 256, 128, ctypes.byref(a_b), ctypes.byref(b_b)) == pm.PM_EINVAL
+    assert L.pm_gemm_prepare(1, None, None, 16, 16, 16, None, None, None, None) == pm.PM_EINVAL
+    Mh = (ctypes.c_int32 * 2)(16, 0)
+    o16 = (ctypes.c_int16 * 2)()
+    launch = (ctypes.c_int32 * 3)()
+    t = ctypes.c_float()
+    assert L.pm_grouped_autotune(2, Mh, 64, 64, 1, ctypes.byref(th), 152, o16, o16, launch, ctypes.byref(t),
+                                 None) == pm.PM_EINVAL
+    assert L.pm_watchdog_selftest(0, None) == pm.PM_EINVAL
+
+
+def test_tile_space_matches_oracle_rule(pm):
+    # the library's validity rule (reached through pm_gemm_run's early check)
+    # and the oracle's independent implementation agree on all 540 points
+    import oracle as O
+    import synthetic as S
+    for dt in (0, 1, 2):
+        for (bm, bn, bk, s, g) in S.tile_space(dt):
+            c = pm.cfg(256, 256, 256, bm, bn, bk, s, g, dt)
+            st = pm._lib.pm_gemm_run(ctypes.byref(c), None, None, None, None, None)
+            lib_valid = st != pm.PM_EUNSUPPORTED
+            assert lib_valid == O.cfg_valid(bm, bn, bk, s, g, dt), (dt, bm, bn, bk, s, g, st)

@@ -1,0 +1,158 @@
+"""GPU parity of the batched model, its adjoint and the autotuners against the
+FP64 CPU oracle (1e-5 relative for predictions)."""
+import numpy as np
+import pytest
+
+import oracle as O
+import synthetic as S
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+N_SM = 152
+THETA = O.prior_theta(N_SM)
+FIELDS = ("M", "N", "K", "BM", "BN", "BK", "stages", "cta_group", "dtype", "kind")
+
+
+def theta32():
+    # the GPU takes FP32 parameters; the oracle gets the same rounded values
+    return THETA.astype(np.float32).astype(np.float64)
+
+
+def random_cfgs(n, seed=4, valid_only=False):
+    c = S.model_config_batch(n, seed)
+    c["kind"] = np.zeros(n, dtype=np.int32)
+    if valid_only:
+        ok = np.array([O.cfg_valid(c["BM"][i], c["BN"][i], c["BK"][i], c["stages"][i], c["cta_group"][i],
+                                   c["dtype"][i]) for i in range(n)])
+        c = {k: v[ok] for k, v in c.items()}
+    return c
+
+
+def probe_cfgs():
+    rows = [dict(M=2 ** k + j, kind=1) for k in range(20, 31) for j in (0, 3)]
+    rows += [dict(M=2 ** k, kind=2) for k in range(20, 31)]
+    rows += [dict(M=16384, N=16384, BM=r, BN=c, kind=3) for r, c in ((64, 64), (128, 64), (128, 128), (256, 64),
+                                                                     (256, 128))]
+    return {f: np.array([r.get(f, 0) for r in rows], dtype=np.int32) for f in FIELDS}
+
+
+def predict_gpu(lib, c, theta):
+    n = len(c["M"])
+    dev = lib.cfg_tensor(c)
+    out = torch.empty(n, dtype=torch.float32, device="cuda")
+    lib.pm_model_predict(dev, n, theta, N_SM, out)
+    return out.cpu().numpy().astype(np.float64)
+
+
+@pytest.mark.parametrize("n", [1, 7, 1000, 100003])
+def test_predict_matches_oracle(lib, n):
+    c = random_cfgs(n, seed=n)
+    th = theta32()
+    t_gpu = predict_gpu(lib, c, th)
+    t_orc = O.model_batch(c, th, N_SM)
+    assert np.all(np.abs(t_gpu - t_orc) <= 1e-5 * t_orc)
+
+
+def test_predict_probes_and_config1(lib):
+    th = theta32()
+    c = probe_cfgs()
+    assert np.all(np.abs(predict_gpu(lib, c, th) - O.model_batch(c, th, N_SM)) <= 1e-5 * O.model_batch(c, th, N_SM))
+    one = {f: np.array([v], dtype=np.int32) for f, v in
+           zip(FIELDS, (512, 512, 512, 128, 128, 32, 2, 1, 0, 0))}
+    assert predict_gpu(lib, one, th)[0] == pytest.approx(O.model_batch(one, th, N_SM)[0], rel=1e-5)
+
+
+def test_predict_invalid_records_are_nan(lib):
+    c = {f: np.array([v], dtype=np.int32) for f, v in zip(FIELDS, (512, 512, 512, 0, 128, 32, 2, 1, 0, 0))}
+    assert np.isnan(predict_gpu(lib, c, theta32())[0])
+
+
+def test_predict_million_configs(lib):
+    n = 10 ** 6
+    c = random_cfgs(n, seed=4)
+    th = theta32()
+    t_gpu = predict_gpu(lib, c, th)
+    idx = S.sampled_rows(5, n, 20000)
+    sub = {k: v[idx] for k, v in c.items()}
+    t_orc = O.model_batch(sub, th, N_SM)
+    assert np.all(np.abs(t_gpu[idx] - t_orc) <= 1e-5 * t_orc)
+
+
+def grad_gpu(lib, c, theta, t_meas):
+    n = len(c["M"])
+    dev = lib.cfg_tensor(c)
+    tm = torch.from_numpy(t_meas.astype(np.float32)).cuda()
+    ws = torch.empty(lib.pm_model_grad_workspace(n) // 8, dtype=torch.float64, device="cuda")
+    out = torch.empty(17, dtype=torch.float64, device="cuda")
+    lib.pm_model_grad(dev, n, theta, N_SM, tm, ws, out)
+    o = out.cpu().numpy()
+    return o[0], o[1:]
+
+
+@pytest.mark.parametrize("n", [1, 1000, 200000])
+def test_grad_matches_oracle(lib, n):
+    c = random_cfgs(n, seed=17 + n)
+    pc = probe_cfgs()
+    c = {k: np.concatenate([c[k], pc[k]]) for k in c}
+    th = theta32()
+    t_true = O.model_batch(c, th, N_SM)
+    noise = S.uniform01_f64(23, len(t_true))
+    t_meas = (t_true * np.exp(0.3 * (noise - 0.5))).astype(np.float32).astype(np.float64)
+    L_gpu, g_gpu = grad_gpu(lib, c, th, t_meas)
+    L_orc, g_orc = O.model_loss_grad(c, th, N_SM, t_meas)
+    assert L_gpu == pytest.approx(L_orc, rel=1e-4, abs=1e-9)
+    # per-component scale: the sum of absolute contributions (FP32 terms)
+    _, gi = O.model_batch(c, th, N_SM, grad=True)
+    r = np.log(t_true) - np.log(t_meas)
+    scale = (2.0 / len(r)) * np.sum(np.abs(r[:, None] * gi / t_true[:, None]), axis=0)
+    assert np.all(np.abs(g_gpu - g_orc) <= 1e-4 * scale + 1e-30), (g_gpu, g_orc, scale)
+
+
+def test_autotune_matches_oracle(lib):
+    rng = S.splitmix64(31, 3 * 600)
+    MNK = (16 * (1 + (rng >> np.uint64(40)) % np.uint64(1024))).astype(np.int32).reshape(-1, 3)
+    MNK = np.concatenate([MNK, np.array([[512, 512, 512], [8192, 8192, 8192], [16384, 16384, 16384]], np.int32)])
+    th = theta32()
+    for dt in (0, 1, 2):
+        n = len(MNK)
+        picks = torch.empty(n * 24, dtype=torch.uint8, device="cuda")
+        t = torch.empty(n, dtype=torch.float32, device="cuda")
+        lib.pm_autotune_pick(torch.from_numpy(MNK.ravel()).cuda(), n, dt, th, N_SM, picks, t)
+        p = picks.cpu().numpy().view(lib.CFG_DTYPE)
+        pick_o, t_o = O.autotune(MNK, dt, th, N_SM)
+        got = np.stack([p["BM"], p["BN"], p["BK"], p["stages"], p["cta_group"]], 1)
+        same = np.all(got == pick_o, axis=1)
+        # a different pick is allowed only where the oracle's own FP64
+        # predictions of the two candidates are within FP32 resolution
+        for i in np.nonzero(~same)[0]:
+            alt = {f: np.array([v], dtype=np.int32) for f, v in
+                   zip(FIELDS, (*MNK[i], *got[i], dt, 0))}
+            t_alt = O.model_batch(alt, th, N_SM)[0]
+            assert abs(t_alt - t_o[i]) <= 2e-6 * t_o[i], (MNK[i], got[i], pick_o[i])
+        assert same.mean() > 0.95
+        assert np.all(np.abs(t.cpu().numpy() - t_o) <= 1e-5 * t_o)
+
+
+def test_autotune_million_configs_per_launch(lib):
+    n_shapes = 10 ** 6 // 180 + 1
+    c = S.model_config_batch(n_shapes, seed=4)
+    MNK = np.stack([c["M"], c["N"], c["K"]], 1).astype(np.int32)
+    picks = torch.empty(n_shapes * 24, dtype=torch.uint8, device="cuda")
+    t = torch.empty(n_shapes, dtype=torch.float32, device="cuda")
+    th = theta32()
+    lib.pm_autotune_pick(torch.from_numpy(MNK.ravel()).cuda(), n_shapes, 1, th, N_SM, picks, t)
+    idx = S.sampled_rows(3, n_shapes, 200)
+    _, t_o = O.autotune(MNK[idx], 1, th, N_SM)
+    assert np.all(np.abs(t.cpu().numpy()[idx] - t_o) <= 1e-5 * t_o)
+
+
+def test_grouped_autotune_matches_oracle(lib):
+    Mg = S.grouped_m(64, 3)
+    th = theta32()
+    t_g, bm_g, bn_g, launch_g = lib.pm_grouped_autotune(Mg, 4096, 4096, 1, th, N_SM)
+    t_o, bm_o, bn_o, launch_o = O.grouped_autotune(Mg, 4096, 4096, 1, th, N_SM)
+    assert t_g == pytest.approx(t_o, rel=1e-5)
+    # the GPU's choice evaluated by the oracle is as good as the oracle's
+    t_check = O.grouped_predict(Mg, 4096, 4096, bm_g, bn_g, *launch_g, 1, th, N_SM)
+    assert t_check == pytest.approx(t_o, rel=1e-5)

@@ -1,0 +1,70 @@
+"""GPU parity of the calibration probes against the CPU oracle (bit-exact)."""
+import numpy as np
+import pytest
+
+import oracle as O
+import synthetic as S
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("n", [1, 3, 4, 1000, 2 ** 20 + 3, 2 ** 24])
+def test_copy_bit_exact(lib, n):
+    a = torch.from_numpy(S.uniform_pm1(1, n)).cuda()
+    b = torch.full_like(a, float("nan"))
+    r = lib.pm_probe_run(lib.probe_args(lib.PM_PROBE_COPY, n=n), a, b, warmup=1, reps=3)
+    assert r["bytes"] == 8 * n and r["median_s"] > 0
+    assert torch.equal(a.view(torch.int32), b.view(torch.int32))
+
+
+@pytest.mark.parametrize("n", [1, 5, 4099, 2 ** 20 + 1])
+def test_triad_bit_exact(lib, n):
+    b = S.normal(1, n) * np.float32(100.0)
+    c = S.uniform_pm1(2, n)
+    s = 3.0
+    a_dev = torch.empty(n, dtype=torch.float32, device="cuda")
+    lib.pm_probe_run(lib.probe_args(lib.PM_PROBE_TRIAD, n=n, scalar=s), a_dev, torch.from_numpy(b).cuda(),
+                     torch.from_numpy(c).cuda(), warmup=0, reps=2)
+    ref = O.triad_f32(b, c, s)
+    assert np.array_equal(a_dev.cpu().numpy().view(np.uint32), ref.view(np.uint32))
+
+
+@pytest.mark.parametrize("nodes,hops,start", [(1, 10, 0), (256, 1000, 3), (4096, 4096, 7), (1 << 20, 100000, 12345)])
+def test_pchase_final_index(lib, nodes, hops, start):
+    buf = S.pchase_buffer(nodes, seed=1)
+    out = torch.zeros(1, dtype=torch.int32, device="cuda")
+    r = lib.pm_probe_run(lib.probe_args(lib.PM_PROBE_PCHASE, n=nodes, hops=hops, start=start),
+                         torch.from_numpy(buf.view(np.int32)).cuda(), out, warmup=0, reps=2)
+    assert r["final_index"] == O.pchase(buf, 16, start, hops)
+
+
+@pytest.mark.parametrize("tile", [(64, 64), (128, 64), (128, 128), (256, 64), (256, 128), (8, 4), (200, 36)])
+@pytest.mark.parametrize("shape", [(1000, 1004), (64, 64), (3, 20)])
+def test_tma2d_copy_bit_exact(lib, tile, shape):
+    rows, cols = shape
+    src = torch.from_numpy(S.uniform_pm1(7, rows * cols).reshape(rows, cols)).cuda()
+    dst = torch.full_like(src, float("nan"))
+    lib.pm_probe_run(lib.probe_args(lib.PM_PROBE_TMA2D, rows=rows, cols=cols, tile_r=tile[0], tile_c=tile[1]),
+                     src, dst, warmup=0, reps=2)
+    assert torch.equal(src.view(torch.int32), dst.view(torch.int32))
+
+
+def test_tma2d_full_size(lib):
+    # 1 GiB FP32 matrix (16384 x 16384), the probe's full configuration
+    src = torch.randn(16384, 16384, device="cuda")
+    dst = torch.zeros_like(src)
+    r = lib.pm_probe_run(lib.probe_args(lib.PM_PROBE_TMA2D, rows=16384, cols=16384, tile_r=128, tile_c=64),
+                         src, dst, warmup=1, reps=3)
+    assert torch.equal(src, dst)
+    assert r["bytes"] == 2 ** 31
+
+
+def test_watchdog_times_out_and_context_survives(lib):
+    st = lib.pm_watchdog_selftest(100000)          # 0.1 s limit on a wait nothing completes
+    assert st == lib.PM_ETIMEOUT
+    assert lib.pm_device_status(True) == lib.PM_OK  # the self-test cleared its record
+    x = torch.arange(1000, device="cuda", dtype=torch.float32)
+    y = torch.empty_like(x)
+    lib.pm_probe_run(lib.probe_args(lib.PM_PROBE_COPY, n=1000), x, y, warmup=0, reps=1)
+    assert torch.equal(x, y)
