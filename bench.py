@@ -1,0 +1,406 @@
+"""Benchmark of the GB300 hot path of the stage-centric performance model
+(arxiv 2605.04178): the model-autotuned BF16 GEMM C = A.B at M = N = K = 8192.
+
+One step = one launch of the tcgen05 GEMM in the tile configuration the
+model's GPU autotuner picked for this shape (the pick is made once, before
+timing).  `value` is whole-job TFLOP/s (2MNK per step per GPU) with the
+operands already in HBM; `e2e` is the same metric through the public C-ABI
+calls from pinned host FP32 buffers (H2D of A and B, operand preparation,
+GEMM, D2H of C inside the timed region).  Secondary figures on the same line:
+the HBM probes, the batched model and its adjoint, and the autotuner.
+
+--impl reference times the CPU FP64 oracle (the reference of this build) on a
+bounded row sample of the same GEMM, on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "model MAE % vs measured; autotuned GEMM TFLOP/s % of peak vs exhaustive best"
+M = N = K = 8192
+SEED = 2
+
+
+def _dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def _measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during a timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append((time.time(), line.strip()))
+
+    def stop(self):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.t.join(timeout=2)
+
+    def summary(self, t0=None, t1=None):
+        sm, mx, reasons = [], None, set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for ts, line in self.lines:
+            if t0 is not None and (ts < t0 or ts > t1 + 0.15):
+                continue
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _cpu_gemm_rate(A, B, rows_per_step: int, steps: int, warmup: int):
+    """Oracle FP64 GEMM on sampled rows; returns (TFLOP/s, seconds, rows)."""
+    import numpy as np
+
+    import oracle as O
+    import synthetic as S
+    Mr = A.shape[0]
+    for i in range(warmup):
+        O.gemm_f64(A[(i * rows_per_step) % Mr:(i * rows_per_step) % Mr + rows_per_step], B)
+    t0 = time.perf_counter()
+    for i in range(steps):
+        r0 = (i * rows_per_step) % (Mr - rows_per_step + 1)
+        O.gemm_f64(A[r0:r0 + rows_per_step], B)
+    dt = time.perf_counter() - t0
+    flops = 2.0 * rows_per_step * B.shape[0] * B.shape[1] * steps
+    return flops / dt / 1e12, dt, rows_per_step * steps
+
+
+def run_reference(args):
+    rank, world, _ = _dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")
+        if rank != 0:
+            dist.barrier()
+            dist.destroy_process_group()
+            return
+    import numpy as np
+
+    import oracle as O
+    import synthetic as S
+    O.build()
+    rows_per_step = 8
+    n_rows = rows_per_step * 64
+    B = S.matrix(SEED, K, N, "normal", M * K)
+    A = S.matrix(SEED, n_rows, K, "normal", 0)          # the first n_rows rows of A
+    tflops, dt, rows = _cpu_gemm_rate(A, B, rows_per_step, args.steps, args.warmup)
+    cores = os.cpu_count()
+    line = {
+        "impl": "reference", "metric": METRIC, "value": tflops, "unit": "TFLOP/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "gemm_8192^3_rows_sample", "M": M, "N": N, "K": K, "rows_per_step": rows_per_step},
+        "cpu_baseline": {"value": tflops, "unit": "TFLOP/s", "cores": cores, "kind": "oracle",
+                         "sample": "%d rows x 8192 x 8192 FP64 per step (C = A.B definition, OpenMP)" % rows_per_step},
+        "e2e": {"value": tflops, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "gpu_launches": 0,
+    }
+    print(json.dumps(line))
+    sys.stdout.flush()
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def run_gpu(args):
+    import numpy as np
+    import torch
+
+    rank, world, local = _dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    from paper_2605_04178_gb300 import build as B_
+    B_.build()
+    import oracle as O
+    import paper_2605_04178_gb300 as pm
+    import synthetic as S
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def max_over_ranks(x: float) -> float:
+        if dist is None:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    peaks, peak_src = _measured_peaks()
+    n_sm = pm.sm_count()
+    theta = O.prior_theta(n_sm).astype(np.float32).astype(np.float64)
+    calib = os.path.join(ROOT, "paper_2605_04178_gb300", "theta_gb300.json")
+    theta_src = "prior"
+    if os.path.exists(calib):
+        with open(calib) as f:
+            theta = np.array(json.load(f)["theta"], dtype=np.float64)
+        theta_src = "calibrated"
+    stream = torch.cuda.current_stream()
+
+    # ------------------------------------------------------ model-driven pick
+    MNK = torch.tensor([M, N, K], dtype=torch.int32, device="cuda")
+    picks = torch.empty(24, dtype=torch.uint8, device="cuda")
+    t_pred = torch.empty(1, dtype=torch.float32, device="cuda")
+    pm.pm_autotune_pick(MNK, 1, pm.PM_BF16, theta, n_sm, picks, t_pred)
+    p = picks.cpu().numpy().view(pm.CFG_DTYPE)[0]
+    pick = tuple(int(p[k]) for k in ("BM", "BN", "BK", "stages", "cta_group"))
+    if args.cfg:
+        pick = tuple(int(v) for v in args.cfg.split(","))
+    cfg = pm.cfg(M, N, K, *pick, dtype=pm.PM_BF16)
+
+    # ------------------------------------------------------------- operands
+    A_h = S.matrix(SEED, M, K, "normal", 0)
+    B_h = S.matrix(SEED, K, N, "normal", M * K)
+    A_pin = torch.from_numpy(A_h).pin_memory()
+    B_pin = torch.from_numpy(B_h).pin_memory()
+    A_d, B_d = A_pin.cuda(), B_pin.cuda()
+    ops = pm.GemmOperands(pm.PM_BF16, M, N, K)
+    ops.prepare(A_d, B_d)
+    C = torch.empty(M, N, dtype=torch.float32, device="cuda")
+    flops = 2.0 * M * N * K
+
+    # ------------------------------------------------- device-resident steps
+    for _ in range(args.warmup):
+        ops.run(cfg, C)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * args.steps)]
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    barrier()
+    t_wall0 = time.time()
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    start.record(stream)
+    for i in range(args.steps):
+        ev[2 * i].record(stream)
+        ops.run(cfg, C)
+        ev[2 * i + 1].record(stream)
+    end.record(stream)
+    barrier()
+    t_wall1 = time.time()
+    clocks.stop()
+    ms_total = start.elapsed_time(end)
+    per_launch = [ev[2 * i].elapsed_time(ev[2 * i + 1]) for i in range(args.steps)]
+    ms_total = max_over_ranks(ms_total)
+    ms_step = ms_total / args.steps
+    value = world * flops * args.steps / (ms_total * 1e-3) / 1e12
+    kern_ms = statistics.mean(per_launch)
+    achieved = flops / (kern_ms * 1e-3) / 1e12
+    peak = float(peaks.get("bf16_tflops", 1900.0))
+    # result check on sampled rows (the oracle never runs inside timing)
+    C_h = C.cpu().numpy()
+    if rank == 0 and not args.no_check:
+        rows = S.sampled_rows(9, M, 16)
+        ref = O.gemm_f64(A_h[rows], B_h)
+        err = float(np.linalg.norm(C_h[rows] - ref) / np.linalg.norm(ref))
+        assert err <= 2e-2, "GEMM result outside the BF16 bound: %g" % err
+    else:
+        err = None
+
+    # ------------------------------------------------------ end-to-end steps
+    C_pin = torch.empty(M, N, dtype=torch.float32).pin_memory()
+    e2e_steps = max(3, args.steps // 50)
+
+    def e2e_step():
+        A_d.copy_(A_pin, non_blocking=True)
+        B_d.copy_(B_pin, non_blocking=True)
+        pm.pm_gemm_prepare(pm.PM_BF16, A_d, B_d, M, N, K, ops.A_op, ops.B_op, ops.scales)
+        pm.pm_gemm_run(cfg, ops.A_op, ops.B_op, C, ops.scales)
+        C_pin.copy_(C, non_blocking=True)
+        torch.cuda.current_stream().synchronize()
+
+    for _ in range(2):
+        e2e_step()
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        e2e_step()
+    barrier()
+    e2e_s = max_over_ranks(time.perf_counter() - t0)
+    e2e_value = world * flops * e2e_steps / e2e_s / 1e12
+
+    extra = {}
+    if not args.skip_extra:
+        extra = secondary(pm, O, S, theta, n_sm, peaks)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+            "config": {"workload": "bf16_gemm_8192^3_model_autotuned", "M": M, "N": N, "K": K,
+                       "inputs": "A,B ~ N(0,1) seed 2, FP32 -> BF16 K-major operands",
+                       "tile": dict(zip(("BM", "BN", "BK", "stages", "cta_group"), pick)),
+                       "theta": theta_src, "l2": "operands 256 MB > 129 MB L2, no flush",
+                       "parallelism": "replicas" if world > 1 else "single"},
+            "pct_of_peak": 100.0 * achieved / peak,
+            "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                         "frac": achieved / peak, "traffic": None,
+                         "peak_source": "%s bf16 burst (cuBLAS 8192^3)" % peak_src,
+                         "kernel": "gemm_kernel<1 or 2, bf16>", "kernel_ms": kern_ms},
+            "e2e": {"value": e2e_value, "unit": "TFLOP/s", "h2d_bytes_per_step": 4 * (M * K + K * N),
+                    "d2h_bytes_per_step": 4 * M * N},
+            "gpu_launches": args.steps,
+            "clocks": clocks.summary(t_wall0, t_wall1),
+            "bf16_rel_frobenius_error": err,
+        }
+        line.update(extra)
+        if not args.skip_cpu:
+            tfl, dt, rows = _cpu_gemm_rate(A_h[:64], B_h, 8, 6, 1)
+            line["cpu_baseline"] = {"value": tfl, "unit": "TFLOP/s", "cores": os.cpu_count(), "kind": "oracle",
+                                    "sample": "6 x 8 rows of the 8192^3 GEMM in FP64 (%.1f s)" % dt}
+        traffic = _traffic_from_profile()
+        if traffic is not None and traffic.get("tile") == list(pick):
+            line["roofline"]["traffic"] = traffic["bytes"]
+        print(json.dumps(line))
+        sys.stdout.flush()
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def _traffic_from_profile():
+    p = os.path.join(ROOT, "profiles", "gemm_bf16_8192_traffic.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f)
+    return None
+
+
+def secondary(pm, O, S, theta, n_sm, peaks):
+    """HBM probes, batched model forward/adjoint and autotuner throughput."""
+    import numpy as np
+    import torch
+    out = {}
+    n = 2 ** 28
+    a = torch.empty(n, dtype=torch.float32, device="cuda").uniform_(-1, 1)
+    b = torch.empty_like(a)
+    c = torch.empty_like(a).uniform_(-1, 1)
+    r_copy = pm.pm_probe_run(pm.probe_args(pm.PM_PROBE_COPY, n=n), a, b, warmup=10, reps=50)
+    r_triad = pm.pm_probe_run(pm.probe_args(pm.PM_PROBE_TRIAD, n=n, scalar=3.0), a, b, c, warmup=10, reps=50)
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    out["probes"] = {
+        "copy_GBps": r_copy["bytes"] / r_copy["median_s"] / 1e9,
+        "triad_GBps": r_triad["bytes"] / r_triad["median_s"] / 1e9,
+        "n_elems": n, "hbm_peak_GBps": hbm,
+    }
+    out["probes"]["copy_frac"] = out["probes"]["copy_GBps"] / hbm
+    out["probes"]["triad_frac"] = out["probes"]["triad_GBps"] / hbm
+    del a, b, c
+    # batched model over 1e6 configurations: forward and adjoint
+    nc = 10 ** 6
+    cf = S.model_config_batch(nc, seed=4)
+    cf["kind"] = np.zeros(nc, dtype=np.int32)
+    dev = pm.cfg_tensor(cf)
+    t_out = torch.empty(nc, dtype=torch.float32, device="cuda")
+    tm = torch.ones(nc, dtype=torch.float32, device="cuda") * 1e-3
+    ws = torch.empty(pm.pm_model_grad_workspace(nc) // 8, dtype=torch.float64, device="cuda")
+    go = torch.empty(17, dtype=torch.float64, device="cuda")
+    MNK = torch.from_numpy(np.stack([cf["M"], cf["N"], cf["K"]], 1)[: nc // 180].astype(np.int32).ravel()).cuda()
+    picks = torch.empty((nc // 180) * 24, dtype=torch.uint8, device="cuda")
+    tp = torch.empty(nc // 180, dtype=torch.float32, device="cuda")
+
+    def timeit(fn, reps=50):
+        for _ in range(5):
+            fn()
+        s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s.record()
+        for _ in range(reps):
+            fn()
+        e.record()
+        torch.cuda.synchronize()
+        return s.elapsed_time(e) / reps * 1e-3
+
+    t_f = timeit(lambda: pm.pm_model_predict(dev, nc, theta, n_sm, t_out))
+    t_g = timeit(lambda: pm.pm_model_grad(dev, nc, theta, n_sm, tm, ws, go))
+    t_a = timeit(lambda: pm.pm_autotune_pick(MNK, nc // 180, 1, theta, n_sm, picks, tp))
+    out["model"] = {"configs": nc, "forward_Mcfg_per_s": nc / t_f / 1e6, "forward_us": t_f * 1e6,
+                    "adjoint_Mcfg_per_s": nc / t_g / 1e6, "adjoint_us": t_g * 1e6,
+                    "autotune_Mcfg_per_s": (nc // 180) * 180 / t_a / 1e6, "autotune_us": t_a * 1e6,
+                    "forward_GBps": 28.0 * nc / t_f / 1e9}
+    return out
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--cfg", default=None, help="override the tile: BM,BN,BK,stages,cta_group")
+    ap.add_argument("--skip-extra", action="store_true")
+    ap.add_argument("--skip-cpu", action="store_true")
+    ap.add_argument("--no-check", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

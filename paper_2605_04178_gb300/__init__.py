@@ -70,8 +70,15 @@ class PMError(RuntimeError):
 
 
 def _load():
+    # Compile on first import (nvcc, sm_103a) when the library is missing or
+    # older than its sources; a failed build raises: there is no fallback.
+    from . import build as _build
+    try:
+        _build.build()
+    except Exception as e:  # noqa: BLE001
+        raise ImportError("libperfmodel.so could not be built: %s" % e) from e
     if not os.path.exists(LIB_PATH):
-        raise ImportError("libperfmodel.so is not built (%s); run paper_2605_04178_gb300.build.build()" % LIB_PATH)
+        raise ImportError("libperfmodel.so is missing (%s)" % LIB_PATH)
     lib = ctypes.CDLL(LIB_PATH)
     P, i32, i64, sz = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_size_t
     sig = {

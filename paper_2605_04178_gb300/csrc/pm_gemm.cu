@@ -43,7 +43,11 @@ struct GemmParams {
   uint32_t stage_bytes, a_part_bytes, b_part_bytes, tx_bytes;
   uint32_t idesc;
   int lo_row_a, lo_row_b;          // row offset of the lo half (three-pass TF32)
-  int m64_layout;                  // TMEM lane layout of 64-row accumulators
+  // TMEM layout of the accumulator: 0 = one row per lane (128-row blocks),
+  // 1 = 64 rows in lanes 0-15 of each 32-lane quarter (M = 64, one SM),
+  // 2 = 64 rows in lanes 0-63 for columns [0, N/2) and again in lanes
+  //     64-127 for columns [N/2, N) (M = 128 split over a CTA pair).
+  int layout;
   float* C;
   const float* scales;             // FP8: {s_A, s_B}
   Watchdog wd;
@@ -214,8 +218,17 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
     const int q = warp & 3;                               // TMEM lane quarter of this warp
     float scale = 1.f;
     if constexpr (KIND == 2) scale = 1.f / (__ldg(p.scales) * __ldg(p.scales + 1));
-    const bool m64 = p.BM == 64;
     const bool vec = (p.N & 3) == 0;
+    // rows and columns this warp's TMEM lane quarter holds
+    int lrow, qcol0, qcols;
+    bool lvalid;
+    if (p.layout == 1) {
+      lrow = 16 * q + lane; lvalid = lane < 16; qcol0 = 0; qcols = p.BN;
+    } else if (p.layout == 2) {
+      lrow = 32 * (q & 1) + lane; lvalid = true; qcol0 = (q >> 1) * (p.BN / 2); qcols = p.BN / 2;
+    } else {
+      lrow = 32 * q + lane; lvalid = true; qcol0 = 0; qcols = p.BN;
+    }
     int it = 0;
     for (int t = cta; t < p.n_tiles; t += n_ctas, ++it) {
       const int buf = it % p.nbuf;
@@ -225,21 +238,12 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
       int tm, tn;
       tile_coords(t, p, tm, tn);
       const int crow0 = (CG == 1) ? tm * p.BM : tm * 2 * p.BM + (int)rank * p.BM;
-      const int ccol0 = tn * p.BN;
-      int lrow;
-      bool lvalid;
-      if (m64) {
-        if (p.m64_layout == 0) { lrow = 16 * q + lane; lvalid = lane < 16; }
-        else { lrow = 32 * q + lane; lvalid = q < 2; }
-      } else {
-        lrow = 32 * q + lane;
-        lvalid = true;
-      }
+      const int ccol0 = tn * p.BN + qcol0;
       for (int m = 0; m < p.n_mblk; ++m) {
         const int row = crow0 + m * 128 + lrow;
         const bool rvalid = lvalid && row < p.M;
         float* crow = p.C + (size_t)row * p.N;
-        for (int j = 0; j < p.BN / 32; ++j) {
+        for (int j = 0; j < qcols / 32; ++j) {
           uint32_t r[32];
           const uint32_t taddr =
               tmem_base + ((uint32_t)(32 * q) << 16) + (uint32_t)(buf * p.acc_cols + m * p.BN + 32 * j);
@@ -386,14 +390,6 @@ bool gemm_tile_valid(int BM, int BN, int BK, int s, int g, int dt) {
   return true;
 }
 
-static int m64_layout() {
-  static int v = [] {
-    const char* s = getenv("PM_M64_LAYOUT");
-    return s ? atoi(s) : 0;
-  }();
-  return v;
-}
-
 struct TmapKey {
   const void* ptr;
   uint64_t rows, cols;
@@ -480,7 +476,8 @@ pm_status gemm_plan(const pm_cfg& c, GemmParams& p, size_t& smem) {
   p.sw = std::min(128, c.BK * e);
   p.n_atoms = c.BK * e / p.sw;
   p.n_mblk = (c.BM + 127) / 128;
-  p.acc_cols = p.n_mblk * c.BN;
+  p.layout = c.BM >= 128 ? 0 : (g == 1 ? 1 : 2);
+  p.acc_cols = p.layout == 2 ? c.BN / 2 : p.n_mblk * c.BN;
   p.nbuf = (2 * p.acc_cols <= 512) ? 2 : 1;
   int need = p.nbuf * p.acc_cols, cols = 32;
   while (cols < need) cols <<= 1;
@@ -495,7 +492,6 @@ pm_status gemm_plan(const pm_cfg& c, GemmParams& p, size_t& smem) {
   p.idesc = instr_desc(fmt, (uint32_t)mma_m, (uint32_t)c.BN);
   p.lo_row_a = (L == 2) ? c.M : 0;
   p.lo_row_b = (L == 2) ? c.N : 0;
-  p.m64_layout = m64_layout();
   smem = (size_t)c.stages * p.stage_bytes + 1024;
   return PM_OK;
 }
