@@ -316,13 +316,18 @@ __global__ void __launch_bounds__(kGradThreads) model_grad_kernel(const pm_cfg* 
   }
 }
 
-__global__ void model_grad_finish_kernel(const double* __restrict__ partials, int blocks, int64_t n,
-                                         double* __restrict__ out) {
-  const int j = threadIdx.x;
-  if (j >= 17) return;
+// Warp j sums component j of the block records: lane l adds records l,
+// l+32, ... in order, then a fixed butterfly combines the lanes, so the
+// result depends only on the number of records (deterministic).
+__global__ void __launch_bounds__(17 * 32) model_grad_finish_kernel(const double* __restrict__ partials,
+                                                                    int blocks, int64_t n,
+                                                                    double* __restrict__ out) {
+  const int j = threadIdx.x >> 5, lane = threadIdx.x & 31;
   double s = 0.0;
-  for (int b = 0; b < blocks; ++b) s += partials[(int64_t)b * 17 + j];
-  out[j] = s / (double)n;
+#pragma unroll 4
+  for (int b = lane; b < blocks; b += 32) s += partials[(int64_t)b * 17 + j];
+  s = warp_sum_d(s);
+  if (lane == 0) out[j] = s / (double)n;
 }
 
 static int grad_blocks(int64_t n) {
@@ -530,7 +535,7 @@ extern "C" pm_status pm_model_grad(const pm_cfg* cfgs_dev, int64_t n, const pm_p
                                                     static_cast<double*>(workspace_dev));
   pm_status st = launch_status("model_grad_kernel");
   if (st != PM_OK) return st;
-  model_grad_finish_kernel<<<1, 32, 0, s>>>(static_cast<const double*>(workspace_dev), blocks, n, out_dev);
+  model_grad_finish_kernel<<<1, 17 * 32, 0, s>>>(static_cast<const double*>(workspace_dev), blocks, n, out_dev);
   return launch_status("model_grad_finish_kernel");
 }
 
