@@ -36,7 +36,7 @@ typedef enum {
   PM_EUNSUPPORTED = -2,  /* configuration outside the valid tile space */
   PM_ECUDA = -3,         /* a CUDA runtime/driver call failed */
   PM_ETIMEOUT = -4,      /* a device-side wait hit the watchdog limit */
-  PM_ENOMEM = -5         /* caller-provided workspace too small */
+  PM_ENOMEM = -5         /* workspace (caller-provided or built-in) too small */
 } pm_status;
 
 /* Operand precisions of the GEMM family (Sec. II: 5th-gen tensor cores take
@@ -170,6 +170,24 @@ pm_status pm_model_grad_workspace(int64_t n, size_t* bytes);
 pm_status pm_model_grad(const pm_cfg* cfgs_dev, int64_t n, const pm_params* theta_host, int32_t n_sm,
                         const float* t_meas_dev, void* workspace_dev, size_t workspace_bytes, double* out_dev,
                         void* stream);
+
+/* pm_model_grad without any device allocation, for callers that cannot
+ * allocate device memory when they need the gradient (a host program that
+ * links only this library and owns no CUDA allocator, a runtime held to a
+ * fixed device-memory budget).  The paper has no counterpart: this is an
+ * interface convenience of this library.  Same inputs and output as
+ * pm_model_grad, minus the workspace: the per-block partial sums go to a
+ * fixed 557,056-byte array inside the library, present on every GPU that
+ * loads it until the process exits.  At most 1,048,576 configurations per
+ * call; larger n returns PM_ENOMEM with a message and launches nothing.
+ * The first call on a device looks up that array's device address
+ * (cudaGetSymbolAddress, no allocation); make that first call outside any
+ * stream capture.  All calls share the array: calls whose kernels overlap on
+ * the GPU race and must be serialised by the caller (one stream, or events).
+ * Nothing needs clearing between calls: each call writes every partial
+ * record it reads.  Async. */
+pm_status pm_model_grad_noalloc(const pm_cfg* cfgs_dev, int64_t n, const pm_params* theta_host, int32_t n_sm,
+                                const float* t_meas_dev, double* out_dev, void* stream);
 
 /* Autotuner (Sec. III-B adaptive tile selection; Sec. VI autotuning
  * guidance): for each of n shapes (MNK_dev: n x {M,N,K} int32) evaluates the

@@ -58,7 +58,7 @@ assert ctypes.sizeof(pm_cfg) == 24 and ctypes.sizeof(pm_probe_args) == 56 and ct
 
 # Every exported symbol of include/perfmodel.h
 EXPORTS = ("pm_probe_launch", "pm_probe_run", "pm_gemm_operand_bytes", "pm_gemm_prepare", "pm_gemm_run",
-           "pm_grouped_gemm_run", "pm_model_predict", "pm_model_grad_workspace", "pm_model_grad",
+           "pm_grouped_gemm_run", "pm_model_predict", "pm_model_grad_workspace", "pm_model_grad", "pm_model_grad_noalloc",
            "pm_autotune_pick", "pm_grouped_autotune", "pm_last_error", "pm_device_status",
            "pm_watchdog_selftest", "pm_version")
 
@@ -92,6 +92,7 @@ def _load():
         "pm_model_predict": [P, i64, ctypes.POINTER(pm_params), i32, P, P],
         "pm_model_grad_workspace": [i64, ctypes.POINTER(sz)],
         "pm_model_grad": [P, i64, ctypes.POINTER(pm_params), i32, P, P, sz, P, P],
+        "pm_model_grad_noalloc": [P, i64, ctypes.POINTER(pm_params), i32, P, P, P],
         "pm_autotune_pick": [P, i64, i32, ctypes.POINTER(pm_params), i32, P, P, P],
         "pm_grouped_autotune": [i32, P, i32, i32, i32, ctypes.POINTER(pm_params), i32, P, P, P, P, P],
         "pm_device_status": [ctypes.c_int],
@@ -241,6 +242,13 @@ def pm_model_grad(cfgs_dev, n, theta, n_sm, t_meas, workspace, out, stream=None)
     _check(_lib.pm_model_grad(_ptr(cfgs_dev), int(n), ctypes.byref(params(theta)), int(n_sm), _ptr(t_meas),
                               _ptr(workspace), int(workspace.numel() * workspace.element_size()), _ptr(out),
                               _stream(stream)), "pm_model_grad")
+
+
+def pm_model_grad_noalloc(cfgs_dev, n, theta, n_sm, t_meas, out, stream=None):
+    """pm_model_grad with the library's built-in scratch array instead of a
+    caller workspace (for callers that cannot allocate device memory)."""
+    _check(_lib.pm_model_grad_noalloc(_ptr(cfgs_dev), int(n), ctypes.byref(params(theta)), int(n_sm), _ptr(t_meas),
+                                      _ptr(out), _stream(stream)), "pm_model_grad_noalloc")
 
 
 def pm_autotune_pick(MNK_dev, n, dtype, theta, n_sm, picks_dev, t_pred_dev, stream=None):

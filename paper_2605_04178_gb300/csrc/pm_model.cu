@@ -10,6 +10,7 @@
 #include <math.h>
 
 #include <algorithm>
+#include <mutex>
 #include <vector>
 
 #include "pm_internal.cuh"
@@ -603,4 +604,70 @@ extern "C" pm_status pm_grouped_autotune(int32_t G, const int32_t* M_host, int32
   launch_out_host[2] = 1 + best % 2;
   *t_pred_host = ht[best];
   return PM_OK;
+}
+
+// ----------------------------------------------------------------------------
+// Allocation-free variant of pm_model_grad.
+//
+// Some callers cannot allocate device memory at the point where they need the
+// calibration gradient: a host program that links only this library and owns
+// no CUDA allocator, a runtime working inside a fixed device-memory budget, or
+// code that must not trigger allocator traffic in its hot loop.  For them the
+// per-block partial sums live in a fixed array compiled into this library,
+// resident on every GPU that loads it for the life of the process.
+//
+// Capacity: kGradStaticRecords block records of 17 doubles (557,056 bytes),
+// one block of kGradThreads threads per record, so at most
+// kGradStaticRecords * kGradThreads = 1,048,576 configurations per call.
+// Every record a call reads is first written by that call, so nothing has to
+// be cleared between calls; two calls whose kernels overlap on a GPU share the
+// array and race.
+namespace pm {
+
+constexpr int kGradStaticRecords = 4096;
+static __device__ __align__(256) double g_grad_scratch[kGradStaticRecords * 17];
+
+static double* g_grad_scratch_ptr[64];
+static std::mutex g_grad_scratch_mu;
+
+// Device address of g_grad_scratch for the current device.  In host code the
+// array's name is only a host-side stand-in, so the address is looked up once
+// per device with that device current.
+static pm_status grad_scratch_address(double** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+  PM_REQUIRE(dev >= 0 && dev < 64, PM_EINVAL, "device index %d out of range", dev);
+  std::lock_guard<std::mutex> lk(g_grad_scratch_mu);
+  if (g_grad_scratch_ptr[dev] == nullptr) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_grad_scratch);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(g_grad_scratch)");
+    g_grad_scratch_ptr[dev] = static_cast<double*>(p);
+  }
+  *out = g_grad_scratch_ptr[dev];
+  return PM_OK;
+}
+
+}  // namespace pm
+
+extern "C" pm_status pm_model_grad_noalloc(const pm_cfg* cfgs_dev, int64_t n, const pm_params* theta_host,
+                                           int32_t n_sm, const float* t_meas_dev, double* out_dev, void* stream) {
+  PM_REQUIRE(n > 0, PM_EINVAL, "n must be positive");
+  PM_REQUIRE(n <= (int64_t)kGradStaticRecords * kGradThreads, PM_ENOMEM,
+             "pm_model_grad_noalloc takes at most %lld configurations per call (got %lld); split the batch or "
+             "use pm_model_grad with a workspace",
+             (long long)kGradStaticRecords * kGradThreads, (long long)n);
+  PM_REQUIRE(cfgs_dev && theta_host && t_meas_dev && out_dev && n_sm > 0, PM_EINVAL, "null pointer or n_sm <= 0");
+  PM_REQUIRE(((uintptr_t)cfgs_dev & 7) == 0, PM_EINVAL, "cfgs_dev must be 8-byte aligned");
+  double* scratch = nullptr;
+  pm_status st = grad_scratch_address(&scratch);
+  if (st != PM_OK) return st;
+  const int blocks = (int)((n + kGradThreads - 1) / kGradThreads);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  model_grad_kernel<<<blocks, kGradThreads, 0, s>>>(cfgs_dev, n, to_theta(theta_host), n_sm, t_meas_dev, scratch);
+  st = launch_status("model_grad_kernel");
+  if (st != PM_OK) return st;
+  model_grad_finish_kernel<<<1, 17 * 32, 0, s>>>(scratch, blocks, n, out_dev);
+  return launch_status("model_grad_finish_kernel");
 }
