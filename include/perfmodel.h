@@ -138,6 +138,14 @@ pm_status pm_gemm_prepare(int32_t dtype, const float* A_dev, const float* B_dev,
 pm_status pm_gemm_run(const pm_cfg* cfg, const void* A_op_dev, const void* B_op_dev, float* C_dev,
                       const float* scales_dev, void* stream);
 
+/* Timing harness for the GEMM (Sec. V-B protocol): `warmup` untimed then
+ * `reps` timed pm_gemm_run launches, each bracketed by CUDA events on
+ * `stream`; result fields as for pm_probe_run (bytes = algorithmic operand
+ * and result bytes of one launch).  Synchronises; reports PM_ETIMEOUT if a
+ * device wait expired during the runs. */
+pm_status pm_gemm_bench(const pm_cfg* cfg, const void* A_op_dev, const void* B_op_dev, float* C_dev,
+                        const float* scales_dev, int warmup, int reps, void* stream, pm_probe_result* out);
+
 /* Grouped BF16 GEMM in one persistent launch: G problems C_g[M_g,N] =
  * A_g[M_g,K] B_g[K,N].  A_op_dev stacks the A_g as bf16 [sum M_g, K]; B_op_dev
  * stacks the B_g transposed, bf16 [G*N, K]; C_dev stacks C_g, FP32

@@ -58,6 +58,7 @@ assert ctypes.sizeof(pm_cfg) == 24 and ctypes.sizeof(pm_probe_args) == 56 and ct
 
 # Every exported symbol of include/perfmodel.h
 EXPORTS = ("pm_probe_launch", "pm_probe_run", "pm_gemm_operand_bytes", "pm_gemm_prepare", "pm_gemm_run",
+           "pm_gemm_bench",
            "pm_grouped_gemm_run", "pm_model_predict", "pm_model_grad_workspace", "pm_model_grad", "pm_model_grad_noalloc",
            "pm_autotune_pick", "pm_grouped_autotune", "pm_last_error", "pm_device_status",
            "pm_watchdog_selftest", "pm_version")
@@ -88,6 +89,8 @@ def _load():
         "pm_gemm_operand_bytes": [i32, i32, i32, i32, ctypes.POINTER(sz), ctypes.POINTER(sz)],
         "pm_gemm_prepare": [i32, P, P, i32, i32, i32, P, P, P, P],
         "pm_gemm_run": [ctypes.POINTER(pm_cfg), P, P, P, P, P],
+        "pm_gemm_bench": [ctypes.POINTER(pm_cfg), P, P, P, P, ctypes.c_int, ctypes.c_int, P,
+                          ctypes.POINTER(pm_probe_result)],
         "pm_grouped_gemm_run": [i32, P, i32, i32, P, P, i32, i32, i32, P, P, P, P],
         "pm_model_predict": [P, i64, ctypes.POINTER(pm_params), i32, P, P],
         "pm_model_grad_workspace": [i64, ctypes.POINTER(sz)],
@@ -199,6 +202,13 @@ def pm_gemm_run(c: pm_cfg, A_op, B_op, C, scales=None, stream=None):
            "pm_gemm_run")
 
 
+def pm_gemm_bench(c: pm_cfg, A_op, B_op, C, scales=None, warmup=10, reps=100, stream=None) -> dict:
+    res = pm_probe_result()
+    _check(_lib.pm_gemm_bench(ctypes.byref(c), _ptr(A_op), _ptr(B_op), _ptr(C), _ptr(scales), int(warmup), int(reps),
+                              _stream(stream), ctypes.byref(res)), "pm_gemm_bench")
+    return dict(median_s=res.median_s, p25_s=res.p25_s, p75_s=res.p75_s, min_s=res.min_s, bytes=res.bytes)
+
+
 def pm_grouped_gemm_run(M_list, N, K, BM_list, BN_list, BK, stages, cta_group, A_op, B_op, C, stream=None):
     G = len(M_list)
     Mh = (ctypes.c_int32 * G)(*[int(m) for m in M_list])
@@ -224,6 +234,9 @@ class GemmOperands:
 
     def run(self, c: pm_cfg, C, stream=None):
         pm_gemm_run(c, self.A_op, self.B_op, C, self.scales, stream)
+
+    def bench(self, c: pm_cfg, C, warmup=10, reps=100, stream=None) -> dict:
+        return pm_gemm_bench(c, self.A_op, self.B_op, C, self.scales, warmup, reps, stream)
 
 
 # ---------------------------------------------------------------------- model

@@ -1,0 +1,341 @@
+"""Calibration of the stage-centric model against device-timed measurements
+(arxiv 2605.04178, Sec. III-D: parameters from microbenchmarks, fitted to
+measured kernel times with a train/holdout split; Sec. V-B protocol: warm-ups,
+timed runs, median).
+
+Pieces
+  * measure_sweep(): the calibration table -- config 1 (FP32 GEMM 512^3 over
+    the FP32 tile space), config 2 (copy/triad 2^20..2^30, TMA 2D tiles on a
+    1 GiB matrix, pointer chase 16 KB..1 GB) and config 3 (every valid BF16 and
+    FP8 tile configuration at M = N = K in {1024..16384}), each timed on the
+    device by the library's own harness (pm_gemm_bench / pm_probe_run).
+  * StageModelLoss: torch.autograd.Function whose forward is the batched model
+    on the GPU and whose backward is the hand-written adjoint kernel
+    (pm_model_grad): mean squared log error and its gradient in theta.
+  * fit(): L-BFGS over phi = ln(theta) with a weak pull to the prior.
+  * report(): MAE per configuration family (train, holdout, all) and the
+    model-picked tile against the exhaustively measured best.
+The fitted parameters are written as a hardware parameter file (JSON), the
+form the paper keeps per platform.
+"""
+from __future__ import annotations
+
+import json
+import math
+import os
+import time
+
+import numpy as np
+import torch
+
+import paper_2605_04178_gb300 as pm
+import synthetic as S
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+THETA_PATH = os.path.join(HERE, "theta_gb300.json")
+SWEEP_PATH = os.path.join(HERE, "data", "sweep_gb300.json")
+FIELDS = ("M", "N", "K", "BM", "BN", "BK", "stages", "cta_group", "dtype", "kind")
+
+
+def prior_theta(n_sm: int, f_hz: float = 1.9e9) -> np.ndarray:
+    """Parameter priors from the paper's printed values (Table "parameters",
+    Sec. II-A sustained figures, Table "arch-params"); cycles at f_hz."""
+    th = np.zeros(16)
+    th[0] = 5e-6
+    th[1] = 6.8e12
+    th[2] = 8.0e12
+    th[3] = 64.0 * 2 ** 20
+    th[4] = 420.0 / f_hz
+    th[5] = th[1] / n_sm
+    th[7] = 8192.0 * f_hz
+    th[6] = th[7] / 2.0
+    th[8] = 2.0 * th[7]
+    th[9] = 12.0 / f_hz
+    th[10] = 16e12
+    th[11] = 8e12
+    th[12] = 45.0 / f_hz
+    th[13] = 100e-9
+    th[14] = 1.0
+    th[15] = 0.3
+    return th
+
+
+def family_of(r: dict) -> str:
+    if r["kind"] == pm.PM_KIND_COPY or r["kind"] == pm.PM_KIND_TRIAD:
+        return "2a_stream"
+    if r["kind"] == pm.PM_KIND_TMA2D:
+        return "2b_tma"
+    return {0: "1_fp32", 1: "3_bf16", 2: "3_fp8"}[int(r["dtype"])]
+
+
+# ------------------------------------------------------------------ measuring
+def _valid(dt, t):
+    bm, bn, bk, s, g = t
+    try:
+        pm.pm_gemm_run(pm.cfg(256, 256, 256, bm, bn, bk, s, g, dt), None, None, None)
+    except pm.PMError as e:
+        return e.status != pm.PM_EUNSUPPORTED
+    return True
+
+
+def measure_sweep(shapes=(1024, 2048, 4096, 8192, 16384), dtypes=(1, 2), log=print) -> dict:
+    """Device-timed calibration table (list of records) plus pointer-chase latencies."""
+    rows = []
+    t0 = time.time()
+    # config 1: FP32 (three-pass TF32) 512^3 over the FP32 tile space
+    A, B = S.gemm_operands(512, 512, 512, seed=0)
+    ops = pm.GemmOperands(pm.PM_FP32, 512, 512, 512)
+    ops.prepare(torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda())
+    C = torch.empty(512, 512, dtype=torch.float32, device="cuda")
+    for t in S.tile_space(0):
+        if not _valid(0, t):
+            continue
+        r = ops.bench(pm.cfg(512, 512, 512, *t, dtype=0), C, warmup=10, reps=100)
+        rows.append(dict(zip(FIELDS, (512, 512, 512, *t, 0, 0)), t=r["median_s"], p25=r["p25_s"], p75=r["p75_s"]))
+    log("config 1 done (%d rows, %.0f s)" % (len(rows), time.time() - t0))
+    # config 2: copy / triad over 2^20 .. 2^30 FP32 elements
+    nmax = 2 ** 30
+    a = torch.from_numpy(S.uniform_pm1(1, nmax)).cuda()
+    b = torch.empty_like(a)
+    c = torch.from_numpy(S.uniform_pm1(1, nmax, offset=nmax)).cuda()
+    for k in range(20, 31):
+        n = 2 ** k
+        for kind, pk in ((pm.PM_KIND_COPY, pm.PM_PROBE_COPY), (pm.PM_KIND_TRIAD, pm.PM_PROBE_TRIAD)):
+            args = pm.probe_args(pk, n=n, scalar=3.0)
+            r = pm.pm_probe_run(args, a, b, c, warmup=10, reps=100) if pk == pm.PM_PROBE_TRIAD else \
+                pm.pm_probe_run(args, a, b, warmup=10, reps=100)
+            rows.append(dict(M=n, N=0, K=0, BM=0, BN=0, BK=0, stages=0, cta_group=0, dtype=0, kind=kind,
+                             t=r["median_s"], p25=r["p25_s"], p75=r["p75_s"]))
+    del b, c
+    # TMA 2D tiles over a 1 GiB FP32 matrix (16384 x 16384)
+    src = a[: 16384 * 16384].view(16384, 16384)
+    dst = torch.empty_like(src)
+    for tr, tc in ((64, 64), (128, 64), (128, 128), (256, 64), (256, 128)):
+        r = pm.pm_probe_run(pm.probe_args(pm.PM_PROBE_TMA2D, rows=16384, cols=16384, tile_r=tr, tile_c=tc),
+                            src, dst, warmup=3, reps=20)
+        rows.append(dict(M=16384, N=16384, K=0, BM=tr, BN=tc, BK=0, stages=0, cta_group=0, dtype=0,
+                         kind=pm.PM_KIND_TMA2D, t=r["median_s"], p25=r["p25_s"], p75=r["p75_s"]))
+    del a, src, dst
+    torch.cuda.empty_cache()
+    log("config 2 probes done (%.0f s)" % (time.time() - t0))
+    # pointer chase: 16 KB .. 1 GB working sets, 64-byte node stride
+    pchase = []
+    for k in range(17):
+        W = 16 * 1024 * 2 ** k
+        nodes = W // 64
+        buf = torch.from_numpy(S.pchase_buffer(nodes, seed=1).view(np.int32)).cuda()
+        out = torch.zeros(1, dtype=torch.int32, device="cuda")
+        hops = 2 ** 18
+        r = pm.pm_probe_run(pm.probe_args(pm.PM_PROBE_PCHASE, n=nodes, hops=hops, start=0), buf, out,
+                            warmup=1, reps=3)
+        pchase.append(dict(W=W, hops=hops, ns_per_hop=1e9 * r["median_s"] / hops, final_index=r["final_index"]))
+        del buf
+    log("pointer chase done (%.0f s)" % (time.time() - t0))
+    # config 3: every valid BF16 / FP8 configuration at M = N = K = s
+    for s in shapes:
+        A, B = S.gemm_operands(s, s, s, seed=2, dist="normal")
+        Ad, Bd = torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()
+        del A, B
+        C = torch.empty(s, s, dtype=torch.float32, device="cuda")
+        reps = 100 if s <= 4096 else (40 if s <= 8192 else 20)
+        for dt in dtypes:
+            ops = pm.GemmOperands(dt, s, s, s)
+            ops.prepare(Ad, Bd)
+            for t in S.tile_space(dt):
+                if not _valid(dt, t):
+                    continue
+                r = ops.bench(pm.cfg(s, s, s, *t, dtype=dt), C, warmup=10, reps=reps)
+                rows.append(dict(zip(FIELDS, (s, s, s, *t, dt, 0)), t=r["median_s"], p25=r["p25_s"],
+                                 p75=r["p75_s"]))
+            del ops
+        del Ad, Bd, C
+        torch.cuda.empty_cache()
+        log("config 3 shape %d done (%d rows, %.0f s)" % (s, len(rows), time.time() - t0))
+    props = torch.cuda.get_device_properties(0)
+    return dict(device=props.name, n_sm=props.multi_processor_count, rows=rows, pchase=pchase,
+                protocol="10 warm-ups; 100 timed runs (20-40 at 8192-16384, 20 for TMA), median of CUDA-event times")
+
+
+# ------------------------------------------------------------ autograd + fit
+class StageModelLoss(torch.autograd.Function):
+    """L(theta) = mean_i (ln T_hat_i(theta) - ln T_i)^2 on the GPU; the backward
+    pass returns the gradient from the hand-written adjoint kernel."""
+
+    @staticmethod
+    def forward(ctx, theta, cfg_dev, n, t_meas_dev, n_sm, workspace):
+        out = torch.empty(17, dtype=torch.float64, device=cfg_dev.device)
+        pm.pm_model_grad(cfg_dev, n, theta.detach().cpu().numpy(), n_sm, t_meas_dev, workspace, out)
+        o = out.cpu()
+        ctx.save_for_backward(o[1:].clone().to(theta.dtype))
+        return o[0].to(theta.dtype)
+
+    @staticmethod
+    def backward(ctx, g):
+        (grad,) = ctx.saved_tensors
+        return g * grad, None, None, None, None, None
+
+
+class GpuObjective:
+    """Binds a calibration table to the GPU loss: call with theta (float64 tensor)."""
+
+    def __init__(self, rows, n_sm):
+        self.n = len(rows)
+        cols = {f: np.array([r[f] for r in rows], dtype=np.int64) for f in FIELDS}
+        self.cfg = pm.cfg_tensor(cols)
+        self.t = torch.tensor([r["t"] for r in rows], dtype=torch.float32, device="cuda")
+        self.ws = torch.empty(pm.pm_model_grad_workspace(self.n) // 8 + 1, dtype=torch.float64, device="cuda")
+        self.n_sm = n_sm
+
+    def __call__(self, theta):
+        return StageModelLoss.apply(theta, self.cfg, self.n, self.t, self.n_sm, self.ws)
+
+    def predict(self, theta) -> np.ndarray:
+        out = torch.empty(self.n, dtype=torch.float32, device="cuda")
+        pm.pm_model_predict(self.cfg, self.n, np.asarray(theta, dtype=np.float64), self.n_sm, out)
+        return out.cpu().numpy().astype(np.float64)
+
+
+def fit(objective, theta0, prior=None, reg=1e-4, iters=400, log=None):
+    """Minimise objective(theta) + reg * ||ln theta - ln prior||^2 over phi = ln theta (L-BFGS)."""
+    theta0 = np.asarray(theta0, dtype=np.float64)
+    prior = theta0 if prior is None else np.asarray(prior, dtype=np.float64)
+    phi = torch.tensor(np.log(theta0), dtype=torch.float64, requires_grad=True)
+    phi_p = torch.tensor(np.log(prior), dtype=torch.float64)
+    opt = torch.optim.LBFGS([phi], lr=1.0, max_iter=iters, tolerance_grad=1e-12, tolerance_change=1e-15,
+                            history_size=50, line_search_fn="strong_wolfe")
+    trace = []
+
+    def closure():
+        opt.zero_grad()
+        loss = objective(torch.exp(phi)) + reg * torch.sum((phi - phi_p) ** 2)
+        loss.backward()
+        trace.append(float(loss.item()))
+        return loss
+
+    opt.step(closure)
+    if log:
+        log("fit: %d evaluations, loss %.4g -> %.4g" % (len(trace), trace[0], trace[-1]))
+    return np.exp(phi.detach().numpy()), trace
+
+
+def split(n: int, holdout: float = 0.2, seed: int = 6):
+    """Seeded train/holdout split (Sec. III-D recommends a holdout)."""
+    order = np.argsort(S.splitmix64(seed, n), kind="stable")
+    k = int(round(n * holdout))
+    hold = np.zeros(n, dtype=bool)
+    hold[order[:k]] = True
+    return ~hold, hold
+
+
+def mae_by_family(rows, t_pred, mask=None) -> dict:
+    out = {}
+    fam = np.array([family_of(r) for r in rows])
+    t = np.array([r["t"] for r in rows])
+    ape = np.abs(t_pred - t) / t * 100.0
+    if mask is None:
+        mask = np.ones(len(rows), dtype=bool)
+    for f in sorted(set(fam)):
+        m = (fam == f) & mask
+        if m.any():
+            out[f] = dict(n=int(m.sum()), mae_pct=float(ape[m].mean()), median_ape_pct=float(np.median(ape[m])),
+                          max_ape_pct=float(ape[m].max()))
+    out["all"] = dict(n=int(mask.sum()), mae_pct=float(ape[mask].mean()))
+    return out
+
+
+def roofline_mae(rows, peaks) -> dict:
+    """Naive roofline with datasheet peaks (Sec. V-A context): max(FLOPs/P, bytes/B)."""
+    fam = np.array([family_of(r) for r in rows])
+    t = np.array([r["t"] for r in rows])
+    pred = np.zeros(len(rows))
+    for i, r in enumerate(rows):
+        if r["kind"] in (pm.PM_KIND_COPY, pm.PM_KIND_TRIAD):
+            pred[i] = (8.0 if r["kind"] == pm.PM_KIND_COPY else 12.0) * r["M"] / peaks["hbm"]
+        elif r["kind"] == pm.PM_KIND_TMA2D:
+            pred[i] = 8.0 * r["M"] * r["N"] / peaks["hbm"]
+        else:
+            e = {0: 4.0, 1: 2.0, 2: 1.0}[r["dtype"]]
+            P = {0: peaks["tf32"], 1: peaks["bf16"], 2: peaks["fp8"]}[r["dtype"]]
+            flops = 2.0 * r["M"] * r["N"] * r["K"]
+            bytes_ = e * (r["M"] * r["K"] + r["N"] * r["K"]) + 4.0 * r["M"] * r["N"]
+            pred[i] = max(flops / P, bytes_ / peaks["hbm"])
+    ape = np.abs(pred - t) / t * 100
+    return {f: float(ape[fam == f].mean()) for f in sorted(set(fam))} | {"all": float(ape.mean())}
+
+
+def autotune_vs_best(rows, theta, n_sm) -> list:
+    """For each measured GEMM shape: the model's pick (GPU autotuner) against the
+    fastest measured configuration."""
+    out = []
+    gem = [r for r in rows if r["kind"] == pm.PM_KIND_GEMM]
+    keys = sorted(set((r["M"], r["N"], r["K"], r["dtype"]) for r in gem))
+    for (M, N, K, dt) in keys:
+        cand = {(r["BM"], r["BN"], r["BK"], r["stages"], r["cta_group"]): r["t"] for r in gem
+                if (r["M"], r["N"], r["K"], r["dtype"]) == (M, N, K, dt)}
+        MNK = torch.tensor([M, N, K], dtype=torch.int32, device="cuda")
+        picks = torch.empty(24, dtype=torch.uint8, device="cuda")
+        tp = torch.empty(1, dtype=torch.float32, device="cuda")
+        pm.pm_autotune_pick(MNK, 1, dt, theta, n_sm, picks, tp)
+        p = picks.cpu().numpy().view(pm.CFG_DTYPE)[0]
+        pick = (int(p["BM"]), int(p["BN"]), int(p["BK"]), int(p["stages"]), int(p["cta_group"]))
+        best = min(cand, key=cand.get)
+        flops = 2.0 * M * N * K
+        out.append(dict(M=M, N=N, K=K, dtype=dt, pick=pick, t_pick=cand.get(pick), best=best, t_best=cand[best],
+                        t_pred=float(tp.item()), pick_over_best=cand.get(pick, math.inf) / cand[best],
+                        tflops_pick=flops / cand.get(pick, math.inf) / 1e12, tflops_best=flops / cand[best] / 1e12))
+    return out
+
+
+def save_theta(theta, meta, path=THETA_PATH):
+    with open(path, "w") as f:
+        json.dump(dict(theta=[float(v) for v in theta], **meta), f, indent=1)
+
+
+def load_theta(path=THETA_PATH):
+    with open(path) as f:
+        return np.array(json.load(f)["theta"], dtype=np.float64)
+
+
+def main():
+    import argparse
+    ap = argparse.ArgumentParser(description="measure the calibration table and fit the stage model")
+    ap.add_argument("--measure", action="store_true")
+    ap.add_argument("--sweep", default=SWEEP_PATH)
+    ap.add_argument("--out", default=THETA_PATH)
+    ap.add_argument("--report", default=None)
+    ap.add_argument("--shapes", default="1024,2048,4096,8192,16384")
+    args = ap.parse_args()
+    n_sm = pm.sm_count()
+    if args.measure:
+        table = measure_sweep(tuple(int(s) for s in args.shapes.split(",")))
+        os.makedirs(os.path.dirname(args.sweep), exist_ok=True)
+        with open(args.sweep, "w") as f:
+            json.dump(table, f)
+    with open(args.sweep) as f:
+        table = json.load(f)
+    rows = table["rows"]
+    train, hold = split(len(rows))
+    th0 = prior_theta(n_sm)
+    obj = GpuObjective([r for r, m in zip(rows, train) if m], n_sm)
+    theta, trace = fit(obj, th0, log=print)
+    allobj = GpuObjective(rows, n_sm)
+    pred0, pred = allobj.predict(th0), allobj.predict(theta)
+    rep = dict(n_rows=len(rows), n_train=int(train.sum()), n_holdout=int(hold.sum()),
+               loss_trace=[trace[0], trace[-1]], theta=theta.tolist(),
+               mae_prior=mae_by_family(rows, pred0), mae_train=mae_by_family(rows, pred, train),
+               mae_holdout=mae_by_family(rows, pred, hold), mae_all=mae_by_family(rows, pred),
+               roofline_mae=roofline_mae(rows, dict(hbm=8.0e12, bf16=2.25e15, fp8=4.5e15, tf32=1.1e15)),
+               autotune=autotune_vs_best(rows, theta, n_sm), pchase=table.get("pchase"))
+    save_theta(theta, dict(device=table.get("device"), n_sm=n_sm, fitted_on=os.path.basename(args.sweep),
+                           mae_holdout=rep["mae_holdout"]), args.out)
+    if args.report:
+        with open(args.report, "w") as f:
+            json.dump(rep, f, indent=1)
+    print(json.dumps({k: rep[k] for k in ("mae_prior", "mae_holdout", "mae_all", "roofline_mae")}, indent=1))
+    for a in rep["autotune"]:
+        print("autotune %(M)d dt=%(dtype)d pick=%(pick)s best=%(best)s pick/best=%(pick_over_best).3f "
+              "TFLOP/s pick %(tflops_pick).0f best %(tflops_best).0f" % a)
+
+
+if __name__ == "__main__":
+    main()

@@ -22,6 +22,7 @@
 
 #include <algorithm>
 #include <mutex>
+#include <vector>
 
 #include "pm_internal.cuh"
 
@@ -31,41 +32,88 @@ constexpr int kGemmThreads = 192;
 constexpr int kMaxStages = 6;
 constexpr int kRasterGroup = 8;
 
+constexpr int kMaxGroups = 128;
+
+// Problems of one launch.  A single GEMM is one group.  Tiles are listed
+// group by group (tile_off is the prefix sum); inside a group they are
+// visited in bands of kRasterGroup (pair-)rows for L2 reuse.
+struct GroupTable {
+  int n_groups;
+  int tile_off[kMaxGroups + 1];
+  int row0[kMaxGroups];        // first row of A_g / C_g in the stacked A / C
+  int rows[kMaxGroups];        // M_g
+  int brow0[kMaxGroups];       // first row of B_g (K-major) in the stacked B
+  int tiles_m[kMaxGroups];     // row tiles (pair rows for cta_group 2)
+  int tiles_n[kMaxGroups];
+  uint8_t bm_idx[kMaxGroups];  // BM = 64 << bm_idx
+  uint8_t bn_idx[kMaxGroups];  // BN = 64 << bn_idx
+};
+
+// TMA descriptors, one per box height in use: A boxes BM rows, B boxes BN/cta_group rows.
+struct TensorMaps {
+  CUtensorMap a[3];
+  CUtensorMap b[3];
+};
+
 struct GemmParams {
-  int M, N, K;
-  int BM, BN, BK, stages;
-  int tiles_m, tiles_n, n_tiles;   // tiles_m counts pair rows (2*BM) for cta_group 2
-  int Kt;
+  int N, BK, stages, Kt;
   int sw;                          // swizzle span in bytes (64 or 128)
   int n_atoms;                     // swizzle atoms along K per stage
-  int n_mblk;                      // 128-row MMA blocks per CTA tile
-  int acc_cols, nbuf, alloc_cols;
-  uint32_t stage_bytes, a_part_bytes, b_part_bytes, tx_bytes;
-  uint32_t idesc;
+  int acc_cols, nbuf, alloc_cols;  // TMEM columns per accumulator buffer (largest tile)
+  uint32_t stage_bytes;            // ring stride (largest tile)
+  uint32_t ab_fmt;                 // tcgen05 operand format code
   int lo_row_a, lo_row_b;          // row offset of the lo half (three-pass TF32)
-  // TMEM layout of the accumulator: 0 = one row per lane (128-row blocks),
-  // 1 = 64 rows in lanes 0-15 of each 32-lane quarter (M = 64, one SM),
-  // 2 = 64 rows in lanes 0-63 for columns [0, N/2) and again in lanes
-  //     64-127 for columns [N/2, N) (M = 128 split over a CTA pair).
-  int layout;
   float* C;
   const float* scales;             // FP8: {s_A, s_B}
   Watchdog wd;
 };
 
-__device__ __forceinline__ void tile_coords(int t, const GemmParams& p, int& tm, int& tn) {
-  const int per_group = kRasterGroup * p.tiles_n;
-  const int gid = t / per_group;
-  const int first = gid * kRasterGroup;
-  const int gsz = min(p.tiles_m - first, kRasterGroup);
-  const int r = t % per_group;
-  tm = first + r % gsz;
-  tn = r / gsz;
+// Everything the three roles need about one tile.
+struct Tile {
+  int arow, brow;                  // first operand rows this CTA loads
+  int crow0, crow_end, ccol0;      // output rows [crow0, crow_end) capped by the group, first column
+  int BM, BN, n_mblk, layout, ma, mb;
+  uint32_t a_part, b_part, tx, idesc;
+};
+
+template <int CG, int L>
+__device__ __forceinline__ void decode_tile(int t, const GemmParams& p, const GroupTable& g, uint32_t rank,
+                                            Tile& T) {
+  int q = 0;
+  while (q + 1 < g.n_groups && t >= g.tile_off[q + 1]) ++q;
+  const int lt = t - g.tile_off[q];
+  const int tiles_n = g.tiles_n[q], tiles_m = g.tiles_m[q];
+  const int per_band = kRasterGroup * tiles_n;
+  const int band = lt / per_band;
+  const int first = band * kRasterGroup;
+  const int bsz = min(tiles_m - first, kRasterGroup);
+  const int r = lt % per_band;
+  const int tm = first + r % bsz, tn = r / bsz;
+  T.ma = g.bm_idx[q];
+  T.mb = g.bn_idx[q];
+  T.BM = 64 << T.ma;
+  T.BN = 64 << T.mb;
+  T.arow = g.row0[q] + tm * CG * T.BM + (int)rank * T.BM;
+  T.brow = g.brow0[q] + tn * T.BN + (int)rank * (T.BN / CG);
+  T.crow0 = T.arow;
+  T.crow_end = g.row0[q] + g.rows[q];
+  T.ccol0 = tn * T.BN;
+  T.n_mblk = (T.BM + 127) >> 7;
+  // TMEM layout of the accumulator: 0 = one row per lane (128-row blocks);
+  // 1 = 64 rows in lanes 0-15 of each 32-lane quarter (M = 64, one SM);
+  // 2 = 64 rows in lanes 0-63 for columns [0, N/2) and again in lanes 64-127
+  //     for columns [N/2, N) (M = 128 split over a CTA pair).
+  T.layout = T.BM >= 128 ? 0 : (CG == 1 ? 1 : 2);
+  T.a_part = (uint32_t)T.BM * p.sw;
+  T.b_part = (uint32_t)(T.BN / CG) * p.sw;
+  T.tx = (uint32_t)(L * p.n_atoms) * (T.a_part + T.b_part);
+  const int mma_m = CG == 1 ? min(T.BM, 128) : 2 * min(T.BM, 128);
+  T.idesc = instr_desc(p.ab_fmt, (uint32_t)mma_m, (uint32_t)T.BN);
 }
 
 template <int CG, int KIND>
 __global__ void __launch_bounds__(kGemmThreads, 1)
-    gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+    gemm_kernel(const __grid_constant__ TensorMaps maps, const __grid_constant__ GroupTable g,
                 const GemmParams p) {
   extern __shared__ __align__(1024) uint8_t dsmem[];
   __shared__ __align__(8) uint64_t full_bar[kMaxStages];
@@ -82,6 +130,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
   const uint32_t rank = (CG == 2) ? cluster_ctarank() : 0u;
   const int cta = (CG == 2) ? (int)(blockIdx.x >> 1) : (int)blockIdx.x;
   const int n_ctas = (CG == 2) ? (int)(gridDim.x >> 1) : (int)gridDim.x;
+  const int n_tiles = g.tile_off[g.n_groups];
   const uint32_t base = (smem_u32(dsmem) + 1023u) & ~1023u;
   const uint32_t swcode = p.sw == 128 ? 2u : 4u;
   volatile int* abort_p = &abort_flag;
@@ -100,8 +149,10 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
     fence_mbar_init();
   }
   if (warp == 0 && lane == 0) {
-    prefetch_tmap(&tmA);
-    prefetch_tmap(&tmB);
+    for (int i = 0; i < 3; ++i) {
+      prefetch_tmap(&maps.a[i]);
+      prefetch_tmap(&maps.b[i]);
+    }
   }
   if (warp == 1) {
     tmem_alloc<CG>(smem_u32(&tmem_slot), (uint32_t)p.alloc_cols);
@@ -118,11 +169,11 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
       int stage = 0;
       uint32_t phase = 0;
       bool ok = true;
-      for (int t = cta; t < p.n_tiles && ok; t += n_ctas) {
-        int tm, tn;
-        tile_coords(t, p, tm, tn);
-        const int arow = (CG == 1) ? tm * p.BM : tm * 2 * p.BM + (int)rank * p.BM;
-        const int brow = tn * p.BN + (CG == 2 ? (int)rank * (p.BN / 2) : 0);
+      for (int t = cta; t < n_tiles && ok; t += n_ctas) {
+        Tile T;
+        decode_tile<CG, L>(t, p, g, rank, T);
+        const CUtensorMap* ma = &maps.a[T.ma];
+        const CUtensorMap* mb = &maps.b[T.mb];
         for (int kt = 0; kt < p.Kt; ++kt) {
           if (!mbar_wait(smem_u32(&empty_bar[stage]), phase ^ 1u, p.wd, abort_p, SITE_GEMM_PRODUCER)) {
             ok = false;
@@ -131,25 +182,25 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
           const uint32_t fb = smem_u32(&full_bar[stage]);
           uint32_t fbc = fb;
           if constexpr (CG == 1) {
-            mbar_arrive_expect_tx(fb, p.tx_bytes);
+            mbar_arrive_expect_tx(fb, T.tx);
           } else {
             fbc = mapa_shared(fb, 0);
-            mbar_arrive_expect_tx_cluster(fbc, p.tx_bytes);
+            mbar_arrive_expect_tx_cluster(fbc, T.tx);
           }
           const uint32_t sbase = base + (uint32_t)stage * p.stage_bytes;
-          const uint32_t bbase = sbase + (uint32_t)(L * p.n_atoms) * p.a_part_bytes;
+          const uint32_t bbase = sbase + (uint32_t)(L * p.n_atoms) * T.a_part;
 #pragma unroll
           for (int h = 0; h < L; ++h) {
             for (int a = 0; a < p.n_atoms; ++a) {
               const int x = kt * p.BK + a * (p.sw / E);
-              const uint32_t da = sbase + (uint32_t)(h * p.n_atoms + a) * p.a_part_bytes;
-              const uint32_t db = bbase + (uint32_t)(h * p.n_atoms + a) * p.b_part_bytes;
+              const uint32_t da = sbase + (uint32_t)(h * p.n_atoms + a) * T.a_part;
+              const uint32_t db = bbase + (uint32_t)(h * p.n_atoms + a) * T.b_part;
               if constexpr (CG == 1) {
-                tma_load_2d(da, &tmA, fb, x, arow + h * p.lo_row_a);
-                tma_load_2d(db, &tmB, fb, x, brow + h * p.lo_row_b);
+                tma_load_2d(da, ma, fb, x, T.arow + h * p.lo_row_a);
+                tma_load_2d(db, mb, fb, x, T.brow + h * p.lo_row_b);
               } else {
-                tma_load_2d_pair(da, &tmA, fbc, x, arow + h * p.lo_row_a);
-                tma_load_2d_pair(db, &tmB, fbc, x, brow + h * p.lo_row_b);
+                tma_load_2d_pair(da, ma, fbc, x, T.arow + h * p.lo_row_a);
+                tma_load_2d_pair(db, mb, fbc, x, T.brow + h * p.lo_row_b);
               }
             }
           }
@@ -165,7 +216,9 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
       bool ok = true;
       const uint32_t sbo = 8u * (uint32_t)p.sw;
       int it = 0;
-      for (int t = cta; t < p.n_tiles && ok; t += n_ctas, ++it) {
+      for (int t = cta; t < n_tiles && ok; t += n_ctas, ++it) {
+        Tile T;
+        decode_tile<CG, L>(t, p, g, 0, T);
         const int buf = it % p.nbuf;
         const uint32_t use = (uint32_t)(it / p.nbuf);
         if (!mbar_wait(smem_u32(&acce_bar[buf]), (use & 1u) ^ 1u, p.wd, abort_p, SITE_GEMM_MMA)) {
@@ -181,21 +234,21 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
           }
           tc_fence_after();
           const uint32_t sbase = base + (uint32_t)stage * p.stage_bytes;
-          const uint32_t bbase = sbase + (uint32_t)(L * p.n_atoms) * p.a_part_bytes;
+          const uint32_t bbase = sbase + (uint32_t)(L * p.n_atoms) * T.a_part;
           constexpr int PASSES = (KIND == 1) ? 3 : 1;
 #pragma unroll
           for (int pass = 0; pass < PASSES; ++pass) {
             const int ha = (pass == 2) ? 1 : 0;   // hi.hi, hi.lo, lo.hi
             const int hb = (pass == 1) ? 1 : 0;
             for (int a = 0; a < p.n_atoms; ++a) {
-              const uint32_t pa = sbase + (uint32_t)(ha * p.n_atoms + a) * p.a_part_bytes;
-              const uint32_t pb = bbase + (uint32_t)(hb * p.n_atoms + a) * p.b_part_bytes;
+              const uint32_t pa = sbase + (uint32_t)(ha * p.n_atoms + a) * T.a_part;
+              const uint32_t pb = bbase + (uint32_t)(hb * p.n_atoms + a) * T.b_part;
               for (int kk = 0; kk < p.sw / 32; ++kk) {
                 const uint64_t bdesc = smem_desc(pb + 32u * kk, sbo, swcode);
                 const uint32_t acc = (kt | pass | a | kk) != 0 ? 1u : 0u;
-                for (int m = 0; m < p.n_mblk; ++m) {
+                for (int m = 0; m < T.n_mblk; ++m) {
                   const uint64_t adesc = smem_desc(pa + (uint32_t)(m * 128 * p.sw) + 32u * kk, sbo, swcode);
-                  umma<CG, KIND>(d0 + (uint32_t)(m * p.BN), adesc, bdesc, p.idesc, acc);
+                  umma<CG, KIND>(d0 + (uint32_t)(m * T.BN), adesc, bdesc, T.idesc, acc);
                 }
               }
             }
@@ -219,34 +272,33 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
     float scale = 1.f;
     if constexpr (KIND == 2) scale = 1.f / (__ldg(p.scales) * __ldg(p.scales + 1));
     const bool vec = (p.N & 3) == 0;
-    // rows and columns this warp's TMEM lane quarter holds
-    int lrow, qcol0, qcols;
-    bool lvalid;
-    if (p.layout == 1) {
-      lrow = 16 * q + lane; lvalid = lane < 16; qcol0 = 0; qcols = p.BN;
-    } else if (p.layout == 2) {
-      lrow = 32 * (q & 1) + lane; lvalid = true; qcol0 = (q >> 1) * (p.BN / 2); qcols = p.BN / 2;
-    } else {
-      lrow = 32 * q + lane; lvalid = true; qcol0 = 0; qcols = p.BN;
-    }
     int it = 0;
-    for (int t = cta; t < p.n_tiles; t += n_ctas, ++it) {
+    for (int t = cta; t < n_tiles; t += n_ctas, ++it) {
       const int buf = it % p.nbuf;
       const uint32_t use = (uint32_t)(it / p.nbuf);
       if (!mbar_wait(smem_u32(&accf_bar[buf]), use & 1u, p.wd, abort_p, SITE_GEMM_EPILOGUE)) break;
       tc_fence_after();
-      int tm, tn;
-      tile_coords(t, p, tm, tn);
-      const int crow0 = (CG == 1) ? tm * p.BM : tm * 2 * p.BM + (int)rank * p.BM;
-      const int ccol0 = tn * p.BN + qcol0;
-      for (int m = 0; m < p.n_mblk; ++m) {
-        const int row = crow0 + m * 128 + lrow;
-        const bool rvalid = lvalid && row < p.M;
+      Tile T;
+      decode_tile<CG, L>(t, p, g, rank, T);
+      // rows and columns this warp's TMEM lane quarter holds
+      int lrow, qcol0, qcols;
+      bool lvalid;
+      if (T.layout == 1) {
+        lrow = 16 * q + lane; lvalid = lane < 16; qcol0 = 0; qcols = T.BN;
+      } else if (T.layout == 2) {
+        lrow = 32 * (q & 1) + lane; lvalid = true; qcol0 = (q >> 1) * (T.BN / 2); qcols = T.BN / 2;
+      } else {
+        lrow = 32 * q + lane; lvalid = true; qcol0 = 0; qcols = T.BN;
+      }
+      const int ccol0 = T.ccol0 + qcol0;
+      for (int m = 0; m < T.n_mblk; ++m) {
+        const int row = T.crow0 + m * 128 + lrow;
+        const bool rvalid = lvalid && row < T.crow_end;
         float* crow = p.C + (size_t)row * p.N;
         for (int j = 0; j < qcols / 32; ++j) {
           uint32_t r[32];
           const uint32_t taddr =
-              tmem_base + ((uint32_t)(32 * q) << 16) + (uint32_t)(buf * p.acc_cols + m * p.BN + 32 * j);
+              tmem_base + ((uint32_t)(32 * q) << 16) + (uint32_t)(buf * p.acc_cols + m * T.BN + 32 * j);
           tmem_ld_32x32b_x32(taddr, r);
           tmem_ld_wait();
           const int col0 = ccol0 + 32 * j;
@@ -430,7 +482,7 @@ pm_status cached_tmap(CUtensorMap* out, const void* ptr, int dtcode, uint64_t ro
 }
 
 template <int CG, int KIND>
-static pm_status launch_gemm(const CUtensorMap& ta, const CUtensorMap& tb, const GemmParams& p, int grid,
+static pm_status launch_gemm(const TensorMaps& maps, const GroupTable& g, const GemmParams& p, int grid,
                              size_t smem, cudaStream_t s) {
   auto kern = gemm_kernel<CG, KIND>;
   static std::once_flag once;
@@ -453,83 +505,151 @@ static pm_status launch_gemm(const CUtensorMap& ta, const CUtensorMap& tb, const
     cfg.attrs = attr;
     cfg.numAttrs = 1;
   }
-  cudaError_t e = cudaLaunchKernelEx(&cfg, kern, ta, tb, p);
+  cudaError_t e = cudaLaunchKernelEx(&cfg, kern, maps, g, p);
   if (e != cudaSuccess) return cuda_fail(e, "cudaLaunchKernelEx(gemm_kernel)");
   return PM_OK;
 }
 
-pm_status gemm_plan(const pm_cfg& c, GemmParams& p, size_t& smem) {
-  const int dt = c.dtype, g = c.cta_group;
-  PM_REQUIRE(c.kind == PM_KIND_GEMM, PM_EINVAL, "cfg.kind must be PM_KIND_GEMM");
-  PM_REQUIRE(c.M > 0 && c.N > 0 && c.K > 0, PM_EINVAL, "M, N, K must be positive");
-  PM_REQUIRE(gemm_tile_valid(c.BM, c.BN, c.BK, c.stages, g, dt), PM_EUNSUPPORTED,
-             "tile configuration BM=%d BN=%d BK=%d stages=%d cta_group=%d dtype=%d is outside the valid space",
-             c.BM, c.BN, c.BK, c.stages, g, dt);
-  const int e = dt_elem(dt), L = dt_halves(dt);
-  PM_REQUIRE(((int64_t)c.K * e) % 16 == 0, PM_EINVAL, "K*%d bytes must be a multiple of 16", e);
-  p.M = c.M; p.N = c.N; p.K = c.K;
-  p.BM = c.BM; p.BN = c.BN; p.BK = c.BK; p.stages = c.stages;
-  p.tiles_m = (c.M + g * c.BM - 1) / (g * c.BM);
-  p.tiles_n = (c.N + c.BN - 1) / c.BN;
-  p.n_tiles = p.tiles_m * p.tiles_n;
-  p.Kt = (c.K + c.BK - 1) / c.BK;
-  p.sw = std::min(128, c.BK * e);
-  p.n_atoms = c.BK * e / p.sw;
-  p.n_mblk = (c.BM + 127) / 128;
-  p.layout = c.BM >= 128 ? 0 : (g == 1 ? 1 : 2);
-  p.acc_cols = p.layout == 2 ? c.BN / 2 : p.n_mblk * c.BN;
-  p.nbuf = (2 * p.acc_cols <= 512) ? 2 : 1;
-  int need = p.nbuf * p.acc_cols, cols = 32;
-  while (cols < need) cols <<= 1;
-  p.alloc_cols = cols;
-  p.a_part_bytes = (uint32_t)c.BM * p.sw;
-  p.b_part_bytes = (uint32_t)(c.BN / g) * p.sw;
-  p.stage_bytes = (uint32_t)(L * p.n_atoms) * (p.a_part_bytes + p.b_part_bytes);
-  p.tx_bytes = p.stage_bytes;
-  const int bm = c.BM;
-  const int mma_m = (g == 1) ? std::min(bm, 128) : 2 * std::min(bm, 128);
-  const uint32_t fmt = dt == PM_BF16 ? 1u : (dt == PM_FP32 ? 2u : 0u);
-  p.idesc = instr_desc(fmt, (uint32_t)mma_m, (uint32_t)c.BN);
-  p.lo_row_a = (L == 2) ? c.M : 0;
-  p.lo_row_b = (L == 2) ? c.N : 0;
-  smem = (size_t)c.stages * p.stage_bytes + 1024;
-  return PM_OK;
-}
+static int size_index(int v) { return v == 64 ? 0 : (v == 128 ? 1 : 2); }
 
-pm_status gemm_launch(const pm_cfg& c, const void* A_op, const void* B_op, float* C, const float* scales,
-                      cudaStream_t s) {
+// Plans one launch over G problems sharing N, K, BK, stages and cta_group:
+// group q is C_q[M_q, N] = A_q B_q with tile BM_q x BN_q.  A_op stacks the A_q
+// (rows row0_q ..), B_op stacks the K-major B_q (b_rows_per_group rows each;
+// 0 means all groups share one B of N rows).
+struct LaunchPlan {
+  TensorMaps maps;
+  GroupTable g;
   GemmParams p;
   size_t smem = 0;
-  pm_status st = gemm_plan(c, p, smem);
-  if (st != PM_OK) return st;
-  PM_REQUIRE(A_op && B_op && C, PM_EINVAL, "null operand or output pointer");
-  PM_REQUIRE(c.dtype != PM_FP8E4M3 || scales, PM_EINVAL, "FP8 GEMM needs scales_dev");
-  const int dt = c.dtype, g = c.cta_group;
+  int grid = 0;
+};
+
+static pm_status plan_launch(int dt, int cg, int BK, int stages, int G, const int32_t* M, int N, int K,
+                             const int16_t* BMv, const int16_t* BNv, bool stacked_b, const void* A_op,
+                             const void* B_op, float* C, const float* scales, LaunchPlan& P) {
+  PM_REQUIRE(G >= 1 && G <= kMaxGroups, PM_EINVAL, "number of groups %d outside [1, %d]", G, kMaxGroups);
+  PM_REQUIRE(N > 0 && K > 0, PM_EINVAL, "N and K must be positive");
   const int e = dt_elem(dt), L = dt_halves(dt);
+  PM_REQUIRE(dt >= 0 && dt <= 2, PM_EUNSUPPORTED, "dtype %d is not a pm_dtype", dt);
+  int64_t sum_m = 0;
+  for (int q = 0; q < G; ++q) {
+    PM_REQUIRE(M[q] > 0, PM_EINVAL, "M of group %d must be positive", q);
+    PM_REQUIRE(gemm_tile_valid(BMv[q], BNv[q], BK, stages, cg, dt), PM_EUNSUPPORTED,
+               "tile configuration BM=%d BN=%d BK=%d stages=%d cta_group=%d dtype=%d is outside the valid space",
+               BMv[q], BNv[q], BK, stages, cg, dt);
+    sum_m += M[q];
+  }
+  PM_REQUIRE(((int64_t)K * e) % 16 == 0, PM_EINVAL, "K*%d bytes must be a multiple of 16", e);
+  const int64_t b_rows = stacked_b ? (int64_t)G * N : N;
+  PM_REQUIRE(sum_m * L < (1ll << 31) && b_rows * L < (1ll << 31), PM_EINVAL, "too many rows for one launch");
+  PM_REQUIRE(A_op && B_op && C, PM_EINVAL, "null operand or output pointer");
+  PM_REQUIRE(dt != PM_FP8E4M3 || scales, PM_EINVAL, "FP8 GEMM needs scales_dev");
+  GemmParams& p = P.p;
+  GroupTable& g = P.g;
+  p.N = N;
+  p.BK = BK;
+  p.stages = stages;
+  p.Kt = (K + BK - 1) / BK;
+  p.sw = std::min(128, BK * e);
+  p.n_atoms = BK * e / p.sw;
+  p.ab_fmt = dt == PM_BF16 ? 1u : (dt == PM_FP32 ? 2u : 0u);
+  p.lo_row_a = L == 2 ? (int)sum_m : 0;
+  p.lo_row_b = L == 2 ? (int)b_rows : 0;
+  g.n_groups = G;
+  g.tile_off[0] = 0;
+  int acc = 0;
+  uint32_t stage = 0;
+  bool used_m[3] = {false, false, false}, used_n[3] = {false, false, false};
+  int64_t row0 = 0;
+  for (int q = 0; q < G; ++q) {
+    const int bm = BMv[q], bn = BNv[q];
+    g.row0[q] = (int)row0;
+    g.rows[q] = M[q];
+    g.brow0[q] = stacked_b ? q * N : 0;
+    g.tiles_m[q] = (M[q] + cg * bm - 1) / (cg * bm);
+    g.tiles_n[q] = (N + bn - 1) / bn;
+    const int64_t off = (int64_t)g.tile_off[q] + (int64_t)g.tiles_m[q] * g.tiles_n[q];
+    PM_REQUIRE(off < (1ll << 31), PM_EINVAL, "too many tiles");
+    g.tile_off[q + 1] = (int)off;
+    g.bm_idx[q] = (uint8_t)size_index(bm);
+    g.bn_idx[q] = (uint8_t)size_index(bn);
+    used_m[g.bm_idx[q]] = used_n[g.bn_idx[q]] = true;
+    const int n_mblk = (bm + 127) / 128;
+    acc = std::max(acc, (bm < 128 && cg == 2) ? bn / 2 : n_mblk * bn);
+    stage = std::max(stage, (uint32_t)(L * p.n_atoms) * (uint32_t)(bm + bn / cg) * (uint32_t)p.sw);
+    row0 += M[q];
+  }
+  p.acc_cols = acc;
+  p.nbuf = (2 * acc <= 512) ? 2 : 1;
+  int cols = 32;
+  while (cols < p.nbuf * acc) cols <<= 1;
+  p.alloc_cols = cols;
+  p.stage_bytes = stage;
+  P.smem = (size_t)stages * stage + 1024;
   const int dtcode = dt == PM_BF16 ? TMAP_BF16 : (dt == PM_FP32 ? TMAP_F32 : TMAP_U8);
-  CUtensorMap ta, tb;
-  st = cached_tmap(&ta, A_op, dtcode, (uint64_t)L * c.M, (uint64_t)c.K, (uint32_t)c.BM, (uint32_t)(p.sw / e), p.sw);
-  if (st != PM_OK) return st;
-  st = cached_tmap(&tb, B_op, dtcode, (uint64_t)L * c.N, (uint64_t)c.K, (uint32_t)(c.BN / g), (uint32_t)(p.sw / e),
-                   p.sw);
-  if (st != PM_OK) return st;
+  int first_m = -1, first_n = -1;
+  for (int i = 0; i < 3; ++i) {
+    if (used_m[i]) {
+      pm_status st = cached_tmap(&P.maps.a[i], A_op, dtcode, (uint64_t)L * sum_m, (uint64_t)K,
+                                 (uint32_t)(64 << i), (uint32_t)(p.sw / e), p.sw);
+      if (st != PM_OK) return st;
+      if (first_m < 0) first_m = i;
+    }
+    if (used_n[i]) {
+      pm_status st = cached_tmap(&P.maps.b[i], B_op, dtcode, (uint64_t)L * b_rows, (uint64_t)K,
+                                 (uint32_t)((64 << i) / cg), (uint32_t)(p.sw / e), p.sw);
+      if (st != PM_OK) return st;
+      if (first_n < 0) first_n = i;
+    }
+  }
+  for (int i = 0; i < 3; ++i) {          // unused slots hold a valid copy (never dereferenced by a tile)
+    if (!used_m[i]) P.maps.a[i] = P.maps.a[first_m];
+    if (!used_n[i]) P.maps.b[i] = P.maps.b[first_n];
+  }
   unsigned int* w = watchdog_word();
   PM_REQUIRE(w != nullptr, PM_ECUDA, "watchdog word unavailable");
   p.wd = Watchdog{w, watchdog_limit_ns()};
   p.C = C;
   p.scales = scales;
   const int sms = sm_count();
-  int grid;
-  if (g == 1) grid = std::min(p.n_tiles, sms);
-  else grid = 2 * std::min(p.n_tiles, sms / 2);
-  if (g == 1) {
-    if (dt == PM_BF16) return launch_gemm<1, 0>(ta, tb, p, grid, smem, s);
-    if (dt == PM_FP32) return launch_gemm<1, 1>(ta, tb, p, grid, smem, s);
-    return launch_gemm<1, 2>(ta, tb, p, grid, smem, s);
+  const int n_tiles = g.tile_off[G];
+  P.grid = cg == 1 ? std::min(n_tiles, sms) : 2 * std::min(n_tiles, sms / 2);
+  return PM_OK;
+}
+
+static pm_status run_plan(const LaunchPlan& P, int dt, int cg, cudaStream_t s) {
+  if (cg == 1) {
+    if (dt == PM_BF16) return launch_gemm<1, 0>(P.maps, P.g, P.p, P.grid, P.smem, s);
+    if (dt == PM_FP32) return launch_gemm<1, 1>(P.maps, P.g, P.p, P.grid, P.smem, s);
+    return launch_gemm<1, 2>(P.maps, P.g, P.p, P.grid, P.smem, s);
   }
-  if (dt == PM_BF16) return launch_gemm<2, 0>(ta, tb, p, grid, smem, s);
-  if (dt == PM_FP32) return launch_gemm<2, 1>(ta, tb, p, grid, smem, s);
-  return launch_gemm<2, 2>(ta, tb, p, grid, smem, s);
+  if (dt == PM_BF16) return launch_gemm<2, 0>(P.maps, P.g, P.p, P.grid, P.smem, s);
+  if (dt == PM_FP32) return launch_gemm<2, 1>(P.maps, P.g, P.p, P.grid, P.smem, s);
+  return launch_gemm<2, 2>(P.maps, P.g, P.p, P.grid, P.smem, s);
+}
+
+pm_status gemm_launch(const pm_cfg& c, const void* A_op, const void* B_op, float* C, const float* scales,
+                      cudaStream_t s) {
+  PM_REQUIRE(c.kind == PM_KIND_GEMM, PM_EINVAL, "cfg.kind must be PM_KIND_GEMM");
+  PM_REQUIRE(c.M > 0 && c.N > 0 && c.K > 0, PM_EINVAL, "M, N, K must be positive");
+  PM_REQUIRE(gemm_tile_valid(c.BM, c.BN, c.BK, c.stages, c.cta_group, c.dtype), PM_EUNSUPPORTED,
+             "tile configuration BM=%d BN=%d BK=%d stages=%d cta_group=%d dtype=%d is outside the valid space",
+             c.BM, c.BN, c.BK, c.stages, c.cta_group, c.dtype);
+  static thread_local LaunchPlan P;
+  const int32_t M = c.M;
+  const int16_t BM = c.BM, BN = c.BN;
+  pm_status st = plan_launch(c.dtype, c.cta_group, c.BK, c.stages, 1, &M, c.N, c.K, &BM, &BN, false, A_op, B_op, C,
+                             scales, P);
+  if (st != PM_OK) return st;
+  return run_plan(P, c.dtype, c.cta_group, s);
+}
+
+pm_status grouped_launch(int G, const int32_t* M, int N, int K, const int16_t* BM, const int16_t* BN, int BK,
+                         int stages, int cg, const void* A_op, const void* B_op, float* C, cudaStream_t s) {
+  static thread_local LaunchPlan P;
+  pm_status st = plan_launch(PM_BF16, cg, BK, stages, G, M, N, K, BM, BN, true, A_op, B_op, C, nullptr, P);
+  if (st != PM_OK) return st;
+  return run_plan(P, PM_BF16, cg, s);
 }
 
 }  // namespace pm
@@ -586,8 +706,61 @@ extern "C" pm_status pm_grouped_gemm_run(int32_t G, const int32_t* M_host, int32
                                          const int16_t* BM_host, const int16_t* BN_host, int32_t BK,
                                          int32_t stages, int32_t cta_group, const void* A_op_dev,
                                          const void* B_op_dev, float* C_dev, void* stream) {
-  (void)G; (void)M_host; (void)N; (void)K; (void)BM_host; (void)BN_host; (void)BK; (void)stages;
-  (void)cta_group; (void)A_op_dev; (void)B_op_dev; (void)C_dev; (void)stream;
-  pm::set_error("grouped GEMM is not built yet");
-  return PM_EUNSUPPORTED;
+  PM_REQUIRE(M_host && BM_host && BN_host, PM_EINVAL, "null host array");
+  return pm::grouped_launch(G, M_host, N, K, BM_host, BN_host, BK, stages, cta_group, A_op_dev, B_op_dev, C_dev,
+                            static_cast<cudaStream_t>(stream));
+}
+
+extern "C" pm_status pm_gemm_bench(const pm_cfg* cfg, const void* A_op_dev, const void* B_op_dev, float* C_dev,
+                                   const float* scales_dev, int warmup, int reps, void* stream,
+                                   pm_probe_result* out) {
+  PM_REQUIRE(cfg != nullptr && out != nullptr, PM_EINVAL, "cfg or out is NULL");
+  PM_REQUIRE(warmup >= 0 && reps >= 1 && reps <= 100000, PM_EINVAL, "warmup >= 0 and 1 <= reps <= 1e5 required");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  for (int i = 0; i < warmup; ++i) {
+    pm_status st = pm::gemm_launch(*cfg, A_op_dev, B_op_dev, C_dev, scales_dev, s);
+    if (st != PM_OK) return st;
+  }
+  std::vector<cudaEvent_t> ev(2 * (size_t)reps);
+  for (auto& e : ev) PM_CUDA(cudaEventCreate(&e));
+  pm_status st = PM_OK;
+  for (int i = 0; i < reps && st == PM_OK; ++i) {
+    cudaEventRecord(ev[2 * i], s);
+    st = pm::gemm_launch(*cfg, A_op_dev, B_op_dev, C_dev, scales_dev, s);
+    cudaEventRecord(ev[2 * i + 1], s);
+  }
+  cudaError_t e = cudaStreamSynchronize(s);
+  std::vector<double> t;
+  if (st == PM_OK && e == cudaSuccess)
+    for (int i = 0; i < reps; ++i) {
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, ev[2 * i], ev[2 * i + 1]);
+      t.push_back(ms * 1e-3);
+    }
+  for (auto& x : ev) cudaEventDestroy(x);
+  if (st != PM_OK) return st;
+  if (e != cudaSuccess) return pm::cuda_fail(e, "cudaStreamSynchronize");
+  std::sort(t.begin(), t.end());
+  auto q = [&](double f) {
+    const double pos = f * (t.size() - 1);
+    const size_t lo = (size_t)pos;
+    const size_t hi = std::min(lo + 1, t.size() - 1);
+    return t[lo] + (pos - lo) * (t[hi] - t[lo]);
+  };
+  out->median_s = q(0.5);
+  out->p25_s = q(0.25);
+  out->p75_s = q(0.75);
+  out->min_s = t.front();
+  const double e_b = cfg->dtype == PM_FP32 ? 8.0 : (cfg->dtype == PM_BF16 ? 2.0 : 1.0);
+  out->bytes = e_b * ((double)cfg->M * cfg->K + (double)cfg->N * cfg->K) + 4.0 * (double)cfg->M * cfg->N;
+  out->final_index = 0;
+  unsigned int* w = pm::watchdog_word();
+  unsigned int h[2] = {0, 0};
+  PM_CUDA(cudaMemcpy(h, w, sizeof(h), cudaMemcpyDeviceToHost));
+  if (h[0] != 0) {
+    PM_CUDA(cudaMemset(w, 0, 4 * sizeof(unsigned int)));
+    pm::set_error("device watchdog expired at site %u", h[1]);
+    return PM_ETIMEOUT;
+  }
+  return PM_OK;
 }
