@@ -111,6 +111,35 @@ __device__ __forceinline__ void decode_tile(int t, const GemmParams& p, const Gr
   T.idesc = instr_desc(p.ab_fmt, (uint32_t)mma_m, (uint32_t)T.BN);
 }
 
+// All MMAs of one pipeline stage, fully unrolled.  Descriptors are built once
+// per stage; each MMA advances them by constant offsets (the start address
+// sits in the low 14 bits in 16-byte units).  NATOMS swizzle atoms along K,
+// NK = swizzle span / 32 B k-steps per atom, NMBLK 128-row blocks; three-pass
+// TF32 adds the hi.lo and lo.hi products.
+template <int CG, int KIND, int NATOMS, int NK, int NMBLK>
+__device__ __forceinline__ void issue_stage(uint32_t d0, uint64_t a0, uint64_t b0, uint32_t a_part16,
+                                            uint32_t b_part16, uint32_t mblk16, uint32_t idesc, uint32_t bn,
+                                            bool first) {
+  constexpr int PASSES = (KIND == 1) ? 3 : 1;
+#pragma unroll
+  for (int pass = 0; pass < PASSES; ++pass) {
+    const uint32_t ha = (pass == 2) ? 1u : 0u, hb = (pass == 1) ? 1u : 0u;
+#pragma unroll
+    for (int a = 0; a < NATOMS; ++a) {
+#pragma unroll
+      for (int kk = 0; kk < NK; ++kk) {
+        const uint64_t bd = b0 + (uint64_t)((hb * NATOMS + a) * b_part16 + 2u * kk);
+        const uint32_t acc = (first && pass == 0 && a == 0 && kk == 0) ? 0u : 1u;
+#pragma unroll
+        for (int m = 0; m < NMBLK; ++m) {
+          const uint64_t ad = a0 + (uint64_t)((ha * NATOMS + a) * a_part16 + m * mblk16 + 2u * kk);
+          umma<CG, KIND>(d0 + (uint32_t)m * bn, ad, bd, idesc, acc);
+        }
+      }
+    }
+  }
+}
+
 template <int CG, int KIND>
 __global__ void __launch_bounds__(kGemmThreads, 1)
     gemm_kernel(const __grid_constant__ TensorMaps maps, const __grid_constant__ GroupTable g,
@@ -137,7 +166,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < p.stages; ++s) {
-      mbar_init(smem_u32(&full_bar[s]), CG);
+      mbar_init(smem_u32(&full_bar[s]), 1);
       mbar_init(smem_u32(&empty_bar[s]), 1);
     }
     for (int b = 0; b < 2; ++b) {
@@ -184,8 +213,12 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
           if constexpr (CG == 1) {
             mbar_arrive_expect_tx(fb, T.tx);
           } else {
+            // The leader arms its own full barrier for both CTAs' bytes; the
+            // peer only points its TMA completions at that barrier (a
+            // completion that lands before the arming leaves the phase pending
+            // until the leader's arrival).
             fbc = mapa_shared(fb, 0);
-            mbar_arrive_expect_tx_cluster(fbc, T.tx);
+            if (rank == 0) mbar_arrive_expect_tx(fb, 2u * T.tx);
           }
           const uint32_t sbase = base + (uint32_t)stage * p.stage_bytes;
           const uint32_t bbase = sbase + (uint32_t)(L * p.n_atoms) * T.a_part;
@@ -234,24 +267,22 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
           }
           tc_fence_after();
           const uint32_t sbase = base + (uint32_t)stage * p.stage_bytes;
-          const uint32_t bbase = sbase + (uint32_t)(L * p.n_atoms) * T.a_part;
-          constexpr int PASSES = (KIND == 1) ? 3 : 1;
-#pragma unroll
-          for (int pass = 0; pass < PASSES; ++pass) {
-            const int ha = (pass == 2) ? 1 : 0;   // hi.hi, hi.lo, lo.hi
-            const int hb = (pass == 1) ? 1 : 0;
-            for (int a = 0; a < p.n_atoms; ++a) {
-              const uint32_t pa = sbase + (uint32_t)(ha * p.n_atoms + a) * T.a_part;
-              const uint32_t pb = bbase + (uint32_t)(hb * p.n_atoms + a) * T.b_part;
-              for (int kk = 0; kk < p.sw / 32; ++kk) {
-                const uint64_t bdesc = smem_desc(pb + 32u * kk, sbo, swcode);
-                const uint32_t acc = (kt | pass | a | kk) != 0 ? 1u : 0u;
-                for (int m = 0; m < T.n_mblk; ++m) {
-                  const uint64_t adesc = smem_desc(pa + (uint32_t)(m * 128 * p.sw) + 32u * kk, sbo, swcode);
-                  umma<CG, KIND>(d0 + (uint32_t)(m * T.BN), adesc, bdesc, T.idesc, acc);
-                }
-              }
+          const uint64_t a0 = smem_desc(sbase, sbo, swcode);
+          const uint64_t b0 = smem_desc(sbase + (uint32_t)(L * p.n_atoms) * T.a_part, sbo, swcode);
+          const uint32_t a16 = T.a_part >> 4, b16 = T.b_part >> 4, m16 = (uint32_t)(128 * p.sw) >> 4;
+          const bool first = kt == 0;
+          const uint32_t bn = (uint32_t)T.BN;
+          if (p.sw == 128) {
+            if (p.n_atoms == 1) {
+              if (T.n_mblk == 1) issue_stage<CG, KIND, 1, 4, 1>(d0, a0, b0, a16, b16, m16, T.idesc, bn, first);
+              else issue_stage<CG, KIND, 1, 4, 2>(d0, a0, b0, a16, b16, m16, T.idesc, bn, first);
+            } else {
+              if (T.n_mblk == 1) issue_stage<CG, KIND, 2, 4, 1>(d0, a0, b0, a16, b16, m16, T.idesc, bn, first);
+              else issue_stage<CG, KIND, 2, 4, 2>(d0, a0, b0, a16, b16, m16, T.idesc, bn, first);
             }
+          } else {
+            if (T.n_mblk == 1) issue_stage<CG, KIND, 1, 2, 1>(d0, a0, b0, a16, b16, m16, T.idesc, bn, first);
+            else issue_stage<CG, KIND, 1, 2, 2>(d0, a0, b0, a16, b16, m16, T.idesc, bn, first);
           }
           if constexpr (CG == 1) umma_commit(smem_u32(&empty_bar[stage]));
           else umma_commit_pair(smem_u32(&empty_bar[stage]), (uint16_t)3);

@@ -218,12 +218,13 @@ __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::
 template <int CG, int KIND>
 __device__ __forceinline__ void umma(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
                                      uint32_t accumulate) {
+// No "memory" clobber: the MMA reads shared memory through the async proxy,
+// ordered after the barrier wait by the volatile asm sequence itself.
 #define PM_UMMA(CGS, KS)                                                                        \
   asm volatile(                                                                                 \
       "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"                                        \
       "tcgen05.mma.cta_group::" CGS ".kind::" KS " [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem), \
-      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)                                       \
-      : "memory")
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate))
   if constexpr (CG == 1) {
     if constexpr (KIND == 0) PM_UMMA("1", "f16");
     else if constexpr (KIND == 1) PM_UMMA("1", "tf32");
