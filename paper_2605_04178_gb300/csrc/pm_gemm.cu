@@ -53,6 +53,7 @@ struct GroupTable {
 struct TensorMaps {
   CUtensorMap a[3];
   CUtensorMap b[3];
+  CUtensorMap c;                   // FP32 C, 32 x 32 boxes, 128-byte swizzle (TMA-store epilogue)
 };
 
 struct GemmParams {
@@ -65,6 +66,8 @@ struct GemmParams {
   int lo_row_a, lo_row_b;          // row offset of the lo half (three-pass TF32)
   float* C;
   const float* scales;             // FP8: {s_A, s_B}
+  int tma_store;                   // epilogue stages 32x32 chunks in shared memory and stores them by TMA
+  uint32_t staging_off;            // byte offset of the epilogue staging area after the ring
   Watchdog wd;
 };
 
@@ -303,6 +306,8 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
     float scale = 1.f;
     if constexpr (KIND == 2) scale = 1.f / (__ldg(p.scales) * __ldg(p.scales + 1));
     const bool vec = (p.N & 3) == 0;
+    const uint32_t stage_base = base + p.staging_off;     // two 4 KB staging buffers per epilogue warp
+    uint32_t sb = 0;
     int it = 0;
     for (int t = cta; t < n_tiles; t += n_ctas, ++it) {
       const int buf = it % p.nbuf;
@@ -333,7 +338,32 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
           tmem_ld_32x32b_x32(taddr, r);
           tmem_ld_wait();
           const int col0 = ccol0 + 32 * j;
-          if (rvalid) {
+          // TMA store of the warp's 32 x 32 chunk when its rows are 32
+          // consecutive rows inside the problem (layouts 0 and 2)
+          const int chunk_row0 = T.crow0 + m * 128 + (lrow - lane);
+          if (col0 >= p.N) {
+            // the chunk lies past the last column: nothing to write
+          } else if (p.tma_store && T.layout != 1 && chunk_row0 + 32 <= T.crow_end) {
+            const uint32_t sbuf = stage_base + (uint32_t)((q * 2 + (sb & 1)) * 4096);
+            if (lane == 0) bulk_wait_read<1>();          // the buffer's previous store has read it
+            __syncwarp();
+            const uint32_t rowp = sbuf + (uint32_t)lane * 128u;
+#pragma unroll
+            for (int v = 0; v < 8; ++v) {
+              const uint32_t addr = rowp + (uint32_t)((v ^ (lane & 7)) * 16);
+              asm volatile("st.shared.v4.f32 [%0], {%1, %2, %3, %4};" ::"r"(addr),
+                           "f"(__uint_as_float(r[4 * v + 0]) * scale), "f"(__uint_as_float(r[4 * v + 1]) * scale),
+                           "f"(__uint_as_float(r[4 * v + 2]) * scale), "f"(__uint_as_float(r[4 * v + 3]) * scale)
+                           : "memory");
+            }
+            fence_proxy_async_smem();
+            __syncwarp();
+            if (lane == 0) {
+              tma_store_2d(&maps.c, sbuf, col0, chunk_row0);
+              bulk_commit();
+            }
+            ++sb;
+          } else if (rvalid) {
             if (vec && col0 + 32 <= p.N) {
 #pragma unroll
               for (int v = 0; v < 8; ++v) {
@@ -359,6 +389,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
         else mbar_arrive_cluster(mapa_shared(eb, 0));
       }
     }
+    if (lane == 0) bulk_wait_all();                       // staged stores complete before exit
   }
 
   // ---------------------------------------------------------------- teardown
@@ -617,6 +648,16 @@ static pm_status plan_launch(int dt, int cg, int BK, int stages, int G, const in
   p.alloc_cols = cols;
   p.stage_bytes = stage;
   P.smem = (size_t)stages * stage + 1024;
+  // TMA-store epilogue: eight 4 KB staging buffers after the ring, when they fit
+  p.staging_off = (uint32_t)stages * stage;
+  p.tma_store = 0;
+  const bool c_ok = (N % 4) == 0 && ((uintptr_t)C & 15) == 0;
+  if (c_ok && P.smem + 32768 <= (size_t)(232448 - 1024)) {
+    pm_status st = cached_tmap(&P.maps.c, C, TMAP_F32, (uint64_t)sum_m, (uint64_t)N, 32u, 32u, 128);
+    if (st != PM_OK) return st;
+    p.tma_store = 1;
+    P.smem += 32768;
+  }
   const int dtcode = dt == PM_BF16 ? TMAP_BF16 : (dt == PM_FP32 ? TMAP_F32 : TMAP_U8);
   int first_m = -1, first_n = -1;
   for (int i = 0; i < 3; ++i) {
