@@ -274,6 +274,35 @@ def run_gpu(args):
     e2e_s = max_over_ranks(time.perf_counter() - t0)
     e2e_value = world * flops * e2e_steps / e2e_s / 1e12
 
+    # exhaustive search at this shape (every valid BF16 tile, same protocol for
+    # all, including the model's pick) and the model's error on those times
+    exhaustive = None
+    if not args.skip_exhaustive:
+        import synthetic as S_
+        meas = {}
+        for t in S_.tile_space(pm.PM_BF16):
+            try:
+                r = ops.bench(pm.cfg(M, N, K, *t, dtype=pm.PM_BF16), C, warmup=3, reps=15)
+            except pm.PMError as e:
+                if e.status == pm.PM_EUNSUPPORTED:
+                    continue
+                raise
+            meas[t] = r["median_s"]
+        tiles = sorted(meas)
+        cols = {f: np.array(v) for f, v in zip(("BM", "BN", "BK", "stages", "cta_group"), zip(*tiles))}
+        cols.update(M=np.full(len(tiles), M), N=np.full(len(tiles), N), K=np.full(len(tiles), K),
+                    dtype=np.full(len(tiles), pm.PM_BF16), kind=np.zeros(len(tiles)))
+        pred = torch.empty(len(tiles), dtype=torch.float32, device="cuda")
+        pm.pm_model_predict(pm.cfg_tensor(cols), len(tiles), theta, n_sm, pred)
+        pred = pred.cpu().numpy().astype(np.float64)
+        tm = np.array([meas[t] for t in tiles])
+        best = min(meas, key=meas.get)
+        exhaustive = {"configs": len(meas), "best_tile": dict(zip(("BM", "BN", "BK", "stages", "cta_group"), best)),
+                      "best_tflops": flops / meas[best] / 1e12, "pick_tflops": flops / meas[pick] / 1e12,
+                      "pick_over_best_time": meas[pick] / meas[best],
+                      "model_mae_pct": float(np.mean(np.abs(pred - tm) / tm) * 100.0),
+                      "protocol": "3 warm-ups, median of 15 CUDA-event timed launches per tile"}
+
     extra = {}
     if not args.skip_extra:
         extra = secondary(pm, S, theta, n_sm, peaks)
@@ -298,6 +327,14 @@ def run_gpu(args):
             "gpu_launches": args.steps,
             "clocks": clocks.summary(t_wall0, t_wall1),
         }
+        if exhaustive is not None:
+            line["exhaustive"] = exhaustive
+            line["vs_exhaustive_best"] = 1.0 / exhaustive["pick_over_best_time"]
+        calib_rep = os.path.join(ROOT, "paper_2605_04178_gb300", "data", "calib_report_gb300.json")
+        if theta_src == "calibrated" and os.path.exists(calib_rep):
+            with open(calib_rep) as f:
+                rep = json.load(f)
+            line["model_mae_pct_holdout"] = {k: round(v["mae_pct"], 2) for k, v in rep["mae_holdout"].items()}
         line.update(extra)
         if not args.skip_cpu:
             # the oracle on the host cores: rows 0..47 of the same product, which
@@ -433,6 +470,7 @@ def main():
     ap.add_argument("--skip-extra", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--no-check", action="store_true")
+    ap.add_argument("--skip-exhaustive", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

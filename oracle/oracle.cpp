@@ -242,6 +242,8 @@ static double mma_passes(int dt) { return dt == DT_FP32 ? 3.0 : 1.0; }
 // Operand copies loaded per element: FP32 loads the hi and lo halves.
 static double load_mult(int dt) { return dt == DT_FP32 ? 2.0 : 1.0; }
 static int rate_index(int dt) { return dt == DT_FP32 ? 6 : (dt == DT_BF16 ? 7 : 8); }
+// K depth of one tcgen05.mma instruction: 32 bytes of each operand row.
+static int instr_k(int dt) { return dt == DT_FP32 ? 8 : (dt == DT_BF16 ? 16 : 32); }
 
 // Tile-space validity (shared-memory ring and TMEM capacity, Sec. III-A.1:
 // accumulators beyond 256 KB of TMEM per SM would spill).
@@ -278,8 +280,12 @@ static void stage_terms(const Cfg& c, i64 Kt, const T* th, T& Tstep, T& Tstore) 
   const double e = elem_bytes(c.dtype), np = mma_passes(c.dtype), l = load_mult(c.dtype);
   const T& R = th[rate_index(c.dtype)];
   // Eq. 2: per K-step TMEM cost, D_accum = FP32 accumulator bytes of the tile.
+  // Reading: the tcgen05.mma latency L_mma is paid once per MMA instruction the
+  // K-step issues -- BK / k_instr K-slices per 128-row block, per TF32 pass --
+  // while the accumulator traffic D is counted once per K-step.
   const double D = 4.0 * c.BM * c.BN;
-  const T T_tmem = D / th[10] + th[9] + D / th[11];
+  const double n_instr = np * (double)(c.BK / instr_k(c.dtype)) * (double)ceil_div(c.BM, 128);
+  const T T_tmem = D / th[10] + n_instr * th[9] + D / th[11];
   // T_TMEM_mgmt amortised over the K-steps (Sec. III-A.5).
   const T T_mgmt = th[13] / lift<T>((double)Kt);
   // Eqs. 3 and 6: S_mode = 1 for one SM, S_2SM for a CTA pair.

@@ -58,14 +58,14 @@ __host__ __device__ inline bool tile_valid(int BM, int BN, int BK, int s, int g,
 struct GemmFwd {
   float T, T_stage, T_rl, A_rl, B_rl;
   float T_c, T_io, T_tma, oma, X, R, S, T_step, T_store;
-  float D, bstep, store_bytes;
+  float D, bstep, store_bytes, n_instr;
   float waves, Kt;
   int ri;
   bool oma_free;
 };
 
 // Stage-centric GEMM time:
-//   T_TMEM = D/BW_rd + L_mma + D/BW_wr                          (Eq. 2)
+//   T_TMEM = D/BW_rd + n_instr L_mma + D/BW_wr                  (Eq. 2)
 //   T_c    = n_p 2 BM BN BK / (R S) + T_TMEM + T_mgmt/K_tiles     (Eqs. 3, 6)
 //   T_tma  = L_TMA + b_step / B_TMA, b_step = l e BK (BM + BN/g) (Eq. 4, P = 1)
 //   T_io   = (1 - alpha) T_tma + T_sync, T_sync = 2 L_mbar       (Eq. 7)
@@ -84,7 +84,10 @@ __device__ __forceinline__ void gemm_forward(const pm_cfg& c, const Theta& th, i
   f.Kt = (float)Kt;
   f.waves = (float)waves;
   f.D = 4.f * c.BM * c.BN;
-  const float T_tmem = f.D / th.v[10] + th.v[9] + f.D / th.v[11];
+  // L_mma once per tcgen05.mma issued in the K-step: BK/k_instr per 128-row block, per pass
+  const int kin = dt == PM_FP32 ? 8 : (dt == PM_BF16 ? 16 : 32);
+  f.n_instr = np * (float)(c.BK / kin) * (float)((c.BM + 127) / 128);
+  const float T_tmem = f.D / th.v[10] + f.n_instr * th.v[9] + f.D / th.v[11];
   const float T_mgmt = th.v[13] / f.Kt;
   f.S = g == 1 ? 1.f : th.v[14];
   f.X = (np * 2.f * c.BM * c.BN * c.BK) / (f.R * f.S);
@@ -146,7 +149,7 @@ __device__ __forceinline__ void gemm_adjoint(const pm_cfg& c, const Theta& th, c
   gR -= g_c * f.X / f.R;
   gS -= g_c * f.X / f.S;
   d[10] -= g_c * (f.D / th.v[10]) / th.v[10];
-  d[9] += g_c;
+  d[9] += g_c * f.n_instr;
   d[11] -= g_c * (f.D / th.v[11]) / th.v[11];
   d[13] += g_c / f.Kt;
   d[f.ri] += gR;
