@@ -179,6 +179,24 @@ pm_status pm_model_grad(const pm_cfg* cfgs_dev, int64_t n, const pm_params* thet
                         const float* t_meas_dev, void* workspace_dev, size_t workspace_bytes, double* out_dev,
                         void* stream);
 
+/* The k predicted-fastest valid configurations per shape (k <= 16), sorted
+ * by predicted time: picks_dev n*k pm_cfg, t_pred_dev n*k floats.  Entries
+ * past the number of valid configurations have BM = 0 and t = +inf.  Async. */
+pm_status pm_autotune_topk(const int32_t* MNK_dev, int64_t n, int32_t dtype, const pm_params* theta_host,
+                           int32_t n_sm, int32_t k, pm_cfg* picks_dev, float* t_pred_dev, void* stream);
+
+/* Model-pruned measured autotuning of one GEMM shape: the model's top-k
+ * configurations (pm_autotune_topk) are each timed with pm_gemm_bench on the
+ * caller's operands and the fastest is returned in *pick_out (its timing in
+ * *pick_time_out, nullable).  `shape` gives M, N, K and dtype.  The paper's
+ * autotuning guidance (Sec. VI) ranks tiles by the model; timing a short list
+ * absorbs the model's residual error at ~k/180 of an exhaustive search's cost.
+ * Allocates a few hundred bytes of device scratch (stream-ordered).
+ * Synchronises. */
+pm_status pm_gemm_autotune(const pm_cfg* shape, int32_t k, const pm_params* theta_host, int32_t n_sm,
+                           const void* A_op_dev, const void* B_op_dev, float* C_dev, const float* scales_dev,
+                           int warmup, int reps, void* stream, pm_cfg* pick_out, pm_probe_result* pick_time_out);
+
 /* pm_model_grad without any device allocation, for callers that cannot
  * allocate device memory when they need the gradient (a host program that
  * links only this library and owns no CUDA allocator, a runtime held to a

@@ -60,7 +60,7 @@ assert ctypes.sizeof(pm_cfg) == 24 and ctypes.sizeof(pm_probe_args) == 56 and ct
 EXPORTS = ("pm_probe_launch", "pm_probe_run", "pm_gemm_operand_bytes", "pm_gemm_prepare", "pm_gemm_run",
            "pm_gemm_bench",
            "pm_grouped_gemm_run", "pm_model_predict", "pm_model_grad_workspace", "pm_model_grad", "pm_model_grad_noalloc",
-           "pm_autotune_pick", "pm_grouped_autotune", "pm_last_error", "pm_device_status",
+           "pm_autotune_pick", "pm_autotune_topk", "pm_gemm_autotune", "pm_grouped_autotune", "pm_last_error", "pm_device_status",
            "pm_watchdog_selftest", "pm_version")
 
 
@@ -97,6 +97,9 @@ def _load():
         "pm_model_grad": [P, i64, ctypes.POINTER(pm_params), i32, P, P, sz, P, P],
         "pm_model_grad_noalloc": [P, i64, ctypes.POINTER(pm_params), i32, P, P, P],
         "pm_autotune_pick": [P, i64, i32, ctypes.POINTER(pm_params), i32, P, P, P],
+        "pm_autotune_topk": [P, i64, i32, ctypes.POINTER(pm_params), i32, i32, P, P, P],
+        "pm_gemm_autotune": [ctypes.POINTER(pm_cfg), i32, ctypes.POINTER(pm_params), i32, P, P, P, P, ctypes.c_int,
+                             ctypes.c_int, P, ctypes.POINTER(pm_cfg), ctypes.POINTER(pm_probe_result)],
         "pm_grouped_autotune": [i32, P, i32, i32, i32, ctypes.POINTER(pm_params), i32, P, P, P, P, P],
         "pm_device_status": [ctypes.c_int],
         "pm_watchdog_selftest": [i32, P],
@@ -267,6 +270,21 @@ def pm_model_grad_noalloc(cfgs_dev, n, theta, n_sm, t_meas, out, stream=None):
 def pm_autotune_pick(MNK_dev, n, dtype, theta, n_sm, picks_dev, t_pred_dev, stream=None):
     _check(_lib.pm_autotune_pick(_ptr(MNK_dev), int(n), int(dtype), ctypes.byref(params(theta)), int(n_sm),
                                  _ptr(picks_dev), _ptr(t_pred_dev), _stream(stream)), "pm_autotune_pick")
+
+
+def pm_autotune_topk(MNK_dev, n, dtype, theta, n_sm, k, picks_dev, t_pred_dev, stream=None):
+    _check(_lib.pm_autotune_topk(_ptr(MNK_dev), int(n), int(dtype), ctypes.byref(params(theta)), int(n_sm), int(k),
+                                 _ptr(picks_dev), _ptr(t_pred_dev), _stream(stream)), "pm_autotune_topk")
+
+
+def pm_gemm_autotune(shape: pm_cfg, k, theta, n_sm, A_op, B_op, C, scales=None, warmup=3, reps=15, stream=None):
+    """(picked pm_cfg, timing dict) of the model-pruned measured search."""
+    pick = pm_cfg()
+    res = pm_probe_result()
+    _check(_lib.pm_gemm_autotune(ctypes.byref(shape), int(k), ctypes.byref(params(theta)), int(n_sm), _ptr(A_op),
+                                 _ptr(B_op), _ptr(C), _ptr(scales), int(warmup), int(reps), _stream(stream),
+                                 ctypes.byref(pick), ctypes.byref(res)), "pm_gemm_autotune")
+    return pick, dict(median_s=res.median_s, p25_s=res.p25_s, p75_s=res.p75_s, min_s=res.min_s)
 
 
 def pm_grouped_autotune(M_list, N, K, dtype, theta, n_sm, stream=None):

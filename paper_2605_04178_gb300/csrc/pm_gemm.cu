@@ -836,3 +836,46 @@ extern "C" pm_status pm_gemm_bench(const pm_cfg* cfg, const void* A_op_dev, cons
   }
   return PM_OK;
 }
+
+extern "C" pm_status pm_gemm_autotune(const pm_cfg* shape, int32_t k, const pm_params* theta_host, int32_t n_sm,
+                                      const void* A_op_dev, const void* B_op_dev, float* C_dev,
+                                      const float* scales_dev, int warmup, int reps, void* stream,
+                                      pm_cfg* pick_out, pm_probe_result* pick_time_out) {
+  PM_REQUIRE(shape && theta_host && pick_out, PM_EINVAL, "null argument");
+  PM_REQUIRE(k >= 1 && k <= 16, PM_EINVAL, "k must be in [1, 16]");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  // model shortlist on the GPU
+  char* buf = nullptr;
+  const size_t bytes = 16 + (size_t)k * (sizeof(pm_cfg) + sizeof(float));
+  PM_CUDA(cudaMallocAsync((void**)&buf, bytes, s));
+  int32_t* dmnk = reinterpret_cast<int32_t*>(buf);
+  pm_cfg* dpicks = reinterpret_cast<pm_cfg*>(buf + 16);
+  float* dt = reinterpret_cast<float*>(buf + 16 + (size_t)k * sizeof(pm_cfg));
+  const int32_t mnk[3] = {shape->M, shape->N, shape->K};
+  std::vector<pm_cfg> cand(k);
+  cudaError_t e = cudaMemcpyAsync(dmnk, mnk, sizeof(mnk), cudaMemcpyHostToDevice, s);
+  pm_status st = PM_OK;
+  if (e == cudaSuccess) {
+    st = pm_autotune_topk(dmnk, 1, shape->dtype, theta_host, n_sm, k, dpicks, dt, stream);
+    if (st == PM_OK) e = cudaMemcpyAsync(cand.data(), dpicks, (size_t)k * sizeof(pm_cfg), cudaMemcpyDeviceToHost, s);
+  }
+  cudaFreeAsync(buf, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (st != PM_OK) return st;
+  if (e != cudaSuccess) return pm::cuda_fail(e, "autotune shortlist");
+  // time the shortlist with the harness and keep the fastest (first on ties)
+  double best = 1e300;
+  int bi = -1;
+  pm_probe_result best_r = {};
+  for (int i = 0; i < k; ++i) {
+    if (cand[i].BM == 0) continue;
+    pm_probe_result r;
+    st = pm_gemm_bench(&cand[i], A_op_dev, B_op_dev, C_dev, scales_dev, warmup, reps, stream, &r);
+    if (st != PM_OK) return st;
+    if (r.median_s < best) { best = r.median_s; bi = i; best_r = r; }
+  }
+  PM_REQUIRE(bi >= 0, PM_EUNSUPPORTED, "no valid configuration for this shape");
+  *pick_out = cand[bi];
+  if (pick_time_out) *pick_time_out = best_r;
+  return PM_OK;
+}

@@ -408,6 +408,74 @@ __global__ void __launch_bounds__(kTuneThreads) autotune_kernel(const int32_t* _
   }
 }
 
+// Top-k variant: the k predicted-fastest valid configurations per shape, in
+// increasing predicted time (ties to the lower index), by k rounds of block
+// argmin over the 180 candidates.
+constexpr int kMaxTopK = 16;
+
+__global__ void __launch_bounds__(kTuneThreads) autotune_topk_kernel(const int32_t* __restrict__ MNK, int64_t n,
+                                                                     int dt, Theta th, int n_sm, int k,
+                                                                     pm_cfg* __restrict__ picks,
+                                                                     float* __restrict__ t_pred) {
+  __shared__ float sv[kTuneThreads / 32];
+  __shared__ int si[kTuneThreads / 32];
+  __shared__ int chosen;
+  const int t = threadIdx.x;
+  for (int64_t shape = blockIdx.x; shape < n; shape += gridDim.x) {
+    pm_cfg c;
+    c.M = __ldg(MNK + 3 * shape);
+    c.N = __ldg(MNK + 3 * shape + 1);
+    c.K = __ldg(MNK + 3 * shape + 2);
+    c.dtype = (int8_t)dt;
+    c.kind = PM_KIND_GEMM;
+    c.reserved = 0;
+    float mine = INFINITY;
+    int BM = 0, BN = 0, BK = 0, s = 0, g = 0;
+    if (t < 180) {
+      decode_tile(t, dt, BM, BN, BK, s, g);
+      if (tile_valid(BM, BN, BK, s, g, dt) && c.M > 0 && c.N > 0 && c.K > 0) {
+        c.BM = (int16_t)BM; c.BN = (int16_t)BN; c.BK = (int16_t)BK;
+        c.stages = (int8_t)s; c.cta_group = (int8_t)g;
+        GemmFwd f;
+        gemm_forward(c, th, n_sm, f);
+        mine = f.T;
+      }
+    }
+    for (int r = 0; r < k; ++r) {
+      float v = mine;
+      int idx = t;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const float ov = __shfl_xor_sync(0xffffffffu, v, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, idx, o);
+        if (ov < v || (ov == v && oi < idx)) { v = ov; idx = oi; }
+      }
+      if ((t & 31) == 0) { sv[t >> 5] = v; si[t >> 5] = idx; }
+      __syncthreads();
+      if (t == 0) {
+        float bv = sv[0];
+        int bi = si[0];
+        for (int w = 1; w < kTuneThreads / 32; ++w)
+          if (sv[w] < bv || (sv[w] == bv && si[w] < bi)) { bv = sv[w]; bi = si[w]; }
+        pm_cfg p = c;
+        if (bv < INFINITY) {
+          decode_tile(bi, dt, BM, BN, BK, s, g);
+          p.BM = (int16_t)BM; p.BN = (int16_t)BN; p.BK = (int16_t)BK;
+          p.stages = (int8_t)s; p.cta_group = (int8_t)g;
+        } else {
+          p.BM = p.BN = p.BK = 0; p.stages = p.cta_group = 0;
+        }
+        picks[shape * k + r] = p;
+        t_pred[shape * k + r] = bv;
+        chosen = bv < INFINITY ? bi : -1;
+      }
+      __syncthreads();
+      if (t == chosen) mine = INFINITY;
+      __syncthreads();
+    }
+  }
+}
+
 // Grouped autotuner: block b handles launch-level combination b =
 // (BK index, stages, cta_group) in lexicographic order; threads pick each
 // group's (BM, BN), then each worker's busy time under the static schedule
@@ -553,6 +621,19 @@ extern "C" pm_status pm_autotune_pick(const int32_t* MNK_dev, int64_t n, int32_t
   autotune_kernel<<<grid, kTuneThreads, 0, static_cast<cudaStream_t>(stream)>>>(
       MNK_dev, n, dtype, to_theta(theta_host), n_sm, picks_dev, t_pred_dev);
   return launch_status("autotune_kernel");
+}
+
+extern "C" pm_status pm_autotune_topk(const int32_t* MNK_dev, int64_t n, int32_t dtype, const pm_params* theta_host,
+                                      int32_t n_sm, int32_t k, pm_cfg* picks_dev, float* t_pred_dev, void* stream) {
+  PM_REQUIRE(n >= 0, PM_EINVAL, "n < 0");
+  if (n == 0) return PM_OK;
+  PM_REQUIRE(MNK_dev && theta_host && picks_dev && t_pred_dev && n_sm > 0, PM_EINVAL, "null pointer or n_sm <= 0");
+  PM_REQUIRE(dtype >= 0 && dtype <= 2, PM_EINVAL, "dtype %d is not a pm_dtype", dtype);
+  PM_REQUIRE(k >= 1 && k <= kMaxTopK, PM_EINVAL, "k must be in [1, %d]", kMaxTopK);
+  const int grid = (int)std::min<int64_t>(n, (int64_t)std::max(1, sm_count()) * 16);
+  autotune_topk_kernel<<<grid, kTuneThreads, 0, static_cast<cudaStream_t>(stream)>>>(
+      MNK_dev, n, dtype, to_theta(theta_host), n_sm, k, picks_dev, t_pred_dev);
+  return launch_status("autotune_topk_kernel");
 }
 
 extern "C" pm_status pm_grouped_autotune(int32_t G, const int32_t* M_host, int32_t N, int32_t K, int32_t dtype,

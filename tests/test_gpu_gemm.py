@@ -150,3 +150,26 @@ def test_large_sampled_rows(lib, dt):
     ref = O.gemm_f64(A[rows], B)
     err = np.linalg.norm(C[rows] - ref) / np.linalg.norm(ref)
     assert err <= (2e-2 if dt == 1 else 6e-2), err
+
+
+def test_gemm_autotune_picks_fastest_of_model_shortlist(lib):
+    M = N = K = 2048
+    A, B = S.gemm_operands(M, N, K, seed=2, dist="normal")
+    ops = lib.GemmOperands(1, M, N, K)
+    ops.prepare(torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda())
+    C = torch.empty(M, N, dtype=torch.float32, device="cuda")
+    th = O.prior_theta(lib.sm_count()).astype(np.float32).astype(np.float64)
+    pick, timing = lib.pm_gemm_autotune(lib.cfg(M, N, K, dtype=1), 4, th, lib.sm_count(), ops.A_op, ops.B_op, C,
+                                        ops.scales, warmup=2, reps=5)
+    MNK = torch.tensor([M, N, K], dtype=torch.int32, device="cuda")
+    picks = torch.empty(4 * 24, dtype=torch.uint8, device="cuda")
+    t = torch.empty(4, dtype=torch.float32, device="cuda")
+    lib.pm_autotune_topk(MNK, 1, 1, th, lib.sm_count(), 4, picks, t)
+    short = [tuple(int(r[f]) for f in ("BM", "BN", "BK", "stages", "cta_group"))
+             for r in picks.cpu().numpy().view(lib.CFG_DTYPE)]
+    assert (pick.BM, pick.BN, pick.BK, pick.stages, pick.cta_group) in short
+    assert timing["median_s"] > 0
+    # the picked configuration computes the product correctly
+    C2, _ = run_gemm(lib, A, B, pick, 1)
+    ref = O.gemm_f64(A[:64], B)
+    assert np.linalg.norm(C2[:64] - ref) / np.linalg.norm(ref) <= 2e-2

@@ -156,3 +156,30 @@ def test_grouped_autotune_matches_oracle(lib):
     # the GPU's choice evaluated by the oracle is as good as the oracle's
     t_check = O.grouped_predict(Mg, 4096, 4096, bm_g, bn_g, *launch_g, 1, th, N_SM)
     assert t_check == pytest.approx(t_o, rel=1e-5)
+
+
+def test_autotune_topk_matches_oracle_order(lib):
+    th = theta32()
+    MNK = np.array([[512, 512, 512], [1024, 2048, 4096], [8192, 8192, 8192], [300, 5000, 1000]], np.int32)
+    k = 8
+    for dt in (0, 1, 2):
+        n = len(MNK)
+        picks = torch.empty(n * k * 24, dtype=torch.uint8, device="cuda")
+        t = torch.empty(n * k, dtype=torch.float32, device="cuda")
+        lib.pm_autotune_topk(torch.from_numpy(MNK.ravel()).cuda(), n, dt, th, N_SM, k, picks, t)
+        p = picks.cpu().numpy().view(lib.CFG_DTYPE).reshape(n, k)
+        tg = t.cpu().numpy().reshape(n, k).astype(np.float64)
+        for i, (M, N, K) in enumerate(MNK):
+            space = [c for c in S.tile_space(dt) if O.cfg_valid(*c, dt)]
+            cols = {f: np.array(v, dtype=np.int32) for f, v in zip(("BM", "BN", "BK", "stages", "cta_group"),
+                                                                    zip(*space))}
+            cols.update(M=np.full(len(space), M), N=np.full(len(space), N), K=np.full(len(space), K),
+                        dtype=np.full(len(space), dt), kind=np.zeros(len(space)))
+            to = O.model_batch(cols, th, N_SM)
+            order = np.argsort(to, kind="stable")[:k]
+            assert np.all(np.abs(tg[i] - to[order]) <= 1e-5 * to[order])
+            got = [tuple(int(p[i, r][f]) for f in ("BM", "BN", "BK", "stages", "cta_group")) for r in range(k)]
+            assert np.all(np.diff(tg[i]) >= 0)
+            for r in range(k):   # each pick's own FP64 prediction sits at its rank (up to FP32 resolution)
+                j = space.index(got[r])
+                assert abs(to[j] - to[order[r]]) <= 2e-6 * to[order[r]]
