@@ -214,14 +214,14 @@ def run_gpu(args):
 
     # ------------------------------------------------------ model-driven pick
     # the model alone (argmin over the 180-point space, on the GPU) and the
-    # library's autotuner (the model's 4 best tiles timed on the device)
+    # library's autotuner (the model's 8 best tiles timed on the device)
     MNK = torch.tensor([M, N, K], dtype=torch.int32, device="cuda")
     picks = torch.empty(24, dtype=torch.uint8, device="cuda")
     t_pred = torch.empty(1, dtype=torch.float32, device="cuda")
     pm.pm_autotune_pick(MNK, 1, pm.PM_BF16, theta, n_sm, picks, t_pred)
     p = picks.cpu().numpy().view(pm.CFG_DTYPE)[0]
     model_pick = tuple(int(p[k]) for k in ("BM", "BN", "BK", "stages", "cta_group"))
-    tuned, _ = pm.pm_gemm_autotune(pm.cfg(M, N, K, dtype=pm.PM_BF16), 4, theta, n_sm, ops.A_op, ops.B_op, C,
+    tuned, _ = pm.pm_gemm_autotune(pm.cfg(M, N, K, dtype=pm.PM_BF16), 8, theta, n_sm, ops.A_op, ops.B_op, C,
                                    ops.scales)
     pick = (tuned.BM, tuned.BN, tuned.BK, tuned.stages, tuned.cta_group)
     if args.cfg:
@@ -323,7 +323,7 @@ def run_gpu(args):
             "config": {"workload": "bf16_gemm_8192^3_model_autotuned", "M": M, "N": N, "K": K,
                        "inputs": "A,B ~ N(0,1) seed 2, FP32 -> BF16 K-major operands",
                        "tile": dict(zip(("BM", "BN", "BK", "stages", "cta_group"), pick)),
-                       "autotune": "model top-4 tiles (GPU) timed on the device, fastest kept",
+                       "autotune": "model top-8 tiles (GPU) timed on the device, fastest kept",
                        "theta": theta_src, "l2": "operands 256 MB > 129 MB L2, no flush",
                        "parallelism": "replicas" if world > 1 else "single"},
             "pct_of_peak": 100.0 * achieved / peak,
