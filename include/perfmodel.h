@@ -84,7 +84,11 @@ typedef struct { float v[16]; } pm_params;
  *                   a shared-memory ring (cols*4 bytes a multiple of 16).
  *  PM_PROBE_PCHASE: j = buf0[j * 16] for `hops` hops from `start` by one
  *                   thread (nodes 64 bytes apart, n nodes); the final j is
- *                   written to ((uint32_t*)buf1)[0]. */
+ *                   written to ((uint32_t*)buf1)[0].  start = 0xFFFFFFFF
+ *                   resumes from the node in buf1[0]; pm_probe_run resumes
+ *                   this way on every launch after its first, so repeated
+ *                   runs walk new nodes rather than re-walk cached ones and
+ *                   final_index is the node after (warmup + reps) * hops hops. */
 typedef enum { PM_PROBE_COPY = 1, PM_PROBE_TRIAD = 2, PM_PROBE_TMA2D = 3, PM_PROBE_PCHASE = 4 } pm_probe_kind;
 
 typedef struct {

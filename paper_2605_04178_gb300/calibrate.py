@@ -126,8 +126,12 @@ def measure_sweep(shapes=(1024, 2048, 4096, 8192, 16384), dtypes=(1, 2), log=pri
         buf = torch.from_numpy(S.pchase_buffer(nodes, seed=1).view(np.int32)).cuda()
         out = torch.zeros(1, dtype=torch.int32, device="cuda")
         hops = 2 ** 18
+        # warm-up launches walk the whole cycle once where that is affordable,
+        # so working sets that fit a cache level are timed resident; larger
+        # ones are walked cold (every launch continues to new nodes)
+        warm = min(-(-nodes // hops) + 1, 9)
         r = pm.pm_probe_run(pm.probe_args(pm.PM_PROBE_PCHASE, n=nodes, hops=hops, start=0), buf, out,
-                            warmup=1, reps=3)
+                            warmup=warm, reps=3)
         pchase.append(dict(W=W, hops=hops, ns_per_hop=1e9 * r["median_s"] / hops, final_index=r["final_index"]))
         del buf
     log("pointer chase done (%.0f s)" % (time.time() - t0))

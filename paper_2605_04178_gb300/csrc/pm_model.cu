@@ -152,7 +152,10 @@ __device__ __forceinline__ void gemm_adjoint(const pm_cfg& c, const Theta& th, c
   d[9] += g_c * f.n_instr;
   d[11] -= g_c * (f.D / th.v[11]) / th.v[11];
   d[13] += g_c / f.Kt;
-  d[f.ri] += gR;
+  // static indices keep d[] in registers
+  d[6] += f.ri == 6 ? gR : 0.f;
+  d[7] += f.ri == 7 ? gR : 0.f;
+  d[8] += f.ri == 8 ? gR : 0.f;
   if (c.cta_group == 2) d[14] += gS;
 }
 

@@ -71,9 +71,13 @@ __global__ void __launch_bounds__(kStreamThreads) triad_kernel(float4* __restric
 
 // ---------------------------------------------------------------- pointer chase
 // One thread follows the cycle; node j's successor is the word at j*16.
+// start == kContinue resumes from the node the previous launch ended on, so
+// repeated launches keep walking new nodes instead of re-walking cached ones.
+constexpr uint32_t kContinue = 0xFFFFFFFFu;
+
 __global__ void pchase_kernel(const uint32_t* __restrict__ buf, uint32_t start, int64_t hops,
                               uint32_t* __restrict__ out) {
-  uint32_t j = start;
+  uint32_t j = start == kContinue ? *out : start;
   for (int64_t h = 0; h < hops; ++h) j = buf[(size_t)j * 16];
   *out = j;
 }
@@ -188,7 +192,8 @@ static pm_status probe_launch(const pm_probe_args* a, void* buf0, void* buf1, vo
     }
     case PM_PROBE_PCHASE: {
       PM_REQUIRE(buf0 && buf1 && a->n > 0 && a->hops >= 0, PM_EINVAL, "pchase probe: bad arguments");
-      PM_REQUIRE(a->start < (uint64_t)a->n, PM_EINVAL, "pchase probe: start outside the node range");
+      PM_REQUIRE(a->start < (uint64_t)a->n || a->start == kContinue, PM_EINVAL,
+                 "pchase probe: start outside the node range");
       pchase_kernel<<<1, 1, 0, s>>>((const uint32_t*)buf0, a->start, a->hops, (uint32_t*)buf1);
       return launch_status("pchase_kernel");
     }
@@ -250,16 +255,20 @@ extern "C" pm_status pm_probe_run(const pm_probe_args* args, void* buf0, void* b
   PM_REQUIRE(args != nullptr && out != nullptr, PM_EINVAL, "args or out is NULL");
   PM_REQUIRE(warmup >= 0 && reps >= 1 && reps <= 100000, PM_EINVAL, "warmup >= 0 and 1 <= reps <= 1e5 required");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  for (int i = 0; i < warmup; ++i) {
-    pm_status st = probe_launch(args, buf0, buf1, buf2, s);
+  // pointer chase: every launch after the first continues the walk
+  pm_probe_args cont = *args;
+  if (args->kind == PM_PROBE_PCHASE) cont.start = kContinue;
+  int launches = 0;
+  for (int i = 0; i < warmup; ++i, ++launches) {
+    pm_status st = probe_launch(launches == 0 ? args : &cont, buf0, buf1, buf2, s);
     if (st != PM_OK) return st;
   }
   std::vector<cudaEvent_t> ev(2 * (size_t)reps);
   for (auto& e : ev) PM_CUDA(cudaEventCreate(&e));
   pm_status st = PM_OK;
-  for (int i = 0; i < reps && st == PM_OK; ++i) {
+  for (int i = 0; i < reps && st == PM_OK; ++i, ++launches) {
     cudaEventRecord(ev[2 * i], s);
-    st = probe_launch(args, buf0, buf1, buf2, s);
+    st = probe_launch(launches == 0 ? args : &cont, buf0, buf1, buf2, s);
     cudaEventRecord(ev[2 * i + 1], s);
   }
   cudaError_t e = cudaStreamSynchronize(s);

@@ -35,8 +35,12 @@ def test_pchase_final_index(lib, nodes, hops, start):
     buf = S.pchase_buffer(nodes, seed=1)
     out = torch.zeros(1, dtype=torch.int32, device="cuda")
     r = lib.pm_probe_run(lib.probe_args(lib.PM_PROBE_PCHASE, n=nodes, hops=hops, start=start),
-                         torch.from_numpy(buf.view(np.int32)).cuda(), out, warmup=0, reps=2)
-    assert r["final_index"] == O.pchase(buf, 16, start, hops)
+                         torch.from_numpy(buf.view(np.int32)).cuda(), out, warmup=1, reps=2)
+    # three launches, each continuing the walk of the previous one
+    assert r["final_index"] == O.pchase(buf, 16, start, 3 * hops)
+    lib.pm_probe_launch(lib.probe_args(lib.PM_PROBE_PCHASE, n=nodes, hops=hops, start=start),
+                        torch.from_numpy(buf.view(np.int32)).cuda(), out)
+    assert int(out.cpu().numpy()[0]) == O.pchase(buf, 16, start, hops)
 
 
 @pytest.mark.parametrize("tile", [(64, 64), (128, 64), (128, 128), (256, 64), (256, 128), (8, 4), (200, 36)])
