@@ -150,6 +150,20 @@ pm_status pm_gemm_run(const pm_cfg* cfg, const void* A_op_dev, const void* B_op_
 pm_status pm_gemm_bench(const pm_cfg* cfg, const void* A_op_dev, const void* B_op_dev, float* C_dev,
                         const float* scales_dev, int warmup, int reps, void* stream, pm_probe_result* out);
 
+/* End-to-end GEMM from host memory: C_host[M,N] = A_host[M,K] B_host[K,N]
+ * (FP32 row-major; pinned host memory lets the copies overlap), in the tile
+ * configuration `cfg`.  B is copied and converted first; A then moves in
+ * `chunks` row chunks on a copy stream, each chunk is converted and
+ * multiplied while the next is in flight, and each finished C chunk is copied
+ * back on a third stream (FP8 uses one chunk: its per-tensor scale needs all
+ * of A).  The work is ordered after prior work on `stream` and `stream` waits
+ * for its completion, so the call is async with respect to `stream`.
+ * ws_dev: pm_gemm_host_workspace bytes, 256-byte aligned, owned by the
+ * caller.  One device per calling host thread. */
+pm_status pm_gemm_host_workspace(const pm_cfg* cfg, int32_t chunks, size_t* bytes);
+pm_status pm_gemm_host(const pm_cfg* cfg, const float* A_host, const float* B_host, float* C_host, void* ws_dev,
+                       size_t ws_bytes, int32_t chunks, void* stream);
+
 /* Grouped BF16 GEMM in one persistent launch: G problems C_g[M_g,N] =
  * A_g[M_g,K] B_g[K,N].  A_op_dev stacks the A_g as bf16 [sum M_g, K]; B_op_dev
  * stacks the B_g transposed, bf16 [G*N, K]; C_dev stacks C_g, FP32

@@ -58,7 +58,7 @@ assert ctypes.sizeof(pm_cfg) == 24 and ctypes.sizeof(pm_probe_args) == 56 and ct
 
 # Every exported symbol of include/perfmodel.h
 EXPORTS = ("pm_probe_launch", "pm_probe_run", "pm_gemm_operand_bytes", "pm_gemm_prepare", "pm_gemm_run",
-           "pm_gemm_bench",
+           "pm_gemm_bench", "pm_gemm_host_workspace", "pm_gemm_host",
            "pm_grouped_gemm_run", "pm_model_predict", "pm_model_grad_workspace", "pm_model_grad", "pm_model_grad_noalloc",
            "pm_autotune_pick", "pm_autotune_topk", "pm_gemm_autotune", "pm_grouped_autotune", "pm_last_error", "pm_device_status",
            "pm_watchdog_selftest", "pm_version")
@@ -89,6 +89,8 @@ def _load():
         "pm_gemm_operand_bytes": [i32, i32, i32, i32, ctypes.POINTER(sz), ctypes.POINTER(sz)],
         "pm_gemm_prepare": [i32, P, P, i32, i32, i32, P, P, P, P],
         "pm_gemm_run": [ctypes.POINTER(pm_cfg), P, P, P, P, P],
+        "pm_gemm_host_workspace": [ctypes.POINTER(pm_cfg), i32, ctypes.POINTER(sz)],
+        "pm_gemm_host": [ctypes.POINTER(pm_cfg), P, P, P, P, sz, i32, P],
         "pm_gemm_bench": [ctypes.POINTER(pm_cfg), P, P, P, P, ctypes.c_int, ctypes.c_int, P,
                           ctypes.POINTER(pm_probe_result)],
         "pm_grouped_gemm_run": [i32, P, i32, i32, P, P, i32, i32, i32, P, P, P, P],
@@ -210,6 +212,19 @@ def pm_gemm_bench(c: pm_cfg, A_op, B_op, C, scales=None, warmup=10, reps=100, st
     _check(_lib.pm_gemm_bench(ctypes.byref(c), _ptr(A_op), _ptr(B_op), _ptr(C), _ptr(scales), int(warmup), int(reps),
                               _stream(stream), ctypes.byref(res)), "pm_gemm_bench")
     return dict(median_s=res.median_s, p25_s=res.p25_s, p75_s=res.p75_s, min_s=res.min_s, bytes=res.bytes)
+
+
+def pm_gemm_host_workspace(c: pm_cfg, chunks) -> int:
+    b = ctypes.c_size_t()
+    _check(_lib.pm_gemm_host_workspace(ctypes.byref(c), int(chunks), ctypes.byref(b)), "pm_gemm_host_workspace")
+    return b.value
+
+
+def pm_gemm_host(c: pm_cfg, A_host, B_host, C_host, workspace, chunks=4, stream=None):
+    """C_host = A_host @ B_host from (pinned) host FP32 tensors, copies overlapped with compute."""
+    _check(_lib.pm_gemm_host(ctypes.byref(c), _ptr(A_host), _ptr(B_host), _ptr(C_host), _ptr(workspace),
+                             int(workspace.numel() * workspace.element_size()), int(chunks), _stream(stream)),
+           "pm_gemm_host")
 
 
 def pm_grouped_gemm_run(M_list, N, K, BM_list, BN_list, BK, stages, cta_group, A_op, B_op, C, stream=None):

@@ -879,3 +879,152 @@ extern "C" pm_status pm_gemm_autotune(const pm_cfg* shape, int32_t k, const pm_p
   if (pick_time_out) *pick_time_out = best_r;
   return PM_OK;
 }
+
+// ----------------------------------------------------------- host-to-host GEMM
+// C_host = A_host B_host with the host link and the GEMM overlapped: B is
+// copied and converted first, then A moves in row chunks on a copy stream,
+// each chunk is converted and multiplied on a compute stream while the next
+// chunk is in flight, and each finished C chunk returns on a third stream.
+// Two staging buffers per chunked operand; events order reuse.
+namespace pm {
+
+struct HostPipe {
+  int dev = -1;
+  cudaStream_t s_in = nullptr, s_comp = nullptr, s_out = nullptr;
+  cudaEvent_t start, b_ready, done, a_loaded[2], a_free[2], c_ready[2], c_free[2];
+};
+static thread_local HostPipe g_pipe;
+
+static pm_status host_pipe() {
+  int dev = 0;
+  PM_CUDA(cudaGetDevice(&dev));
+  HostPipe& P = g_pipe;
+  if (P.dev == dev) return PM_OK;
+  PM_REQUIRE(P.dev < 0, PM_EUNSUPPORTED, "pm_gemm_host: one device per host thread");
+  PM_CUDA(cudaStreamCreateWithFlags(&P.s_in, cudaStreamNonBlocking));
+  PM_CUDA(cudaStreamCreateWithFlags(&P.s_comp, cudaStreamNonBlocking));
+  PM_CUDA(cudaStreamCreateWithFlags(&P.s_out, cudaStreamNonBlocking));
+  cudaEvent_t* evs[] = {&P.start, &P.b_ready, &P.done, &P.a_loaded[0], &P.a_loaded[1], &P.a_free[0],
+                        &P.a_free[1], &P.c_ready[0], &P.c_ready[1], &P.c_free[0], &P.c_free[1]};
+  for (cudaEvent_t* e : evs) PM_CUDA(cudaEventCreateWithFlags(e, cudaEventDisableTiming));
+  P.dev = dev;
+  return PM_OK;
+}
+
+struct HostLayout {
+  int64_t Mc;
+  int chunks;
+  size_t off_b32, off_bop, off_a32[2], off_aop[2], off_c[2], off_scales, total;
+};
+
+static HostLayout host_layout(const pm_cfg& c, int chunks) {
+  HostLayout Lh;
+  if (c.dtype == PM_FP8E4M3) chunks = 1;              // the per-tensor scale needs all of A first
+  chunks = std::max(1, std::min(chunks, (int)c.M));
+  Lh.chunks = chunks;
+  Lh.Mc = (c.M + chunks - 1) / chunks;
+  const size_t op = (size_t)dt_halves(c.dtype) * dt_elem(c.dtype);
+  auto up = [](size_t v) { return (v + 255) & ~(size_t)255; };
+  size_t o = 0;
+  Lh.off_b32 = o; o += up((size_t)c.K * c.N * 4);
+  Lh.off_bop = o; o += up(op * c.N * c.K);
+  const int nbuf = chunks > 1 ? 2 : 1;
+  for (int j = 0; j < 2; ++j) { Lh.off_a32[j] = o; if (j < nbuf) o += up((size_t)Lh.Mc * c.K * 4); }
+  for (int j = 0; j < 2; ++j) { Lh.off_aop[j] = o; if (j < nbuf) o += up(op * Lh.Mc * c.K); }
+  for (int j = 0; j < 2; ++j) { Lh.off_c[j] = o; if (j < nbuf) o += up((size_t)Lh.Mc * c.N * 4); }
+  Lh.off_scales = o; o += 256;
+  if (nbuf == 1) {
+    Lh.off_a32[1] = Lh.off_a32[0]; Lh.off_aop[1] = Lh.off_aop[0]; Lh.off_c[1] = Lh.off_c[0];
+  }
+  Lh.total = o;
+  return Lh;
+}
+
+}  // namespace pm
+
+extern "C" pm_status pm_gemm_host_workspace(const pm_cfg* cfg, int32_t chunks, size_t* bytes) {
+  PM_REQUIRE(cfg && bytes, PM_EINVAL, "null argument");
+  PM_REQUIRE(cfg->M > 0 && cfg->N > 0 && cfg->K > 0 && cfg->dtype >= 0 && cfg->dtype <= 2, PM_EINVAL,
+             "bad shape or dtype");
+  *bytes = pm::host_layout(*cfg, chunks).total;
+  return PM_OK;
+}
+
+extern "C" pm_status pm_gemm_host(const pm_cfg* cfg, const float* A_host, const float* B_host, float* C_host,
+                                  void* ws_dev, size_t ws_bytes, int32_t chunks, void* stream) {
+  using namespace pm;
+  PM_REQUIRE(cfg && A_host && B_host && C_host && ws_dev, PM_EINVAL, "null argument");
+  PM_REQUIRE(cfg->kind == PM_KIND_GEMM && cfg->M > 0 && cfg->N > 0 && cfg->K > 0, PM_EINVAL, "bad shape");
+  PM_REQUIRE(gemm_tile_valid(cfg->BM, cfg->BN, cfg->BK, cfg->stages, cfg->cta_group, cfg->dtype), PM_EUNSUPPORTED,
+             "tile configuration outside the valid space");
+  PM_REQUIRE(((uintptr_t)ws_dev & 255) == 0, PM_EINVAL, "workspace must be 256-byte aligned");
+  const HostLayout Lh = host_layout(*cfg, chunks);
+  PM_REQUIRE(ws_bytes >= Lh.total, PM_ENOMEM, "workspace of %zu bytes is smaller than the %zu needed", ws_bytes,
+             Lh.total);
+  pm_status st = host_pipe();
+  if (st != PM_OK) return st;
+  HostPipe& P = g_pipe;
+  cudaStream_t caller = static_cast<cudaStream_t>(stream);
+  char* ws = static_cast<char*>(ws_dev);
+  const int dt = cfg->dtype;
+  const int M = cfg->M, N = cfg->N, K = cfg->K;
+  float* b32 = reinterpret_cast<float*>(ws + Lh.off_b32);
+  void* bop = ws + Lh.off_bop;
+  float* scales = reinterpret_cast<float*>(ws + Lh.off_scales);
+  unsigned int* amax = reinterpret_cast<unsigned int*>(scales + 2);
+  const int sms = std::max(1, sm_count());
+  PM_CUDA(cudaEventRecord(P.start, caller));
+  PM_CUDA(cudaStreamWaitEvent(P.s_in, P.start, 0));
+  PM_CUDA(cudaStreamWaitEvent(P.s_comp, P.start, 0));
+  PM_CUDA(cudaStreamWaitEvent(P.s_out, P.start, 0));
+  // B: copy, then convert to the K-major operand
+  PM_CUDA(cudaMemcpyAsync(b32, B_host, (size_t)K * N * 4, cudaMemcpyHostToDevice, P.s_in));
+  PM_CUDA(cudaEventRecord(P.b_ready, P.s_in));
+  PM_CUDA(cudaStreamWaitEvent(P.s_comp, P.b_ready, 0));
+  if (dt == PM_FP8E4M3) {
+    PM_CUDA(cudaMemsetAsync(amax, 0, 2 * sizeof(unsigned int), P.s_comp));
+    amax_kernel<<<sms * 4, 256, 0, P.s_comp>>>(b32, (int64_t)K * N, amax + 1);
+  }
+  dim3 tgrid((N + 31) / 32, (K + 31) / 32);
+  PM_REQUIRE(tgrid.y <= 65535, PM_EINVAL, "K too large for the transpose grid");
+  transpose_convert_kernel<<<tgrid, dim3(32, 8), 0, P.s_comp>>>(
+      b32, K, N, dt, bop, dt == PM_FP32 ? static_cast<float*>(bop) + (int64_t)N * K : nullptr,
+      dt == PM_FP8E4M3 ? amax + 1 : nullptr, dt == PM_FP8E4M3 ? scales + 1 : nullptr);
+  st = launch_status("transpose_convert_kernel");
+  if (st != PM_OK) return st;
+  // A in row chunks
+  const int nch = (int)((M + Lh.Mc - 1) / Lh.Mc);
+  for (int i = 0; i < nch; ++i) {
+    const int j = i & 1;
+    const int64_t r0 = (int64_t)i * Lh.Mc;
+    const int rows = (int)std::min<int64_t>(Lh.Mc, M - r0);
+    float* a32 = reinterpret_cast<float*>(ws + Lh.off_a32[j]);
+    void* aop = ws + Lh.off_aop[j];
+    float* cd = reinterpret_cast<float*>(ws + Lh.off_c[j]);
+    if (i >= 2) PM_CUDA(cudaStreamWaitEvent(P.s_in, P.a_free[j], 0));
+    PM_CUDA(cudaMemcpyAsync(a32, A_host + r0 * K, (size_t)rows * K * 4, cudaMemcpyHostToDevice, P.s_in));
+    PM_CUDA(cudaEventRecord(P.a_loaded[j], P.s_in));
+    PM_CUDA(cudaStreamWaitEvent(P.s_comp, P.a_loaded[j], 0));
+    const int64_t nA = (int64_t)rows * K;
+    if (dt == PM_FP8E4M3) amax_kernel<<<sms * 4, 256, 0, P.s_comp>>>(a32, nA, amax);
+    convert_rows_kernel<<<sms * 8, 256, 0, P.s_comp>>>(a32, nA, dt, aop,
+                                                       dt == PM_FP32 ? static_cast<float*>(aop) + nA : nullptr,
+                                                       dt == PM_FP8E4M3 ? amax : nullptr,
+                                                       dt == PM_FP8E4M3 ? scales : nullptr);
+    st = launch_status("convert_rows_kernel");
+    if (st != PM_OK) return st;
+    PM_CUDA(cudaEventRecord(P.a_free[j], P.s_comp));
+    if (i >= 2) PM_CUDA(cudaStreamWaitEvent(P.s_comp, P.c_free[j], 0));
+    pm_cfg cc = *cfg;
+    cc.M = rows;
+    st = gemm_launch(cc, aop, bop, cd, scales, P.s_comp);
+    if (st != PM_OK) return st;
+    PM_CUDA(cudaEventRecord(P.c_ready[j], P.s_comp));
+    PM_CUDA(cudaStreamWaitEvent(P.s_out, P.c_ready[j], 0));
+    PM_CUDA(cudaMemcpyAsync(C_host + r0 * N, cd, (size_t)rows * N * 4, cudaMemcpyDeviceToHost, P.s_out));
+    PM_CUDA(cudaEventRecord(P.c_free[j], P.s_out));
+  }
+  PM_CUDA(cudaEventRecord(P.done, P.s_out));
+  PM_CUDA(cudaStreamWaitEvent(caller, P.done, 0));
+  return PM_OK;
+}

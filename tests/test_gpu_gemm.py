@@ -173,3 +173,26 @@ def test_gemm_autotune_picks_fastest_of_model_shortlist(lib):
     C2, _ = run_gemm(lib, A, B, pick, 1)
     ref = O.gemm_f64(A[:64], B)
     assert np.linalg.norm(C2[:64] - ref) / np.linalg.norm(ref) <= 2e-2
+
+
+@pytest.mark.parametrize("dt,chunks,t", [(1, 3, (128, 256, 64, 4, 2)), (1, 1, (256, 256, 64, 4, 2)),
+                                         (0, 4, (128, 128, 32, 3, 1)), (2, 4, (128, 256, 128, 3, 1)),
+                                         (1, 7, (64, 128, 64, 4, 1))])
+def test_gemm_host_pipeline_exact(lib, dt, chunks, t):
+    # host FP32 in, host FP32 out, copies overlapped with compute in row chunks
+    M, N, K = 1000, 768, 512
+    A, B, ref = _int_case(M, N, K)
+    Ah = torch.from_numpy(A).pin_memory()
+    Bh = torch.from_numpy(B).pin_memory()
+    Ch = torch.full((M, N), float("nan"), dtype=torch.float32).pin_memory()
+    c = lib.cfg(M, N, K, *t, dtype=dt)
+    ws = torch.empty(lib.pm_gemm_host_workspace(c, chunks), dtype=torch.uint8, device="cuda")
+    for _ in range(2):                      # the second call reuses the staging buffers
+        Ch.fill_(float("nan"))
+        lib.pm_gemm_host(c, Ah, Bh, Ch, ws, chunks)
+        torch.cuda.synchronize()
+        C = Ch.numpy().astype(np.float64)
+        if dt == 2:
+            assert np.all(np.abs(C - ref) <= 2.0 ** -23 * np.abs(ref))
+        else:
+            assert np.array_equal(C, ref)
