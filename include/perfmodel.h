@@ -89,7 +89,29 @@ typedef struct { float v[16]; } pm_params;
  *                   this way on every launch after its first, so repeated
  *                   runs walk new nodes rather than re-walk cached ones and
  *                   final_index is the node after (warmup + reps) * hops hops. */
-typedef enum { PM_PROBE_COPY = 1, PM_PROBE_TRIAD = 2, PM_PROBE_TMA2D = 3, PM_PROBE_PCHASE = 4 } pm_probe_kind;
+/* Blackwell instruction and host-link probes (Sec. V-A (i), (iii), (iv); Eq. 15):
+ *  PM_PROBE_MMA    : one CTA (cta_group 1) or CTA pair (2) per SM issues n
+ *                    (<= 2^19) back-to-back tcgen05.mma of one shape from
+ *                    operands equal to 1.0 into one TMEM accumulator; rows =
+ *                    cta_group, cols = pm_dtype, tile_c = instruction M (64/128
+ *                    for one SM, 128/256 for a pair), tile_r = N (16..256, step
+ *                    16), start = CTAs (0 = one per SM).  ((uint32_t*)buf0)[cta]
+ *                    = bits of D[0][0] = n * k (k = 8 TF32, 16 BF16, 32 FP8).
+ *                    result.bytes holds the launch's FLOPs.
+ *  PM_PROBE_MBAR   : two threads of different warps pass a token through two
+ *                    mbarriers n times; final_index = completed round trips.
+ *  PM_PROBE_TMEM_LD: every SM fills 128 lanes x 512 columns of TMEM with
+ *                    lane*512 + column and reads them n times with
+ *                    tcgen05.ld; ((uint32_t*)buf0)[sm*128 + lane] = the sum of
+ *                    everything that lane read (mod 2^32).
+ *  PM_PROBE_TMEM_ST: n passes of tcgen05.st writing lane*512 + column + pass,
+ *                    then one read pass; buf0 as above (sum of the last pass).
+ *  PM_PROBE_H2D / PM_PROBE_D2H: cudaMemcpyAsync of n bytes from buf0 to buf1
+ *                    (host memory pinned for full speed). */
+typedef enum {
+  PM_PROBE_COPY = 1, PM_PROBE_TRIAD = 2, PM_PROBE_TMA2D = 3, PM_PROBE_PCHASE = 4, PM_PROBE_H2D = 5,
+  PM_PROBE_D2H = 6, PM_PROBE_MMA = 7, PM_PROBE_MBAR = 8, PM_PROBE_TMEM_LD = 9, PM_PROBE_TMEM_ST = 10
+} pm_probe_kind;
 
 typedef struct {
   int32_t kind;          /* pm_probe_kind */

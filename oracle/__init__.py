@@ -11,10 +11,11 @@ Parity status of each part (pins are in tests/test_oracle_*.py):
   to_bf16/tf32/e4m3   pinned: exhaustive/structural checks against the format definitions
   triad_f32           pinned: exact rational arithmetic (fractions) on random cases
   pchase              pinned: single-cycle walk returns to its start after n hops
-  model_batch         pinned: survey golden rows, closed forms, homogeneity, monotonicity
+  model_batch         pinned: hand-evaluated rows, closed forms, homogeneity, monotonicity
   model gradient      pinned: central differences and Euler's homogeneity identity
   autotune            pinned: brute force in plain Python on small spaces
   grouped model       pinned: reduces to the single-GEMM stage time for one group
+  mma/tmem probe sums closed forms (exact integer arithmetic)
 """
 from __future__ import annotations
 
@@ -270,3 +271,23 @@ def prior_theta(n_sm: int, f_hz: float = 1.9e9) -> np.ndarray:
     th[14] = 1.0                      # S_2SM
     th[15] = 0.3                      # alpha(2) = 0.85, alpha(6) = 0.95
     return th
+
+
+# ----------------------------------------------------------------- instruction probes
+def mma_probe_value(n: int, dtype: int) -> np.float32:
+    """D[0][0] after n MMAs of 1.0 x 1.0 with K = 32 bytes of each operand row
+    (8 TF32, 16 BF16, 32 FP8 products per instruction), accumulated exactly."""
+    k = {DT_FP32: 8, DT_BF16: 16, DT_FP8: 32}[dtype]
+    return np.float32(n * k)
+
+
+def tmem_probe_sums(iters: int, store: bool) -> np.ndarray:
+    """Per-lane sums (mod 2^32) of the TMEM probe: lanes hold lane*512 + column;
+    loads sum `iters` passes, stores leave lane*512 + column + iters - 1."""
+    lane = np.arange(128, dtype=np.int64)
+    col_sum = 511 * 512 // 2
+    if store:
+        s = 512 * 512 * lane + col_sum + 512 * (iters - 1)
+    else:
+        s = iters * (512 * 512 * lane + col_sum)
+    return (s % (1 << 32)).astype(np.uint32)

@@ -9,6 +9,11 @@
 
 namespace pm {
 
+// TMEM address of lane 32*warp, column 0 (a warp may only touch its quarter).
+__device__ __forceinline__ uint32_t tmem_base_row(uint32_t base, int warp) {
+  return base + ((uint32_t)(32 * (warp & 3)) << 16);
+}
+
 // ------------------------------------------------------------------- copy/triad
 // 128-bit loads and stores, four independent vectors in flight per thread,
 // grid sized to a multiple of the SM count (HBM-bound: 8 B/elem copy,
@@ -147,6 +152,148 @@ __global__ void __launch_bounds__(32) tma2d_copy_kernel(const __grid_constant__ 
   bulk_wait_all();
 }
 
+// ------------------------------------------------ Blackwell instruction probes
+// (Sec. V-A (iii)-(iv): tcgen05.mma throughput by shape and precision, mbarrier
+// wait latency, TMEM load/store bandwidth.)  Each computes a checkable value.
+
+// One CTA (pair) per SM issues `iters` back-to-back MMAs of one shape from
+// operands of 1.0 into one accumulator, so D = iters * k_instr exactly.
+template <int CG, int KIND>
+__global__ void __launch_bounds__(128, 1) mma_probe_kernel(int64_t iters, int M, int N, uint32_t* __restrict__ out,
+                                                           Watchdog wd) {
+  extern __shared__ __align__(1024) uint8_t smp[];
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ uint32_t slot;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t rank = CG == 2 ? cluster_ctarank() : 0u;
+  const uint32_t base = (smem_u32(smp) + 1023u) & ~1023u;
+  uint32_t* p = reinterpret_cast<uint32_t*>(smp + (base - smem_u32(smp)));
+  const uint32_t one = KIND == 0 ? 0x3F803F80u : (KIND == 1 ? 0x3F800000u : 0x38383838u);
+  for (int i = threadIdx.x; i < 48 * 1024 / 4; i += blockDim.x) p[i] = one;   // A 16 KB, B 32 KB
+  fence_proxy_async_smem();
+  if (threadIdx.x == 0) {
+    mbar_init(smem_u32(&bar), 1);
+    fence_mbar_init();
+  }
+  if (warp == 0) {
+    tmem_alloc<CG>(smem_u32(&slot), 256);
+    tmem_relinquish<CG>();
+  }
+  tc_fence_before();
+  if constexpr (CG == 2) cluster_sync(); else __syncthreads();
+  tc_fence_after();
+  const uint32_t tm = slot;
+  if (warp == 1 && lane == 0 && rank == 0) {
+    const uint32_t fmt = KIND == 0 ? 1u : (KIND == 1 ? 2u : 0u);
+    const uint32_t idesc = instr_desc(fmt, (uint32_t)M, (uint32_t)N);
+    const uint64_t ad = smem_desc(base, 1024, 2), bd = smem_desc(base + 16384, 1024, 2);
+    for (int64_t i = 0; i < iters; ++i) umma<CG, KIND>(tm, ad, bd, idesc, i > 0 ? 1u : 0u);
+    if constexpr (CG == 1) umma_commit(smem_u32(&bar));
+    else umma_commit_pair(smem_u32(&bar), (uint16_t)3);
+  }
+  if (warp == 0 && lane == 0) mbar_wait(smem_u32(&bar), 0u, wd, nullptr, SITE_MMA_PROBE);
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 0) {
+    uint32_t r[32];
+    tmem_ld_32x32b_x32(tm, r);
+    tmem_ld_wait();
+    if (lane == 0) out[blockIdx.x] = r[0];
+  }
+  tc_fence_before();
+  __syncthreads();
+  if constexpr (CG == 2) cluster_sync();
+  if (warp == 0) {
+    tc_fence_after();
+    tmem_dealloc<CG>(tm, 256);
+  }
+}
+
+// Two threads of different warps pass a token through two mbarriers `iters`
+// times; out[0] = completed round trips.
+__global__ void __launch_bounds__(64) mbar_probe_kernel(int64_t iters, uint32_t* __restrict__ out, Watchdog wd) {
+  __shared__ __align__(8) uint64_t bar[2];
+  if (threadIdx.x == 0) {
+    mbar_init(smem_u32(&bar[0]), 1);
+    mbar_init(smem_u32(&bar[1]), 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int64_t done = 0;
+    for (int64_t i = 0; i < iters; ++i) {
+      mbar_arrive(smem_u32(&bar[0]));
+      if (!mbar_wait(smem_u32(&bar[1]), (uint32_t)(i & 1), wd, nullptr, SITE_MBAR_PROBE)) break;
+      ++done;
+    }
+    out[0] = (uint32_t)done;
+  } else if (threadIdx.x == 32) {
+    for (int64_t i = 0; i < iters; ++i) {
+      if (!mbar_wait(smem_u32(&bar[0]), (uint32_t)(i & 1), wd, nullptr, SITE_MBAR_PROBE)) break;
+      mbar_arrive(smem_u32(&bar[1]));
+    }
+  }
+}
+
+// TMEM bandwidth: every SM fills its 128 lanes x 512 columns with
+// lane*512 + column, then `iters` passes of tcgen05.ld (store = 0) summing
+// what they read, or of tcgen05.st writing value + pass (store = 1) followed
+// by one summing read pass.  out[cta*128 + thread] = the sum (mod 2^32).
+__global__ void __launch_bounds__(128, 1) tmem_probe_kernel(int64_t iters, int store, uint32_t* __restrict__ out) {
+  __shared__ uint32_t slot;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (warp == 0) {
+    tmem_alloc<1>(smem_u32(&slot), 512);
+    tmem_relinquish<1>();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t row = tmem_base_row(slot, warp);
+  const uint32_t lg = (uint32_t)threadIdx.x;
+  uint32_t r[32];
+  for (int c = 0; c < 16; ++c) {
+#pragma unroll
+    for (int v = 0; v < 32; ++v) r[v] = lg * 512u + (uint32_t)(32 * c + v);
+    tmem_st_32x32b_x32(row + 32u * c, r);
+  }
+  tmem_st_wait();
+  uint32_t acc = 0;
+  if (!store) {
+    for (int64_t it = 0; it < iters; ++it)
+      for (int c = 0; c < 16; c += 2) {
+        uint32_t r2[32];
+        tmem_ld_32x32b_x32(row + 32u * c, r);
+        tmem_ld_32x32b_x32(row + 32u * (c + 1), r2);
+        tmem_ld_wait();
+#pragma unroll
+        for (int v = 0; v < 32; ++v) acc += r[v] + r2[v];
+      }
+  } else {
+    for (int64_t it = 0; it < iters; ++it) {
+      for (int c = 0; c < 16; ++c) {
+#pragma unroll
+        for (int v = 0; v < 32; ++v) r[v] = lg * 512u + (uint32_t)(32 * c + v) + (uint32_t)it;
+        tmem_st_32x32b_x32(row + 32u * c, r);
+      }
+      tmem_st_wait();
+    }
+    for (int c = 0; c < 16; ++c) {
+      tmem_ld_32x32b_x32(row + 32u * c, r);
+      tmem_ld_wait();
+#pragma unroll
+      for (int v = 0; v < 32; ++v) acc += r[v];
+    }
+  }
+  out[(size_t)blockIdx.x * 128 + threadIdx.x] = acc;
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    tmem_dealloc<1>(slot, 512);
+  }
+}
+
 static int stream_grid(int64_t n4) {
   const int sms = std::max(1, sm_count());
   const int64_t need = (n4 + (int64_t)kStreamThreads * kStreamUnroll - 1) / ((int64_t)kStreamThreads * kStreamUnroll);
@@ -225,6 +372,68 @@ static pm_status probe_launch(const pm_probe_args* a, void* buf0, void* buf1, vo
                                                Watchdog{w, watchdog_limit_ns()});
       return launch_status("tma2d_copy_kernel");
     }
+    case PM_PROBE_H2D:
+    case PM_PROBE_D2H: {
+      PM_REQUIRE(buf0 && buf1 && a->n > 0, PM_EINVAL, "copy-engine probe: null buffer or n <= 0");
+      PM_CUDA(cudaMemcpyAsync(buf1, buf0, (size_t)a->n,
+                              a->kind == PM_PROBE_H2D ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToHost, s));
+      return PM_OK;
+    }
+    case PM_PROBE_MMA: {
+      const int cg = (int)a->rows, dt = (int)a->cols, M = a->tile_c, N = a->tile_r;
+      PM_REQUIRE(buf0 && a->n >= 1 && a->n <= (1 << 19), PM_EINVAL, "mma probe: need buf0 and 1 <= n <= 2^19");
+      PM_REQUIRE(cg == 1 || cg == 2, PM_EINVAL, "mma probe: rows (cta_group) must be 1 or 2");
+      PM_REQUIRE(dt >= 0 && dt <= 2, PM_EINVAL, "mma probe: cols (dtype) must be a pm_dtype");
+      PM_REQUIRE(cg == 1 ? (M == 64 || M == 128) : (M == 128 || M == 256), PM_EINVAL,
+                 "mma probe: M %d not an instruction height for cta_group %d", M, cg);
+      PM_REQUIRE(N >= 16 && N <= 256 && N % 16 == 0, PM_EINVAL, "mma probe: N must be a multiple of 16 in [16,256]");
+      int grid = a->start ? (int)a->start : sm_count();
+      if (cg == 2) grid &= ~1;
+      PM_REQUIRE(grid >= cg, PM_EINVAL, "mma probe: grid too small");
+      unsigned int* w = watchdog_word();
+      PM_REQUIRE(w != nullptr, PM_ECUDA, "watchdog word unavailable");
+      Watchdog wd{w, watchdog_limit_ns()};
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = dim3(grid);
+      cfg.blockDim = dim3(128);
+      cfg.dynamicSmemBytes = 49 * 1024;
+      cfg.stream = s;
+      cudaLaunchAttribute attr[1];
+      attr[0].id = cudaLaunchAttributeClusterDimension;
+      attr[0].val.clusterDim.x = 2;
+      attr[0].val.clusterDim.y = 1;
+      attr[0].val.clusterDim.z = 1;
+      if (cg == 2) { cfg.attrs = attr; cfg.numAttrs = 1; }
+      uint32_t* out = static_cast<uint32_t*>(buf0);
+      cudaError_t e;
+#define PM_MMA_PROBE(CG, KIND)                                                                           \
+  do {                                                                                                   \
+    cudaFuncSetAttribute(mma_probe_kernel<CG, KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize, 49 * 1024); \
+    e = cudaLaunchKernelEx(&cfg, mma_probe_kernel<CG, KIND>, a->n, M, N, out, wd);                     \
+  } while (0)
+      if (cg == 1) {
+        if (dt == PM_BF16) PM_MMA_PROBE(1, 0); else if (dt == PM_FP32) PM_MMA_PROBE(1, 1); else PM_MMA_PROBE(1, 2);
+      } else {
+        if (dt == PM_BF16) PM_MMA_PROBE(2, 0); else if (dt == PM_FP32) PM_MMA_PROBE(2, 1); else PM_MMA_PROBE(2, 2);
+      }
+#undef PM_MMA_PROBE
+      if (e != cudaSuccess) return cuda_fail(e, "mma_probe_kernel");
+      return PM_OK;
+    }
+    case PM_PROBE_MBAR: {
+      PM_REQUIRE(buf0 && a->n >= 1, PM_EINVAL, "mbarrier probe: need buf0 and n >= 1");
+      unsigned int* w = watchdog_word();
+      PM_REQUIRE(w != nullptr, PM_ECUDA, "watchdog word unavailable");
+      mbar_probe_kernel<<<1, 64, 0, s>>>(a->n, static_cast<uint32_t*>(buf0), Watchdog{w, watchdog_limit_ns()});
+      return launch_status("mbar_probe_kernel");
+    }
+    case PM_PROBE_TMEM_LD:
+    case PM_PROBE_TMEM_ST: {
+      PM_REQUIRE(buf0 && a->n >= 1, PM_EINVAL, "tmem probe: need buf0 and n >= 1");
+      tmem_probe_kernel<<<sm_count(), 128, 0, s>>>(a->n, a->kind == PM_PROBE_TMEM_ST ? 1 : 0,
+                                                    static_cast<uint32_t*>(buf0));
+      return launch_status("tmem_probe_kernel");
+    }
     default:
       set_error("unknown probe kind %d", a->kind);
       return PM_EINVAL;
@@ -237,6 +446,19 @@ static double probe_bytes(const pm_probe_args* a) {
     case PM_PROBE_TRIAD: return 12.0 * (double)a->n;
     case PM_PROBE_TMA2D: return 8.0 * (double)a->rows * (double)a->cols;
     case PM_PROBE_PCHASE: return 4.0 * (double)a->hops;
+    case PM_PROBE_H2D:
+    case PM_PROBE_D2H: return (double)a->n;
+    case PM_PROBE_MMA: {
+      // FLOPs of the launch: issuing CTAs x n x 2 M N k_instr
+      const int cg = (int)a->rows, dt = (int)a->cols;
+      int grid = a->start ? (int)a->start : sm_count();
+      if (cg == 2) grid &= ~1;
+      const double kin = dt == PM_FP32 ? 8.0 : (dt == PM_BF16 ? 16.0 : 32.0);
+      return (double)(grid / cg) * (double)a->n * 2.0 * a->tile_c * a->tile_r * kin;
+    }
+    case PM_PROBE_MBAR: return 0.0;
+    case PM_PROBE_TMEM_LD:
+    case PM_PROBE_TMEM_ST: return (double)sm_count() * 128.0 * 512.0 * 4.0 * (double)a->n;
     default: return 0.0;
   }
 }
@@ -296,12 +518,12 @@ extern "C" pm_status pm_probe_run(const pm_probe_args* args, void* buf0, void* b
   out->min_s = t.front();
   out->bytes = probe_bytes(args);
   out->final_index = 0;
-  if (args->kind == PM_PROBE_PCHASE) {
+  if (args->kind == PM_PROBE_PCHASE || args->kind == PM_PROBE_MBAR) {
     uint32_t fi = 0;
-    PM_CUDA(cudaMemcpy(&fi, buf1, 4, cudaMemcpyDeviceToHost));
+    PM_CUDA(cudaMemcpy(&fi, args->kind == PM_PROBE_PCHASE ? buf1 : buf0, 4, cudaMemcpyDeviceToHost));
     out->final_index = fi;
   }
-  if (args->kind == PM_PROBE_TMA2D) {
+  if (args->kind == PM_PROBE_TMA2D || args->kind == PM_PROBE_MMA || args->kind == PM_PROBE_MBAR) {
     unsigned int* w = watchdog_word();
     unsigned int h[2] = {0, 0};
     PM_CUDA(cudaMemcpy(h, w, sizeof(h), cudaMemcpyDeviceToHost));
