@@ -135,6 +135,9 @@ def measure_sweep(shapes=(1024, 2048, 4096, 8192, 16384), dtypes=(1, 2), log=pri
         pchase.append(dict(W=W, hops=hops, ns_per_hop=1e9 * r["median_s"] / hops, final_index=r["final_index"]))
         del buf
     log("pointer chase done (%.0f s)" % (time.time() - t0))
+    # Blackwell instruction probes (Sec. V-A (iii)-(iv)) and the host link (Eq. 15)
+    instr = measure_instructions()
+    log("instruction and host-link probes done (%.0f s)" % (time.time() - t0))
     # config 3: every valid BF16 / FP8 configuration at M = N = K = s
     for s in shapes:
         A, B = S.gemm_operands(s, s, s, seed=2, dist="normal")
@@ -156,8 +159,69 @@ def measure_sweep(shapes=(1024, 2048, 4096, 8192, 16384), dtypes=(1, 2), log=pri
         torch.cuda.empty_cache()
         log("config 3 shape %d done (%d rows, %.0f s)" % (s, len(rows), time.time() - t0))
     props = torch.cuda.get_device_properties(0)
-    return dict(device=props.name, n_sm=props.multi_processor_count, rows=rows, pchase=pchase,
+    return dict(device=props.name, n_sm=props.multi_processor_count, rows=rows, pchase=pchase, instr=instr,
                 protocol="10 warm-ups; 100 timed runs (20-40 at 8192-16384, 20 for TMA), median of CUDA-event times")
+
+
+def measure_instructions() -> dict:
+    """tcgen05.mma time per instruction by shape and dtype (all SMs issuing),
+    mbarrier round trip, TMEM load/store bandwidth per SM, and copy-engine
+    transfer times over the host link for Eq. 15."""
+    n_sm = pm.sm_count()
+    out = {"mma": [], "host": []}
+    buf = torch.zeros(max(n_sm, 2) * 128, dtype=torch.int32, device="cuda")
+    n = 1 << 15
+    for dt in (0, 1, 2):
+        for cg, M, N in ((1, 64, 256), (1, 128, 128), (1, 128, 256), (2, 128, 256), (2, 256, 128), (2, 256, 256)):
+            r = pm.pm_probe_run(pm.probe_args(pm.PM_PROBE_MMA, n=n, tile_r=N, tile_c=M, rows=cg, cols=dt), buf,
+                                warmup=2, reps=5)
+            out["mma"].append(dict(dtype=dt, cta_group=cg, M=M, N=N, ns_per_instr=1e9 * r["median_s"] / n,
+                                   tflops=r["bytes"] / r["median_s"] / 1e12))
+    r = pm.pm_probe_run(pm.probe_args(pm.PM_PROBE_MBAR, n=1 << 16), buf, warmup=1, reps=5)
+    out["mbar_round_trip_ns"] = 1e9 * r["median_s"] / (1 << 16)
+    for kind, name in ((pm.PM_PROBE_TMEM_LD, "tmem_ld"), (pm.PM_PROBE_TMEM_ST, "tmem_st")):
+        r = pm.pm_probe_run(pm.probe_args(kind, n=256), buf, warmup=1, reps=5)
+        out[name + "_bytes_per_s_per_sm"] = r["bytes"] / r["median_s"] / n_sm
+    for k in range(12, 31, 2):
+        nb = 1 << k
+        h = torch.empty(nb, dtype=torch.uint8).pin_memory()
+        d = torch.empty(nb, dtype=torch.uint8, device="cuda")
+        r1 = pm.pm_probe_run(pm.probe_args(pm.PM_PROBE_H2D, n=nb), h, d, warmup=2, reps=10)
+        r2 = pm.pm_probe_run(pm.probe_args(pm.PM_PROBE_D2H, n=nb), d, h, warmup=2, reps=10)
+        out["host"].append(dict(bytes=nb, h2d_s=r1["median_s"], d2h_s=r2["median_s"]))
+        del h, d
+    out["eq15"] = fit_eq15(out["host"])
+    return out
+
+
+def fit_eq15(host_rows) -> dict:
+    """Least-squares fit of Eq. 15, T = S / B_dir + tau, per direction
+    (weighted by 1/T so small and large transfers count alike)."""
+    res = {}
+    S_ = np.array([r["bytes"] for r in host_rows], dtype=np.float64)
+    for d in ("h2d", "d2h"):
+        T = np.array([r[d + "_s"] for r in host_rows], dtype=np.float64)
+        A = np.stack([S_ / T, 1.0 / T], 1)          # rows scaled by 1/T: S/T * (1/B) + (1/T) * tau = 1
+        coef, *_ = np.linalg.lstsq(A, np.ones_like(T), rcond=None)
+        inv_b, tau = coef
+        pred = S_ * inv_b + tau
+        res[d] = dict(B_eff=1.0 / inv_b, tau_s=tau, mae_pct=float(np.mean(np.abs(pred - T) / T) * 100))
+    return res
+
+
+def probe_priors(instr: dict, n_sm: int, f_hz: float = 1.9e9) -> np.ndarray:
+    """Priors with the instruction-probe measurements in place of the paper's
+    printed values (Sec. V-A: parameters come from microbenchmarks): L_mma from
+    the time one tcgen05.mma holds the tensor pipe, L_mbar from half an mbarrier
+    round trip, TMEM read/write bandwidth per SM from the TMEM probes."""
+    th = prior_theta(n_sm, f_hz)
+    bf16 = [m for m in instr["mma"] if m["dtype"] == 1 and m["cta_group"] == 1 and m["M"] == 128 and m["N"] == 256]
+    if bf16:
+        th[9] = bf16[0]["ns_per_instr"] * 1e-9
+    th[12] = 0.5 * instr["mbar_round_trip_ns"] * 1e-9
+    th[10] = instr["tmem_ld_bytes_per_s_per_sm"]
+    th[11] = instr["tmem_st_bytes_per_s_per_sm"]
+    return th
 
 
 # ------------------------------------------------------------ autograd + fit
@@ -319,23 +383,29 @@ def main():
         table = json.load(f)
     rows = table["rows"]
     train, hold = split(len(rows))
-    th0 = prior_theta(n_sm)
+    th_paper = prior_theta(n_sm)
+    th0 = probe_priors(table["instr"], n_sm) if "instr" in table else th_paper
     obj = GpuObjective([r for r, m in zip(rows, train) if m], n_sm)
     theta, trace = fit(obj, th0, log=print)
     allobj = GpuObjective(rows, n_sm)
     pred0, pred = allobj.predict(th0), allobj.predict(theta)
     rep = dict(n_rows=len(rows), n_train=int(train.sum()), n_holdout=int(hold.sum()),
-               loss_trace=[trace[0], trace[-1]], theta=theta.tolist(),
+               loss_trace=[trace[0], trace[-1]], theta=theta.tolist(), prior=th0.tolist(),
+               mae_paper_prior=mae_by_family(rows, allobj.predict(th_paper)),
                mae_prior=mae_by_family(rows, pred0), mae_train=mae_by_family(rows, pred, train),
                mae_holdout=mae_by_family(rows, pred, hold), mae_all=mae_by_family(rows, pred),
                roofline_mae=roofline_mae(rows, dict(hbm=8.0e12, bf16=2.25e15, fp8=4.5e15, tf32=1.1e15)),
-               autotune=autotune_vs_best(rows, theta, n_sm), pchase=table.get("pchase"))
+               autotune=autotune_vs_best(rows, theta, n_sm), pchase=table.get("pchase"),
+               instr=table.get("instr"))
     save_theta(theta, dict(device=table.get("device"), n_sm=n_sm, fitted_on=os.path.basename(args.sweep),
                            mae_holdout=rep["mae_holdout"]), args.out)
     if args.report:
         with open(args.report, "w") as f:
             json.dump(rep, f, indent=1)
-    print(json.dumps({k: rep[k] for k in ("mae_prior", "mae_holdout", "mae_all", "roofline_mae")}, indent=1))
+    print(json.dumps({k: rep[k] for k in ("mae_paper_prior", "mae_prior", "mae_holdout", "mae_all", "roofline_mae")},
+                     indent=1))
+    if rep.get("instr"):
+        print(json.dumps({k: v for k, v in rep["instr"].items() if k not in ("host",)}, indent=1))
     for a in rep["autotune"]:
         print("autotune %(M)d dt=%(dtype)d pick=%(pick)s best=%(best)s pick/best=%(pick_over_best).3f "
               "TFLOP/s pick %(tflops_pick).0f best %(tflops_best).0f" % a)

@@ -81,3 +81,22 @@ def test_mae_definition():
     assert m["3_bf16"]["mae_pct"] == pytest.approx(10.0)
     assert m["2a_stream"]["mae_pct"] == pytest.approx(0.0)
     assert m["all"]["mae_pct"] == pytest.approx(20.0 / 3)
+
+
+def test_eq15_fit_recovers_link_parameters():
+    # Eq. 15: T = S / B_dir + tau; exact data gives back B and tau
+    rows = [dict(bytes=b, h2d_s=b / 2.1e11 + 8e-6, d2h_s=b / 1.93e11 + 9e-6) for b in [2 ** k for k in range(12, 31, 2)]]
+    f = C.fit_eq15(rows)
+    assert f["h2d"]["B_eff"] == pytest.approx(2.1e11, rel=1e-9) and f["h2d"]["tau_s"] == pytest.approx(8e-6, rel=1e-9)
+    assert f["d2h"]["B_eff"] == pytest.approx(1.93e11, rel=1e-9) and f["d2h"]["tau_s"] == pytest.approx(9e-6, rel=1e-9)
+
+
+def test_probe_priors_replace_only_measured_parameters():
+    instr = dict(mma=[dict(dtype=1, cta_group=1, M=128, N=256, ns_per_instr=70.0)], mbar_round_trip_ns=100.0,
+                 tmem_ld_bytes_per_s_per_sm=2e12, tmem_st_bytes_per_s_per_sm=1e12)
+    th = C.probe_priors(instr, N_SM)
+    base = C.prior_theta(N_SM)
+    assert th[9] == pytest.approx(70e-9) and th[12] == pytest.approx(50e-9)
+    assert th[10] == 2e12 and th[11] == 1e12
+    keep = [j for j in range(16) if j not in (9, 10, 11, 12)]
+    assert np.array_equal(th[keep], base[keep])
