@@ -101,9 +101,10 @@ typedef struct { float v[16]; } pm_params;
  *  PM_PROBE_MBAR   : two threads of different warps pass a token through two
  *                    mbarriers n times; final_index = completed round trips.
  *  PM_PROBE_TMEM_LD: every SM fills 128 lanes x 512 columns of TMEM with
- *                    lane*512 + column and reads them n times with
- *                    tcgen05.ld; ((uint32_t*)buf0)[sm*128 + lane] = the sum of
- *                    everything that lane read (mod 2^32).
+ *                    lane*512 + column; 8 warps (warp w: lanes 32*(w%4).., columns
+ *                    256*(w/4)..) read their part n times with tcgen05.ld;
+ *                    ((uint32_t*)buf0)[sm*256 + thread] = the sum of everything
+ *                    that thread read (mod 2^32).
  *  PM_PROBE_TMEM_ST: n passes of tcgen05.st writing lane*512 + column + pass,
  *                    then one read pass; buf0 as above (sum of the last pass).
  *  PM_PROBE_H2D / PM_PROBE_D2H: cudaMemcpyAsync of n bytes from buf0 to buf1

@@ -282,12 +282,17 @@ def mma_probe_value(n: int, dtype: int) -> np.float32:
 
 
 def tmem_probe_sums(iters: int, store: bool) -> np.ndarray:
-    """Per-lane sums (mod 2^32) of the TMEM probe: lanes hold lane*512 + column;
-    loads sum `iters` passes, stores leave lane*512 + column + iters - 1."""
-    lane = np.arange(128, dtype=np.int64)
-    col_sum = 511 * 512 // 2
+    """Per-thread sums (mod 2^32) of the TMEM probe for the 256 threads of one
+    SM: thread t covers lane 32*(w%4) + t%32 and columns 256*(w/4) .. +255
+    (w = t // 32); lanes hold lane*512 + column, loads sum `iters` passes,
+    stores leave lane*512 + column + iters - 1."""
+    t = np.arange(256, dtype=np.int64)
+    w = t // 32
+    lane = 32 * (w % 4) + t % 32
+    c0 = 256 * (w // 4)
+    col_sum = 256 * c0 + 255 * 256 // 2
     if store:
-        s = 512 * 512 * lane + col_sum + 512 * (iters - 1)
+        s = 256 * 512 * lane + col_sum + 256 * (iters - 1)
     else:
-        s = iters * (512 * 512 * lane + col_sum)
+        s = iters * (256 * 512 * lane + col_sum)
     return (s % (1 << 32)).astype(np.uint32)

@@ -169,7 +169,7 @@ def measure_instructions() -> dict:
     transfer times over the host link for Eq. 15."""
     n_sm = pm.sm_count()
     out = {"mma": [], "host": []}
-    buf = torch.zeros(max(n_sm, 2) * 128, dtype=torch.int32, device="cuda")
+    buf = torch.zeros(max(n_sm, 2) * 256, dtype=torch.int32, device="cuda")
     n = 1 << 15
     for dt in (0, 1, 2):
         for cg, M, N in ((1, 64, 256), (1, 128, 128), (1, 128, 256), (2, 128, 256), (2, 256, 128), (2, 256, 256)):
@@ -210,14 +210,17 @@ def fit_eq15(host_rows) -> dict:
 
 
 def probe_priors(instr: dict, n_sm: int, f_hz: float = 1.9e9) -> np.ndarray:
-    """Priors with the instruction-probe measurements in place of the paper's
-    printed values (Sec. V-A: parameters come from microbenchmarks): L_mma from
-    the time one tcgen05.mma holds the tensor pipe, L_mbar from half an mbarrier
-    round trip, TMEM read/write bandwidth per SM from the TMEM probes."""
+    """Priors with the probe measurements in place of the paper's printed
+    values where a probe measures the parameter itself (Sec. V-A: parameters
+    come from microbenchmarks): R_TC^SM per precision from the back-to-back
+    tcgen05.mma rate (one SM, M = 128, N = 256), L_mbar from half an mbarrier
+    round trip, TMEM read/write bandwidth per SM from the TMEM probes.  L_mma
+    keeps the printed instruction latency (the probe measures throughput)."""
     th = prior_theta(n_sm, f_hz)
-    bf16 = [m for m in instr["mma"] if m["dtype"] == 1 and m["cta_group"] == 1 and m["M"] == 128 and m["N"] == 256]
-    if bf16:
-        th[9] = bf16[0]["ns_per_instr"] * 1e-9
+    for dt, j in ((0, 6), (1, 7), (2, 8)):
+        m = [x for x in instr["mma"] if x["dtype"] == dt and x["cta_group"] == 1 and x["M"] == 128 and x["N"] == 256]
+        if m:
+            th[j] = m[0]["tflops"] * 1e12 / n_sm
     th[12] = 0.5 * instr["mbar_round_trip_ns"] * 1e-9
     th[10] = instr["tmem_ld_bytes_per_s_per_sm"]
     th[11] = instr["tmem_st_bytes_per_s_per_sm"]
@@ -368,6 +371,7 @@ def main():
     import argparse
     ap = argparse.ArgumentParser(description="measure the calibration table and fit the stage model")
     ap.add_argument("--measure", action="store_true")
+    ap.add_argument("--measure-instr", action="store_true", help="re-measure only the instruction/host probes")
     ap.add_argument("--sweep", default=SWEEP_PATH)
     ap.add_argument("--out", default=THETA_PATH)
     ap.add_argument("--report", default=None)
@@ -381,6 +385,10 @@ def main():
             json.dump(table, f)
     with open(args.sweep) as f:
         table = json.load(f)
+    if args.measure_instr:
+        table["instr"] = measure_instructions()
+        with open(args.sweep, "w") as f:
+            json.dump(table, f)
     rows = table["rows"]
     train, hold = split(len(rows))
     th_paper = prior_theta(n_sm)

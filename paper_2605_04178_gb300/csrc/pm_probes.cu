@@ -236,10 +236,12 @@ __global__ void __launch_bounds__(64) mbar_probe_kernel(int64_t iters, uint32_t*
 }
 
 // TMEM bandwidth: every SM fills its 128 lanes x 512 columns with
-// lane*512 + column, then `iters` passes of tcgen05.ld (store = 0) summing
-// what they read, or of tcgen05.st writing value + pass (store = 1) followed
-// by one summing read pass.  out[cta*128 + thread] = the sum (mod 2^32).
-__global__ void __launch_bounds__(128, 1) tmem_probe_kernel(int64_t iters, int store, uint32_t* __restrict__ out) {
+// lane*512 + column; 8 warps (two per 32-lane quarter, one per column half)
+// then make `iters` passes of tcgen05.ld, four 32-column loads in flight per
+// wait, summing what they read (store = 0), or of tcgen05.st writing
+// value + pass (store = 1) followed by one summing read pass.
+// out[cta*256 + thread] = the thread's sum (mod 2^32) over its 256 columns.
+__global__ void __launch_bounds__(256, 1) tmem_probe_kernel(int64_t iters, int store, uint32_t* __restrict__ out) {
   __shared__ uint32_t slot;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (warp == 0) {
@@ -249,43 +251,46 @@ __global__ void __launch_bounds__(128, 1) tmem_probe_kernel(int64_t iters, int s
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  const uint32_t row = tmem_base_row(slot, warp);
-  const uint32_t lg = (uint32_t)threadIdx.x;
+  const uint32_t row = tmem_base_row(slot, warp) + (uint32_t)(256 * (warp >> 2));
+  const uint32_t lg = (uint32_t)(32 * (warp & 3) + lane);
+  const uint32_t c0 = (uint32_t)(256 * (warp >> 2));
   uint32_t r[32];
-  for (int c = 0; c < 16; ++c) {
+  for (int c = 0; c < 8; ++c) {
 #pragma unroll
-    for (int v = 0; v < 32; ++v) r[v] = lg * 512u + (uint32_t)(32 * c + v);
+    for (int v = 0; v < 32; ++v) r[v] = lg * 512u + c0 + (uint32_t)(32 * c + v);
     tmem_st_32x32b_x32(row + 32u * c, r);
   }
   tmem_st_wait();
   uint32_t acc = 0;
   if (!store) {
     for (int64_t it = 0; it < iters; ++it)
-      for (int c = 0; c < 16; c += 2) {
-        uint32_t r2[32];
+      for (int c = 0; c < 8; c += 4) {
+        uint32_t r1[32], r2[32], r3[32];
         tmem_ld_32x32b_x32(row + 32u * c, r);
-        tmem_ld_32x32b_x32(row + 32u * (c + 1), r2);
+        tmem_ld_32x32b_x32(row + 32u * (c + 1), r1);
+        tmem_ld_32x32b_x32(row + 32u * (c + 2), r2);
+        tmem_ld_32x32b_x32(row + 32u * (c + 3), r3);
         tmem_ld_wait();
 #pragma unroll
-        for (int v = 0; v < 32; ++v) acc += r[v] + r2[v];
+        for (int v = 0; v < 32; ++v) acc += (r[v] + r1[v]) + (r2[v] + r3[v]);
       }
   } else {
     for (int64_t it = 0; it < iters; ++it) {
-      for (int c = 0; c < 16; ++c) {
+      for (int c = 0; c < 8; ++c) {
 #pragma unroll
-        for (int v = 0; v < 32; ++v) r[v] = lg * 512u + (uint32_t)(32 * c + v) + (uint32_t)it;
+        for (int v = 0; v < 32; ++v) r[v] = lg * 512u + c0 + (uint32_t)(32 * c + v) + (uint32_t)it;
         tmem_st_32x32b_x32(row + 32u * c, r);
       }
       tmem_st_wait();
     }
-    for (int c = 0; c < 16; ++c) {
+    for (int c = 0; c < 8; ++c) {
       tmem_ld_32x32b_x32(row + 32u * c, r);
       tmem_ld_wait();
 #pragma unroll
       for (int v = 0; v < 32; ++v) acc += r[v];
     }
   }
-  out[(size_t)blockIdx.x * 128 + threadIdx.x] = acc;
+  out[(size_t)blockIdx.x * 256 + threadIdx.x] = acc;
   tc_fence_before();
   __syncthreads();
   if (warp == 0) {
@@ -430,7 +435,7 @@ static pm_status probe_launch(const pm_probe_args* a, void* buf0, void* buf1, vo
     case PM_PROBE_TMEM_LD:
     case PM_PROBE_TMEM_ST: {
       PM_REQUIRE(buf0 && a->n >= 1, PM_EINVAL, "tmem probe: need buf0 and n >= 1");
-      tmem_probe_kernel<<<sm_count(), 128, 0, s>>>(a->n, a->kind == PM_PROBE_TMEM_ST ? 1 : 0,
+      tmem_probe_kernel<<<sm_count(), 256, 0, s>>>(a->n, a->kind == PM_PROBE_TMEM_ST ? 1 : 0,
                                                     static_cast<uint32_t*>(buf0));
       return launch_status("tmem_probe_kernel");
     }

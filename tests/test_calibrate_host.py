@@ -92,11 +92,13 @@ def test_eq15_fit_recovers_link_parameters():
 
 
 def test_probe_priors_replace_only_measured_parameters():
-    instr = dict(mma=[dict(dtype=1, cta_group=1, M=128, N=256, ns_per_instr=70.0)], mbar_round_trip_ns=100.0,
-                 tmem_ld_bytes_per_s_per_sm=2e12, tmem_st_bytes_per_s_per_sm=1e12)
+    instr = dict(mma=[dict(dtype=d, cta_group=1, M=128, N=256, tflops=t) for d, t in ((0, 1200.0), (1, 2400.0),
+                                                                                        (2, 4800.0))],
+                 mbar_round_trip_ns=100.0, tmem_ld_bytes_per_s_per_sm=2e12, tmem_st_bytes_per_s_per_sm=1e12)
     th = C.probe_priors(instr, N_SM)
     base = C.prior_theta(N_SM)
-    assert th[9] == pytest.approx(70e-9) and th[12] == pytest.approx(50e-9)
-    assert th[10] == 2e12 and th[11] == 1e12
-    keep = [j for j in range(16) if j not in (9, 10, 11, 12)]
+    assert th[6] == pytest.approx(1.2e15 / N_SM) and th[7] == pytest.approx(2.4e15 / N_SM)
+    assert th[8] == pytest.approx(4.8e15 / N_SM)
+    assert th[12] == pytest.approx(50e-9) and th[10] == 2e12 and th[11] == 1e12
+    keep = [j for j in range(16) if j not in (6, 7, 8, 10, 11, 12)]
     assert np.array_equal(th[keep], base[keep])

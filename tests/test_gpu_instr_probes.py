@@ -46,10 +46,10 @@ def test_mbar_probe_round_trips(lib, n):
 @pytest.mark.parametrize("iters", [1, 3, 257])
 def test_tmem_probe_checksums(lib, kind, store, iters):
     sms = lib.sm_count()
-    out = torch.zeros(sms * 128, dtype=torch.int32, device="cuda")
+    out = torch.zeros(sms * 256, dtype=torch.int32, device="cuda")
     lib.pm_probe_run(lib.probe_args(kind, n=iters), out, warmup=0, reps=1)
-    got = out.cpu().numpy().view(np.uint32).reshape(sms, 128)
-    assert np.array_equal(got, np.broadcast_to(O.tmem_probe_sums(iters, store), (sms, 128)))
+    got = out.cpu().numpy().view(np.uint32).reshape(sms, 256)
+    assert np.array_equal(got, np.broadcast_to(O.tmem_probe_sums(iters, store), (sms, 256)))
 
 
 @pytest.mark.parametrize("nbytes", [16, 1000, 1 << 26])
