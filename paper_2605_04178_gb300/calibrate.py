@@ -266,8 +266,9 @@ class GpuObjective:
         return out.cpu().numpy().astype(np.float64)
 
 
-def fit(objective, theta0, prior=None, reg=1e-4, iters=400, log=None):
-    """Minimise objective(theta) + reg * ||ln theta - ln prior||^2 over phi = ln theta (L-BFGS)."""
+def fit(objective, theta0, prior=None, reg=1e-4, iters=500, rounds=3, log=None):
+    """Minimise objective(theta) + reg * ||ln theta - ln prior||^2 over phi = ln theta
+    (L-BFGS, restarted `rounds` times from its own end point)."""
     theta0 = np.asarray(theta0, dtype=np.float64)
     prior = theta0 if prior is None else np.asarray(prior, dtype=np.float64)
     phi = torch.tensor(np.log(theta0), dtype=torch.float64, requires_grad=True)
@@ -283,7 +284,8 @@ def fit(objective, theta0, prior=None, reg=1e-4, iters=400, log=None):
         trace.append(float(loss.item()))
         return loss
 
-    opt.step(closure)
+    for _ in range(rounds):
+        opt.step(closure)
     if log:
         log("fit: %d evaluations, loss %.4g -> %.4g" % (len(trace), trace[0], trace[-1]))
     return np.exp(phi.detach().numpy()), trace
