@@ -53,17 +53,24 @@ typedef enum { PM_KIND_GEMM = 0, PM_KIND_COPY = 1, PM_KIND_TRIAD = 2, PM_KIND_TM
  *         shared-memory ring, cta_group 1 (one SM) or 2 (CTA pair, the pair
  *         covers 2*BM x BN), dtype a pm_dtype.  These are the model inputs of
  *         Sec. III-E (b_M, b_N, b_K, K_tiles, bytes per CTA; P = 1).
+ *         tmem_a selects the TMEM strategy of Sec. III-A.1: 0 = A (only the
+ *         accumulators in TMEM, both operands read from shared memory),
+ *         1 = B (each stage's A tile also copied into TMEM by tcgen05.cp and
+ *         read from there by the MMAs).
  *  COPY/TRIAD: M = FP32 elements.  TMA2D: M x N FP32 matrix in BM x BN tiles.
+ *  Probe kinds take tmem_a = 0.
  * Valid GEMM tile space: BM, BN in {64,128,256}; BK in {32,64} (FP32) or
  * {64,128} (BF16, FP8); stages 2..6; cta_group 1..2; stages * stage bytes
  * <= 227 KiB - 2 KiB where stage bytes = l*e*BK*(BM + BN/cta_group) with e the
  * element size and l = 2 for FP32 (hi and lo), else 1; ceil(BM/128)*BN <= 512
- * TMEM columns (the 256 KB TMEM limit of Sec. III-A.1). */
+ * TMEM columns (the 256 KB TMEM limit of Sec. III-A.1).  Strategy B further
+ * needs cta_group 1, BM >= 128 and ceil(BM/128)*(BN + stages*l*BK*e/4) <= 512
+ * columns (accumulator plus the A ring in TMEM). */
 typedef struct {
   int32_t M, N, K;
   int16_t BM, BN, BK;
   int8_t stages, cta_group, dtype, kind;
-  int16_t reserved;      /* must be 0 */
+  int16_t tmem_a;        /* TMEM strategy: 0 = A, 1 = B */
 } pm_cfg;
 
 /* Model parameters theta, SI units (Sec. III-A and Eq. 16):

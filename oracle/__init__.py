@@ -74,10 +74,10 @@ def _load():
             lib.orc_triad_f32.argtypes = [P, P, ctypes.c_float, i64, P]
             lib.orc_pchase.argtypes = [P, i64, ctypes.c_uint32, i64]
             lib.orc_pchase.restype = ctypes.c_uint32
-            lib.orc_cfg_valid.argtypes = [ctypes.c_int] * 6
+            lib.orc_cfg_valid.argtypes = [ctypes.c_int] * 7
             lib.orc_cfg_valid.restype = ctypes.c_int
-            lib.orc_model_batch.argtypes = [i64] + [P] * 10 + [P, ctypes.c_int, P, P]
-            lib.orc_model_loss_grad.argtypes = [i64] + [P] * 10 + [P, ctypes.c_int, P, P, P]
+            lib.orc_model_batch.argtypes = [i64] + [P] * 11 + [P, ctypes.c_int, P, P]
+            lib.orc_model_loss_grad.argtypes = [i64] + [P] * 11 + [P, ctypes.c_int, P, P, P]
             lib.orc_autotune.argtypes = [i64, P, ctypes.c_int, P, ctypes.c_int, P, P]
             lib.orc_grouped_predict.argtypes = [ctypes.c_int, P, ctypes.c_int32, ctypes.c_int32, P, P,
                                                 ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
@@ -175,11 +175,12 @@ def pchase(buf: np.ndarray, stride_words: int, start: int, hops: int) -> int:
 
 
 # ----------------------------------------------------------------------------- model
-def cfg_valid(BM, BN, BK, s, g, dtype) -> bool:
-    return bool(_load().orc_cfg_valid(int(BM), int(BN), int(BK), int(s), int(g), int(dtype)))
+def cfg_valid(BM, BN, BK, s, g, dtype, tmem_a=0) -> bool:
+    """Tile-space validity; tmem_a = 1 asks for TMEM strategy B (Sec. III-A.1)."""
+    return bool(_load().orc_cfg_valid(int(BM), int(BN), int(BK), int(s), int(g), int(dtype), int(tmem_a)))
 
 
-_FIELDS = ("M", "N", "K", "BM", "BN", "BK", "stages", "cta_group", "dtype", "kind")
+_FIELDS = ("M", "N", "K", "BM", "BN", "BK", "stages", "cta_group", "dtype", "kind", "tmem_a")
 
 
 def _soa(cfgs: dict):

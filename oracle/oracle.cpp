@@ -234,6 +234,7 @@ enum { DT_FP32 = 0, DT_BF16 = 1, DT_FP8 = 2 };
 struct Cfg {
   i64 M, N, K;
   int BM, BN, BK, s, g, dtype, kind;
+  int tmem_a = 0;   // TMEM strategy of Sec. III-A.1: 0 = A, 1 = B (A operand also in TMEM)
 };
 
 static double elem_bytes(int dt) { return dt == DT_FP32 ? 4.0 : (dt == DT_BF16 ? 2.0 : 1.0); }
@@ -249,7 +250,7 @@ static int instr_k(int dt) { return dt == DT_FP32 ? 8 : (dt == DT_BF16 ? 16 : 32
 // accumulators beyond 256 KB of TMEM per SM would spill).
 static const i64 SMEM_OPTIN = 232448;     // 227 KiB per block
 static const i64 SMEM_RESERVE = 2048;     // barriers, TMEM slot, alignment
-extern "C" int orc_cfg_valid(int BM, int BN, int BK, int s, int g, int dtype) {
+extern "C" int orc_cfg_valid(int BM, int BN, int BK, int s, int g, int dtype, int tmem_a) {
   const bool bm_ok = BM == 64 || BM == 128 || BM == 256;
   const bool bn_ok = BN == 64 || BN == 128 || BN == 256;
   bool bk_ok;
@@ -261,7 +262,14 @@ extern "C" int orc_cfg_valid(int BM, int BN, int BK, int s, int g, int dtype) {
   if (s * stage > SMEM_OPTIN - SMEM_RESERVE) return 0;
   const i64 acc_cols = ceil_div(BM, 128) * BN;   // FP32 accumulator columns of one tile
   if (acc_cols > 512) return 0;
-  return 1;
+  if (tmem_a == 0) return 1;
+  if (tmem_a != 1) return 0;
+  // Strategy B: the A tile of every stage also lives in TMEM, 128 rows per
+  // block in the lanes and l*BK*e bytes of K in 32-bit columns; built for
+  // single-SM tiles of whole 128-row blocks.
+  if (g != 1 || BM < 128) return 0;
+  const i64 a_cols = (i64)s * ceil_div(BM, 128) * (i64)(load_mult(dtype) * elem_bytes(dtype)) * BK / 4;
+  return acc_cols + a_cols <= 512 ? 1 : 0;
 }
 
 static inline bool operator<=(const Dual& a, const Dual& b) { return a.v <= b.v; }
@@ -285,7 +293,12 @@ static void stage_terms(const Cfg& c, i64 Kt, const T* th, T& Tstep, T& Tstore) 
   // while the accumulator traffic D is counted once per K-step.
   const double D = 4.0 * c.BM * c.BN;
   const double n_instr = np * (double)(c.BK / instr_k(c.dtype)) * (double)ceil_div(c.BM, 128);
-  const T T_tmem = D / th[10] + n_instr * th[9] + D / th[11];
+  // Strategy B ("A and accumulators in TMEM", Sec. III-A.1) adds the A tile's
+  // TMEM traffic: written once per K-step by the copy into TMEM (l planes),
+  // read by every tensor pass.
+  const double DA_w = c.tmem_a ? l * e * c.BM * c.BK : 0.0;
+  const double DA_r = c.tmem_a ? np * e * c.BM * c.BK : 0.0;
+  const T T_tmem = (D + DA_r) / th[10] + n_instr * th[9] + (D + DA_w) / th[11];
   // T_TMEM_mgmt amortised over the K-steps (Sec. III-A.5).
   const T T_mgmt = th[13] / lift<T>((double)Kt);
   // Eqs. 3 and 6: S_mode = 1 for one SM, S_2SM for a CTA pair.
@@ -355,10 +368,10 @@ static T model_any(const Cfg& c, const T* th, int n_sm) {
 
 static Cfg make_cfg(i64 i, const int32_t* M, const int32_t* N, const int32_t* K, const int32_t* BM,
                     const int32_t* BN, const int32_t* BK, const int32_t* s, const int32_t* g,
-                    const int32_t* dt, const int32_t* kind) {
+                    const int32_t* dt, const int32_t* kind, const int32_t* ta) {
   Cfg c;
   c.M = M[i]; c.N = N[i]; c.K = K[i]; c.BM = BM[i]; c.BN = BN[i]; c.BK = BK[i];
-  c.s = s[i]; c.g = g[i]; c.dtype = dt[i]; c.kind = kind[i];
+  c.s = s[i]; c.g = g[i]; c.dtype = dt[i]; c.kind = kind[i]; c.tmem_a = ta[i];
   return c;
 }
 
@@ -366,11 +379,11 @@ static Cfg make_cfg(i64 i, const int32_t* M, const int32_t* N, const int32_t* K,
 extern "C" void orc_model_batch(i64 n, const int32_t* M, const int32_t* N, const int32_t* K,
                                 const int32_t* BM, const int32_t* BN, const int32_t* BK,
                                 const int32_t* s, const int32_t* g, const int32_t* dt,
-                                const int32_t* kind, const double* theta, int n_sm,
+                                const int32_t* kind, const int32_t* tmem_a, const double* theta, int n_sm,
                                 double* t_out, double* grad) {
 #pragma omp parallel for schedule(static)
   for (i64 i = 0; i < n; ++i) {
-    const Cfg c = make_cfg(i, M, N, K, BM, BN, BK, s, g, dt, kind);
+    const Cfg c = make_cfg(i, M, N, K, BM, BN, BK, s, g, dt, kind, tmem_a);
     if (grad) {
       Dual th[NP];
       for (int j = 0; j < NP; ++j) th[j] = dvar(theta[j], j);
@@ -389,10 +402,10 @@ extern "C" void orc_model_batch(i64 n, const int32_t* M, const int32_t* N, const
 extern "C" void orc_model_loss_grad(i64 n, const int32_t* M, const int32_t* N, const int32_t* K,
                                     const int32_t* BM, const int32_t* BN, const int32_t* BK,
                                     const int32_t* s, const int32_t* g, const int32_t* dt,
-                                    const int32_t* kind, const double* theta, int n_sm,
+                                    const int32_t* kind, const int32_t* tmem_a, const double* theta, int n_sm,
                                     const double* t_meas, double* loss, double* grad) {
   std::vector<double> t(n), gr((size_t)n * NP);
-  orc_model_batch(n, M, N, K, BM, BN, BK, s, g, dt, kind, theta, n_sm, t.data(), gr.data());
+  orc_model_batch(n, M, N, K, BM, BN, BK, s, g, dt, kind, tmem_a, theta, n_sm, t.data(), gr.data());
   double L = 0.0;
   double G[NP] = {0};
   for (i64 i = 0; i < n; ++i) {
@@ -424,7 +437,7 @@ extern "C" void orc_autotune(i64 n, const int32_t* MNK, int dtype, const double*
         for (int k = 0; k < 2; ++k)
           for (int s = 2; s <= 6; ++s)
             for (int g = 1; g <= 2; ++g) {
-              if (!orc_cfg_valid(BMS[a], BNS[b], BKS[dtype][k], s, g, dtype)) continue;
+              if (!orc_cfg_valid(BMS[a], BNS[b], BKS[dtype][k], s, g, dtype, 0)) continue;
               Cfg c;
               c.M = MNK[3 * i]; c.N = MNK[3 * i + 1]; c.K = MNK[3 * i + 2];
               c.BM = BMS[a]; c.BN = BNS[b]; c.BK = BKS[dtype][k]; c.s = s; c.g = g;
@@ -486,7 +499,7 @@ extern "C" double orc_grouped_autotune(int G, const int32_t* Mg, int32_t N, int3
           double bq = INFINITY;
           for (int a = 0; a < 3; ++a)
             for (int b = 0; b < 3; ++b) {
-              if (!orc_cfg_valid(BMS[a], BNS[b], BK, s, g, dtype)) continue;
+              if (!orc_cfg_valid(BMS[a], BNS[b], BK, s, g, dtype, 0)) continue;
               Cfg c;
               c.M = Mg[q]; c.N = N; c.K = K; c.BM = BMS[a]; c.BN = BNS[b]; c.BK = BK; c.s = s;
               c.g = g; c.dtype = dtype; c.kind = K_GEMM;

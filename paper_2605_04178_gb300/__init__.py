@@ -27,7 +27,7 @@ PM_PROBE_H2D, PM_PROBE_D2H, PM_PROBE_MMA, PM_PROBE_MBAR, PM_PROBE_TMEM_LD, PM_PR
 # numpy view of pm_cfg (24 bytes)
 CFG_DTYPE = np.dtype([("M", "<i4"), ("N", "<i4"), ("K", "<i4"), ("BM", "<i2"), ("BN", "<i2"), ("BK", "<i2"),
                       ("stages", "i1"), ("cta_group", "i1"), ("dtype", "i1"), ("kind", "i1"),
-                      ("reserved", "<i2")], align=True)
+                      ("tmem_a", "<i2")], align=True)
 assert CFG_DTYPE.itemsize == 24
 
 
@@ -35,7 +35,7 @@ class pm_cfg(ctypes.Structure):
     _fields_ = [("M", ctypes.c_int32), ("N", ctypes.c_int32), ("K", ctypes.c_int32), ("BM", ctypes.c_int16),
                 ("BN", ctypes.c_int16), ("BK", ctypes.c_int16), ("stages", ctypes.c_int8),
                 ("cta_group", ctypes.c_int8), ("dtype", ctypes.c_int8), ("kind", ctypes.c_int8),
-                ("reserved", ctypes.c_int16)]
+                ("tmem_a", ctypes.c_int16)]
 
 
 class pm_params(ctypes.Structure):
@@ -150,9 +150,11 @@ def params(theta) -> pm_params:
     return p
 
 
-def cfg(M, N, K, BM=128, BN=128, BK=64, stages=4, cta_group=1, dtype=PM_BF16, kind=PM_KIND_GEMM) -> pm_cfg:
+def cfg(M, N, K, BM=128, BN=128, BK=64, stages=4, cta_group=1, dtype=PM_BF16, kind=PM_KIND_GEMM,
+        tmem_a=0) -> pm_cfg:
+    """One pm_cfg; tmem_a = 1 selects TMEM strategy B (A operand copied into tensor memory)."""
     return pm_cfg(int(M), int(N), int(K), int(BM), int(BN), int(BK), int(stages), int(cta_group), int(dtype),
-                  int(kind), 0)
+                  int(kind), int(tmem_a))
 
 
 def cfg_array(fields: dict) -> np.ndarray:

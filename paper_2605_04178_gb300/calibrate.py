@@ -9,6 +9,8 @@ Pieces
     1 GiB matrix, pointer chase 16 KB..1 GB) and config 3 (every valid BF16 and
     FP8 tile configuration at M = N = K in {1024..16384}), each timed on the
     device by the library's own harness (pm_gemm_bench / pm_probe_run).
+  * measure_tmem_b(): the same GEMM classes under TMEM strategy B (A operand
+    copied into tensor memory, Sec. III-A.1) over the strategy-B tile space.
   * StageModelLoss: torch.autograd.Function whose forward is the batched model
     on the GPU and whose backward is the hand-written adjoint kernel
     (pm_model_grad): mean squared log error and its gradient in theta.
@@ -34,7 +36,7 @@ import synthetic as S
 HERE = os.path.dirname(os.path.abspath(__file__))
 THETA_PATH = os.path.join(HERE, "theta_gb300.json")
 SWEEP_PATH = os.path.join(HERE, "data", "sweep_gb300.json")
-FIELDS = ("M", "N", "K", "BM", "BN", "BK", "stages", "cta_group", "dtype", "kind")
+FIELDS = ("M", "N", "K", "BM", "BN", "BK", "stages", "cta_group", "dtype", "kind", "tmem_a")
 
 
 def prior_theta(n_sm: int, f_hz: float = 1.9e9) -> np.ndarray:
@@ -65,14 +67,15 @@ def family_of(r: dict) -> str:
         return "2a_stream"
     if r["kind"] == pm.PM_KIND_TMA2D:
         return "2b_tma"
-    return {0: "1_fp32", 1: "3_bf16", 2: "3_fp8"}[int(r["dtype"])]
+    fam = {0: "1_fp32", 1: "3_bf16", 2: "3_fp8"}[int(r["dtype"])]
+    return fam + "_tmemB" if r.get("tmem_a", 0) else fam
 
 
 # ------------------------------------------------------------------ measuring
-def _valid(dt, t):
+def _valid(dt, t, tmem_a=0):
     bm, bn, bk, s, g = t
     try:
-        pm.pm_gemm_run(pm.cfg(256, 256, 256, bm, bn, bk, s, g, dt), None, None, None)
+        pm.pm_gemm_run(pm.cfg(256, 256, 256, bm, bn, bk, s, g, dt, tmem_a=tmem_a), None, None, None)
     except pm.PMError as e:
         return e.status != pm.PM_EUNSUPPORTED
     return True
@@ -91,7 +94,8 @@ def measure_sweep(shapes=(1024, 2048, 4096, 8192, 16384), dtypes=(1, 2), log=pri
         if not _valid(0, t):
             continue
         r = ops.bench(pm.cfg(512, 512, 512, *t, dtype=0), C, warmup=10, reps=100)
-        rows.append(dict(zip(FIELDS, (512, 512, 512, *t, 0, 0)), t=r["median_s"], p25=r["p25_s"], p75=r["p75_s"]))
+        rows.append(dict(zip(FIELDS, (512, 512, 512, *t, 0, 0, 0)), t=r["median_s"], p25=r["p25_s"],
+                         p75=r["p75_s"]))
     log("config 1 done (%d rows, %.0f s)" % (len(rows), time.time() - t0))
     # config 2: copy / triad over 2^20 .. 2^30 FP32 elements
     nmax = 2 ** 30
@@ -152,15 +156,44 @@ def measure_sweep(shapes=(1024, 2048, 4096, 8192, 16384), dtypes=(1, 2), log=pri
                 if not _valid(dt, t):
                     continue
                 r = ops.bench(pm.cfg(s, s, s, *t, dtype=dt), C, warmup=10, reps=reps)
-                rows.append(dict(zip(FIELDS, (s, s, s, *t, dt, 0)), t=r["median_s"], p25=r["p25_s"],
+                rows.append(dict(zip(FIELDS, (s, s, s, *t, dt, 0, 0)), t=r["median_s"], p25=r["p25_s"],
                                  p75=r["p75_s"]))
             del ops
         del Ad, Bd, C
         torch.cuda.empty_cache()
         log("config 3 shape %d done (%d rows, %.0f s)" % (s, len(rows), time.time() - t0))
+    rows += measure_tmem_b(shapes, dtypes, log)
     props = torch.cuda.get_device_properties(0)
     return dict(device=props.name, n_sm=props.multi_processor_count, rows=rows, pchase=pchase, instr=instr,
                 protocol="10 warm-ups; 100 timed runs (20-40 at 8192-16384, 20 for TMA), median of CUDA-event times")
+
+
+def measure_tmem_b(shapes=(1024, 2048, 4096, 8192, 16384), dtypes=(1, 2), log=print) -> list:
+    """GEMM rows under TMEM strategy B: FP32 512^3 and BF16/FP8 at M = N = K in
+    `shapes`, every strategy-B tile, same protocol as the strategy-A rows."""
+    rows = []
+    t0 = time.time()
+    cases = [(512, (0,))] + [(s, tuple(dtypes)) for s in shapes]
+    for s, dts in cases:
+        A, B = S.gemm_operands(s, s, s, seed=0 if s == 512 else 2, dist="uniform" if s == 512 else "normal")
+        Ad, Bd = torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()
+        del A, B
+        C = torch.empty(s, s, dtype=torch.float32, device="cuda")
+        reps = 100 if s <= 4096 else (40 if s <= 8192 else 20)
+        for dt in dts:
+            ops = pm.GemmOperands(dt, s, s, s)
+            ops.prepare(Ad, Bd)
+            for t in S.tile_space(dt):
+                if not _valid(dt, t, 1):
+                    continue
+                r = ops.bench(pm.cfg(s, s, s, *t, dtype=dt, tmem_a=1), C, warmup=10, reps=reps)
+                rows.append(dict(zip(FIELDS, (s, s, s, *t, dt, 0, 1)), t=r["median_s"], p25=r["p25_s"],
+                                 p75=r["p75_s"]))
+            del ops
+        del Ad, Bd, C
+        torch.cuda.empty_cache()
+        log("strategy B shape %d done (%d rows, %.0f s)" % (s, len(rows), time.time() - t0))
+    return rows
 
 
 def measure_instructions() -> dict:
@@ -251,7 +284,7 @@ class GpuObjective:
 
     def __init__(self, rows, n_sm):
         self.n = len(rows)
-        cols = {f: np.array([r[f] for r in rows], dtype=np.int64) for f in FIELDS}
+        cols = {f: np.array([r.get(f, 0) for r in rows], dtype=np.int64) for f in FIELDS}
         self.cfg = pm.cfg_tensor(cols)
         self.t = torch.tensor([r["t"] for r in rows], dtype=torch.float32, device="cuda")
         self.ws = torch.empty(pm.pm_model_grad_workspace(self.n) // 8 + 1, dtype=torch.float64, device="cuda")
@@ -340,7 +373,7 @@ def autotune_vs_best(rows, theta, n_sm) -> list:
     """For each measured GEMM shape: the model's pick (GPU autotuner) against the
     fastest measured configuration."""
     out = []
-    gem = [r for r in rows if r["kind"] == pm.PM_KIND_GEMM]
+    gem = [r for r in rows if r["kind"] == pm.PM_KIND_GEMM and not r.get("tmem_a", 0)]
     keys = sorted(set((r["M"], r["N"], r["K"], r["dtype"]) for r in gem))
     for (M, N, K, dt) in keys:
         cand = {(r["BM"], r["BN"], r["BK"], r["stages"], r["cta_group"]): r["t"] for r in gem
@@ -359,6 +392,29 @@ def autotune_vs_best(rows, theta, n_sm) -> list:
     return out
 
 
+def tmem_strategy_report(rows, t_pred) -> list:
+    """Per GEMM shape with strategy-B rows: the fastest measured tile of each
+    TMEM strategy and what the model predicts for the two (Sec. III-A.1: B
+    relieves shared memory but adds TMEM traffic)."""
+    out = []
+    keys = sorted(set((r["M"], r["dtype"]) for r in rows if r["kind"] == pm.PM_KIND_GEMM and r.get("tmem_a", 0)))
+    for (M, dt) in keys:
+        best = {}
+        for ta in (0, 1):
+            idx = [i for i, r in enumerate(rows) if r["kind"] == pm.PM_KIND_GEMM and r["M"] == M and
+                   r["dtype"] == dt and r.get("tmem_a", 0) == ta]
+            if not idx:
+                break
+            i = min(idx, key=lambda j: rows[j]["t"])
+            ip = min(idx, key=lambda j: t_pred[j])
+            best[ta] = dict(tile=[rows[i][f] for f in ("BM", "BN", "BK", "stages", "cta_group")], t=rows[i]["t"],
+                            t_pred_of_best=float(t_pred[i]), model_pick_t=rows[ip]["t"])
+        if len(best) == 2:
+            out.append(dict(M=M, dtype=dt, A=best[0], B=best[1], measured_B_over_A=best[1]["t"] / best[0]["t"],
+                            predicted_B_over_A=best[1]["t_pred_of_best"] / best[0]["t_pred_of_best"]))
+    return out
+
+
 def save_theta(theta, meta, path=THETA_PATH):
     with open(path, "w") as f:
         json.dump(dict(theta=[float(v) for v in theta], **meta), f, indent=1)
@@ -374,6 +430,7 @@ def main():
     ap = argparse.ArgumentParser(description="measure the calibration table and fit the stage model")
     ap.add_argument("--measure", action="store_true")
     ap.add_argument("--measure-instr", action="store_true", help="re-measure only the instruction/host probes")
+    ap.add_argument("--measure-tmem-b", action="store_true", help="re-measure only the strategy-B GEMM rows")
     ap.add_argument("--sweep", default=SWEEP_PATH)
     ap.add_argument("--out", default=THETA_PATH)
     ap.add_argument("--report", default=None)
@@ -389,6 +446,10 @@ def main():
         table = json.load(f)
     if args.measure_instr:
         table["instr"] = measure_instructions()
+    if args.measure_tmem_b:
+        table["rows"] = [r for r in table["rows"] if not r.get("tmem_a", 0)] + \
+            measure_tmem_b(tuple(int(s) for s in args.shapes.split(",")))
+    if args.measure_instr or args.measure_tmem_b:
         with open(args.sweep, "w") as f:
             json.dump(table, f)
     rows = table["rows"]
@@ -406,7 +467,7 @@ def main():
                mae_holdout=mae_by_family(rows, pred, hold), mae_all=mae_by_family(rows, pred),
                roofline_mae=roofline_mae(rows, dict(hbm=8.0e12, bf16=2.25e15, fp8=4.5e15, tf32=1.1e15)),
                autotune=autotune_vs_best(rows, theta, n_sm), pchase=table.get("pchase"),
-               instr=table.get("instr"))
+               instr=table.get("instr"), tmem_strategy=tmem_strategy_report(rows, pred))
     save_theta(theta, dict(device=table.get("device"), n_sm=n_sm, fitted_on=os.path.basename(args.sweep),
                            mae_holdout=rep["mae_holdout"]), args.out)
     if args.report:
@@ -419,6 +480,10 @@ def main():
     for a in rep["autotune"]:
         print("autotune %(M)d dt=%(dtype)d pick=%(pick)s best=%(best)s pick/best=%(pick_over_best).3f "
               "TFLOP/s pick %(tflops_pick).0f best %(tflops_best).0f" % a)
+    for r in rep["tmem_strategy"]:
+        print("TMEM strategy %d dt=%d: best A %s %.3g s, best B %s %.3g s, measured B/A %.3f, predicted %.3f" % (
+            r["M"], r["dtype"], r["A"]["tile"], r["A"]["t"], r["B"]["tile"], r["B"]["t"], r["measured_B_over_A"],
+            r["predicted_B_over_A"]))
 
 
 if __name__ == "__main__":

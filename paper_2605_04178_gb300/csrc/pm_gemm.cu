@@ -12,6 +12,10 @@
 //               after the last K-step commits to acc_full[buffer];
 //   warps 2..5  epilogue: wait acc_full, tcgen05.ld 32-column chunks, scale,
 //               store FP32 C (masked at the M/N edges), release the buffer.
+// TMEM strategy A keeps only the accumulators in tensor memory and feeds both
+// operands from shared memory; strategy B (one SM, 128-row blocks) first
+// copies each A K-slice of the stage into tensor memory with tcgen05.cp and
+// the MMAs read A from there (Sec. III-A.1, "two TMEM strategies").
 // Two TMEM accumulator buffers when they fit, so the epilogue of tile i
 // overlaps the main loop of tile i+1.  Each CTA of a pair loads its own A
 // rows and half of B (traffic 2 M_A + M_B per pair, no multicast); the pair
@@ -61,6 +65,7 @@ struct GemmParams {
   int sw;                          // swizzle span in bytes (64 or 128)
   int n_atoms;                     // swizzle atoms along K per stage
   int acc_cols, nbuf, alloc_cols;  // TMEM columns per accumulator buffer (largest tile)
+  int a_col0, a_cols;              // strategy B: first TMEM column of the A ring, columns per stage
   uint32_t stage_bytes;            // ring stride (largest tile)
   uint32_t ab_fmt;                 // tcgen05 operand format code
   int lo_row_a, lo_row_b;          // row offset of the lo half (three-pass TF32)
@@ -114,16 +119,37 @@ __device__ __forceinline__ void decode_tile(int t, const GemmParams& p, const Gr
   T.idesc = instr_desc(p.ab_fmt, (uint32_t)mma_m, (uint32_t)T.BN);
 }
 
+// TMEM column (relative to the stage's A slot) of the 128 x 32-byte A slice
+// (plane h, swizzle atom a, k-step kk, 128-row block m) under strategy B.
+template <int NATOMS, int NK, int NMBLK>
+__device__ __forceinline__ constexpr uint32_t ta_col(int h, int a, int kk, int m) {
+  return 8u * (uint32_t)(((h * NATOMS + a) * NK + kk) * NMBLK + m);
+}
+
 // All MMAs of one pipeline stage, fully unrolled.  Descriptors are built once
 // per stage; each MMA advances them by constant offsets (the start address
 // sits in the low 14 bits in 16-byte units).  NATOMS swizzle atoms along K,
 // NK = swizzle span / 32 B k-steps per atom, NMBLK 128-row blocks; three-pass
-// TF32 adds the hi.lo and lo.hi products.
-template <int CG, int KIND, int NATOMS, int NK, int NMBLK>
+// TF32 adds the hi.lo and lo.hi products.  TA (strategy B): the stage's A
+// slices are first copied to TMEM at a_tm and the MMAs read A from there.
+template <int CG, int KIND, int NATOMS, int NK, int NMBLK, int TA>
 __device__ __forceinline__ void issue_stage(uint32_t d0, uint64_t a0, uint64_t b0, uint32_t a_part16,
                                             uint32_t b_part16, uint32_t mblk16, uint32_t idesc, uint32_t bn,
-                                            bool first) {
+                                            bool first, uint32_t a_tm) {
   constexpr int PASSES = (KIND == 1) ? 3 : 1;
+  if constexpr (TA) {
+    constexpr int L = (KIND == 1) ? 2 : 1;
+#pragma unroll
+    for (int h = 0; h < L; ++h)
+#pragma unroll
+      for (int a = 0; a < NATOMS; ++a)
+#pragma unroll
+        for (int kk = 0; kk < NK; ++kk)
+#pragma unroll
+          for (int m = 0; m < NMBLK; ++m)
+            tmem_cp_128x256b(a_tm + ta_col<NATOMS, NK, NMBLK>(h, a, kk, m),
+                             a0 + (uint64_t)((h * NATOMS + a) * a_part16 + m * mblk16 + 2u * kk));
+  }
 #pragma unroll
   for (int pass = 0; pass < PASSES; ++pass) {
     const uint32_t ha = (pass == 2) ? 1u : 0u, hb = (pass == 1) ? 1u : 0u;
@@ -135,15 +161,19 @@ __device__ __forceinline__ void issue_stage(uint32_t d0, uint64_t a0, uint64_t b
         const uint32_t acc = (first && pass == 0 && a == 0 && kk == 0) ? 0u : 1u;
 #pragma unroll
         for (int m = 0; m < NMBLK; ++m) {
-          const uint64_t ad = a0 + (uint64_t)((ha * NATOMS + a) * a_part16 + m * mblk16 + 2u * kk);
-          umma<CG, KIND>(d0 + (uint32_t)m * bn, ad, bd, idesc, acc);
+          if constexpr (TA) {
+            umma_ta<KIND>(d0 + (uint32_t)m * bn, a_tm + ta_col<NATOMS, NK, NMBLK>(ha, a, kk, m), bd, idesc, acc);
+          } else {
+            const uint64_t ad = a0 + (uint64_t)((ha * NATOMS + a) * a_part16 + m * mblk16 + 2u * kk);
+            umma<CG, KIND>(d0 + (uint32_t)m * bn, ad, bd, idesc, acc);
+          }
         }
       }
     }
   }
 }
 
-template <int CG, int KIND>
+template <int CG, int KIND, int TA>
 __global__ void __launch_bounds__(kGemmThreads, 1)
     gemm_kernel(const __grid_constant__ TensorMaps maps, const __grid_constant__ GroupTable g,
                 const GemmParams p) {
@@ -275,18 +305,22 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
           const uint32_t a16 = T.a_part >> 4, b16 = T.b_part >> 4, m16 = (uint32_t)(128 * p.sw) >> 4;
           const bool first = kt == 0;
           const uint32_t bn = (uint32_t)T.BN;
+          const uint32_t a_tm = TA ? tmem_base + (uint32_t)(p.a_col0 + stage * p.a_cols) : 0u;
+#define PM_ISSUE(NA, NK, NM) \
+  issue_stage<CG, KIND, NA, NK, NM, TA>(d0, a0, b0, a16, b16, m16, T.idesc, bn, first, a_tm)
           if (p.sw == 128) {
             if (p.n_atoms == 1) {
-              if (T.n_mblk == 1) issue_stage<CG, KIND, 1, 4, 1>(d0, a0, b0, a16, b16, m16, T.idesc, bn, first);
-              else issue_stage<CG, KIND, 1, 4, 2>(d0, a0, b0, a16, b16, m16, T.idesc, bn, first);
+              if (T.n_mblk == 1) PM_ISSUE(1, 4, 1);
+              else PM_ISSUE(1, 4, 2);
             } else {
-              if (T.n_mblk == 1) issue_stage<CG, KIND, 2, 4, 1>(d0, a0, b0, a16, b16, m16, T.idesc, bn, first);
-              else issue_stage<CG, KIND, 2, 4, 2>(d0, a0, b0, a16, b16, m16, T.idesc, bn, first);
+              if (T.n_mblk == 1) PM_ISSUE(2, 4, 1);
+              else PM_ISSUE(2, 4, 2);
             }
           } else {
-            if (T.n_mblk == 1) issue_stage<CG, KIND, 1, 2, 1>(d0, a0, b0, a16, b16, m16, T.idesc, bn, first);
-            else issue_stage<CG, KIND, 1, 2, 2>(d0, a0, b0, a16, b16, m16, T.idesc, bn, first);
+            if (T.n_mblk == 1) PM_ISSUE(1, 2, 1);
+            else PM_ISSUE(1, 2, 2);
           }
+#undef PM_ISSUE
           if constexpr (CG == 1) umma_commit(smem_u32(&empty_bar[stage]));
           else umma_commit_pair(smem_u32(&empty_bar[stage]), (uint16_t)3);
           if (++stage == p.stages) { stage = 0; phase ^= 1u; }
@@ -488,7 +522,7 @@ __global__ void transpose_convert_kernel(const float* __restrict__ x, int K, int
 static inline int dt_elem(int dt) { return dt == PM_FP32 ? 4 : (dt == PM_BF16 ? 2 : 1); }
 static inline int dt_halves(int dt) { return dt == PM_FP32 ? 2 : 1; }
 
-bool gemm_tile_valid(int BM, int BN, int BK, int s, int g, int dt) {
+bool gemm_tile_valid(int BM, int BN, int BK, int s, int g, int dt, int tmem_a) {
   if (!(BM == 64 || BM == 128 || BM == 256) || !(BN == 64 || BN == 128 || BN == 256)) return false;
   if (dt == PM_FP32) {
     if (BK != 32 && BK != 64) return false;
@@ -500,7 +534,16 @@ bool gemm_tile_valid(int BM, int BN, int BK, int s, int g, int dt) {
   if (s < 2 || s > kMaxStages || (g != 1 && g != 2)) return false;
   const int64_t stage = (int64_t)dt_halves(dt) * dt_elem(dt) * BK * (BM + BN / g);
   if ((int64_t)s * stage > 232448 - 2048) return false;
-  if (((BM + 127) / 128) * BN > 512) return false;
+  const int n_mblk = (BM + 127) / 128;
+  if (n_mblk * BN > 512) return false;
+  if (tmem_a == 1) {
+    // strategy B: one SM, 128-row blocks, accumulator plus a TMEM copy of
+    // every stage's A tile within the 512 columns
+    if (g != 1 || BM < 128) return false;
+    if (n_mblk * BN + s * n_mblk * dt_halves(dt) * (BK * dt_elem(dt) / 4) > 512) return false;
+  } else if (tmem_a != 0) {
+    return false;
+  }
   return true;
 }
 
@@ -543,10 +586,10 @@ pm_status cached_tmap(CUtensorMap* out, const void* ptr, int dtcode, uint64_t ro
   return PM_OK;
 }
 
-template <int CG, int KIND>
+template <int CG, int KIND, int TA>
 static pm_status launch_gemm(const TensorMaps& maps, const GroupTable& g, const GemmParams& p, int grid,
                              size_t smem, cudaStream_t s) {
-  auto kern = gemm_kernel<CG, KIND>;
+  auto kern = gemm_kernel<CG, KIND, TA>;
   static std::once_flag once;
   static cudaError_t attr_err = cudaSuccess;
   std::call_once(once, [&] {
@@ -586,7 +629,7 @@ struct LaunchPlan {
   int grid = 0;
 };
 
-static pm_status plan_launch(int dt, int cg, int BK, int stages, int G, const int32_t* M, int N, int K,
+static pm_status plan_launch(int dt, int cg, int BK, int stages, int tmem_a, int G, const int32_t* M, int N, int K,
                              const int16_t* BMv, const int16_t* BNv, bool stacked_b, const void* A_op,
                              const void* B_op, float* C, const float* scales, LaunchPlan& P) {
   PM_REQUIRE(G >= 1 && G <= kMaxGroups, PM_EINVAL, "number of groups %d outside [1, %d]", G, kMaxGroups);
@@ -596,9 +639,9 @@ static pm_status plan_launch(int dt, int cg, int BK, int stages, int G, const in
   int64_t sum_m = 0;
   for (int q = 0; q < G; ++q) {
     PM_REQUIRE(M[q] > 0, PM_EINVAL, "M of group %d must be positive", q);
-    PM_REQUIRE(gemm_tile_valid(BMv[q], BNv[q], BK, stages, cg, dt), PM_EUNSUPPORTED,
-               "tile configuration BM=%d BN=%d BK=%d stages=%d cta_group=%d dtype=%d is outside the valid space",
-               BMv[q], BNv[q], BK, stages, cg, dt);
+    PM_REQUIRE(gemm_tile_valid(BMv[q], BNv[q], BK, stages, cg, dt, tmem_a), PM_EUNSUPPORTED,
+               "tile configuration BM=%d BN=%d BK=%d stages=%d cta_group=%d dtype=%d tmem_a=%d is outside the "
+               "valid space", BMv[q], BNv[q], BK, stages, cg, dt, tmem_a);
     sum_m += M[q];
   }
   PM_REQUIRE(((int64_t)K * e) % 16 == 0, PM_EINVAL, "K*%d bytes must be a multiple of 16", e);
@@ -619,7 +662,7 @@ static pm_status plan_launch(int dt, int cg, int BK, int stages, int G, const in
   p.lo_row_b = L == 2 ? (int)b_rows : 0;
   g.n_groups = G;
   g.tile_off[0] = 0;
-  int acc = 0;
+  int acc = 0, max_mblk = 1;
   uint32_t stage = 0;
   bool used_m[3] = {false, false, false}, used_n[3] = {false, false, false};
   int64_t row0 = 0;
@@ -638,13 +681,18 @@ static pm_status plan_launch(int dt, int cg, int BK, int stages, int G, const in
     used_m[g.bm_idx[q]] = used_n[g.bn_idx[q]] = true;
     const int n_mblk = (bm + 127) / 128;
     acc = std::max(acc, (bm < 128 && cg == 2) ? bn / 2 : n_mblk * bn);
+    max_mblk = std::max(max_mblk, n_mblk);
     stage = std::max(stage, (uint32_t)(L * p.n_atoms) * (uint32_t)(bm + bn / cg) * (uint32_t)p.sw);
     row0 += M[q];
   }
   p.acc_cols = acc;
-  p.nbuf = (2 * acc <= 512) ? 2 : 1;
+  // strategy B: one 8-column slot per 128-row x 32-byte A slice, per stage
+  p.a_cols = tmem_a ? L * (BK * e / 4) * max_mblk : 0;
+  const int a_ring = stages * p.a_cols;
+  p.nbuf = (2 * acc + a_ring <= 512) ? 2 : 1;
+  p.a_col0 = p.nbuf * acc;
   int cols = 32;
-  while (cols < p.nbuf * acc) cols <<= 1;
+  while (cols < p.nbuf * acc + a_ring) cols <<= 1;
   p.alloc_cols = cols;
   p.stage_bytes = stage;
   P.smem = (size_t)stages * stage + 1024;
@@ -689,39 +737,44 @@ static pm_status plan_launch(int dt, int cg, int BK, int stages, int G, const in
   return PM_OK;
 }
 
-static pm_status run_plan(const LaunchPlan& P, int dt, int cg, cudaStream_t s) {
-  if (cg == 1) {
-    if (dt == PM_BF16) return launch_gemm<1, 0>(P.maps, P.g, P.p, P.grid, P.smem, s);
-    if (dt == PM_FP32) return launch_gemm<1, 1>(P.maps, P.g, P.p, P.grid, P.smem, s);
-    return launch_gemm<1, 2>(P.maps, P.g, P.p, P.grid, P.smem, s);
+static pm_status run_plan(const LaunchPlan& P, int dt, int cg, int tmem_a, cudaStream_t s) {
+  if (tmem_a) {
+    if (dt == PM_BF16) return launch_gemm<1, 0, 1>(P.maps, P.g, P.p, P.grid, P.smem, s);
+    if (dt == PM_FP32) return launch_gemm<1, 1, 1>(P.maps, P.g, P.p, P.grid, P.smem, s);
+    return launch_gemm<1, 2, 1>(P.maps, P.g, P.p, P.grid, P.smem, s);
   }
-  if (dt == PM_BF16) return launch_gemm<2, 0>(P.maps, P.g, P.p, P.grid, P.smem, s);
-  if (dt == PM_FP32) return launch_gemm<2, 1>(P.maps, P.g, P.p, P.grid, P.smem, s);
-  return launch_gemm<2, 2>(P.maps, P.g, P.p, P.grid, P.smem, s);
+  if (cg == 1) {
+    if (dt == PM_BF16) return launch_gemm<1, 0, 0>(P.maps, P.g, P.p, P.grid, P.smem, s);
+    if (dt == PM_FP32) return launch_gemm<1, 1, 0>(P.maps, P.g, P.p, P.grid, P.smem, s);
+    return launch_gemm<1, 2, 0>(P.maps, P.g, P.p, P.grid, P.smem, s);
+  }
+  if (dt == PM_BF16) return launch_gemm<2, 0, 0>(P.maps, P.g, P.p, P.grid, P.smem, s);
+  if (dt == PM_FP32) return launch_gemm<2, 1, 0>(P.maps, P.g, P.p, P.grid, P.smem, s);
+  return launch_gemm<2, 2, 0>(P.maps, P.g, P.p, P.grid, P.smem, s);
 }
 
 pm_status gemm_launch(const pm_cfg& c, const void* A_op, const void* B_op, float* C, const float* scales,
                       cudaStream_t s) {
   PM_REQUIRE(c.kind == PM_KIND_GEMM, PM_EINVAL, "cfg.kind must be PM_KIND_GEMM");
   PM_REQUIRE(c.M > 0 && c.N > 0 && c.K > 0, PM_EINVAL, "M, N, K must be positive");
-  PM_REQUIRE(gemm_tile_valid(c.BM, c.BN, c.BK, c.stages, c.cta_group, c.dtype), PM_EUNSUPPORTED,
-             "tile configuration BM=%d BN=%d BK=%d stages=%d cta_group=%d dtype=%d is outside the valid space",
-             c.BM, c.BN, c.BK, c.stages, c.cta_group, c.dtype);
+  PM_REQUIRE(gemm_tile_valid(c.BM, c.BN, c.BK, c.stages, c.cta_group, c.dtype, c.tmem_a), PM_EUNSUPPORTED,
+             "tile configuration BM=%d BN=%d BK=%d stages=%d cta_group=%d dtype=%d tmem_a=%d is outside the "
+             "valid space", c.BM, c.BN, c.BK, c.stages, c.cta_group, c.dtype, c.tmem_a);
   static thread_local LaunchPlan P;
   const int32_t M = c.M;
   const int16_t BM = c.BM, BN = c.BN;
-  pm_status st = plan_launch(c.dtype, c.cta_group, c.BK, c.stages, 1, &M, c.N, c.K, &BM, &BN, false, A_op, B_op, C,
-                             scales, P);
+  pm_status st = plan_launch(c.dtype, c.cta_group, c.BK, c.stages, c.tmem_a, 1, &M, c.N, c.K, &BM, &BN, false, A_op,
+                             B_op, C, scales, P);
   if (st != PM_OK) return st;
-  return run_plan(P, c.dtype, c.cta_group, s);
+  return run_plan(P, c.dtype, c.cta_group, c.tmem_a, s);
 }
 
 pm_status grouped_launch(int G, const int32_t* M, int N, int K, const int16_t* BM, const int16_t* BN, int BK,
                          int stages, int cg, const void* A_op, const void* B_op, float* C, cudaStream_t s) {
   static thread_local LaunchPlan P;
-  pm_status st = plan_launch(PM_BF16, cg, BK, stages, G, M, N, K, BM, BN, true, A_op, B_op, C, nullptr, P);
+  pm_status st = plan_launch(PM_BF16, cg, BK, stages, 0, G, M, N, K, BM, BN, true, A_op, B_op, C, nullptr, P);
   if (st != PM_OK) return st;
-  return run_plan(P, PM_BF16, cg, s);
+  return run_plan(P, PM_BF16, cg, 0, s);
 }
 
 }  // namespace pm
@@ -955,7 +1008,8 @@ extern "C" pm_status pm_gemm_host(const pm_cfg* cfg, const float* A_host, const 
   using namespace pm;
   PM_REQUIRE(cfg && A_host && B_host && C_host && ws_dev, PM_EINVAL, "null argument");
   PM_REQUIRE(cfg->kind == PM_KIND_GEMM && cfg->M > 0 && cfg->N > 0 && cfg->K > 0, PM_EINVAL, "bad shape");
-  PM_REQUIRE(gemm_tile_valid(cfg->BM, cfg->BN, cfg->BK, cfg->stages, cfg->cta_group, cfg->dtype), PM_EUNSUPPORTED,
+  PM_REQUIRE(gemm_tile_valid(cfg->BM, cfg->BN, cfg->BK, cfg->stages, cfg->cta_group, cfg->dtype, cfg->tmem_a),
+             PM_EUNSUPPORTED,
              "tile configuration outside the valid space");
   PM_REQUIRE(((uintptr_t)ws_dev & 255) == 0, PM_EINVAL, "workspace must be 256-byte aligned");
   const HostLayout Lh = host_layout(*cfg, chunks);

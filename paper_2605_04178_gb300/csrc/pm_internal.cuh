@@ -237,6 +237,31 @@ __device__ __forceinline__ void umma(uint32_t d_tmem, uint64_t adesc, uint64_t b
 #undef PM_UMMA
 }
 
+// TMEM strategy B (Sec. III-A.1): the A operand is read from tensor memory
+// (128 lanes = rows, 32-bit columns packing K) instead of shared memory.
+// One SM (cta_group::1); B still comes from a shared-memory descriptor.
+template <int KIND>
+__device__ __forceinline__ void umma_ta(uint32_t d_tmem, uint32_t a_tmem, uint64_t bdesc, uint32_t idesc,
+                                        uint32_t accumulate) {
+#define PM_UMMA_TA(KS)                                                                            \
+  asm volatile(                                                                                   \
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"                                          \
+      "tcgen05.mma.cta_group::1.kind::" KS " [%0], [%1], %2, %3, p;\n\t}" ::"r"(d_tmem),         \
+      "r"(a_tmem), "l"(bdesc), "r"(idesc), "r"(accumulate))
+  if constexpr (KIND == 0) PM_UMMA_TA("f16");
+  else if constexpr (KIND == 1) PM_UMMA_TA("tf32");
+  else PM_UMMA_TA("f8f6f4");
+#undef PM_UMMA_TA
+}
+
+// Copy a 128-row x 32-byte shared-memory matrix (described like an MMA
+// operand) into 128 lanes x 8 columns of tensor memory.  Asynchronous; a
+// later tcgen05.mma of the same thread sees the data, and tcgen05.commit
+// tracks its completion together with the MMAs.
+__device__ __forceinline__ void tmem_cp_128x256b(uint32_t taddr, uint64_t sdesc) {
+  asm volatile("tcgen05.cp.cta_group::1.128x256b [%0], %1;" ::"r"(taddr), "l"(sdesc));
+}
+
 // Arrive once on an mbarrier when all prior tcgen05.mma of this thread are done.
 __device__ __forceinline__ void umma_commit(uint32_t bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)

@@ -34,8 +34,9 @@ __constant__ int16_t kBM[3] = {64, 128, 256};
 __constant__ int16_t kBN[3] = {64, 128, 256};
 __constant__ int16_t kBK[3][2] = {{32, 64}, {64, 128}, {64, 128}};
 
-// Valid tile space: ring of `s` stages within 227 KiB - 2 KiB, FP32
-// accumulator columns ceil(BM/128)*BN within the 512 TMEM columns.
+// Valid tile space of the autotuners (TMEM strategy A): ring of `s` stages
+// within 227 KiB - 2 KiB, FP32 accumulator columns ceil(BM/128)*BN within the
+// 512 TMEM columns.
 __host__ __device__ inline bool tile_valid(int BM, int BN, int BK, int s, int g, int dt) {
   if (!(BM == 64 || BM == 128 || BM == 256) || !(BN == 64 || BN == 128 || BN == 256)) return false;
   if (dt == PM_FP32) {
@@ -58,14 +59,17 @@ __host__ __device__ inline bool tile_valid(int BM, int BN, int BK, int s, int g,
 struct GemmFwd {
   float T, T_stage, T_rl, A_rl, B_rl;
   float T_c, T_io, T_tma, oma, X, R, S, T_step, T_store;
-  float D, bstep, store_bytes, n_instr;
+  float D, DA_r, DA_w, bstep, store_bytes, n_instr;
   float waves, Kt;
   int ri;
   bool oma_free;
 };
 
 // Stage-centric GEMM time:
-//   T_TMEM = D/BW_rd + n_instr L_mma + D/BW_wr                  (Eq. 2)
+//   T_TMEM = (D + D_A,r)/BW_rd + n_instr L_mma + (D + D_A,w)/BW_wr   (Eq. 2)
+//            D_A = 0 for TMEM strategy A; strategy B writes the A tile
+//            into TMEM (D_A,w = l e BM BK) and every pass reads it back
+//            (D_A,r = n_p e BM BK)
 //   T_c    = n_p 2 BM BN BK / (R S) + T_TMEM + T_mgmt/K_tiles     (Eqs. 3, 6)
 //   T_tma  = L_TMA + b_step / B_TMA, b_step = l e BK (BM + BN/g) (Eq. 4, P = 1)
 //   T_io   = (1 - alpha) T_tma + T_sync, T_sync = 2 L_mbar       (Eq. 7)
@@ -87,7 +91,9 @@ __device__ __forceinline__ void gemm_forward(const pm_cfg& c, const Theta& th, i
   // L_mma once per tcgen05.mma issued in the K-step: BK/k_instr per 128-row block, per pass
   const int kin = dt == PM_FP32 ? 8 : (dt == PM_BF16 ? 16 : 32);
   f.n_instr = np * (float)(c.BK / kin) * (float)((c.BM + 127) / 128);
-  const float T_tmem = f.D / th.v[10] + f.n_instr * th.v[9] + f.D / th.v[11];
+  f.DA_w = c.tmem_a ? l * e * c.BM * c.BK : 0.f;
+  f.DA_r = c.tmem_a ? np * e * c.BM * c.BK : 0.f;
+  const float T_tmem = (f.D + f.DA_r) / th.v[10] + f.n_instr * th.v[9] + (f.D + f.DA_w) / th.v[11];
   const float T_mgmt = th.v[13] / f.Kt;
   f.S = g == 1 ? 1.f : th.v[14];
   f.X = (np * 2.f * c.BM * c.BN * c.BK) / (f.R * f.S);
@@ -145,12 +151,12 @@ __device__ __forceinline__ void gemm_adjoint(const pm_cfg& c, const Theta& th, c
   d[4] += g_tma;
   d[5] -= g_tma * (f.bstep / th.v[5]) / th.v[5];
   d[12] += 2.f * g_sync;
-  // T_c = X + D/BW_rd + L_mma + D/BW_wr + L_mgmt/K_tiles
+  // T_c = X + (D + D_A,r)/BW_rd + n_instr L_mma + (D + D_A,w)/BW_wr + L_mgmt/K_tiles
   gR -= g_c * f.X / f.R;
   gS -= g_c * f.X / f.S;
-  d[10] -= g_c * (f.D / th.v[10]) / th.v[10];
+  d[10] -= g_c * ((f.D + f.DA_r) / th.v[10]) / th.v[10];
   d[9] += g_c * f.n_instr;
-  d[11] -= g_c * (f.D / th.v[11]) / th.v[11];
+  d[11] -= g_c * ((f.D + f.DA_w) / th.v[11]) / th.v[11];
   d[13] += g_c / f.Kt;
   // static indices keep d[] in registers
   d[6] += f.ri == 6 ? gR : 0.f;
@@ -226,7 +232,7 @@ __device__ __forceinline__ void probe_adjoint(const pm_cfg& c, const Theta& th, 
 __device__ __forceinline__ bool cfg_sane(const pm_cfg& c) {
   if (c.kind == PM_KIND_GEMM)
     return c.M > 0 && c.N > 0 && c.K > 0 && c.BM > 0 && c.BN > 0 && c.BK > 0 && c.stages > 0 &&
-           (c.cta_group == 1 || c.cta_group == 2) && c.dtype >= 0 && c.dtype <= 2;
+           (c.cta_group == 1 || c.cta_group == 2) && c.dtype >= 0 && c.dtype <= 2 && (c.tmem_a == 0 || c.tmem_a == 1);
   if (c.kind == PM_KIND_COPY || c.kind == PM_KIND_TRIAD) return c.M > 0;
   if (c.kind == PM_KIND_TMA2D) return c.M > 0 && c.N > 0 && c.BM > 0 && c.BN > 0;
   return false;
@@ -368,7 +374,7 @@ __global__ void __launch_bounds__(kTuneThreads) autotune_kernel(const int32_t* _
     c.K = __ldg(MNK + 3 * shape + 2);
     c.dtype = (int8_t)dt;
     c.kind = PM_KIND_GEMM;
-    c.reserved = 0;
+    c.tmem_a = 0;
     float v = INFINITY;
     int BM = 0, BN = 0, BK = 0, s = 0, g = 0;
     if (t < 180) {
@@ -431,7 +437,7 @@ __global__ void __launch_bounds__(kTuneThreads) autotune_topk_kernel(const int32
     c.K = __ldg(MNK + 3 * shape + 2);
     c.dtype = (int8_t)dt;
     c.kind = PM_KIND_GEMM;
-    c.reserved = 0;
+    c.tmem_a = 0;
     float mine = INFINITY;
     int BM = 0, BN = 0, BK = 0, s = 0, g = 0;
     if (t < 180) {
@@ -516,7 +522,7 @@ __global__ void __launch_bounds__(kGroupThreads) grouped_tune_kernel(const int32
         if (!tile_valid(BM, BN, BK, s, g, dt)) continue;
         pm_cfg c;
         c.M = Mg[q]; c.N = N; c.K = K; c.BM = (int16_t)BM; c.BN = (int16_t)BN; c.BK = (int16_t)BK;
-        c.stages = (int8_t)s; c.cta_group = (int8_t)g; c.dtype = (int8_t)dt; c.kind = 0; c.reserved = 0;
+        c.stages = (int8_t)s; c.cta_group = (int8_t)g; c.dtype = (int8_t)dt; c.kind = 0; c.tmem_a = 0;
         GemmFwd f;
         gemm_forward(c, th, n_sm, f);
         const float tq = f.Kt * f.T_step + f.T_store;   // one tile of this group

@@ -54,6 +54,12 @@ def test_invalid_tile_rejected_before_launch(pm):
         st = pm._lib.pm_gemm_run(ctypes.byref(c), None, None, None, None, None)
         assert st == pm.PM_EUNSUPPORTED, (c.BM, c.BK, c.stages, st)
         assert "valid space" in pm.pm_last_error()
+    # TMEM strategy B: one-SM tiles of whole 128-row blocks with room for the A ring
+    for c in (pm.cfg(512, 512, 512, BM=128, BN=128, cta_group=2, tmem_a=1), pm.cfg(512, 512, 512, BM=64, tmem_a=1),
+              pm.cfg(512, 512, 512, BM=256, BN=256, BK=64, stages=2, dtype=2, tmem_a=1),
+              pm.cfg(512, 512, 512, tmem_a=2)):
+        st = pm._lib.pm_gemm_run(ctypes.byref(c), None, None, None, None, None)
+        assert st == pm.PM_EUNSUPPORTED, (c.BM, c.BN, c.cta_group, c.tmem_a, st)
     c = pm.cfg(512, 512, 512, kind=pm.PM_KIND_COPY)
     assert pm._lib.pm_gemm_run(ctypes.byref(c), None, None, None, None, None) == pm.PM_EINVAL
     c = pm.cfg(0, 512, 512)
@@ -99,12 +105,14 @@ def test_bad_arguments_rejected(pm):
 
 def test_tile_space_matches_oracle_rule(pm):
     # the library's validity rule (reached through pm_gemm_run's early check)
-    # and the oracle's independent implementation agree on all 540 points
+    # and the oracle's independent implementation agree on all 540 points of
+    # each TMEM strategy
     import oracle as O
     import synthetic as S
-    for dt in (0, 1, 2):
-        for (bm, bn, bk, s, g) in S.tile_space(dt):
-            c = pm.cfg(256, 256, 256, bm, bn, bk, s, g, dt)
-            st = pm._lib.pm_gemm_run(ctypes.byref(c), None, None, None, None, None)
-            lib_valid = st != pm.PM_EUNSUPPORTED
-            assert lib_valid == O.cfg_valid(bm, bn, bk, s, g, dt), (dt, bm, bn, bk, s, g, st)
+    for ta in (0, 1):
+        for dt in (0, 1, 2):
+            for (bm, bn, bk, s, g) in S.tile_space(dt):
+                c = pm.cfg(256, 256, 256, bm, bn, bk, s, g, dt, tmem_a=ta)
+                st = pm._lib.pm_gemm_run(ctypes.byref(c), None, None, None, None, None)
+                lib_valid = st != pm.PM_EUNSUPPORTED
+                assert lib_valid == O.cfg_valid(bm, bn, bk, s, g, dt, ta), (ta, dt, bm, bn, bk, s, g, st)

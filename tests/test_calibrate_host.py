@@ -24,12 +24,16 @@ def table(theta):
     for t in S.tile_space(0):
         if O.cfg_valid(*t, 0):
             rows.append(dict(zip(FIELDS, (512, 512, 512, *t, 0, 0))))
+    for dt in (0, 1, 2):                               # TMEM strategy B rows
+        for t in S.tile_space(dt):
+            if O.cfg_valid(*t, dt, 1):
+                rows.append(dict(zip(FIELDS, (4096, 4096, 4096, *t, dt, 0, 1))))
     for k in range(20, 31):
         rows.append(dict(M=2 ** k, N=0, K=0, BM=0, BN=0, BK=0, stages=0, cta_group=0, dtype=0, kind=1))
         rows.append(dict(M=2 ** k, N=0, K=0, BM=0, BN=0, BK=0, stages=0, cta_group=0, dtype=0, kind=2))
     for tr, tc in ((64, 64), (128, 64), (128, 128), (256, 64), (256, 128)):
         rows.append(dict(M=16384, N=16384, K=0, BM=tr, BN=tc, BK=0, stages=0, cta_group=0, dtype=0, kind=3))
-    cols = {f: np.array([r[f] for r in rows], dtype=np.int32) for f in FIELDS}
+    cols = {f: np.array([r.get(f, 0) for r in rows], dtype=np.int32) for f in FIELDS}
     t = O.model_batch(cols, theta, N_SM)
     for r, v in zip(rows, t):
         r["t"] = float(v)

@@ -33,12 +33,16 @@ def run_gemm(lib, A, B, c, dtype):
     return C.cpu().numpy(), ops
 
 
-def valid_space(dt):
-    return [t for t in S.tile_space(dt) if O.cfg_valid(*t, dt)]
+def valid_space(dt, tmem_a=0):
+    return [t for t in S.tile_space(dt) if O.cfg_valid(*t, dt, tmem_a)]
 
 
-def space_ids(dt):
-    return ["%s-bm%d-bn%d-bk%d-s%d-g%d" % ((DT_NAMES[dt],) + t) for t in valid_space(dt)]
+def space_ids(dt, tmem_a=0):
+    return ["%s-bm%d-bn%d-bk%d-s%d-g%d" % ((DT_NAMES[dt],) + t) for t in valid_space(dt, tmem_a)]
+
+
+B_SPACE = [(dt, t) for dt in (0, 1, 2) for t in valid_space(dt, 1)]
+B_IDS = ["tmemB-" + i for dt in (0, 1, 2) for i in space_ids(dt, 1)]
 
 
 # ------------------------------------------------------------------ operand prep
@@ -115,6 +119,46 @@ def test_exact_integer_ragged_shapes(lib, shape, t):
     A, B, ref = _int_case(M, N, K)
     C, _ = run_gemm(lib, A, B, lib.cfg(M, N, K, *t, dtype=1), 1)
     assert np.array_equal(C.astype(np.float64), ref)
+
+
+# ------------------------------------------- TMEM strategy B (A operand in TMEM)
+@pytest.mark.parametrize("dt,t", B_SPACE, ids=B_IDS)
+def test_exact_integer_tmem_strategy_b(lib, dt, t):
+    A, B, ref = _int_case(300, 200, 320)
+    C, _ = run_gemm(lib, A, B, lib.cfg(300, 200, 320, *t, dtype=dt, tmem_a=1), dt)
+    if dt == 2:
+        assert np.all(np.abs(C - ref) <= 2.0 ** -23 * np.abs(ref))
+    else:
+        assert np.array_equal(C.astype(np.float64), ref)
+
+
+@pytest.mark.parametrize("shape", [(1, 1, 16), (17, 33, 64), (129, 260, 4096), (1000, 8, 48), (300, 1024, 1040)])
+@pytest.mark.parametrize("dt,t", [(1, (128, 128, 64, 4, 1)), (1, (256, 128, 64, 4, 1)), (2, (128, 256, 128, 4, 1)),
+                                  (0, (128, 128, 32, 3, 1))])
+def test_exact_integer_tmem_strategy_b_ragged(lib, shape, dt, t):
+    M, N, K = shape
+    if (K * (4 if dt == 0 else (2 if dt == 1 else 1))) % 16:
+        pytest.skip("K rows must be 16-byte multiples for TMA")
+    A, B, ref = _int_case(M, N, K)
+    C, _ = run_gemm(lib, A, B, lib.cfg(M, N, K, *t, dtype=dt, tmem_a=1), dt)
+    if dt == 2:
+        assert np.all(np.abs(C - ref) <= 2.0 ** -23 * np.abs(ref))
+    else:
+        assert np.array_equal(C.astype(np.float64), ref)
+
+
+@pytest.mark.parametrize("dt,tol,t", [(1, 2e-2, (128, 256, 64, 4, 1)), (2, 6e-2, (256, 128, 128, 4, 1)),
+                                      (0, 1e-5, (128, 128, 32, 2, 1))])
+def test_tmem_strategy_b_accuracy(lib, dt, tol, t):
+    M = N = K = 1024 if dt else 512
+    A, B = S.gemm_operands(M, N, K, seed=2 if dt else 0, dist="normal" if dt else "uniform")
+    C, _ = run_gemm(lib, A, B, lib.cfg(M, N, K, *t, dtype=dt, tmem_a=1), dt)
+    ref = O.gemm_f64(A, B)
+    if dt == 0:
+        err = np.max(np.abs(C - ref)) / np.max(np.abs(ref))
+    else:
+        err = np.linalg.norm(C - ref) / np.linalg.norm(ref)
+    assert err <= tol, err
 
 
 # ---------------------------------------------------------- real-valued accuracy

@@ -11,7 +11,7 @@ pytestmark = pytest.mark.gpu
 
 N_SM = 152
 THETA = O.prior_theta(N_SM)
-FIELDS = ("M", "N", "K", "BM", "BN", "BK", "stages", "cta_group", "dtype", "kind")
+FIELDS = ("M", "N", "K", "BM", "BN", "BK", "stages", "cta_group", "dtype", "kind", "tmem_a")
 
 
 def theta32():
@@ -19,9 +19,12 @@ def theta32():
     return THETA.astype(np.float32).astype(np.float64)
 
 
-def random_cfgs(n, seed=4, valid_only=False):
+def random_cfgs(n, seed=4, valid_only=False, strategy_b=False):
     c = S.model_config_batch(n, seed)
     c["kind"] = np.zeros(n, dtype=np.int32)
+    if strategy_b:
+        # half the rows ask for TMEM strategy B (the model evaluates any tile)
+        c["tmem_a"] = (S.uniform01_f64(seed + 1000, n) < 0.5).astype(np.int32)
     if valid_only:
         ok = np.array([O.cfg_valid(c["BM"][i], c["BN"][i], c["BK"][i], c["stages"][i], c["cta_group"][i],
                                    c["dtype"][i]) for i in range(n)])
@@ -47,7 +50,7 @@ def predict_gpu(lib, c, theta):
 
 @pytest.mark.parametrize("n", [1, 7, 1000, 100003])
 def test_predict_matches_oracle(lib, n):
-    c = random_cfgs(n, seed=n)
+    c = random_cfgs(n, seed=n, strategy_b=True)
     th = theta32()
     t_gpu = predict_gpu(lib, c, th)
     t_orc = O.model_batch(c, th, N_SM)
@@ -92,7 +95,7 @@ def grad_gpu(lib, c, theta, t_meas):
 
 @pytest.mark.parametrize("n", [1, 1000, 200000])
 def test_grad_matches_oracle(lib, n):
-    c = random_cfgs(n, seed=17 + n)
+    c = random_cfgs(n, seed=17 + n, strategy_b=True)
     pc = probe_cfgs()
     c = {k: np.concatenate([c[k], pc[k]]) for k in c}
     th = theta32()
