@@ -292,12 +292,15 @@ static void stage_terms(const Cfg& c, i64 Kt, const T* th, T& Tstep, T& Tstore) 
   // K-step issues -- BK / k_instr K-slices per 128-row block, per TF32 pass --
   // while the accumulator traffic D is counted once per K-step.
   const double D = 4.0 * c.BM * c.BN;
-  const double n_instr = np * (double)(c.BK / instr_k(c.dtype)) * (double)ceil_div(c.BM, 128);
+  double n_instr = np * (double)(c.BK / instr_k(c.dtype)) * (double)ceil_div(c.BM, 128);
   // Strategy B ("A and accumulators in TMEM", Sec. III-A.1) adds the A tile's
   // TMEM traffic: written once per K-step by the copy into TMEM (l planes),
-  // read by every tensor pass.
+  // read by every tensor pass.  The copies are tensor-pipe instructions of
+  // the same K-step (one per 128-row x 32-byte slice of each plane), so under
+  // the per-instruction reading of L_mma each is charged L_mma as well.
   const double DA_w = c.tmem_a ? l * e * c.BM * c.BK : 0.0;
   const double DA_r = c.tmem_a ? np * e * c.BM * c.BK : 0.0;
+  if (c.tmem_a) n_instr += l * (c.BK * e / 32.0) * (double)ceil_div(c.BM, 128);
   const T T_tmem = (D + DA_r) / th[10] + n_instr * th[9] + (D + DA_w) / th[11];
   // T_TMEM_mgmt amortised over the K-steps (Sec. III-A.5).
   const T T_mgmt = th[13] / lift<T>((double)Kt);

@@ -69,7 +69,7 @@ struct GemmFwd {
 //   T_TMEM = (D + D_A,r)/BW_rd + n_instr L_mma + (D + D_A,w)/BW_wr   (Eq. 2)
 //            D_A = 0 for TMEM strategy A; strategy B writes the A tile
 //            into TMEM (D_A,w = l e BM BK) and every pass reads it back
-//            (D_A,r = n_p e BM BK)
+//            (D_A,r = n_p e BM BK); n_instr counts its tcgen05.cp copies too
 //   T_c    = n_p 2 BM BN BK / (R S) + T_TMEM + T_mgmt/K_tiles     (Eqs. 3, 6)
 //   T_tma  = L_TMA + b_step / B_TMA, b_step = l e BK (BM + BN/g) (Eq. 4, P = 1)
 //   T_io   = (1 - alpha) T_tma + T_sync, T_sync = 2 L_mbar       (Eq. 7)
@@ -93,6 +93,8 @@ __device__ __forceinline__ void gemm_forward(const pm_cfg& c, const Theta& th, i
   f.n_instr = np * (float)(c.BK / kin) * (float)((c.BM + 127) / 128);
   f.DA_w = c.tmem_a ? l * e * c.BM * c.BK : 0.f;
   f.DA_r = c.tmem_a ? np * e * c.BM * c.BK : 0.f;
+  // strategy B also issues one tcgen05.cp per 128-row x 32-byte A slice, each charged L_mma
+  if (c.tmem_a) f.n_instr += l * (float)(c.BK * (int)e / 32) * (float)((c.BM + 127) / 128);
   const float T_tmem = (f.D + f.DA_r) / th.v[10] + f.n_instr * th.v[9] + (f.D + f.DA_w) / th.v[11];
   const float T_mgmt = th.v[13] / f.Kt;
   f.S = g == 1 ? 1.f : th.v[14];

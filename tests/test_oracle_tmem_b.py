@@ -3,7 +3,8 @@
 Sec. III-A.1 names two TMEM strategies: (A) only the accumulators live in
 tensor memory, both operands are read from shared memory; (B) the A operand
 is also staged in tensor memory, which adds TMEM traffic and is covered by
-the same T_TMEM term of Eq. 2.  The pins: hand-checked capacity boundaries of
+the same T_TMEM term of Eq. 2 (its tcgen05.cp copies are tensor-pipe
+instructions and pay L_mma like the MMAs).  The pins: hand-checked capacity boundaries of
 the strategy-B tile space, the closed-form time difference B - A when the
 K-step is compute-bound, the reduction to strategy A at unbounded TMEM
 bandwidth, and the homogeneity / gradient identities on strategy-B rows.
@@ -71,6 +72,8 @@ def test_strategy_b_adds_a_tile_traffic_when_compute_bound(dt, bk, e, n_p, l):
     # T_c + T_sync and the two strategies differ only in T_TMEM:
     #   per K-step   n_p e BM BK / BW_rd  (every pass reads A from TMEM)
     #              + l e BM BK / BW_wr    (the A planes are copied in)
+    #              + n_cp L_mma           (one tcgen05.cp per 128 x 32-byte
+    #                                      slice: l * BK e / 32 of them)
     th = PRIOR160.copy()
     th[15] = 0.0
     M = N = 1024                       # 8 x 8 = 64 tiles of 128 x 128: one wave on 160 SMs
@@ -78,13 +81,15 @@ def test_strategy_b_adds_a_tile_traffic_when_compute_bound(dt, bk, e, n_p, l):
     base = dict(M=M, N=N, K=K, BM=128, BN=128, BK=bk, stages=2, cta_group=1, dtype=dt)
     t_a = one(th, **base)
     t_b = one(th, tmem_a=1, **base)
-    per_step = n_p * e * 128 * bk / th[10] + l * e * 128 * bk / th[11]
+    n_cp = l * bk * e // 32
+    per_step = n_p * e * 128 * bk / th[10] + l * e * 128 * bk / th[11] + n_cp * th[9]
     assert t_b - t_a == pytest.approx(50 * per_step, rel=1e-9)
 
 
 def test_strategy_b_equals_a_at_unbounded_tmem_bandwidth():
     th = PRIOR160.copy()
     th[10] = th[11] = 1e30
+    th[9] = 0.0                                        # and free tensor-pipe instructions
     rows = []
     for dt in (0, 1, 2):
         for t in S.tile_space(dt):
@@ -127,7 +132,7 @@ def test_strategy_b_tmem_gradient_central_differences():
             dict(M=2048, N=1024, K=128 * 30, BM=256, BN=128, BK=128, stages=4, cta_group=1, dtype=2, tmem_a=1)]
     c = cfgs(rows)
     t, g = O.model_batch(c, th, 160, grad=True)
-    for j in (10, 11):
+    for j in (9, 10, 11):
         h = 1e-4
         tp, tm = th.copy(), th.copy()
         tp[j] *= np.exp(h)
