@@ -221,11 +221,12 @@ def run_gpu(args):
     pm.pm_autotune_pick(MNK, 1, pm.PM_BF16, theta, n_sm, picks, t_pred)
     p = picks.cpu().numpy().view(pm.CFG_DTYPE)[0]
     model_pick = tuple(int(p[k]) for k in ("BM", "BN", "BK", "stages", "cta_group"))
-    tuned, _ = pm.pm_gemm_autotune(pm.cfg(M, N, K, dtype=pm.PM_BF16), 8, theta, n_sm, ops.A_op, ops.B_op, C,
-                                   ops.scales)
-    pick = (tuned.BM, tuned.BN, tuned.BK, tuned.stages, tuned.cta_group)
     if args.cfg:
         pick = tuple(int(v) for v in args.cfg.split(","))
+    else:
+        tuned, _ = pm.pm_gemm_autotune(pm.cfg(M, N, K, dtype=pm.PM_BF16), 8, theta, n_sm, ops.A_op, ops.B_op, C,
+                                       ops.scales)
+        pick = (tuned.BM, tuned.BN, tuned.BK, tuned.stages, tuned.cta_group)
     cfg = pm.cfg(M, N, K, *pick, dtype=pm.PM_BF16)
 
 
@@ -310,6 +311,35 @@ def run_gpu(args):
                       "model_only_over_best_time": meas[model_pick] / meas[best],
                       "model_mae_pct": float(np.mean(np.abs(pred - tm) / tm) * 100.0),
                       "protocol": "3 warm-ups, median of 15 CUDA-event timed launches per tile"}
+        # TMEM strategy B (A operand copied into tensor memory) over its tile
+        # space at the same shape: fastest of each strategy, measured and predicted
+        measB = {}
+        for t in S_.tile_space(pm.PM_BF16):
+            try:
+                r = ops.bench(pm.cfg(M, N, K, *t, dtype=pm.PM_BF16, tmem_a=1), C, warmup=3, reps=15)
+            except pm.PMError as e:
+                if e.status == pm.PM_EUNSUPPORTED:
+                    continue
+                raise
+            measB[t] = r["median_s"]
+        tilesB = sorted(measB)
+        colsB = {f: np.array(v) for f, v in zip(("BM", "BN", "BK", "stages", "cta_group"), zip(*tilesB))}
+        colsB.update(M=np.full(len(tilesB), M), N=np.full(len(tilesB), N), K=np.full(len(tilesB), K),
+                     dtype=np.full(len(tilesB), pm.PM_BF16), kind=np.zeros(len(tilesB)),
+                     tmem_a=np.ones(len(tilesB)))
+        predB = torch.empty(len(tilesB), dtype=torch.float32, device="cuda")
+        pm.pm_model_predict(pm.cfg_tensor(colsB), len(tilesB), theta, n_sm, predB)
+        predB = predB.cpu().numpy().astype(np.float64)
+        tB = np.array([measB[t] for t in tilesB])
+        bestB = min(measB, key=measB.get)
+        iA, iB = tiles.index(best), tilesB.index(bestB)
+        same = [t for t in tilesB if t in meas]
+        exhaustive["tmem_strategy_b"] = {
+            "configs": len(measB), "best_tile": dict(zip(("BM", "BN", "BK", "stages", "cta_group"), bestB)),
+            "best_tflops": flops / measB[bestB] / 1e12, "measured_best_B_over_best_A": measB[bestB] / meas[best],
+            "predicted_best_B_over_best_A": predB[iB] / pred[iA],
+            "median_B_over_A_same_tile": float(np.median([measB[t] / meas[t] for t in same])),
+            "model_mae_pct": float(np.mean(np.abs(predB - tB) / tB) * 100.0)}
 
     extra = {}
     if not args.skip_extra:
@@ -323,7 +353,8 @@ def run_gpu(args):
             "config": {"workload": "bf16_gemm_8192^3_model_autotuned", "M": M, "N": N, "K": K,
                        "inputs": "A,B ~ N(0,1) seed 2, FP32 -> BF16 K-major operands",
                        "tile": dict(zip(("BM", "BN", "BK", "stages", "cta_group"), pick)),
-                       "autotune": "model top-8 tiles (GPU) timed on the device, fastest kept",
+                       "autotune": ("tile given by --cfg" if args.cfg else
+                                    "model top-8 tiles (GPU) timed on the device, fastest kept"),
                        "theta": theta_src, "l2": "operands 256 MB > 129 MB L2, no flush",
                        "parallelism": "replicas" if world > 1 else "single"},
             "pct_of_peak": 100.0 * achieved / peak,

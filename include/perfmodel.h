@@ -139,6 +139,20 @@ typedef struct {
   uint32_t reserved;
 } pm_probe_result;
 
+/* Concurrent-stream interference probe (Sec. III-A.6: N_c concurrent streams
+ * add (N_c - 1) tau_c to the single-stream time).  Launches the probe
+ * `per_stream` (PM_PROBE_COPY, PM_PROBE_TRIAD or PM_PROBE_MMA) once on each of
+ * n_streams (1..8) library-owned non-blocking streams, stream i on buffers
+ * buf0[i], buf1[i], buf2[i] (host arrays of n_streams device pointers; buf1
+ * may be NULL for MMA, buf2 is needed for TRIAD only).  All streams are
+ * released by one event on `stream` and joined back on it; each rep's time is
+ * the makespan between those two events.  `warmup` untimed then `reps` timed
+ * reps; result as for pm_probe_run with bytes (FLOPs for MMA) summed over the
+ * streams.  The streams are created on first use per device and kept until
+ * process exit.  Synchronises `stream`. */
+pm_status pm_streams_run(const pm_probe_args* per_stream, int32_t n_streams, void* const* buf0, void* const* buf1,
+                         void* const* buf2, int warmup, int reps, void* stream, pm_probe_result* out);
+
 /* One probe launch on `stream` (async). */
 pm_status pm_probe_launch(const pm_probe_args* args, void* buf0, void* buf1, void* buf2, void* stream);
 

@@ -58,7 +58,7 @@ class pm_probe_result(ctypes.Structure):
 assert ctypes.sizeof(pm_cfg) == 24 and ctypes.sizeof(pm_probe_args) == 56 and ctypes.sizeof(pm_probe_result) == 48
 
 # Every exported symbol of include/perfmodel.h
-EXPORTS = ("pm_probe_launch", "pm_probe_run", "pm_gemm_operand_bytes", "pm_gemm_prepare", "pm_gemm_run",
+EXPORTS = ("pm_probe_launch", "pm_probe_run", "pm_streams_run", "pm_gemm_operand_bytes", "pm_gemm_prepare", "pm_gemm_run",
            "pm_gemm_bench", "pm_gemm_host_workspace", "pm_gemm_host",
            "pm_grouped_gemm_run", "pm_model_predict", "pm_model_grad_workspace", "pm_model_grad", "pm_model_grad_noalloc",
            "pm_autotune_pick", "pm_autotune_topk", "pm_gemm_autotune", "pm_grouped_autotune", "pm_last_error", "pm_device_status",
@@ -87,6 +87,8 @@ def _load():
         "pm_probe_launch": [ctypes.POINTER(pm_probe_args), P, P, P, P],
         "pm_probe_run": [ctypes.POINTER(pm_probe_args), P, P, P, ctypes.c_int, ctypes.c_int, P,
                          ctypes.POINTER(pm_probe_result)],
+        "pm_streams_run": [ctypes.POINTER(pm_probe_args), i32, P, P, P, ctypes.c_int, ctypes.c_int, P,
+                           ctypes.POINTER(pm_probe_result)],
         "pm_gemm_operand_bytes": [i32, i32, i32, i32, ctypes.POINTER(sz), ctypes.POINTER(sz)],
         "pm_gemm_prepare": [i32, P, P, i32, i32, i32, P, P, P, P],
         "pm_gemm_run": [ctypes.POINTER(pm_cfg), P, P, P, P, P],
@@ -190,6 +192,25 @@ def pm_probe_run(args: pm_probe_args, buf0, buf1=None, buf2=None, warmup=10, rep
                              _stream(stream), ctypes.byref(res)), "pm_probe_run")
     return dict(median_s=res.median_s, p25_s=res.p25_s, p75_s=res.p75_s, min_s=res.min_s, bytes=res.bytes,
                 final_index=res.final_index)
+
+
+def pm_streams_run(args: pm_probe_args, bufs0, bufs1=None, bufs2=None, warmup=10, reps=100, stream=None) -> dict:
+    """The probe `args` on len(bufs0) concurrent streams (stream i on bufs0[i], bufs1[i], bufs2[i]);
+    median/quartiles of the makespan."""
+    n = len(bufs0)
+
+    def arr(bufs):
+        if bufs is None:
+            return None
+        assert len(bufs) == n
+        a = (ctypes.c_void_p * n)(*[_ptr(b) for b in bufs])
+        return ctypes.cast(a, ctypes.c_void_p), a
+
+    a0, a1, a2 = arr(bufs0), arr(bufs1), arr(bufs2)
+    res = pm_probe_result()
+    _check(_lib.pm_streams_run(ctypes.byref(args), int(n), a0[0], a1[0] if a1 else None, a2[0] if a2 else None,
+                               int(warmup), int(reps), _stream(stream), ctypes.byref(res)), "pm_streams_run")
+    return dict(median_s=res.median_s, p25_s=res.p25_s, p75_s=res.p75_s, min_s=res.min_s, bytes=res.bytes)
 
 
 # ----------------------------------------------------------------------- GEMM

@@ -11,6 +11,8 @@ Pieces
     device by the library's own harness (pm_gemm_bench / pm_probe_run).
   * measure_tmem_b(): the same GEMM classes under TMEM strategy B (A operand
     copied into tensor memory, Sec. III-A.1) over the strategy-B tile space.
+  * measure_streams() / fit_tau_c(): the concurrent-stream term of Sec.
+    III-A.6, T(N_c) = T(1) + (N_c - 1) tau_c, per workload class.
   * StageModelLoss: torch.autograd.Function whose forward is the batched model
     on the GPU and whose backward is the hand-written adjoint kernel
     (pm_model_grad): mean squared log error and its gradient in theta.
@@ -142,6 +144,8 @@ def measure_sweep(shapes=(1024, 2048, 4096, 8192, 16384), dtypes=(1, 2), log=pri
     # Blackwell instruction probes (Sec. V-A (iii)-(iv)) and the host link (Eq. 15)
     instr = measure_instructions()
     log("instruction and host-link probes done (%.0f s)" % (time.time() - t0))
+    streams = measure_streams()
+    log("concurrent-stream probes done (%.0f s)" % (time.time() - t0))
     # config 3: every valid BF16 / FP8 configuration at M = N = K = s
     for s in shapes:
         A, B = S.gemm_operands(s, s, s, seed=2, dist="normal")
@@ -165,7 +169,7 @@ def measure_sweep(shapes=(1024, 2048, 4096, 8192, 16384), dtypes=(1, 2), log=pri
     rows += measure_tmem_b(shapes, dtypes, log)
     props = torch.cuda.get_device_properties(0)
     return dict(device=props.name, n_sm=props.multi_processor_count, rows=rows, pchase=pchase, instr=instr,
-                protocol="10 warm-ups; 100 timed runs (20-40 at 8192-16384, 20 for TMA), median of CUDA-event times")
+                streams=streams, protocol="10 warm-ups; 100 timed runs (20-40 at 8192-16384, 20 for TMA), median of CUDA-event times")
 
 
 def measure_tmem_b(shapes=(1024, 2048, 4096, 8192, 16384), dtypes=(1, 2), log=print) -> list:
@@ -224,6 +228,56 @@ def measure_instructions() -> dict:
         out["host"].append(dict(bytes=nb, h2d_s=r1["median_s"], d2h_s=r2["median_s"]))
         del h, d
     out["eq15"] = fit_eq15(out["host"])
+    return out
+
+
+STREAM_COUNTS = (1, 2, 3, 4, 6, 8)
+
+
+def fit_tau_c(counts, times) -> dict:
+    """Least-squares tau_c of T(N_c) = T(1) + (N_c - 1) tau_c (Sec. III-A.6),
+    with T(1) the measured single-stream time, and the MAE of that law over
+    the N_c > 1 points."""
+    counts = np.asarray(counts, dtype=np.float64)
+    times = np.asarray(times, dtype=np.float64)
+    t1 = float(times[counts == 1][0])
+    x = counts - 1.0
+    tau = float(np.sum(x * (times - t1)) / np.sum(x * x))
+    pred = t1 + x * tau
+    m = counts > 1
+    return dict(T1_s=t1, tau_c_s=tau, tau_over_T1=tau / t1,
+                mae_pct=float(np.mean(np.abs(pred[m] - times[m]) / times[m]) * 100.0))
+
+
+def measure_streams(counts=STREAM_COUNTS) -> dict:
+    """Makespan of N_c concurrent copies of one probe kernel on N_c streams:
+    a bandwidth-bound triad that fills the GPU, a launch-bound small copy, and
+    tcgen05.mma streams that occupy an eighth of the SMs or all of them."""
+    n_sm = pm.sm_count()
+    k = max(counts)
+    out = {}
+    nt = 1 << 24
+    a = [torch.empty(nt, dtype=torch.float32, device="cuda") for _ in range(k)]
+    b = [torch.empty(nt, dtype=torch.float32, device="cuda").uniform_(-1, 1) for _ in range(k)]
+    c = [torch.empty(nt, dtype=torch.float32, device="cuda").uniform_(-1, 1) for _ in range(k)]
+    mma = [torch.zeros(n_sm, dtype=torch.int32, device="cuda") for _ in range(k)]
+    classes = {
+        "triad_2^24_per_stream": (pm.probe_args(pm.PM_PROBE_TRIAD, n=nt, scalar=3.0), (a, b, c)),
+        "copy_2^16_per_stream": (pm.probe_args(pm.PM_PROBE_COPY, n=1 << 16), (b, a, None)),
+        "mma_bf16_%d_ctas_per_stream" % (n_sm // 8): (
+            pm.probe_args(pm.PM_PROBE_MMA, n=1 << 13, tile_r=256, tile_c=128, rows=1, cols=1, start=n_sm // 8),
+            (mma, None, None)),
+        "mma_bf16_%d_ctas_per_stream" % n_sm: (
+            pm.probe_args(pm.PM_PROBE_MMA, n=1 << 13, tile_r=256, tile_c=128, rows=1, cols=1, start=n_sm),
+            (mma, None, None)),
+    }
+    for name, (args, (x0, x1, x2)) in classes.items():
+        times = []
+        for nc in counts:
+            r = pm.pm_streams_run(args, x0[:nc], x1[:nc] if x1 else None, x2[:nc] if x2 else None, warmup=5,
+                                  reps=30)
+            times.append(r["median_s"])
+        out[name] = dict(counts=list(counts), t_s=times, fit=fit_tau_c(counts, times))
     return out
 
 
@@ -431,6 +485,7 @@ def main():
     ap.add_argument("--measure", action="store_true")
     ap.add_argument("--measure-instr", action="store_true", help="re-measure only the instruction/host probes")
     ap.add_argument("--measure-tmem-b", action="store_true", help="re-measure only the strategy-B GEMM rows")
+    ap.add_argument("--measure-streams", action="store_true", help="re-measure only the concurrent-stream probes")
     ap.add_argument("--sweep", default=SWEEP_PATH)
     ap.add_argument("--out", default=THETA_PATH)
     ap.add_argument("--report", default=None)
@@ -449,7 +504,9 @@ def main():
     if args.measure_tmem_b:
         table["rows"] = [r for r in table["rows"] if not r.get("tmem_a", 0)] + \
             measure_tmem_b(tuple(int(s) for s in args.shapes.split(",")))
-    if args.measure_instr or args.measure_tmem_b:
+    if args.measure_streams:
+        table["streams"] = measure_streams()
+    if args.measure_instr or args.measure_tmem_b or args.measure_streams:
         with open(args.sweep, "w") as f:
             json.dump(table, f)
     rows = table["rows"]
@@ -467,7 +524,8 @@ def main():
                mae_holdout=mae_by_family(rows, pred, hold), mae_all=mae_by_family(rows, pred),
                roofline_mae=roofline_mae(rows, dict(hbm=8.0e12, bf16=2.25e15, fp8=4.5e15, tf32=1.1e15)),
                autotune=autotune_vs_best(rows, theta, n_sm), pchase=table.get("pchase"),
-               instr=table.get("instr"), tmem_strategy=tmem_strategy_report(rows, pred))
+               instr=table.get("instr"), tmem_strategy=tmem_strategy_report(rows, pred),
+               streams=table.get("streams"))
     save_theta(theta, dict(device=table.get("device"), n_sm=n_sm, fitted_on=os.path.basename(args.sweep),
                            mae_holdout=rep["mae_holdout"]), args.out)
     if args.report:
@@ -480,6 +538,9 @@ def main():
     for a in rep["autotune"]:
         print("autotune %(M)d dt=%(dtype)d pick=%(pick)s best=%(best)s pick/best=%(pick_over_best).3f "
               "TFLOP/s pick %(tflops_pick).0f best %(tflops_best).0f" % a)
+    for name, v in (rep.get("streams") or {}).items():
+        print("streams %s: T(N_c) %s s, tau_c %.3g s (%.2f T1), additive-law MAE %.1f %%" % (
+            name, ["%.3g" % x for x in v["t_s"]], v["fit"]["tau_c_s"], v["fit"]["tau_over_T1"], v["fit"]["mae_pct"]))
     for r in rep["tmem_strategy"]:
         print("TMEM strategy %d dt=%d: best A %s %.3g s, best B %s %.3g s, measured B/A %.3f, predicted %.3f" % (
             r["M"], r["dtype"], r["A"]["tile"], r["A"]["t"], r["B"]["tile"], r["B"]["t"], r["measured_B_over_A"],

@@ -3,6 +3,7 @@
 // a TMA 2D tile copy for L_TMA / B_TMA (Eq. 4), and a pointer chase for the
 // latency of each memory level (Sec. III-B cites Mei & Chu's p-chase).
 #include <algorithm>
+#include <mutex>
 #include <vector>
 
 #include "pm_internal.cuh"
@@ -529,6 +530,106 @@ extern "C" pm_status pm_probe_run(const pm_probe_args* args, void* buf0, void* b
     out->final_index = fi;
   }
   if (args->kind == PM_PROBE_TMA2D || args->kind == PM_PROBE_MMA || args->kind == PM_PROBE_MBAR) {
+    unsigned int* w = watchdog_word();
+    unsigned int h[2] = {0, 0};
+    PM_CUDA(cudaMemcpy(h, w, sizeof(h), cudaMemcpyDeviceToHost));
+    if (h[0] != 0) {
+      PM_CUDA(cudaMemset(w, 0, 4 * sizeof(unsigned int)));
+      set_error("device watchdog expired at site %u", h[1]);
+      return PM_ETIMEOUT;
+    }
+  }
+  return PM_OK;
+}
+
+// ------------------------------------------------ concurrent-stream probe
+// Sec. III-A.6: N_c kernels in flight on N_c streams of one GPU take the
+// single-stream time plus (N_c - 1) tau_c.  The probe launches one copy of a
+// probe kernel on each of n_streams library-owned non-blocking streams, all
+// released by one event recorded on the caller's stream and joined back on
+// it, and times the makespan between the two events.
+namespace pm {
+constexpr int kMaxConcStreams = 8;
+struct ConcStreams {
+  bool made = false;
+  cudaStream_t s[kMaxConcStreams];
+};
+static std::mutex g_conc_mu;
+static ConcStreams g_conc[64];
+
+static pm_status conc_streams(cudaStream_t** out) {
+  int dev = 0;
+  PM_CUDA(cudaGetDevice(&dev));
+  PM_REQUIRE(dev >= 0 && dev < 64, PM_EINVAL, "device index %d out of range", dev);
+  std::lock_guard<std::mutex> lk(g_conc_mu);
+  ConcStreams& c = g_conc[dev];
+  if (!c.made) {
+    for (int i = 0; i < kMaxConcStreams; ++i) PM_CUDA(cudaStreamCreateWithFlags(&c.s[i], cudaStreamNonBlocking));
+    c.made = true;
+  }
+  *out = c.s;
+  return PM_OK;
+}
+}  // namespace pm
+
+extern "C" pm_status pm_streams_run(const pm_probe_args* per_stream, int32_t n_streams, void* const* buf0,
+                                    void* const* buf1, void* const* buf2, int warmup, int reps, void* stream,
+                                    pm_probe_result* out) {
+  using namespace pm;
+  PM_REQUIRE(per_stream != nullptr && out != nullptr && buf0 != nullptr, PM_EINVAL, "null argument");
+  PM_REQUIRE(n_streams >= 1 && n_streams <= kMaxConcStreams, PM_EINVAL, "n_streams %d outside [1, %d]", n_streams,
+             kMaxConcStreams);
+  const int k = per_stream->kind;
+  PM_REQUIRE(k == PM_PROBE_COPY || k == PM_PROBE_TRIAD || k == PM_PROBE_MMA, PM_EINVAL,
+             "concurrent-stream probe runs COPY, TRIAD or MMA kernels (kind %d)", k);
+  PM_REQUIRE(k == PM_PROBE_MMA || buf1 != nullptr, PM_EINVAL, "copy/triad need buf1 arrays");
+  PM_REQUIRE(k != PM_PROBE_TRIAD || buf2 != nullptr, PM_EINVAL, "triad needs buf2 arrays");
+  PM_REQUIRE(warmup >= 0 && reps >= 1 && reps <= 100000, PM_EINVAL, "warmup >= 0 and 1 <= reps <= 1e5 required");
+  cudaStream_t* cs = nullptr;
+  pm_status st = conc_streams(&cs);
+  if (st != PM_OK) return st;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int total = warmup + reps;
+  std::vector<cudaEvent_t> ev(2 * (size_t)total), done((size_t)total * n_streams);
+  for (auto& e : ev) PM_CUDA(cudaEventCreate(&e));
+  for (auto& e : done) PM_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+  for (int r = 0; r < total && st == PM_OK; ++r) {
+    cudaEventRecord(ev[2 * r], s);
+    for (int i = 0; i < n_streams && st == PM_OK; ++i) {
+      cudaStreamWaitEvent(cs[i], ev[2 * r], 0);
+      st = probe_launch(per_stream, buf0[i], buf1 ? buf1[i] : nullptr, buf2 ? buf2[i] : nullptr, cs[i]);
+      cudaEventRecord(done[(size_t)r * n_streams + i], cs[i]);
+      cudaStreamWaitEvent(s, done[(size_t)r * n_streams + i], 0);
+    }
+    cudaEventRecord(ev[2 * r + 1], s);
+  }
+  cudaError_t e = cudaStreamSynchronize(s);
+  std::vector<double> t;
+  if (st == PM_OK && e == cudaSuccess) {
+    for (int r = warmup; r < total; ++r) {
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, ev[2 * r], ev[2 * r + 1]);
+      t.push_back(ms * 1e-3);
+    }
+  }
+  for (auto& x : ev) cudaEventDestroy(x);
+  for (auto& x : done) cudaEventDestroy(x);
+  if (st != PM_OK) return st;
+  if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+  std::sort(t.begin(), t.end());
+  auto q = [&](double f) {
+    const double pos = f * (t.size() - 1);
+    const size_t lo = (size_t)pos;
+    const size_t hi = std::min(lo + 1, t.size() - 1);
+    return t[lo] + (pos - lo) * (t[hi] - t[lo]);
+  };
+  out->median_s = q(0.5);
+  out->p25_s = q(0.25);
+  out->p75_s = q(0.75);
+  out->min_s = t.front();
+  out->bytes = (double)n_streams * probe_bytes(per_stream);
+  out->final_index = 0;
+  if (k == PM_PROBE_MMA) {
     unsigned int* w = watchdog_word();
     unsigned int h[2] = {0, 0};
     PM_CUDA(cudaMemcpy(h, w, sizeof(h), cudaMemcpyDeviceToHost));

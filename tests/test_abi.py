@@ -101,6 +101,19 @@ def test_bad_arguments_rejected(pm):
     assert L.pm_grouped_autotune(2, Mh, 64, 64, 1, ctypes.byref(th), 152, o16, o16, launch, ctypes.byref(t),
                                  None) == pm.PM_EINVAL
     assert L.pm_watchdog_selftest(0, None) == pm.PM_EINVAL
+    # concurrent-stream probe: argument checks come before any CUDA call
+    bufs = (ctypes.c_void_p * 8)(*([16] * 8))
+    vp = ctypes.cast(bufs, ctypes.c_void_p)
+    copy = pm.probe_args(pm.PM_PROBE_COPY, n=1024)
+    assert L.pm_streams_run(ctypes.byref(copy), 0, vp, vp, None, 1, 1, None, ctypes.byref(res)) == pm.PM_EINVAL
+    assert L.pm_streams_run(ctypes.byref(copy), 9, vp, vp, None, 1, 1, None, ctypes.byref(res)) == pm.PM_EINVAL
+    assert L.pm_streams_run(ctypes.byref(copy), 2, vp, None, None, 1, 1, None, ctypes.byref(res)) == pm.PM_EINVAL
+    triad = pm.probe_args(pm.PM_PROBE_TRIAD, n=1024)
+    assert L.pm_streams_run(ctypes.byref(triad), 2, vp, vp, None, 1, 1, None, ctypes.byref(res)) == pm.PM_EINVAL
+    chase = pm.probe_args(pm.PM_PROBE_PCHASE, n=1024, hops=10)
+    assert L.pm_streams_run(ctypes.byref(chase), 2, vp, vp, None, 1, 1, None, ctypes.byref(res)) == pm.PM_EINVAL
+    assert L.pm_streams_run(ctypes.byref(copy), 2, vp, vp, None, 1, 0, None, ctypes.byref(res)) == pm.PM_EINVAL
+    assert L.pm_streams_run(None, 2, vp, vp, None, 1, 1, None, ctypes.byref(res)) == pm.PM_EINVAL
 
 
 def test_tile_space_matches_oracle_rule(pm):

@@ -106,3 +106,14 @@ def test_probe_priors_replace_only_measured_parameters():
     assert th[12] == pytest.approx(50e-9) and th[10] == 2e12 and th[11] == 1e12
     keep = [j for j in range(16) if j not in (6, 7, 8, 10, 11, 12)]
     assert np.array_equal(th[keep], base[keep])
+
+
+def test_tau_c_fit_recovers_additive_law():
+    # T(N_c) = T1 + (N_c - 1) tau_c exactly: the fit returns tau_c, MAE 0
+    counts = C.STREAM_COUNTS
+    t = [2e-5 + (n - 1) * 7e-6 for n in counts]
+    f = C.fit_tau_c(counts, t)
+    assert f["T1_s"] == 2e-5 and f["tau_c_s"] == pytest.approx(7e-6, rel=1e-12) and f["mae_pct"] < 1e-9
+    # perfect overlap gives tau_c = 0; full serialisation gives tau_c = T1
+    assert C.fit_tau_c(counts, [3e-5] * len(counts))["tau_c_s"] == pytest.approx(0.0, abs=1e-18)
+    assert C.fit_tau_c(counts, [3e-5 * n for n in counts])["tau_over_T1"] == pytest.approx(1.0, rel=1e-12)
