@@ -77,7 +77,8 @@ typedef struct {
  *  0 T_launch   1 B_sus      2 B_peak     3 w0          4 L_TMA      5 B_TMA/SM
  *  6 R_TC tf32  7 R_TC bf16  8 R_TC fp8   9 L_mma      10 BW_TMEM_rd 11 BW_TMEM_wr
  * 12 L_mbar    13 L_alloc+L_dealloc      14 S_2SM      15 c_alpha
- * with the overlap law alpha(stages) = clamp(1 - c_alpha/stages, 0, 1). */
+ * with the overlap law alpha(stages) = clamp(1 - c_alpha/(stages - 1), 0, 1)
+ * (alpha = 0 for a single stage). */
 typedef struct { float v[16]; } pm_params;
 
 /* ------------------------------------------------------------------ probes */

@@ -270,7 +270,7 @@ def prior_theta(n_sm: int, f_hz: float = 1.9e9) -> np.ndarray:
     th[12] = 45.0 / f_hz              # L_mbar 40-50 cycles
     th[13] = 100e-9                   # TMEM alloc + dealloc (not printed)
     th[14] = 1.0                      # S_2SM
-    th[15] = 0.3                      # alpha(2) = 0.85, alpha(6) = 0.95
+    th[15] = 0.15                     # alpha(2) = 0.85, alpha(3) = 0.925 (double to triple buffering)
     return th
 
 

@@ -225,7 +225,7 @@ template <> inline Dual lift<Dual>(double v) { return dconst(v); }
 // 12 L_mbar        mbarrier latency                          (T_sync)
 // 13 L_alloc+L_dealloc  TMEM management                      (T_TMEM_mgmt)
 // 14 S_2SM         2-SM cooperative speedup                  (Eq. 6)
-// 15 c_alpha       overlap law alpha(s) = clamp(1 - c_alpha/s, 0, 1)
+// 15 c_alpha       overlap law alpha(s) = clamp(1 - c_alpha/(s-1), 0, 1)
 // ---------------------------------------------------------------------------
 
 enum { K_GEMM = 0, K_COPY = 1, K_TRIAD = 2, K_TMA2D = 3 };
@@ -313,8 +313,10 @@ static void stage_terms(const Cfg& c, i64 Kt, const T* th, T& Tstep, T& Tstore) 
   const T T_tma = th[4] + b_step / th[5];
   // T_sync = N_bar * L_mbar with N_bar = 2 (full and empty barrier per stage).
   const T T_sync = 2.0 * th[12];
-  // Eq. 7 with T_decomp = 0 and alpha from the pipeline depth.
-  const T alpha = dclamp01(1.0 - th[15] / lift<T>((double)c.s));
+  // Eq. 7 with T_decomp = 0 and alpha from the pipeline depth: while one
+  // stage is consumed the ring keeps s - 1 loads in flight, so the exposed
+  // share of a load falls as c_alpha / (s - 1); one stage overlaps nothing.
+  const T alpha = c.s <= 1 ? lift<T>(0.0) : dclamp01(1.0 - th[15] / lift<T>((double)(c.s - 1)));
   const T T_io = (1.0 - alpha) * T_tma + T_sync;
   // Eq. 8, O_misc = 0.
   Tstep = dmax(T_c, T_io) + T_sync;

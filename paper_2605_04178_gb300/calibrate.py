@@ -60,7 +60,7 @@ def prior_theta(n_sm: int, f_hz: float = 1.9e9) -> np.ndarray:
     th[12] = 45.0 / f_hz
     th[13] = 100e-9
     th[14] = 1.0
-    th[15] = 0.3
+    th[15] = 0.15
     return th
 
 

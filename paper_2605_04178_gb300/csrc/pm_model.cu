@@ -103,8 +103,9 @@ __device__ __forceinline__ void gemm_forward(const pm_cfg& c, const Theta& th, i
   f.bstep = l * e * c.BK * ((float)c.BM + (float)c.BN / (float)g);
   f.T_tma = th.v[4] + f.bstep / th.v[5];
   const float T_sync = 2.f * th.v[12];
-  // 1 - alpha = clamp(c_alpha / s, 0, 1)
-  const float r = th.v[15] / (float)c.stages;
+  // 1 - alpha = clamp(c_alpha / (s - 1), 0, 1): s - 1 loads in flight while
+  // one stage is consumed; a single stage hides nothing
+  const float r = c.stages > 1 ? th.v[15] / (float)(c.stages - 1) : 1.f;
   f.oma_free = r > 0.f && r < 1.f;
   f.oma = r <= 0.f ? 0.f : (r >= 1.f ? 1.f : r);
   f.T_io = f.oma * f.T_tma + T_sync;
@@ -149,7 +150,7 @@ __device__ __forceinline__ void gemm_adjoint(const pm_cfg& c, const Theta& th, c
   // T_io = oma * T_tma + T_sync
   g_sync += g_io;
   const float g_tma = g_io * f.oma;
-  if (f.oma_free) d[15] += g_io * f.T_tma / (float)c.stages;
+  if (f.oma_free) d[15] += g_io * f.T_tma / (float)(c.stages - 1);
   d[4] += g_tma;
   d[5] -= g_tma * (f.bstep / th.v[5]) / th.v[5];
   d[12] += 2.f * g_sync;

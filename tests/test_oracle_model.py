@@ -47,6 +47,22 @@ def test_hand_evaluated_rows(row, expect):
     assert one(PRIOR160, **row) == pytest.approx(expect, rel=2e-6)
 
 
+# Load-bound rows (T_io > T_c) that pin the overlap law alpha(s) = 1 - c/(s-1)
+# of Eq. 7: hand evaluated as above with c_alpha = 0.9, so 1 - alpha = 0.3 at
+# 4 stages and 0.18 at 6.
+HAND_ROWS_LOAD_BOUND = [
+    (dict(M=4096, N=4096, K=4096, BM=64, BN=64, BK=128, stages=4, cta_group=1, dtype=1), 3.472108e-04),
+    (dict(M=4096, N=4096, K=4096, BM=64, BN=64, BK=128, stages=6, cta_group=1, dtype=1), 2.481631e-04),
+]
+
+
+@pytest.mark.parametrize("row,expect", HAND_ROWS_LOAD_BOUND)
+def test_hand_evaluated_load_bound_rows(row, expect):
+    th = PRIOR160.copy()
+    th[15] = 0.9
+    assert one(th, **row) == pytest.approx(expect, rel=2e-6)
+
+
 def test_valid_config_counts():
     counts = {d: sum(O.cfg_valid(*t, d) for t in S.tile_space(d)) for d in (0, 1, 2)}
     assert counts[1] == 121 and counts[2] == 168
