@@ -242,6 +242,16 @@ pm_status pm_model_grad(const pm_cfg* cfgs_dev, int64_t n, const pm_params* thet
                         const float* t_meas_dev, void* workspace_dev, size_t workspace_bytes, double* out_dev,
                         void* stream);
 
+/* pm_model_grad evaluated entirely in FP64 (parameters, per-configuration
+ * model and adjoint, log residuals), for the calibration fit: the FP32
+ * objective is piecewise flat at the 1e-7 level, which stalls the line
+ * searches of a quasi-Newton fit near its optimum.  theta_host: 16 doubles
+ * in the pm_params order; t_meas_dev: n doubles (8-byte aligned); workspace
+ * and output as for pm_model_grad.  Async. */
+pm_status pm_model_grad_f64(const pm_cfg* cfgs_dev, int64_t n, const double* theta_host, int32_t n_sm,
+                            const double* t_meas_dev, void* workspace_dev, size_t workspace_bytes, double* out_dev,
+                            void* stream);
+
 /* The k predicted-fastest valid configurations per shape (k <= 16), sorted
  * by predicted time: picks_dev n*k pm_cfg, t_pred_dev n*k floats.  Entries
  * past the number of valid configurations have BM = 0 and t = +inf.  Async. */

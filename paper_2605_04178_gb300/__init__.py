@@ -60,7 +60,7 @@ assert ctypes.sizeof(pm_cfg) == 24 and ctypes.sizeof(pm_probe_args) == 56 and ct
 # Every exported symbol of include/perfmodel.h
 EXPORTS = ("pm_probe_launch", "pm_probe_run", "pm_streams_run", "pm_gemm_operand_bytes", "pm_gemm_prepare", "pm_gemm_run",
            "pm_gemm_bench", "pm_gemm_host_workspace", "pm_gemm_host",
-           "pm_grouped_gemm_run", "pm_model_predict", "pm_model_grad_workspace", "pm_model_grad", "pm_model_grad_noalloc",
+           "pm_grouped_gemm_run", "pm_model_predict", "pm_model_grad_workspace", "pm_model_grad", "pm_model_grad_f64", "pm_model_grad_noalloc",
            "pm_autotune_pick", "pm_autotune_topk", "pm_gemm_autotune", "pm_grouped_autotune", "pm_last_error", "pm_device_status",
            "pm_watchdog_selftest", "pm_version")
 
@@ -101,6 +101,7 @@ def _load():
         "pm_model_grad_workspace": [i64, ctypes.POINTER(sz)],
         "pm_model_grad": [P, i64, ctypes.POINTER(pm_params), i32, P, P, sz, P, P],
         "pm_model_grad_noalloc": [P, i64, ctypes.POINTER(pm_params), i32, P, P, P],
+        "pm_model_grad_f64": [P, i64, P, i32, P, P, sz, P, P],
         "pm_autotune_pick": [P, i64, i32, ctypes.POINTER(pm_params), i32, P, P, P],
         "pm_autotune_topk": [P, i64, i32, ctypes.POINTER(pm_params), i32, i32, P, P, P],
         "pm_gemm_autotune": [ctypes.POINTER(pm_cfg), i32, ctypes.POINTER(pm_params), i32, P, P, P, P, ctypes.c_int,
@@ -297,6 +298,14 @@ def pm_model_grad(cfgs_dev, n, theta, n_sm, t_meas, workspace, out, stream=None)
     _check(_lib.pm_model_grad(_ptr(cfgs_dev), int(n), ctypes.byref(params(theta)), int(n_sm), _ptr(t_meas),
                               _ptr(workspace), int(workspace.numel() * workspace.element_size()), _ptr(out),
                               _stream(stream)), "pm_model_grad")
+
+
+def pm_model_grad_f64(cfgs_dev, n, theta, n_sm, t_meas, workspace, out, stream=None):
+    """pm_model_grad in FP64 throughout: theta as 16 doubles, t_meas a float64 device tensor."""
+    th = (ctypes.c_double * 16)(*[float(v) for v in theta])
+    _check(_lib.pm_model_grad_f64(_ptr(cfgs_dev), int(n), ctypes.cast(th, ctypes.c_void_p), int(n_sm), _ptr(t_meas),
+                                  _ptr(workspace), int(workspace.numel() * workspace.element_size()), _ptr(out),
+                                  _stream(stream)), "pm_model_grad_f64")
 
 
 def pm_model_grad_noalloc(cfgs_dev, n, theta, n_sm, t_meas, out, stream=None):

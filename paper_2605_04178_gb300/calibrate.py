@@ -317,12 +317,14 @@ def probe_priors(instr: dict, n_sm: int, f_hz: float = 1.9e9) -> np.ndarray:
 # ------------------------------------------------------------ autograd + fit
 class StageModelLoss(torch.autograd.Function):
     """L(theta) = mean_i (ln T_hat_i(theta) - ln T_i)^2 on the GPU; the backward
-    pass returns the gradient from the hand-written adjoint kernel."""
+    pass returns the gradient from the hand-written adjoint kernel.  A float64
+    t_meas selects the all-FP64 evaluation (pm_model_grad_f64)."""
 
     @staticmethod
     def forward(ctx, theta, cfg_dev, n, t_meas_dev, n_sm, workspace):
         out = torch.empty(17, dtype=torch.float64, device=cfg_dev.device)
-        pm.pm_model_grad(cfg_dev, n, theta.detach().cpu().numpy(), n_sm, t_meas_dev, workspace, out)
+        grad_fn = pm.pm_model_grad_f64 if t_meas_dev.dtype == torch.float64 else pm.pm_model_grad
+        grad_fn(cfg_dev, n, theta.detach().cpu().numpy(), n_sm, t_meas_dev, workspace, out)
         o = out.cpu()
         ctx.save_for_backward(o[1:].clone().to(theta.dtype))
         return o[0].to(theta.dtype)
@@ -340,7 +342,7 @@ class GpuObjective:
         self.n = len(rows)
         cols = {f: np.array([r.get(f, 0) for r in rows], dtype=np.int64) for f in FIELDS}
         self.cfg = pm.cfg_tensor(cols)
-        self.t = torch.tensor([r["t"] for r in rows], dtype=torch.float32, device="cuda")
+        self.t = torch.tensor([r["t"] for r in rows], dtype=torch.float64, device="cuda")
         self.ws = torch.empty(pm.pm_model_grad_workspace(self.n) // 8 + 1, dtype=torch.float64, device="cuda")
         self.n_sm = n_sm
 

@@ -17,9 +17,20 @@
 
 namespace pm {
 
-struct Theta {
-  float v[16];
+// Parameters in the arithmetic type F: FP32 for the batched throughput
+// paths, FP64 for the calibration objective (pm_model_grad_f64).
+template <class F>
+struct ThetaT {
+  F v[16];
 };
+using Theta = ThetaT<float>;
+
+__device__ __forceinline__ float pm_exp(float x) { return expf(x); }
+__device__ __forceinline__ double pm_exp(double x) { return exp(x); }
+__device__ __forceinline__ float pm_log(float x) { return logf(x); }
+__device__ __forceinline__ double pm_log(double x) { return log(x); }
+__device__ __forceinline__ float pm_max(float a, float b) { return fmaxf(a, b); }
+__device__ __forceinline__ double pm_max(double a, double b) { return fmax(a, b); }
 
 __device__ __forceinline__ int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
@@ -56,14 +67,16 @@ __host__ __device__ inline bool tile_valid(int BM, int BN, int BK, int s, int g,
 }
 
 // Intermediate values of one GEMM evaluation, kept for the adjoint.
-struct GemmFwd {
-  float T, T_stage, T_rl, A_rl, B_rl;
-  float T_c, T_io, T_tma, oma, X, R, S, T_step, T_store;
-  float D, DA_r, DA_w, bstep, store_bytes, n_instr;
-  float waves, Kt;
+template <class F>
+struct GemmFwdT {
+  F T, T_stage, T_rl, A_rl, B_rl;
+  F T_c, T_io, T_tma, oma, X, R, S, T_step, T_store;
+  F D, DA_r, DA_w, bstep, store_bytes, n_instr;
+  F waves, Kt;
   int ri;
   bool oma_free;
 };
+using GemmFwd = GemmFwdT<float>;
 
 // Stage-centric GEMM time:
 //   T_TMEM = (D + D_A,r)/BW_rd + n_instr L_mma + (D + D_A,w)/BW_wr   (Eq. 2)
@@ -76,46 +89,47 @@ struct GemmFwd {
 //   T_step = max(T_c, T_io) + T_sync                             (Eq. 8)
 //   T_stage = T_launch + waves (K_tiles T_step + T_store)
 //   T_hat = max(T_stage, T_launch + max(FLOPs/(n_SM R S), bytes_min/B_peak))
-__device__ __forceinline__ void gemm_forward(const pm_cfg& c, const Theta& th, int n_sm, GemmFwd& f) {
+template <class F>
+__device__ __forceinline__ void gemm_forward(const pm_cfg& c, const ThetaT<F>& th, int n_sm, GemmFwdT<F>& f) {
   const int dt = c.dtype, g = c.cta_group;
-  const float e = dt_bytes(dt), np = dt_passes(dt), l = dt_loads(dt);
+  const F e = dt_bytes(dt), np = dt_passes(dt), l = dt_loads(dt);
   f.ri = dt_rate(dt);
   f.R = th.v[f.ri];
   const int64_t Kt = cdiv(c.K, c.BK);
   const int64_t tiles = (int64_t)g * cdiv(c.M, (int64_t)g * c.BM) * cdiv(c.N, c.BN);
   const int64_t n_conc = g == 1 ? n_sm : 2 * (n_sm / 2);
   const int64_t waves = cdiv(tiles, n_conc);
-  f.Kt = (float)Kt;
-  f.waves = (float)waves;
-  f.D = 4.f * c.BM * c.BN;
+  f.Kt = (F)Kt;
+  f.waves = (F)waves;
+  f.D = F(4) * c.BM * c.BN;
   // L_mma once per tcgen05.mma issued in the K-step: BK/k_instr per 128-row block, per pass
   const int kin = dt == PM_FP32 ? 8 : (dt == PM_BF16 ? 16 : 32);
-  f.n_instr = np * (float)(c.BK / kin) * (float)((c.BM + 127) / 128);
-  f.DA_w = c.tmem_a ? l * e * c.BM * c.BK : 0.f;
-  f.DA_r = c.tmem_a ? np * e * c.BM * c.BK : 0.f;
+  f.n_instr = np * (F)(c.BK / kin) * (F)((c.BM + 127) / 128);
+  f.DA_w = c.tmem_a ? l * e * c.BM * c.BK : F(0);
+  f.DA_r = c.tmem_a ? np * e * c.BM * c.BK : F(0);
   // strategy B also issues one tcgen05.cp per 128-row x 32-byte A slice, each charged L_mma
-  if (c.tmem_a) f.n_instr += l * (float)(c.BK * (int)e / 32) * (float)((c.BM + 127) / 128);
-  const float T_tmem = (f.D + f.DA_r) / th.v[10] + f.n_instr * th.v[9] + (f.D + f.DA_w) / th.v[11];
-  const float T_mgmt = th.v[13] / f.Kt;
-  f.S = g == 1 ? 1.f : th.v[14];
-  f.X = (np * 2.f * c.BM * c.BN * c.BK) / (f.R * f.S);
+  if (c.tmem_a) f.n_instr += l * (F)(c.BK * (int)e / 32) * (F)((c.BM + 127) / 128);
+  const F T_tmem = (f.D + f.DA_r) / th.v[10] + f.n_instr * th.v[9] + (f.D + f.DA_w) / th.v[11];
+  const F T_mgmt = th.v[13] / f.Kt;
+  f.S = g == 1 ? F(1) : th.v[14];
+  f.X = (np * F(2) * c.BM * c.BN * c.BK) / (f.R * f.S);
   f.T_c = f.X + T_tmem + T_mgmt;
-  f.bstep = l * e * c.BK * ((float)c.BM + (float)c.BN / (float)g);
+  f.bstep = l * e * c.BK * ((F)c.BM + (F)c.BN / (F)g);
   f.T_tma = th.v[4] + f.bstep / th.v[5];
-  const float T_sync = 2.f * th.v[12];
+  const F T_sync = F(2) * th.v[12];
   // 1 - alpha = clamp(c_alpha / (s - 1), 0, 1): s - 1 loads in flight while
   // one stage is consumed; a single stage hides nothing
-  const float r = c.stages > 1 ? th.v[15] / (float)(c.stages - 1) : 1.f;
-  f.oma_free = r > 0.f && r < 1.f;
-  f.oma = r <= 0.f ? 0.f : (r >= 1.f ? 1.f : r);
+  const F r = c.stages > 1 ? th.v[15] / (F)(c.stages - 1) : F(1);
+  f.oma_free = r > F(0) && r < F(1);
+  f.oma = r <= F(0) ? F(0) : (r >= F(1) ? F(1) : r);
   f.T_io = f.oma * f.T_tma + T_sync;
-  f.T_step = fmaxf(f.T_c, f.T_io) + T_sync;
-  f.store_bytes = 4.f * c.BM * c.BN;
+  f.T_step = pm_max(f.T_c, f.T_io) + T_sync;
+  f.store_bytes = F(4) * c.BM * c.BN;
   f.T_store = th.v[4] + f.store_bytes / th.v[5];
   f.T_stage = th.v[0] + f.waves * (f.Kt * f.T_step + f.T_store);
-  const float flops = np * 2.f * (float)c.M * (float)c.N * (float)c.K;
-  const float bytes_min = l * e * ((float)c.M * c.K + (float)c.N * c.K) + 4.f * (float)c.M * (float)c.N;
-  f.A_rl = flops / ((float)n_sm * f.R * f.S);
+  const F flops = np * F(2) * (F)c.M * (F)c.N * (F)c.K;
+  const F bytes_min = l * e * ((F)c.M * c.K + (F)c.N * c.K) + F(4) * (F)c.M * (F)c.N;
+  f.A_rl = flops / ((F)n_sm * f.R * f.S);
   f.B_rl = bytes_min / th.v[2];
   f.T_rl = th.v[0] + (f.A_rl >= f.B_rl ? f.A_rl : f.B_rl);
   f.T = f.T_stage >= f.T_rl ? f.T_stage : f.T_rl;
@@ -123,14 +137,15 @@ __device__ __forceinline__ void gemm_forward(const pm_cfg& c, const Theta& th, i
 
 // Adjoint of gemm_forward: d[j] += w * dT_hat/dtheta_j.  max() passes the
 // gradient to its first argument on ties; the clamp stops it outside (0,1).
-__device__ __forceinline__ void gemm_adjoint(const pm_cfg& c, const Theta& th, const GemmFwd& f, float w,
-                                             float (&d)[16]) {
-  float g_stage = 0.f, g_rl = 0.f;
+template <class F>
+__device__ __forceinline__ void gemm_adjoint(const pm_cfg& c, const ThetaT<F>& th, const GemmFwdT<F>& f, F w,
+                                             F (&d)[16]) {
+  F g_stage = F(0), g_rl = F(0);
   if (f.T_stage >= f.T_rl) g_stage = w; else g_rl = w;
-  float gR = 0.f, gS = 0.f;
+  F gR = F(0), gS = F(0);
   // roofline branch
   d[0] += g_rl;
-  if (g_rl != 0.f) {
+  if (g_rl != F(0)) {
     if (f.A_rl >= f.B_rl) {
       gR -= g_rl * f.A_rl / f.R;
       gS -= g_rl * f.A_rl / f.S;
@@ -140,20 +155,20 @@ __device__ __forceinline__ void gemm_adjoint(const pm_cfg& c, const Theta& th, c
   }
   // stage branch
   d[0] += g_stage;
-  const float g_step = g_stage * f.waves * f.Kt;
-  const float g_store = g_stage * f.waves;
+  const F g_step = g_stage * f.waves * f.Kt;
+  const F g_store = g_stage * f.waves;
   d[4] += g_store;
   d[5] -= g_store * (f.store_bytes / th.v[5]) / th.v[5];
-  float g_sync = g_step;
-  float g_c = 0.f, g_io = 0.f;
+  F g_sync = g_step;
+  F g_c = F(0), g_io = F(0);
   if (f.T_c >= f.T_io) g_c = g_step; else g_io = g_step;
   // T_io = oma * T_tma + T_sync
   g_sync += g_io;
-  const float g_tma = g_io * f.oma;
-  if (f.oma_free) d[15] += g_io * f.T_tma / (float)(c.stages - 1);
+  const F g_tma = g_io * f.oma;
+  if (f.oma_free) d[15] += g_io * f.T_tma / (F)(c.stages - 1);
   d[4] += g_tma;
   d[5] -= g_tma * (f.bstep / th.v[5]) / th.v[5];
-  d[12] += 2.f * g_sync;
+  d[12] += F(2) * g_sync;
   // T_c = X + (D + D_A,r)/BW_rd + n_instr L_mma + (D + D_A,w)/BW_wr + L_mgmt/K_tiles
   gR -= g_c * f.X / f.R;
   gS -= g_c * f.X / f.S;
@@ -162,37 +177,40 @@ __device__ __forceinline__ void gemm_adjoint(const pm_cfg& c, const Theta& th, c
   d[11] -= g_c * ((f.D + f.DA_w) / th.v[11]) / th.v[11];
   d[13] += g_c / f.Kt;
   // static indices keep d[] in registers
-  d[6] += f.ri == 6 ? gR : 0.f;
-  d[7] += f.ri == 7 ? gR : 0.f;
-  d[8] += f.ri == 8 ? gR : 0.f;
+  d[6] += f.ri == 6 ? gR : F(0);
+  d[7] += f.ri == 7 ? gR : F(0);
+  d[8] += f.ri == 8 ? gR : F(0);
   if (c.cta_group == 2) d[14] += gS;
 }
 
 // Memory probes.  Copy/triad through Eq. 16 with W = beta bytes moved;
 // TMA2D: tile latency plus ceil(tiles/SMs) tile round trips (Eq. 4),
 // bounded below by the streaming time of Eq. 16.
-struct ProbeFwd {
-  float T, T1, T2, Bw, E, W, beta, moved_tiles;
+template <class F>
+struct ProbeFwdT {
+  F T, T1, T2, Bw, E, W, beta, moved_tiles;
   bool blend;
 };
+using ProbeFwd = ProbeFwdT<float>;
 
-__device__ __forceinline__ void probe_forward(const pm_cfg& c, const Theta& th, int n_sm, ProbeFwd& f) {
-  float W, t2num;
+template <class F>
+__device__ __forceinline__ void probe_forward(const pm_cfg& c, const ThetaT<F>& th, int n_sm, ProbeFwdT<F>& f) {
+  F W, t2num;
   if (c.kind == PM_KIND_COPY || c.kind == PM_KIND_TRIAD) {
-    f.beta = (c.kind == PM_KIND_COPY ? 8.f : 12.f) * (float)c.M;
+    f.beta = (c.kind == PM_KIND_COPY ? F(8) : F(12)) * (F)c.M;
     W = f.beta;
     t2num = f.beta;
   } else {
-    const float t = 4.f * c.BM * c.BN;
+    const F t = F(4) * c.BM * c.BN;
     const int64_t nt = cdiv(c.M, c.BM) * cdiv(c.N, c.BN);
-    f.moved_tiles = (float)cdiv(nt, n_sm) * 2.f * t;
-    f.beta = 8.f * (float)c.M * (float)c.N;
+    f.moved_tiles = (F)cdiv(nt, n_sm) * F(2) * t;
+    f.beta = F(8) * (F)c.M * (F)c.N;
     W = f.beta;
     t2num = f.moved_tiles;
   }
   f.W = W;
-  f.blend = th.v[3] > 0.f;
-  f.E = f.blend ? expf(-W / th.v[3]) : 0.f;
+  f.blend = th.v[3] > F(0);
+  f.E = f.blend ? pm_exp(-W / th.v[3]) : F(0);
   f.Bw = f.blend ? th.v[1] + (th.v[2] - th.v[1]) * f.E : th.v[1];
   if (c.kind == PM_KIND_COPY || c.kind == PM_KIND_TRIAD) {
     f.T1 = th.v[0] + f.beta / f.Bw;
@@ -204,19 +222,21 @@ __device__ __forceinline__ void probe_forward(const pm_cfg& c, const Theta& th, 
   f.T = f.T1 >= f.T2 ? f.T1 : f.T2;
 }
 
-__device__ __forceinline__ void bw_adjoint(const Theta& th, const ProbeFwd& f, float gB, float (&d)[16]) {
+template <class F>
+__device__ __forceinline__ void bw_adjoint(const ThetaT<F>& th, const ProbeFwdT<F>& f, F gB, F (&d)[16]) {
   if (f.blend) {
-    d[1] += gB * (1.f - f.E);
+    d[1] += gB * (F(1) - f.E);
     d[2] += gB * f.E;
-    const float gE = gB * (th.v[2] - th.v[1]);
+    const F gE = gB * (th.v[2] - th.v[1]);
     d[3] += gE * f.E * f.W / (th.v[3] * th.v[3]);
   } else {
     d[1] += gB;
   }
 }
 
-__device__ __forceinline__ void probe_adjoint(const pm_cfg& c, const Theta& th, const ProbeFwd& f, float w,
-                                              float (&d)[16]) {
+template <class F>
+__device__ __forceinline__ void probe_adjoint(const pm_cfg& c, const ThetaT<F>& th, const ProbeFwdT<F>& f, F w,
+                                              F (&d)[16]) {
   d[0] += w;
   const bool first = f.T1 >= f.T2;
   if (c.kind == PM_KIND_COPY || c.kind == PM_KIND_TRIAD) {
@@ -282,38 +302,42 @@ __device__ __forceinline__ double warp_sum_d(double v) {
   return v;
 }
 
+// F = float: per-configuration FP32 terms (throughput path); F = double: the
+// whole evaluation in FP64 so the calibration's line searches see a smooth
+// objective.
+template <class F>
 __global__ void __launch_bounds__(kGradThreads) model_grad_kernel(const pm_cfg* __restrict__ cfgs, int64_t n,
-                                                                  Theta th, int n_sm,
-                                                                  const float* __restrict__ t_meas,
+                                                                  ThetaT<F> th, int n_sm,
+                                                                  const F* __restrict__ t_meas,
                                                                   double* __restrict__ partials) {
-  float acc[17];
+  F acc[17];
 #pragma unroll
-  for (int j = 0; j < 17; ++j) acc[j] = 0.f;
+  for (int j = 0; j < 17; ++j) acc[j] = F(0);
   double loss = 0.0;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     const pm_cfg c = load_cfg(cfgs + i);
-    float d[16];
+    F d[16];
 #pragma unroll
-    for (int j = 0; j < 16; ++j) d[j] = 0.f;
-    float T;
+    for (int j = 0; j < 16; ++j) d[j] = F(0);
+    F T;
     if (!cfg_sane(c)) {
-      T = __int_as_float(0x7fc00000);
+      T = (F)__int_as_float(0x7fc00000);
     } else if (c.kind == PM_KIND_GEMM) {
-      GemmFwd f;
+      GemmFwdT<F> f;
       gemm_forward(c, th, n_sm, f);
       T = f.T;
-      gemm_adjoint(c, th, f, 1.f, d);
+      gemm_adjoint(c, th, f, F(1), d);
     } else {
-      ProbeFwd f;
+      ProbeFwdT<F> f;
       probe_forward(c, th, n_sm, f);
       T = f.T;
-      probe_adjoint(c, th, f, 1.f, d);
+      probe_adjoint(c, th, f, F(1), d);
     }
-    const float r = logf(T) - logf(__ldg(t_meas + i));
+    const F r = pm_log(T) - pm_log(__ldg(t_meas + i));
     loss += (double)r * (double)r;
-    const float w = 2.f * r / T;
+    const F w = F(2) * r / T;
 #pragma unroll
-    for (int j = 0; j < 16; ++j) acc[j] = fmaf(w, d[j], acc[j]);
+    for (int j = 0; j < 16; ++j) acc[j] = fma(w, d[j], acc[j]);
   }
   __shared__ double red[kGradThreads / 32][17];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -615,8 +639,31 @@ extern "C" pm_status pm_model_grad(const pm_cfg* cfgs_dev, int64_t n, const pm_p
              "workspace of %zu bytes is smaller than the %zu needed", workspace_bytes,
              (size_t)blocks * 17 * sizeof(double));
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  model_grad_kernel<<<blocks, kGradThreads, 0, s>>>(cfgs_dev, n, to_theta(theta_host), n_sm, t_meas_dev,
-                                                    static_cast<double*>(workspace_dev));
+  model_grad_kernel<float><<<blocks, kGradThreads, 0, s>>>(cfgs_dev, n, to_theta(theta_host), n_sm, t_meas_dev,
+                                                           static_cast<double*>(workspace_dev));
+  pm_status st = launch_status("model_grad_kernel");
+  if (st != PM_OK) return st;
+  model_grad_finish_kernel<<<1, 17 * 32, 0, s>>>(static_cast<const double*>(workspace_dev), blocks, n, out_dev);
+  return launch_status("model_grad_finish_kernel");
+}
+
+extern "C" pm_status pm_model_grad_f64(const pm_cfg* cfgs_dev, int64_t n, const double* theta_host, int32_t n_sm,
+                                       const double* t_meas_dev, void* workspace_dev, size_t workspace_bytes,
+                                       double* out_dev, void* stream) {
+  PM_REQUIRE(n > 0, PM_EINVAL, "n must be positive");
+  PM_REQUIRE(cfgs_dev && theta_host && t_meas_dev && workspace_dev && out_dev && n_sm > 0, PM_EINVAL,
+             "null pointer or n_sm <= 0");
+  PM_REQUIRE(((uintptr_t)cfgs_dev & 7) == 0 && ((uintptr_t)workspace_dev & 7) == 0 && ((uintptr_t)t_meas_dev & 7) == 0,
+             PM_EINVAL, "cfgs_dev, t_meas_dev and workspace_dev must be 8-byte aligned");
+  const int blocks = grad_blocks(n);
+  PM_REQUIRE(workspace_bytes >= (size_t)blocks * 17 * sizeof(double), PM_ENOMEM,
+             "workspace of %zu bytes is smaller than the %zu needed", workspace_bytes,
+             (size_t)blocks * 17 * sizeof(double));
+  ThetaT<double> th;
+  for (int j = 0; j < 16; ++j) th.v[j] = theta_host[j];
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  model_grad_kernel<double><<<blocks, kGradThreads, 0, s>>>(cfgs_dev, n, th, n_sm, t_meas_dev,
+                                                            static_cast<double*>(workspace_dev));
   pm_status st = launch_status("model_grad_kernel");
   if (st != PM_OK) return st;
   model_grad_finish_kernel<<<1, 17 * 32, 0, s>>>(static_cast<const double*>(workspace_dev), blocks, n, out_dev);
@@ -761,7 +808,7 @@ extern "C" pm_status pm_model_grad_noalloc(const pm_cfg* cfgs_dev, int64_t n, co
   if (st != PM_OK) return st;
   const int blocks = (int)((n + kGradThreads - 1) / kGradThreads);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  model_grad_kernel<<<blocks, kGradThreads, 0, s>>>(cfgs_dev, n, to_theta(theta_host), n_sm, t_meas_dev, scratch);
+  model_grad_kernel<float><<<blocks, kGradThreads, 0, s>>>(cfgs_dev, n, to_theta(theta_host), n_sm, t_meas_dev, scratch);
   st = launch_status("model_grad_kernel");
   if (st != PM_OK) return st;
   model_grad_finish_kernel<<<1, 17 * 32, 0, s>>>(scratch, blocks, n, out_dev);

@@ -83,6 +83,11 @@ def test_bad_arguments_rejected(pm):
     assert L.pm_model_predict(ctypes.c_void_p(8), 10, ctypes.byref(th), 0, ctypes.c_void_p(8), None) == pm.PM_EINVAL
     assert L.pm_model_predict(None, 0, ctypes.byref(th), 152, None, None) == pm.PM_OK   # empty batch: nothing to do
     assert L.pm_model_grad(None, 0, ctypes.byref(th), 152, None, None, 0, None, None) == pm.PM_EINVAL
+    th64 = (ctypes.c_double * 16)(*([1.0] * 16))
+    assert L.pm_model_grad_f64(None, 10, ctypes.cast(th64, ctypes.c_void_p), 152, None, None, 0, None,
+                               None) == pm.PM_EINVAL
+    assert L.pm_model_grad_f64(ctypes.c_void_p(8), 1000, ctypes.cast(th64, ctypes.c_void_p), 152, ctypes.c_void_p(8),
+                               ctypes.c_void_p(8), 8, ctypes.c_void_p(8), None) == pm.PM_ENOMEM
     sz = ctypes.c_size_t()
     assert L.pm_model_grad_workspace(1000, ctypes.byref(sz)) == pm.PM_OK and sz.value >= 17 * 8
     assert L.pm_model_grad(ctypes.c_void_p(8), 1000, ctypes.byref(th), 152, ctypes.c_void_p(8), ctypes.c_void_p(8),

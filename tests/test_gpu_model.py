@@ -186,3 +186,26 @@ def test_autotune_topk_matches_oracle_order(lib):
             for r in range(k):   # each pick's own FP64 prediction sits at its rank (up to FP32 resolution)
                 j = space.index(got[r])
                 assert abs(to[j] - to[order[r]]) <= 2e-6 * to[order[r]]
+
+
+@pytest.mark.parametrize("n", [1, 1000, 50000])
+def test_grad_f64_matches_oracle_tightly(lib, n):
+    # the all-FP64 objective agrees with the FP64 oracle to rounding order
+    c = random_cfgs(n, seed=29 + n, strategy_b=True)
+    pc = probe_cfgs()
+    c = {k: np.concatenate([c[k], pc[k]]) for k in c}
+    th = THETA.copy()
+    t_true = O.model_batch(c, th, N_SM)
+    t_meas = t_true * np.exp(0.3 * (S.uniform01_f64(31, len(t_true)) - 0.5))
+    dev = lib.cfg_tensor(c)
+    m = len(t_meas)
+    ws = torch.empty(lib.pm_model_grad_workspace(m) // 8, dtype=torch.float64, device="cuda")
+    out = torch.empty(17, dtype=torch.float64, device="cuda")
+    lib.pm_model_grad_f64(dev, m, th, N_SM, torch.from_numpy(t_meas).cuda(), ws, out)
+    o = out.cpu().numpy()
+    L_orc, g_orc = O.model_loss_grad(c, th, N_SM, t_meas)
+    assert o[0] == pytest.approx(L_orc, rel=1e-10)
+    _, gi = O.model_batch(c, th, N_SM, grad=True)
+    r = np.log(t_true) - np.log(t_meas)
+    scale = (2.0 / len(r)) * np.sum(np.abs(r[:, None] * gi / t_true[:, None]), axis=0)
+    assert np.all(np.abs(o[1:] - g_orc) <= 1e-10 * scale + 1e-300), (o[1:], g_orc)
