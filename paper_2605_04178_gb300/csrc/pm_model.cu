@@ -32,7 +32,20 @@ __device__ __forceinline__ double pm_log(double x) { return log(x); }
 __device__ __forceinline__ float pm_max(float a, float b) { return fmaxf(a, b); }
 __device__ __forceinline__ double pm_max(double a, double b) { return fmax(a, b); }
 
-__device__ __forceinline__ int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
+// ceil(a / b) for a >= 0, b > 0: 32-bit unsigned division whenever both fit
+// (64-bit division is a long software sequence), exact either way.
+__device__ __forceinline__ int64_t cdiv(int64_t a, int64_t b) {
+  if (((uint64_t)a | (uint64_t)b) < 0x80000000ull)
+    return (int64_t)(((uint32_t)a + (uint32_t)b - 1u) / (uint32_t)b);
+  return (a + b - 1) / b;
+}
+
+// Non-negative count to the arithmetic type, through a 32-bit conversion
+// when it fits (64-bit conversions run on the narrow FP64 pipe).
+template <class F>
+__device__ __forceinline__ F count_to(int64_t v) {
+  return (uint64_t)v < 0x80000000ull ? (F)(int32_t)v : (F)v;
+}
 
 // Element bytes, tensor passes per K-step (three-pass TF32 for FP32) and
 // operand copies loaded per element (FP32: hi and lo).
@@ -99,8 +112,8 @@ __device__ __forceinline__ void gemm_forward(const pm_cfg& c, const ThetaT<F>& t
   const int64_t tiles = (int64_t)g * cdiv(c.M, (int64_t)g * c.BM) * cdiv(c.N, c.BN);
   const int64_t n_conc = g == 1 ? n_sm : 2 * (n_sm / 2);
   const int64_t waves = cdiv(tiles, n_conc);
-  f.Kt = (F)Kt;
-  f.waves = (F)waves;
+  f.Kt = count_to<F>(Kt);
+  f.waves = count_to<F>(waves);
   f.D = F(4) * c.BM * c.BN;
   // L_mma once per tcgen05.mma issued in the K-step: BK/k_instr per 128-row block, per pass
   const int kin = dt == PM_FP32 ? 8 : (dt == PM_BF16 ? 16 : 32);
@@ -291,16 +304,18 @@ __global__ void __launch_bounds__(256) model_predict_kernel(const pm_cfg* __rest
   }
 }
 
-// Loss and gradient: per-thread FP32 terms, block sums in FP64, one FP64
-// partial record of 17 values per block; a second kernel adds the records
-// in block order (deterministic).
+// Loss and gradient: per-thread terms and warp sums in F, warp totals
+// combined in FP64 into one partial record of 17 values per block; a second
+// kernel adds the records in block order (deterministic).
 constexpr int kGradThreads = 256;
 
-__device__ __forceinline__ double warp_sum_d(double v) {
+template <class T>
+__device__ __forceinline__ T warp_sum(T v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
 }
+__device__ __forceinline__ double warp_sum_d(double v) { return warp_sum<double>(v); }
 
 // F = float: per-configuration FP32 terms (throughput path); F = double: the
 // whole evaluation in FP64 so the calibration's line searches see a smooth
@@ -310,10 +325,10 @@ __global__ void __launch_bounds__(kGradThreads) model_grad_kernel(const pm_cfg* 
                                                                   ThetaT<F> th, int n_sm,
                                                                   const F* __restrict__ t_meas,
                                                                   double* __restrict__ partials) {
-  F acc[17];
+  F acc[16];
 #pragma unroll
-  for (int j = 0; j < 17; ++j) acc[j] = F(0);
-  double loss = 0.0;
+  for (int j = 0; j < 16; ++j) acc[j] = F(0);
+  F loss = F(0);
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     const pm_cfg c = load_cfg(cfgs + i);
     F d[16];
@@ -334,19 +349,21 @@ __global__ void __launch_bounds__(kGradThreads) model_grad_kernel(const pm_cfg* 
       probe_adjoint(c, th, f, F(1), d);
     }
     const F r = pm_log(T) - pm_log(__ldg(t_meas + i));
-    loss += (double)r * (double)r;
+    loss = fma(r, r, loss);
     const F w = F(2) * r / T;
 #pragma unroll
     for (int j = 0; j < 16; ++j) acc[j] = fma(w, d[j], acc[j]);
   }
+  // warp sums in F (FP64 arithmetic is scarce on this GPU), warp totals
+  // combined in FP64
   __shared__ double red[kGradThreads / 32][17];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  double v = warp_sum_d(loss);
-  if (lane == 0) red[warp][0] = v;
+  F v = warp_sum<F>(loss);
+  if (lane == 0) red[warp][0] = (double)v;
 #pragma unroll
   for (int j = 0; j < 16; ++j) {
-    v = warp_sum_d((double)acc[j]);
-    if (lane == 0) red[warp][j + 1] = v;
+    v = warp_sum<F>(acc[j]);
+    if (lane == 0) red[warp][j + 1] = (double)v;
   }
   __syncthreads();
   if (threadIdx.x < 17) {
@@ -372,7 +389,7 @@ __global__ void __launch_bounds__(17 * 32) model_grad_finish_kernel(const double
 
 static int grad_blocks(int64_t n) {
   const int64_t want = (n + kGradThreads - 1) / kGradThreads;
-  const int cap = std::max(1, sm_count()) * 8;
+  const int cap = std::max(1, sm_count()) * 3;             // one wave at the register-limited occupancy
   return (int)std::max<int64_t>(1, std::min<int64_t>(want, cap));
 }
 
