@@ -306,6 +306,19 @@ pm_status pm_grouped_autotune(int32_t G, const int32_t* M_host, int32_t N, int32
                               const pm_params* theta_host, int32_t n_sm, int16_t* BM_out_host,
                               int16_t* BN_out_host, int32_t* launch_out_host, float* t_pred_host, void* stream);
 
+/* Model-pruned measured grouped autotuning (BF16): the grouped autotuner's
+ * k best launch-level candidates (k in 1..20, each with its per-group tiles)
+ * are timed on the caller's operands (pm_grouped_gemm_run layout; warmup
+ * untimed, reps timed launches, CUDA events on `stream`) and the fastest by
+ * median is returned in BM_out_host/BN_out_host/launch_out_host; t_pred_host
+ * (nullable) receives its predicted makespan, pick_time_out (nullable) its
+ * timing.  Overwrites C_dev.  Synchronises. */
+pm_status pm_grouped_gemm_autotune(int32_t G, const int32_t* M_host, int32_t N, int32_t K,
+                                   const pm_params* theta_host, int32_t n_sm, int32_t k, const void* A_op_dev,
+                                   const void* B_op_dev, float* C_dev, int warmup, int reps, void* stream,
+                                   int16_t* BM_out_host, int16_t* BN_out_host, int32_t* launch_out_host,
+                                   float* t_pred_host, pm_probe_result* pick_time_out);
+
 /* ----------------------------------------------------------- diagnostics */
 /* Text of the last error on this host thread (valid until the next call). */
 const char* pm_last_error(void);

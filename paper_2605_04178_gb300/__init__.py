@@ -61,7 +61,7 @@ assert ctypes.sizeof(pm_cfg) == 24 and ctypes.sizeof(pm_probe_args) == 56 and ct
 EXPORTS = ("pm_probe_launch", "pm_probe_run", "pm_streams_run", "pm_gemm_operand_bytes", "pm_gemm_prepare", "pm_gemm_run",
            "pm_gemm_bench", "pm_gemm_host_workspace", "pm_gemm_host",
            "pm_grouped_gemm_run", "pm_model_predict", "pm_model_grad_workspace", "pm_model_grad", "pm_model_grad_f64", "pm_model_grad_noalloc",
-           "pm_autotune_pick", "pm_autotune_topk", "pm_gemm_autotune", "pm_grouped_autotune", "pm_last_error", "pm_device_status",
+           "pm_autotune_pick", "pm_autotune_topk", "pm_gemm_autotune", "pm_grouped_autotune", "pm_grouped_gemm_autotune", "pm_last_error", "pm_device_status",
            "pm_watchdog_selftest", "pm_version")
 
 
@@ -107,6 +107,8 @@ def _load():
         "pm_gemm_autotune": [ctypes.POINTER(pm_cfg), i32, ctypes.POINTER(pm_params), i32, P, P, P, P, ctypes.c_int,
                              ctypes.c_int, P, ctypes.POINTER(pm_cfg), ctypes.POINTER(pm_probe_result)],
         "pm_grouped_autotune": [i32, P, i32, i32, i32, ctypes.POINTER(pm_params), i32, P, P, P, P, P],
+        "pm_grouped_gemm_autotune": [i32, P, i32, i32, ctypes.POINTER(pm_params), i32, i32, P, P, P, ctypes.c_int,
+                                     ctypes.c_int, P, P, P, P, P, ctypes.POINTER(pm_probe_result)],
         "pm_device_status": [ctypes.c_int],
         "pm_watchdog_selftest": [i32, P],
         "pm_version": [],
@@ -345,6 +347,24 @@ def pm_grouped_autotune(M_list, N, K, dtype, theta, n_sm, stream=None):
     _check(_lib.pm_grouped_autotune(G, Mh, int(N), int(K), int(dtype), ctypes.byref(params(theta)), int(n_sm), bm,
                                     bn, launch, ctypes.byref(t), _stream(stream)), "pm_grouped_autotune")
     return float(t.value), list(bm), list(bn), tuple(launch)
+
+
+def pm_grouped_gemm_autotune(M_list, N, K, theta, n_sm, k, A_op, B_op, C, warmup=2, reps=5, stream=None):
+    """The grouped autotuner's k best launches timed on these operands; returns
+    (t_pred, BM list, BN list, (BK, stages, cta_group), timing dict)."""
+    G = len(M_list)
+    Mh = (ctypes.c_int32 * G)(*[int(m) for m in M_list])
+    bm = (ctypes.c_int16 * G)()
+    bn = (ctypes.c_int16 * G)()
+    launch = (ctypes.c_int32 * 3)()
+    t = ctypes.c_float()
+    res = pm_probe_result()
+    _check(_lib.pm_grouped_gemm_autotune(G, Mh, int(N), int(K), ctypes.byref(params(theta)), int(n_sm), int(k),
+                                         _ptr(A_op), _ptr(B_op), _ptr(C), int(warmup), int(reps), _stream(stream),
+                                         bm, bn, launch, ctypes.byref(t), ctypes.byref(res)),
+           "pm_grouped_gemm_autotune")
+    return float(t.value), list(bm), list(bn), tuple(launch), dict(median_s=res.median_s, p25_s=res.p25_s,
+                                                                   p75_s=res.p75_s, min_s=res.min_s)
 
 
 # ---------------------------------------------------------------- diagnostics

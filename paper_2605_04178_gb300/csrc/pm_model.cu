@@ -607,13 +607,6 @@ __global__ void __launch_bounds__(kGroupThreads) grouped_tune_kernel(const int32
   }
 }
 
-__global__ void grouped_pick_kernel(const float* __restrict__ t, int* __restrict__ best) {
-  int b = 0;
-  for (int i = 1; i < 20; ++i)
-    if (t[i] < t[b]) b = i;
-  *best = b;
-}
-
 static Theta to_theta(const pm_params* p) {
   Theta t;
   for (int j = 0; j < 16; ++j) t.v[j] = p->v[j];
@@ -712,17 +705,18 @@ extern "C" pm_status pm_autotune_topk(const int32_t* MNK_dev, int64_t n, int32_t
   return launch_status("autotune_topk_kernel");
 }
 
-extern "C" pm_status pm_grouped_autotune(int32_t G, const int32_t* M_host, int32_t N, int32_t K, int32_t dtype,
-                                         const pm_params* theta_host, int32_t n_sm, int16_t* BM_out_host,
-                                         int16_t* BN_out_host, int32_t* launch_out_host, float* t_pred_host,
-                                         void* stream) {
+namespace pm {
+
+// All 20 launch-level candidates (BK, stages, cta_group) of the grouped
+// autotuner: predicted makespan ht[i] and per-group tiles hbm/hbn[i * G + q].
+static pm_status grouped_candidates(int32_t G, const int32_t* M_host, int32_t N, int32_t K, int32_t dtype,
+                                    const pm_params* theta_host, int32_t n_sm, cudaStream_t s, float* ht,
+                                    std::vector<int16_t>& hbm, std::vector<int16_t>& hbn) {
   PM_REQUIRE(G > 0 && G <= kMaxGroups, PM_EINVAL, "G must be in [1, %d]", kMaxGroups);
-  PM_REQUIRE(M_host && theta_host && BM_out_host && BN_out_host && launch_out_host && t_pred_host && n_sm > 0,
-             PM_EINVAL, "null pointer or n_sm <= 0");
+  PM_REQUIRE(M_host && theta_host && n_sm > 0, PM_EINVAL, "null pointer or n_sm <= 0");
   PM_REQUIRE(N > 0 && K > 0 && dtype >= 0 && dtype <= 2, PM_EINVAL, "bad N, K or dtype");
   for (int q = 0; q < G; ++q) PM_REQUIRE(M_host[q] > 0, PM_EINVAL, "M[%d] <= 0", q);
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
-  // device scratch: M (G int32), t (20 floats), bm/bn (20 x G int16 each), best index
+  // device scratch: M (G int32), t (20 floats), bm/bn (20 x G int16 each)
   const size_t bytes = 256 + G * 4 + 20 * 4 + 2 * 20 * (size_t)G * 2 + 16;
   char* buf = nullptr;
   PM_CUDA(cudaMallocAsync((void**)&buf, bytes, s));
@@ -730,21 +724,14 @@ extern "C" pm_status pm_grouped_autotune(int32_t G, const int32_t* M_host, int32
   float* dt = (float*)(buf + ((G * 4 + 15) & ~15));
   int16_t* dbm = (int16_t*)((char*)dt + 96);
   int16_t* dbn = dbm + 20 * G;
-  int* dbest = (int*)(((uintptr_t)(dbn + 20 * G) + 15) & ~(uintptr_t)15);
+  hbm.assign(20 * (size_t)G, 0);
+  hbn.assign(20 * (size_t)G, 0);
   pm_status st = PM_OK;
-  std::vector<int16_t> hbm(20 * (size_t)G), hbn(20 * (size_t)G);
-  float ht[20];
-  int best = 0;
   cudaError_t e = cudaMemcpyAsync(dM, M_host, G * 4, cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) {
     grouped_tune_kernel<<<20, kGroupThreads, 0, s>>>(dM, G, N, K, dtype, to_theta(theta_host), n_sm, dt, dbm, dbn);
     st = launch_status("grouped_tune_kernel");
-    if (st == PM_OK) {
-      grouped_pick_kernel<<<1, 1, 0, s>>>(dt, dbest);
-      st = launch_status("grouped_pick_kernel");
-    }
-    if (st == PM_OK) e = cudaMemcpyAsync(ht, dt, sizeof(ht), cudaMemcpyDeviceToHost, s);
-    if (st == PM_OK && e == cudaSuccess) e = cudaMemcpyAsync(&best, dbest, 4, cudaMemcpyDeviceToHost, s);
+    if (st == PM_OK) e = cudaMemcpyAsync(ht, dt, 20 * sizeof(float), cudaMemcpyDeviceToHost, s);
     if (st == PM_OK && e == cudaSuccess)
       e = cudaMemcpyAsync(hbm.data(), dbm, hbm.size() * 2, cudaMemcpyDeviceToHost, s);
     if (st == PM_OK && e == cudaSuccess)
@@ -754,15 +741,111 @@ extern "C" pm_status pm_grouped_autotune(int32_t G, const int32_t* M_host, int32
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (st != PM_OK) return st;
   if (e != cudaSuccess) return cuda_fail(e, "grouped autotune copies");
+  return PM_OK;
+}
+
+// Launch-level parameters of candidate i: {BK, stages, cta_group}.
+static void grouped_launch_of(int i, int dtype, int32_t* launch) {
+  launch[0] = (int32_t)(dtype == PM_FP32 ? (i / 10 ? 64 : 32) : (i / 10 ? 128 : 64));
+  launch[1] = 2 + (i / 2) % 5;
+  launch[2] = 1 + i % 2;
+}
+
+}  // namespace pm
+
+extern "C" pm_status pm_grouped_autotune(int32_t G, const int32_t* M_host, int32_t N, int32_t K, int32_t dtype,
+                                         const pm_params* theta_host, int32_t n_sm, int16_t* BM_out_host,
+                                         int16_t* BN_out_host, int32_t* launch_out_host, float* t_pred_host,
+                                         void* stream) {
+  PM_REQUIRE(BM_out_host && BN_out_host && launch_out_host && t_pred_host, PM_EINVAL, "null output pointer");
+  float ht[20];
+  std::vector<int16_t> hbm, hbn;
+  pm_status st = grouped_candidates(G, M_host, N, K, dtype, theta_host, n_sm, static_cast<cudaStream_t>(stream), ht,
+                                    hbm, hbn);
+  if (st != PM_OK) return st;
+  int best = 0;                                   // first minimum, as the GPU's pick kernel scans
+  for (int i = 1; i < 20; ++i)
+    if (ht[i] < ht[best]) best = i;
   PM_REQUIRE(ht[best] < INFINITY, PM_EUNSUPPORTED, "no valid grouped configuration");
   for (int q = 0; q < G; ++q) {
     BM_out_host[q] = hbm[(size_t)best * G + q];
     BN_out_host[q] = hbn[(size_t)best * G + q];
   }
-  launch_out_host[0] = (int32_t)(dtype == PM_FP32 ? (best / 10 ? 64 : 32) : (best / 10 ? 128 : 64));
-  launch_out_host[1] = 2 + (best / 2) % 5;
-  launch_out_host[2] = 1 + best % 2;
+  grouped_launch_of(best, dtype, launch_out_host);
   *t_pred_host = ht[best];
+  return PM_OK;
+}
+
+extern "C" pm_status pm_grouped_gemm_autotune(int32_t G, const int32_t* M_host, int32_t N, int32_t K,
+                                              const pm_params* theta_host, int32_t n_sm, int32_t k,
+                                              const void* A_op_dev, const void* B_op_dev, float* C_dev, int warmup,
+                                              int reps, void* stream, int16_t* BM_out_host, int16_t* BN_out_host,
+                                              int32_t* launch_out_host, float* t_pred_host,
+                                              pm_probe_result* pick_time_out) {
+  PM_REQUIRE(BM_out_host && BN_out_host && launch_out_host, PM_EINVAL, "null output pointer");
+  PM_REQUIRE(k >= 1 && k <= 20, PM_EINVAL, "k must be in [1, 20]");
+  PM_REQUIRE(warmup >= 0 && reps >= 1 && reps <= 100000, PM_EINVAL, "warmup >= 0 and 1 <= reps <= 1e5 required");
+  PM_REQUIRE(A_op_dev && B_op_dev && C_dev, PM_EINVAL, "null operand or output pointer");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  float ht[20];
+  std::vector<int16_t> hbm, hbn;
+  pm_status st = grouped_candidates(G, M_host, N, K, PM_BF16, theta_host, n_sm, s, ht, hbm, hbn);
+  if (st != PM_OK) return st;
+  // the model's k best launches (stable order), each timed; the fastest wins
+  int order[20];
+  for (int i = 0; i < 20; ++i) order[i] = i;
+  std::stable_sort(order, order + 20, [&](int a, int b) { return ht[a] < ht[b]; });
+  cudaEvent_t e0, e1;
+  PM_CUDA(cudaEventCreate(&e0));
+  PM_CUDA(cudaEventCreate(&e1));
+  double best_t = 1e300;
+  int best = -1;
+  pm_probe_result best_r = {};
+  for (int j = 0; j < k && st == PM_OK; ++j) {
+    const int i = order[j];
+    if (!(ht[i] < INFINITY)) break;
+    int32_t L[3];
+    grouped_launch_of(i, PM_BF16, L);
+    const int16_t* bm = hbm.data() + (size_t)i * G;
+    const int16_t* bn = hbn.data() + (size_t)i * G;
+    for (int w = 0; w < warmup && st == PM_OK; ++w)
+      st = pm_grouped_gemm_run(G, M_host, N, K, bm, bn, L[0], L[1], L[2], A_op_dev, B_op_dev, C_dev, stream);
+    std::vector<double> t;
+    for (int r = 0; r < reps && st == PM_OK; ++r) {
+      cudaEventRecord(e0, s);
+      st = pm_grouped_gemm_run(G, M_host, N, K, bm, bn, L[0], L[1], L[2], A_op_dev, B_op_dev, C_dev, stream);
+      cudaEventRecord(e1, s);
+      cudaError_t ce = cudaEventSynchronize(e1);
+      if (ce != cudaSuccess) { st = cuda_fail(ce, "cudaEventSynchronize"); break; }
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      t.push_back(ms * 1e-3);
+    }
+    if (st != PM_OK) break;
+    std::sort(t.begin(), t.end());
+    const double med = t.size() % 2 ? t[t.size() / 2] : 0.5 * (t[t.size() / 2 - 1] + t[t.size() / 2]);
+    if (med < best_t) {
+      best_t = med;
+      best = i;
+      best_r.median_s = med;
+      best_r.p25_s = t[t.size() / 4];
+      best_r.p75_s = t[(3 * t.size()) / 4];
+      best_r.min_s = t.front();
+      best_r.bytes = 0.0;
+      best_r.final_index = 0;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st != PM_OK) return st;
+  PM_REQUIRE(best >= 0, PM_EUNSUPPORTED, "no valid grouped configuration");
+  for (int q = 0; q < G; ++q) {
+    BM_out_host[q] = hbm[(size_t)best * G + q];
+    BN_out_host[q] = hbn[(size_t)best * G + q];
+  }
+  grouped_launch_of(best, PM_BF16, launch_out_host);
+  if (t_pred_host) *t_pred_host = ht[best];
+  if (pick_time_out) *pick_time_out = best_r;
   return PM_OK;
 }
 

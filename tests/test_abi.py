@@ -106,6 +106,12 @@ def test_bad_arguments_rejected(pm):
     assert L.pm_grouped_autotune(2, Mh, 64, 64, 1, ctypes.byref(th), 152, o16, o16, launch, ctypes.byref(t),
                                  None) == pm.PM_EINVAL
     assert L.pm_watchdog_selftest(0, None) == pm.PM_EINVAL
+    Mg = (ctypes.c_int32 * 2)(16, 32)
+    assert L.pm_grouped_gemm_autotune(2, Mg, 64, 64, ctypes.byref(th), 152, 0, ctypes.c_void_p(16),
+                                      ctypes.c_void_p(16), ctypes.c_void_p(16), 1, 1, None, o16, o16, launch,
+                                      None, None) == pm.PM_EINVAL
+    assert L.pm_grouped_gemm_autotune(2, Mg, 64, 64, ctypes.byref(th), 152, 4, None, None, None, 1, 1, None,
+                                      o16, o16, launch, None, None) == pm.PM_EINVAL
     # concurrent-stream probe: argument checks come before any CUDA call
     bufs = (ctypes.c_void_p * 8)(*([16] * 8))
     vp = ctypes.cast(bufs, ctypes.c_void_p)

@@ -92,3 +92,24 @@ def test_grouped_config4_shape_reduced_with_graph(lib):
         err = np.linalg.norm(C[row0 + rows] - ref) / np.linalg.norm(ref)
         assert err <= 2e-2, (q, err)
         row0 += m
+
+
+def test_grouped_measured_autotune_picks_from_model_shortlist(lib):
+    # the measured grouped autotuner times the model's k best launches; its
+    # pick is one of them and computes the product exactly
+    Ms = [int(m) for m in S.grouped_m(16, 5, lo=16, hi=1024)]
+    N, K = 512, 1024
+    A_list, B_list = int_groups(Ms, N, K, seed=41)
+    A_op, B_op, sum_m = stacked_operands(lib, A_list, B_list, N, K)
+    C = torch.full((sum_m, N), float("nan"), dtype=torch.float32, device="cuda")
+    th = O.prior_theta(lib.sm_count())
+    t_pred, bm, bn, launch, timing = lib.pm_grouped_gemm_autotune(Ms, N, K, th, lib.sm_count(), 4, A_op, B_op, C,
+                                                                  warmup=1, reps=3)
+    assert timing["median_s"] > 0 and t_pred > 0
+    t_best, _, _, _ = lib.pm_grouped_autotune(Ms, N, K, lib.PM_BF16, th, lib.sm_count())
+    assert t_pred >= t_best * (1 - 1e-6)                 # a shortlist member: never predicted better than the best
+    C = run_grouped(lib, A_list, B_list, N, K, bm, bn, launch)
+    row0 = 0
+    for A, B in zip(A_list, B_list):
+        assert np.array_equal(C[row0:row0 + A.shape[0]].astype(np.float64), O.gemm_f64(A, B))
+        row0 += A.shape[0]
