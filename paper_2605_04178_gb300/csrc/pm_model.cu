@@ -19,9 +19,12 @@ namespace pm {
 
 // Parameters in the arithmetic type F: FP32 for the batched throughput
 // paths, FP64 for the calibration objective (pm_model_grad_f64).
+// inv[j] = 1 / v[j], rounded once on the host: the per-configuration model
+// multiplies where the equations divide by a parameter.
 template <class F>
 struct ThetaT {
   F v[16];
+  F inv[16];
 };
 using Theta = ThetaT<float>;
 
@@ -83,7 +86,7 @@ __host__ __device__ inline bool tile_valid(int BM, int BN, int BK, int s, int g,
 template <class F>
 struct GemmFwdT {
   F T, T_stage, T_rl, A_rl, B_rl;
-  F T_c, T_io, T_tma, oma, X, R, S, T_step, T_store;
+  F T_c, T_io, T_tma, oma, X, R, S, invR, invS, T_step, T_store;
   F D, DA_r, DA_w, bstep, store_bytes, n_instr;
   F waves, Kt;
   int ri;
@@ -108,6 +111,7 @@ __device__ __forceinline__ void gemm_forward(const pm_cfg& c, const ThetaT<F>& t
   const F e = dt_bytes(dt), np = dt_passes(dt), l = dt_loads(dt);
   f.ri = dt_rate(dt);
   f.R = th.v[f.ri];
+  f.invR = th.inv[f.ri];
   const int64_t Kt = cdiv(c.K, c.BK);
   const int64_t tiles = (int64_t)g * cdiv(c.M, (int64_t)g * c.BM) * cdiv(c.N, c.BN);
   const int64_t n_conc = g == 1 ? n_sm : 2 * (n_sm / 2);
@@ -122,13 +126,14 @@ __device__ __forceinline__ void gemm_forward(const pm_cfg& c, const ThetaT<F>& t
   f.DA_r = c.tmem_a ? np * e * c.BM * c.BK : F(0);
   // strategy B also issues one tcgen05.cp per 128-row x 32-byte A slice, each charged L_mma
   if (c.tmem_a) f.n_instr += l * (F)(c.BK * (int)e / 32) * (F)((c.BM + 127) / 128);
-  const F T_tmem = (f.D + f.DA_r) / th.v[10] + f.n_instr * th.v[9] + (f.D + f.DA_w) / th.v[11];
+  const F T_tmem = (f.D + f.DA_r) * th.inv[10] + f.n_instr * th.v[9] + (f.D + f.DA_w) * th.inv[11];
   const F T_mgmt = th.v[13] / f.Kt;
   f.S = g == 1 ? F(1) : th.v[14];
-  f.X = (np * F(2) * c.BM * c.BN * c.BK) / (f.R * f.S);
+  f.invS = g == 1 ? F(1) : th.inv[14];
+  f.X = (np * F(2) * c.BM * c.BN * c.BK) * (f.invR * f.invS);
   f.T_c = f.X + T_tmem + T_mgmt;
   f.bstep = l * e * c.BK * ((F)c.BM + (F)c.BN / (F)g);
-  f.T_tma = th.v[4] + f.bstep / th.v[5];
+  f.T_tma = th.v[4] + f.bstep * th.inv[5];
   const F T_sync = F(2) * th.v[12];
   // 1 - alpha = clamp(c_alpha / (s - 1), 0, 1): s - 1 loads in flight while
   // one stage is consumed; a single stage hides nothing
@@ -138,12 +143,12 @@ __device__ __forceinline__ void gemm_forward(const pm_cfg& c, const ThetaT<F>& t
   f.T_io = f.oma * f.T_tma + T_sync;
   f.T_step = pm_max(f.T_c, f.T_io) + T_sync;
   f.store_bytes = F(4) * c.BM * c.BN;
-  f.T_store = th.v[4] + f.store_bytes / th.v[5];
+  f.T_store = th.v[4] + f.store_bytes * th.inv[5];
   f.T_stage = th.v[0] + f.waves * (f.Kt * f.T_step + f.T_store);
   const F flops = np * F(2) * (F)c.M * (F)c.N * (F)c.K;
   const F bytes_min = l * e * ((F)c.M * c.K + (F)c.N * c.K) + F(4) * (F)c.M * (F)c.N;
-  f.A_rl = flops / ((F)n_sm * f.R * f.S);
-  f.B_rl = bytes_min / th.v[2];
+  f.A_rl = flops * (f.invR * f.invS) / (F)n_sm;
+  f.B_rl = bytes_min * th.inv[2];
   f.T_rl = th.v[0] + (f.A_rl >= f.B_rl ? f.A_rl : f.B_rl);
   f.T = f.T_stage >= f.T_rl ? f.T_stage : f.T_rl;
 }
@@ -160,10 +165,10 @@ __device__ __forceinline__ void gemm_adjoint(const pm_cfg& c, const ThetaT<F>& t
   d[0] += g_rl;
   if (g_rl != F(0)) {
     if (f.A_rl >= f.B_rl) {
-      gR -= g_rl * f.A_rl / f.R;
-      gS -= g_rl * f.A_rl / f.S;
+      gR -= g_rl * f.A_rl * f.invR;
+      gS -= g_rl * f.A_rl * f.invS;
     } else {
-      d[2] -= g_rl * f.B_rl / th.v[2];
+      d[2] -= g_rl * f.B_rl * th.inv[2];
     }
   }
   // stage branch
@@ -171,7 +176,7 @@ __device__ __forceinline__ void gemm_adjoint(const pm_cfg& c, const ThetaT<F>& t
   const F g_step = g_stage * f.waves * f.Kt;
   const F g_store = g_stage * f.waves;
   d[4] += g_store;
-  d[5] -= g_store * (f.store_bytes / th.v[5]) / th.v[5];
+  d[5] -= g_store * (f.store_bytes * th.inv[5]) * th.inv[5];
   F g_sync = g_step;
   F g_c = F(0), g_io = F(0);
   if (f.T_c >= f.T_io) g_c = g_step; else g_io = g_step;
@@ -180,14 +185,14 @@ __device__ __forceinline__ void gemm_adjoint(const pm_cfg& c, const ThetaT<F>& t
   const F g_tma = g_io * f.oma;
   if (f.oma_free) d[15] += g_io * f.T_tma / (F)(c.stages - 1);
   d[4] += g_tma;
-  d[5] -= g_tma * (f.bstep / th.v[5]) / th.v[5];
+  d[5] -= g_tma * (f.bstep * th.inv[5]) * th.inv[5];
   d[12] += F(2) * g_sync;
   // T_c = X + (D + D_A,r)/BW_rd + n_instr L_mma + (D + D_A,w)/BW_wr + L_mgmt/K_tiles
-  gR -= g_c * f.X / f.R;
-  gS -= g_c * f.X / f.S;
-  d[10] -= g_c * ((f.D + f.DA_r) / th.v[10]) / th.v[10];
+  gR -= g_c * f.X * f.invR;
+  gS -= g_c * f.X * f.invS;
+  d[10] -= g_c * ((f.D + f.DA_r) * th.inv[10]) * th.inv[10];
   d[9] += g_c * f.n_instr;
-  d[11] -= g_c * ((f.D + f.DA_w) / th.v[11]) / th.v[11];
+  d[11] -= g_c * ((f.D + f.DA_w) * th.inv[11]) * th.inv[11];
   d[13] += g_c / f.Kt;
   // static indices keep d[] in registers
   d[6] += f.ri == 6 ? gR : F(0);
@@ -609,7 +614,10 @@ __global__ void __launch_bounds__(kGroupThreads) grouped_tune_kernel(const int32
 
 static Theta to_theta(const pm_params* p) {
   Theta t;
-  for (int j = 0; j < 16; ++j) t.v[j] = p->v[j];
+  for (int j = 0; j < 16; ++j) {
+    t.v[j] = p->v[j];
+    t.inv[j] = (float)(1.0 / (double)p->v[j]);
+  }
   return t;
 }
 
@@ -670,7 +678,10 @@ extern "C" pm_status pm_model_grad_f64(const pm_cfg* cfgs_dev, int64_t n, const 
              "workspace of %zu bytes is smaller than the %zu needed", workspace_bytes,
              (size_t)blocks * 17 * sizeof(double));
   ThetaT<double> th;
-  for (int j = 0; j < 16; ++j) th.v[j] = theta_host[j];
+  for (int j = 0; j < 16; ++j) {
+    th.v[j] = theta_host[j];
+    th.inv[j] = 1.0 / theta_host[j];
+  }
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   model_grad_kernel<double><<<blocks, kGradThreads, 0, s>>>(cfgs_dev, n, th, n_sm, t_meas_dev,
                                                             static_cast<double*>(workspace_dev));
