@@ -116,10 +116,16 @@ typedef struct { float v[16]; } pm_params;
  *  PM_PROBE_TMEM_ST: n passes of tcgen05.st writing lane*512 + column + pass,
  *                    then one read pass; buf0 as above (sum of the last pass).
  *  PM_PROBE_H2D / PM_PROBE_D2H: cudaMemcpyAsync of n bytes from buf0 to buf1
- *                    (host memory pinned for full speed). */
+ *                    (host memory pinned for full speed).
+ *  PM_PROBE_HOST_READ / PM_PROBE_HOST_WRITE: the SMs copy n FP32 elements from
+ *                    buf0 to buf1 through the device mapping of CUDA
+ *                    page-locked host memory (buf0 host for READ, buf1 host
+ *                    for WRITE; no copy engine); PM_EINVAL if the host buffer
+ *                    is not such memory.  result.bytes = 4n. */
 typedef enum {
   PM_PROBE_COPY = 1, PM_PROBE_TRIAD = 2, PM_PROBE_TMA2D = 3, PM_PROBE_PCHASE = 4, PM_PROBE_H2D = 5,
-  PM_PROBE_D2H = 6, PM_PROBE_MMA = 7, PM_PROBE_MBAR = 8, PM_PROBE_TMEM_LD = 9, PM_PROBE_TMEM_ST = 10
+  PM_PROBE_D2H = 6, PM_PROBE_MMA = 7, PM_PROBE_MBAR = 8, PM_PROBE_TMEM_LD = 9, PM_PROBE_TMEM_ST = 10,
+  PM_PROBE_HOST_READ = 11, PM_PROBE_HOST_WRITE = 12
 } pm_probe_kind;
 
 typedef struct {

@@ -23,6 +23,7 @@ PM_FP32, PM_BF16, PM_FP8E4M3 = 0, 1, 2
 PM_KIND_GEMM, PM_KIND_COPY, PM_KIND_TRIAD, PM_KIND_TMA2D = 0, 1, 2, 3
 PM_PROBE_COPY, PM_PROBE_TRIAD, PM_PROBE_TMA2D, PM_PROBE_PCHASE = 1, 2, 3, 4
 PM_PROBE_H2D, PM_PROBE_D2H, PM_PROBE_MMA, PM_PROBE_MBAR, PM_PROBE_TMEM_LD, PM_PROBE_TMEM_ST = 5, 6, 7, 8, 9, 10
+PM_PROBE_HOST_READ, PM_PROBE_HOST_WRITE = 11, 12
 
 # numpy view of pm_cfg (24 bytes)
 CFG_DTYPE = np.dtype([("M", "<i4"), ("N", "<i4"), ("K", "<i4"), ("BM", "<i2"), ("BN", "<i2"), ("BK", "<i2"),

@@ -225,7 +225,11 @@ def measure_instructions() -> dict:
         d = torch.empty(nb, dtype=torch.uint8, device="cuda")
         r1 = pm.pm_probe_run(pm.probe_args(pm.PM_PROBE_H2D, n=nb), h, d, warmup=2, reps=10)
         r2 = pm.pm_probe_run(pm.probe_args(pm.PM_PROBE_D2H, n=nb), d, h, warmup=2, reps=10)
-        out["host"].append(dict(bytes=nb, h2d_s=r1["median_s"], d2h_s=r2["median_s"]))
+        # the same transfers driven by the SMs through the host mapping (no copy engine)
+        r3 = pm.pm_probe_run(pm.probe_args(pm.PM_PROBE_HOST_READ, n=nb // 4), h, d, warmup=2, reps=10)
+        r4 = pm.pm_probe_run(pm.probe_args(pm.PM_PROBE_HOST_WRITE, n=nb // 4), d, h, warmup=2, reps=10)
+        out["host"].append(dict(bytes=nb, h2d_s=r1["median_s"], d2h_s=r2["median_s"], h2d_sm_s=r3["median_s"],
+                                d2h_sm_s=r4["median_s"]))
         del h, d
     out["eq15"] = fit_eq15(out["host"])
     return out
@@ -286,7 +290,9 @@ def fit_eq15(host_rows) -> dict:
     (weighted by 1/T so small and large transfers count alike)."""
     res = {}
     S_ = np.array([r["bytes"] for r in host_rows], dtype=np.float64)
-    for d in ("h2d", "d2h"):
+    for d in ("h2d", "d2h", "h2d_sm", "d2h_sm"):
+        if not all((d + "_s") in r for r in host_rows):
+            continue
         T = np.array([r[d + "_s"] for r in host_rows], dtype=np.float64)
         A = np.stack([S_ / T, 1.0 / T], 1)          # rows scaled by 1/T: S/T * (1/B) + (1/T) * tau = 1
         coef, *_ = np.linalg.lstsq(A, np.ones_like(T), rcond=None)

@@ -300,6 +300,18 @@ __global__ void __launch_bounds__(256, 1) tmem_probe_kernel(int64_t iters, int s
   }
 }
 
+// Device address of page-locked host memory registered with CUDA (the
+// allocation must be CUDA pinned memory; anything else is refused).
+static pm_status mapped_host_pointer(void* host, void** out) {
+  cudaPointerAttributes at;
+  cudaError_t e = cudaPointerGetAttributes(&at, host);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaPointerGetAttributes");
+  PM_REQUIRE(at.type == cudaMemoryTypeHost && at.devicePointer != nullptr, PM_EINVAL,
+             "buffer is not CUDA page-locked host memory mapped into the device address space");
+  *out = at.devicePointer;
+  return PM_OK;
+}
+
 static int stream_grid(int64_t n4) {
   const int sms = std::max(1, sm_count());
   const int64_t need = (n4 + (int64_t)kStreamThreads * kStreamUnroll - 1) / ((int64_t)kStreamThreads * kStreamUnroll);
@@ -385,6 +397,24 @@ static pm_status probe_launch(const pm_probe_args* a, void* buf0, void* buf1, vo
                               a->kind == PM_PROBE_H2D ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToHost, s));
       return PM_OK;
     }
+    case PM_PROBE_HOST_READ:
+    case PM_PROBE_HOST_WRITE: {
+      // SMs stream the host buffer through its device mapping (no copy engine)
+      PM_REQUIRE(buf0 && buf1 && a->n > 0, PM_EINVAL, "host-link probe: null buffer or n <= 0");
+      void* host = a->kind == PM_PROBE_HOST_READ ? buf0 : buf1;
+      void* mapped = nullptr;
+      pm_status st = mapped_host_pointer(host, &mapped);
+      if (st != PM_OK) return st;
+      const void* src = a->kind == PM_PROBE_HOST_READ ? mapped : buf0;
+      void* dst = a->kind == PM_PROBE_HOST_READ ? buf1 : mapped;
+      PM_REQUIRE((((uintptr_t)src | (uintptr_t)dst) & 15) == 0, PM_EINVAL,
+                 "host-link probe: buffers must be 16-byte aligned");
+      const int64_t n4 = a->n / 4;
+      const int tail = (int)(a->n - n4 * 4);
+      copy_kernel<<<stream_grid(n4), kStreamThreads, 0, s>>>((const float4*)src, (float4*)dst, n4,
+                                                             (const float*)src + n4 * 4, (float*)dst + n4 * 4, tail);
+      return launch_status("copy_kernel");
+    }
     case PM_PROBE_MMA: {
       const int cg = (int)a->rows, dt = (int)a->cols, M = a->tile_c, N = a->tile_r;
       PM_REQUIRE(buf0 && a->n >= 1 && a->n <= (1 << 19), PM_EINVAL, "mma probe: need buf0 and 1 <= n <= 2^19");
@@ -454,6 +484,8 @@ static double probe_bytes(const pm_probe_args* a) {
     case PM_PROBE_PCHASE: return 4.0 * (double)a->hops;
     case PM_PROBE_H2D:
     case PM_PROBE_D2H: return (double)a->n;
+    case PM_PROBE_HOST_READ:
+    case PM_PROBE_HOST_WRITE: return 4.0 * (double)a->n;
     case PM_PROBE_MMA: {
       // FLOPs of the launch: issuing CTAs x n x 2 M N k_instr
       const int cg = (int)a->rows, dt = (int)a->cols;

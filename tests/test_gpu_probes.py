@@ -72,3 +72,24 @@ def test_watchdog_times_out_and_context_survives(lib):
     y = torch.empty_like(x)
     lib.pm_probe_run(lib.probe_args(lib.PM_PROBE_COPY, n=1000), x, y, warmup=0, reps=1)
     assert torch.equal(x, y)
+
+
+@pytest.mark.parametrize("n", [1, 5, 4099, 2 ** 22 + 3])
+def test_host_link_sm_copies_bit_exact(lib, n):
+    # SM-driven copies through the device mapping of page-locked host memory
+    h = torch.from_numpy(S.uniform_pm1(9, n)).pin_memory()
+    d = torch.full((n,), float("nan"), dtype=torch.float32, device="cuda")
+    r = lib.pm_probe_run(lib.probe_args(lib.PM_PROBE_HOST_READ, n=n), h, d, warmup=1, reps=2)
+    assert r["bytes"] == 4 * n
+    assert torch.equal(d.cpu().view(torch.int32), h.view(torch.int32))
+    back = torch.full((n,), float("nan"), dtype=torch.float32).pin_memory()
+    lib.pm_probe_run(lib.probe_args(lib.PM_PROBE_HOST_WRITE, n=n), d, back, warmup=0, reps=1)
+    torch.cuda.synchronize()
+    assert torch.equal(back.view(torch.int32), h.view(torch.int32))
+
+
+def test_host_link_probe_refuses_unpinned_memory(lib):
+    d = torch.empty(1024, dtype=torch.float32, device="cuda")
+    with pytest.raises(lib.PMError) as e:
+        lib.pm_probe_run(lib.probe_args(lib.PM_PROBE_HOST_READ, n=1024), d, d, warmup=0, reps=1)
+    assert e.value.status == lib.PM_EINVAL
