@@ -121,11 +121,16 @@ typedef struct { float v[16]; } pm_params;
  *                    buf0 to buf1 through the device mapping of CUDA
  *                    page-locked host memory (buf0 host for READ, buf1 host
  *                    for WRITE; no copy engine); PM_EINVAL if the host buffer
- *                    is not such memory.  result.bytes = 4n. */
+ *                    is not such memory.  result.bytes = 4n.
+ *  PM_PROBE_STENCIL: buf1 = five-point stencil of the rows x cols FP32 grid
+ *                    buf0 (distinct buffers): interior points
+ *                    0.5 x + 0.125 ((up + down) + (left + right)), each
+ *                    operation rounded separately; border points copied.
+ *                    result.bytes = 8 rows cols (one read, one write). */
 typedef enum {
   PM_PROBE_COPY = 1, PM_PROBE_TRIAD = 2, PM_PROBE_TMA2D = 3, PM_PROBE_PCHASE = 4, PM_PROBE_H2D = 5,
   PM_PROBE_D2H = 6, PM_PROBE_MMA = 7, PM_PROBE_MBAR = 8, PM_PROBE_TMEM_LD = 9, PM_PROBE_TMEM_ST = 10,
-  PM_PROBE_HOST_READ = 11, PM_PROBE_HOST_WRITE = 12
+  PM_PROBE_HOST_READ = 11, PM_PROBE_HOST_WRITE = 12, PM_PROBE_STENCIL = 13
 } pm_probe_kind;
 
 typedef struct {
@@ -324,6 +329,47 @@ pm_status pm_grouped_gemm_autotune(int32_t G, const int32_t* M_host, int32_t N, 
                                    const void* B_op_dev, float* C_dev, int warmup, int reps, void* stream,
                                    int16_t* BM_out_host, int16_t* BN_out_host, int32_t* launch_out_host,
                                    float* t_pred_host, pm_probe_result* pick_time_out);
+
+/* -------------------------------------------------- generic segment model */
+/* The paper's generic roofline path for work that the stage model does not
+ * cover (Sec. III-E "Generic roofline path" and "Host-device transfer and
+ * synchronization"; Eqs. 15 and 16).  A segment is one step of a workload,
+ * executed `execs` times; per execution
+ *   T = kernels * T_launch
+ *     + s_class * max(flops / (n_SM * R_TC[precision] * eta[precision]),
+ *                     bytes / B_eff(working_set))            (Eq. 16)
+ *     + [h2d_bytes > 0] (h2d_bytes / B_h2d + tau_h2d)           (Eq. 15)
+ *     + [d2h_bytes > 0] (d2h_bytes / B_d2h + tau_d2h)
+ *     + syncs * tau_sync
+ * (the roofline term only when kernels >= 1; copies and kernels are summed,
+ * not overlapped, as the paper states).  T_launch, B_sus, B_peak, w0 and the
+ * per-SM rates R_TC come from the stage model's theta. */
+typedef enum { PM_SEG_MEMORY = 0, PM_SEG_COMPUTE = 1, PM_SEG_BALANCED = 2, PM_SEG_STENCIL = 3 } pm_segment_class;
+
+typedef struct {
+  double flops;          /* FLOPs of the segment's kernels per execution */
+  double bytes;          /* DRAM bytes they move per execution */
+  double working_set;    /* W of Eq. 16, bytes */
+  double h2d_bytes;      /* host-to-device bytes per execution */
+  double d2h_bytes;      /* device-to-host bytes per execution */
+  int32_t cls;           /* pm_segment_class */
+  int32_t precision;     /* pm_dtype of the arithmetic (selects R_TC and eta) */
+  int32_t kernels;       /* kernel launches per execution (>= 0) */
+  int32_t syncs;         /* host synchronisation points per execution */
+  int32_t execs;         /* executions of the segment (>= 1) */
+  int32_t reserved;      /* must be 0 */
+} pm_segment;            /* 64 bytes */
+
+/* Segment parameters psi (SI units): 0-3 class scales s_class (memory,
+ * compute, balanced, stencil), 4-6 precision efficiencies eta (FP32, BF16,
+ * FP8), 7 B_h2d, 8 tau_h2d, 9 B_d2h, 10 tau_d2h, 11 tau_sync. */
+typedef struct { double v[12]; } pm_segment_params;
+
+/* T (seconds, FP64) of n segments on the GPU.  segs_dev: n pm_segment;
+ * t_out_dev: n doubles.  A record with an unknown class or precision, a
+ * negative size or count, or execs < 1 yields NaN.  Async. */
+pm_status pm_segment_predict(const pm_segment* segs_dev, int64_t n, const pm_params* theta_host,
+                             const pm_segment_params* psi_host, int32_t n_sm, double* t_out_dev, void* stream);
 
 /* ----------------------------------------------------------- diagnostics */
 /* Text of the last error on this host thread (valid until the next call). */

@@ -10,11 +10,14 @@ Parity status of each part (pins are in tests/test_oracle_*.py):
   gemm_f64            pinned: numpy FP64 matmul, integer matrices, identity/permutation
   to_bf16/tf32/e4m3   pinned: exhaustive/structural checks against the format definitions
   triad_f32           pinned: exact rational arithmetic (fractions) on random cases
+  stencil5_f32        pinned: exact rational arithmetic of each rounding step on random grids
   pchase              pinned: single-cycle walk returns to its start after n hops
   model_batch         pinned: hand-evaluated rows, closed forms, homogeneity, monotonicity
   model gradient      pinned: central differences and Euler's homogeneity identity
   autotune            pinned: brute force in plain Python on small spaces
   grouped model       pinned: reduces to the single-GEMM stage time for one group
+  segment_predict     pinned: closed forms of each term (Eq. 16 off, pure transfers, extra launches,
+                      executions), hand-evaluated rows, homogeneity
   mma/tmem probe sums closed forms (exact integer arithmetic)
 """
 from __future__ import annotations
@@ -86,6 +89,8 @@ def _load():
             lib.orc_grouped_autotune.argtypes = [ctypes.c_int, P, ctypes.c_int32, ctypes.c_int32,
                                                  ctypes.c_int, P, ctypes.c_int, P, P, P]
             lib.orc_grouped_autotune.restype = ctypes.c_double
+            lib.orc_segment_predict.argtypes = [i64] + [P] * 10 + [P, P, ctypes.c_int, P]
+            lib.orc_stencil5_f32.argtypes = [P, i64, i64, P]
             _lib = lib
     return _lib
 
@@ -249,6 +254,34 @@ def grouped_autotune(Mg, N, K, dtype, theta, n_sm):
     t = _load().orc_grouped_autotune(G, _ptr(Mg), int(N), int(K), int(dtype), _ptr(th), int(n_sm),
                                      _ptr(bm), _ptr(bn), _ptr(launch))
     return float(t), bm, bn, tuple(int(v) for v in launch)
+
+
+def stencil5_f32(x: np.ndarray) -> np.ndarray:
+    """Five-point stencil of a 2-D FP32 grid (interior 0.5 x + 0.125 (vertical + horizontal sums),
+    every operation rounded separately; border copied)."""
+    x = _c(x, np.float32)
+    assert x.ndim == 2
+    y = np.empty_like(x)
+    _load().orc_stencil5_f32(_ptr(x), x.shape[0], x.shape[1], _ptr(y))
+    return y
+
+
+_SEG_F64 = ("flops", "bytes", "working_set", "h2d_bytes", "d2h_bytes")
+_SEG_I32 = ("cls", "precision", "kernels", "syncs", "execs")
+
+
+def segment_predict(segs: dict, theta, psi, n_sm: int) -> np.ndarray:
+    """Generic-path time (FP64) of each segment; segs holds equal-length columns
+    (missing: 0, execs 1)."""
+    n = len(next(iter(segs.values())))
+    cols = [_c(segs.get(f, np.zeros(n)), np.float64) for f in _SEG_F64]
+    cols += [_c(segs.get(f, np.ones(n) if f == "execs" else np.zeros(n)), np.int32) for f in _SEG_I32]
+    th = _c(theta, np.float64)
+    ps = _c(psi, np.float64)
+    assert th.size == N_PARAMS and ps.size == 12
+    t = np.empty(n, dtype=np.float64)
+    _load().orc_segment_predict(n, *[_ptr(c) for c in cols], _ptr(th), _ptr(ps), int(n_sm), _ptr(t))
+    return t
 
 
 def prior_theta(n_sm: int, f_hz: float = 1.9e9) -> np.ndarray:

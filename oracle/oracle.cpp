@@ -527,3 +527,65 @@ extern "C" double orc_grouped_autotune(int G, const int32_t* Mg, int32_t N, int3
       }
   return best;
 }
+
+// ---------------------------------------------------------------------------
+// Generic roofline path (Sec. III-E "Generic roofline path: scaling, working
+// set, and launches" and "Host-device transfer and synchronization"): a
+// workload segment outside the stage model takes, per execution, its kernel
+// launches, a class-scaled roofline whose bandwidth follows Eq. 16, the host
+// transfers of Eq. 15 and its synchronisation points; the total multiplies by
+// the number of executions.  Copies and kernels are summed (no overlap).
+//   psi: 0-3 class scales (memory, compute, balanced, stencil),
+//        4-6 precision efficiencies (FP32, BF16, FP8),
+//        7 B_h2d, 8 tau_h2d, 9 B_d2h, 10 tau_d2h, 11 tau_sync.
+// ---------------------------------------------------------------------------
+extern "C" void orc_segment_predict(i64 n, const double* flops, const double* bytes, const double* wset,
+                                    const double* h2d, const double* d2h, const int32_t* cls,
+                                    const int32_t* prec, const int32_t* kernels, const int32_t* syncs,
+                                    const int32_t* execs, const double* theta, const double* psi, int n_sm,
+                                    double* t_out) {
+  for (i64 i = 0; i < n; ++i) {
+    const bool ok = cls[i] >= 0 && cls[i] <= 3 && prec[i] >= 0 && prec[i] <= 2 && kernels[i] >= 0 &&
+                    syncs[i] >= 0 && execs[i] >= 1 && flops[i] >= 0 && bytes[i] >= 0 && wset[i] >= 0 &&
+                    h2d[i] >= 0 && d2h[i] >= 0;
+    if (!ok) {
+      t_out[i] = NAN;
+      continue;
+    }
+    double t = 0.0;
+    if (kernels[i] > 0) {
+      // the extra launches of a multi-kernel segment, then one roofline
+      const double launches = kernels[i] * theta[0];
+      const double bandwidth = b_eff<double>(theta, wset[i]);               // Eq. 16
+      const double peak = n_sm * theta[rate_index(prec[i])] * psi[4 + prec[i]];
+      const double memory_time = bytes[i] / bandwidth;
+      const double compute_time = flops[i] / peak;
+      t += launches + psi[cls[i]] * (compute_time > memory_time ? compute_time : memory_time);
+    }
+    if (h2d[i] > 0) t += h2d[i] / psi[7] + psi[8];                          // Eq. 15
+    if (d2h[i] > 0) t += d2h[i] / psi[9] + psi[10];
+    t += syncs[i] * psi[11];
+    t_out[i] = execs[i] * t;
+  }
+}
+
+// Five-point stencil of the generic path's stencil class: interior points
+// 0.5 x + 0.125 ((up + down) + (left + right)) in FP32 with every operation
+// rounded on its own (the file is compiled without contraction); border
+// points copied.
+extern "C" void orc_stencil5_f32(const float* in, i64 rows, i64 cols, float* out) {
+#pragma omp parallel for schedule(static)
+  for (i64 i = 0; i < rows; ++i)
+    for (i64 j = 0; j < cols; ++j) {
+      const i64 k = i * cols + j;
+      if (i == 0 || j == 0 || i == rows - 1 || j == cols - 1) {
+        out[k] = in[k];
+        continue;
+      }
+      const float vert = in[k - cols] + in[k + cols];
+      const float horz = in[k - 1] + in[k + 1];
+      const float half = 0.5f * in[k];
+      const float eighth = 0.125f * (vert + horz);
+      out[k] = half + eighth;
+    }
+}

@@ -23,7 +23,7 @@ PM_FP32, PM_BF16, PM_FP8E4M3 = 0, 1, 2
 PM_KIND_GEMM, PM_KIND_COPY, PM_KIND_TRIAD, PM_KIND_TMA2D = 0, 1, 2, 3
 PM_PROBE_COPY, PM_PROBE_TRIAD, PM_PROBE_TMA2D, PM_PROBE_PCHASE = 1, 2, 3, 4
 PM_PROBE_H2D, PM_PROBE_D2H, PM_PROBE_MMA, PM_PROBE_MBAR, PM_PROBE_TMEM_LD, PM_PROBE_TMEM_ST = 5, 6, 7, 8, 9, 10
-PM_PROBE_HOST_READ, PM_PROBE_HOST_WRITE = 11, 12
+PM_PROBE_HOST_READ, PM_PROBE_HOST_WRITE, PM_PROBE_STENCIL = 11, 12, 13
 
 # numpy view of pm_cfg (24 bytes)
 CFG_DTYPE = np.dtype([("M", "<i4"), ("N", "<i4"), ("K", "<i4"), ("BM", "<i2"), ("BN", "<i2"), ("BK", "<i2"),
@@ -41,6 +41,18 @@ class pm_cfg(ctypes.Structure):
 
 class pm_params(ctypes.Structure):
     _fields_ = [("v", ctypes.c_float * 16)]
+
+
+# numpy view of pm_segment (64 bytes)
+SEGMENT_DTYPE = np.dtype([("flops", "<f8"), ("bytes", "<f8"), ("working_set", "<f8"), ("h2d_bytes", "<f8"),
+                          ("d2h_bytes", "<f8"), ("cls", "<i4"), ("precision", "<i4"), ("kernels", "<i4"),
+                          ("syncs", "<i4"), ("execs", "<i4"), ("reserved", "<i4")], align=True)
+assert SEGMENT_DTYPE.itemsize == 64
+PM_SEG_MEMORY, PM_SEG_COMPUTE, PM_SEG_BALANCED, PM_SEG_STENCIL = 0, 1, 2, 3
+
+
+class pm_segment_params(ctypes.Structure):
+    _fields_ = [("v", ctypes.c_double * 12)]
 
 
 class pm_probe_args(ctypes.Structure):
@@ -62,7 +74,7 @@ assert ctypes.sizeof(pm_cfg) == 24 and ctypes.sizeof(pm_probe_args) == 56 and ct
 EXPORTS = ("pm_probe_launch", "pm_probe_run", "pm_streams_run", "pm_gemm_operand_bytes", "pm_gemm_prepare", "pm_gemm_run",
            "pm_gemm_bench", "pm_gemm_host_workspace", "pm_gemm_host",
            "pm_grouped_gemm_run", "pm_model_predict", "pm_model_grad_workspace", "pm_model_grad", "pm_model_grad_f64", "pm_model_grad_noalloc",
-           "pm_autotune_pick", "pm_autotune_topk", "pm_gemm_autotune", "pm_grouped_autotune", "pm_grouped_gemm_autotune", "pm_last_error", "pm_device_status",
+           "pm_autotune_pick", "pm_autotune_topk", "pm_gemm_autotune", "pm_grouped_autotune", "pm_grouped_gemm_autotune", "pm_segment_predict", "pm_last_error", "pm_device_status",
            "pm_watchdog_selftest", "pm_version")
 
 
@@ -108,6 +120,7 @@ def _load():
         "pm_gemm_autotune": [ctypes.POINTER(pm_cfg), i32, ctypes.POINTER(pm_params), i32, P, P, P, P, ctypes.c_int,
                              ctypes.c_int, P, ctypes.POINTER(pm_cfg), ctypes.POINTER(pm_probe_result)],
         "pm_grouped_autotune": [i32, P, i32, i32, i32, ctypes.POINTER(pm_params), i32, P, P, P, P, P],
+        "pm_segment_predict": [P, i64, ctypes.POINTER(pm_params), ctypes.POINTER(pm_segment_params), i32, P, P],
         "pm_grouped_gemm_autotune": [i32, P, i32, i32, ctypes.POINTER(pm_params), i32, i32, P, P, P, ctypes.c_int,
                                      ctypes.c_int, P, P, P, P, P, ctypes.POINTER(pm_probe_result)],
         "pm_device_status": [ctypes.c_int],
@@ -366,6 +379,29 @@ def pm_grouped_gemm_autotune(M_list, N, K, theta, n_sm, k, A_op, B_op, C, warmup
            "pm_grouped_gemm_autotune")
     return float(t.value), list(bm), list(bn), tuple(launch), dict(median_s=res.median_s, p25_s=res.p25_s,
                                                                    p75_s=res.p75_s, min_s=res.min_s)
+
+
+# ------------------------------------------------------- generic segment model
+def segment_array(fields: dict) -> np.ndarray:
+    """Structured pm_segment array from a dict of equal-length columns (missing columns are 0; execs 1)."""
+    n = len(next(iter(fields.values())))
+    a = np.zeros(n, dtype=SEGMENT_DTYPE)
+    a["execs"] = 1
+    for k, v in fields.items():
+        a[k] = v
+    return a
+
+
+def pm_segment_predict(segs: np.ndarray, theta, psi, n_sm, stream=None) -> np.ndarray:
+    """Generic-path time (FP64 seconds) of each pm_segment record, evaluated on the GPU."""
+    import torch
+    n = len(segs)
+    dev = torch.from_numpy(np.ascontiguousarray(segs).view(np.uint8).copy()).cuda()
+    out = torch.empty(max(n, 1), dtype=torch.float64, device="cuda")
+    ps = pm_segment_params((ctypes.c_double * 12)(*[float(v) for v in psi]))
+    _check(_lib.pm_segment_predict(_ptr(dev), int(n), ctypes.byref(params(theta)), ctypes.byref(ps), int(n_sm),
+                                   _ptr(out), _stream(stream)), "pm_segment_predict")
+    return out[:n].cpu().numpy()
 
 
 # ---------------------------------------------------------------- diagnostics

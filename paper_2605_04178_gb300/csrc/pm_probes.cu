@@ -300,6 +300,27 @@ __global__ void __launch_bounds__(256, 1) tmem_probe_kernel(int64_t iters, int s
   }
 }
 
+// Five-point stencil over a rows x cols FP32 grid (the stencil class of the
+// generic roofline path): interior points take
+//   out = 0.5 x + 0.125 ((up + down) + (left + right)),
+// each operation rounded on its own (no contraction), border points are
+// copied.  One thread per output point, 32 x 8 blocks.
+__global__ void __launch_bounds__(256) stencil5_kernel(const float* __restrict__ in, float* __restrict__ out,
+                                                       int64_t rows, int64_t cols) {
+  const int64_t j = (int64_t)blockIdx.x * 32 + threadIdx.x;
+  const int64_t i = (int64_t)blockIdx.y * 8 + threadIdx.y;
+  if (i >= rows || j >= cols) return;
+  const int64_t k = i * cols + j;
+  const float x = __ldg(in + k);
+  if (i == 0 || j == 0 || i == rows - 1 || j == cols - 1) {
+    out[k] = x;
+    return;
+  }
+  const float vert = __fadd_rn(__ldg(in + k - cols), __ldg(in + k + cols));
+  const float horz = __fadd_rn(__ldg(in + k - 1), __ldg(in + k + 1));
+  out[k] = __fadd_rn(__fmul_rn(0.5f, x), __fmul_rn(0.125f, __fadd_rn(vert, horz)));
+}
+
 // Device address of page-locked host memory registered with CUDA (the
 // allocation must be CUDA pinned memory; anything else is refused).
 static pm_status mapped_host_pointer(void* host, void** out) {
@@ -415,6 +436,15 @@ static pm_status probe_launch(const pm_probe_args* a, void* buf0, void* buf1, vo
                                                              (const float*)src + n4 * 4, (float*)dst + n4 * 4, tail);
       return launch_status("copy_kernel");
     }
+    case PM_PROBE_STENCIL: {
+      PM_REQUIRE(buf0 && buf1 && buf0 != buf1 && a->rows > 0 && a->cols > 0, PM_EINVAL,
+                 "stencil probe: need distinct buffers and a positive grid");
+      PM_REQUIRE((a->rows + 7) / 8 < 65536 && (a->cols + 31) / 32 < (1ll << 31), PM_EINVAL,
+                 "stencil probe: grid too large");
+      const dim3 grid((unsigned)((a->cols + 31) / 32), (unsigned)((a->rows + 7) / 8));
+      stencil5_kernel<<<grid, dim3(32, 8), 0, s>>>((const float*)buf0, (float*)buf1, a->rows, a->cols);
+      return launch_status("stencil5_kernel");
+    }
     case PM_PROBE_MMA: {
       const int cg = (int)a->rows, dt = (int)a->cols, M = a->tile_c, N = a->tile_r;
       PM_REQUIRE(buf0 && a->n >= 1 && a->n <= (1 << 19), PM_EINVAL, "mma probe: need buf0 and 1 <= n <= 2^19");
@@ -486,6 +516,7 @@ static double probe_bytes(const pm_probe_args* a) {
     case PM_PROBE_D2H: return (double)a->n;
     case PM_PROBE_HOST_READ:
     case PM_PROBE_HOST_WRITE: return 4.0 * (double)a->n;
+    case PM_PROBE_STENCIL: return 8.0 * (double)a->rows * (double)a->cols;
     case PM_PROBE_MMA: {
       // FLOPs of the launch: issuing CTAs x n x 2 M N k_instr
       const int cg = (int)a->rows, dt = (int)a->cols;

@@ -93,3 +93,14 @@ def test_host_link_probe_refuses_unpinned_memory(lib):
     with pytest.raises(lib.PMError) as e:
         lib.pm_probe_run(lib.probe_args(lib.PM_PROBE_HOST_READ, n=1024), d, d, warmup=0, reps=1)
     assert e.value.status == lib.PM_EINVAL
+
+
+@pytest.mark.parametrize("shape", [(1, 1), (2, 7), (3, 3), (37, 1000), (1000, 37), (1024, 1024), (4099, 2053)])
+def test_stencil_bit_exact(lib, shape):
+    rows, cols = shape
+    x = S.uniform_pm1(21, rows * cols).reshape(rows, cols)
+    src = torch.from_numpy(x).cuda()
+    dst = torch.full_like(src, float("nan"))
+    r = lib.pm_probe_run(lib.probe_args(lib.PM_PROBE_STENCIL, rows=rows, cols=cols), src, dst, warmup=1, reps=2)
+    assert r["bytes"] == 8 * rows * cols
+    assert np.array_equal(dst.cpu().numpy().view(np.uint32), O.stencil5_f32(x).view(np.uint32))

@@ -84,3 +84,34 @@ def test_model_config_batch_shapes():
         assert c[f].min() >= 16 and c[f].max() <= 16384 and np.all(c[f] % 16 == 0)
     assert set(np.unique(c["dtype"])) == {0, 1, 2}
     assert len(S.tile_space(1)) == 180
+
+
+def test_stencil_fixed_points_and_closed_forms():
+    # integer grids keep every intermediate exact: an affine (discrete
+    # harmonic) grid is a fixed point, x = i^2 gains 0.125 * 2 per interior point
+    rows, cols = 37, 53
+    i, j = np.meshgrid(np.arange(rows), np.arange(cols), indexing="ij")
+    aff = (3 * i - 2 * j + 7).astype(np.float32)
+    assert np.array_equal(O.stencil5_f32(aff), aff)
+    quad = (i * i).astype(np.float32)
+    out = O.stencil5_f32(quad)
+    expect = quad.copy()
+    expect[1:-1, 1:-1] += 0.25
+    assert np.array_equal(out, expect)
+    const = np.full((5, 4), 1.75, np.float32)
+    assert np.array_equal(O.stencil5_f32(const), const)
+
+
+def test_stencil_matches_stepwise_float32_on_random_grid():
+    x = S.uniform_pm1(17, 9 * 11).reshape(9, 11)
+    out = O.stencil5_f32(x)
+    f = np.float32
+    for r in range(9):
+        for c in range(11):
+            if r in (0, 8) or c in (0, 10):
+                assert out[r, c] == x[r, c]
+                continue
+            vert = f(x[r - 1, c]) + f(x[r + 1, c])
+            horz = f(x[r, c - 1]) + f(x[r, c + 1])
+            want = f(f(0.5) * x[r, c]) + f(f(0.125) * f(vert + horz))
+            assert out[r, c] == want, (r, c)
