@@ -13,6 +13,11 @@ Pieces
     copied into tensor memory, Sec. III-A.1) over the strategy-B tile space.
   * measure_streams() / fit_tau_c(): the concurrent-stream term of Sec.
     III-A.6, T(N_c) = T(1) + (N_c - 1) tau_c, per workload class.
+  * measure_segments() / fit_segments(): the generic roofline path (Sec.
+    III-E): memory-bound, compute-bound, balanced and stencil segments,
+    multi-kernel segments and segments with host transfers and syncs; one
+    scale per class and an efficiency per precision, fitted with the model
+    evaluated by pm_segment_predict.
   * StageModelLoss: torch.autograd.Function whose forward is the batched model
     on the GPU and whose backward is the hand-written adjoint kernel
     (pm_model_grad): mean squared log error and its gradient in theta.
@@ -168,8 +173,9 @@ def measure_sweep(shapes=(1024, 2048, 4096, 8192, 16384), dtypes=(1, 2), log=pri
         log("config 3 shape %d done (%d rows, %.0f s)" % (s, len(rows), time.time() - t0))
     rows += measure_tmem_b(shapes, dtypes, log)
     props = torch.cuda.get_device_properties(0)
+    segments = measure_segments(dict(rows=rows), log)
     return dict(device=props.name, n_sm=props.multi_processor_count, rows=rows, pchase=pchase, instr=instr,
-                streams=streams, protocol="10 warm-ups; 100 timed runs (20-40 at 8192-16384, 20 for TMA), median of CUDA-event times")
+                streams=streams, segments=segments, protocol="10 warm-ups; 100 timed runs (20-40 at 8192-16384, 20 for TMA), median of CUDA-event times")
 
 
 def measure_tmem_b(shapes=(1024, 2048, 4096, 8192, 16384), dtypes=(1, 2), log=print) -> list:
@@ -487,6 +493,217 @@ def load_theta(path=THETA_PATH):
         return np.array(json.load(f)["theta"], dtype=np.float64)
 
 
+# ---------------------------------------------------------- generic segments
+SEG_FIELDS = ("flops", "bytes", "working_set", "h2d_bytes", "d2h_bytes", "cls", "precision", "kernels", "syncs",
+              "execs")
+SEG_CLASS_NAMES = ("memory", "compute", "balanced", "stencil")
+
+
+def _seg(name, t, **kw):
+    r = dict(name=name, t=float(t), flops=0.0, bytes=0.0, working_set=0.0, h2d_bytes=0.0, d2h_bytes=0.0, cls=0,
+             precision=pm.PM_BF16, kernels=1, syncs=0, execs=1)
+    r.update(kw)
+    return r
+
+
+def _events_median(fn, warmup=3, reps=20):
+    for _ in range(warmup):
+        fn()
+    s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t = []
+    for _ in range(reps):
+        s.record()
+        fn()
+        e.record()
+        e.synchronize()
+        t.append(s.elapsed_time(e) * 1e-3)
+    return float(np.median(t))
+
+
+def measure_segments(table, log=print) -> dict:
+    """Measured workload segments for the generic path: the table's copy/triad
+    rows (memory) and fastest GEMM tile per shape and dtype (compute), grouped
+    GEMMs (balanced), the five-point stencil (stencil), copy-triad chains
+    (multi-kernel) and triads wrapped in host transfers and a sync."""
+    rows = []
+    for r in table["rows"]:
+        if r["kind"] in (pm.PM_KIND_COPY, pm.PM_KIND_TRIAD):
+            n = r["M"]
+            b = (8.0 if r["kind"] == pm.PM_KIND_COPY else 12.0) * n
+            rows.append(_seg("copy" if r["kind"] == pm.PM_KIND_COPY else "triad", r["t"], cls=0,
+                             precision=pm.PM_FP32, flops=0.0 if r["kind"] == pm.PM_KIND_COPY else 2.0 * n, bytes=b,
+                             working_set=b))
+    best = {}
+    for r in table["rows"]:
+        if r["kind"] == pm.PM_KIND_GEMM and not r.get("tmem_a", 0):
+            key = (r["M"], r["N"], r["K"], r["dtype"])
+            if key not in best or r["t"] < best[key]["t"]:
+                best[key] = r
+    for (M, N, K, dt), r in sorted(best.items()):
+        e = {0: 8.0, 1: 2.0, 2: 1.0}[dt]                   # operand bytes per element (FP32: hi and lo)
+        b = e * (M * K + N * K) + 4.0 * M * N
+        rows.append(_seg("gemm_%d_%s" % (M, ("fp32", "bf16", "fp8")[dt]), r["t"], cls=1, precision=dt,
+                         flops=2.0 * M * N * K, bytes=b, working_set=b))
+    n_sm = pm.sm_count()
+    theta = prior_theta(n_sm)
+    # balanced: grouped GEMMs, launch from the measured grouped autotuner
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(3)
+    for G, seed, NK in ((64, 3, 1024), (64, 3, 2048), (64, 3, 4096), (16, 5, 2048), (16, 5, 4096)):
+        Mg = S.grouped_m(G, seed)
+        sum_m = int(Mg.sum())
+        A = torch.randn(sum_m, NK, device="cuda", generator=gen).to(torch.bfloat16)
+        B = torch.randn(G * NK, NK, device="cuda", generator=gen).to(torch.bfloat16)
+        C = torch.empty(sum_m, NK, dtype=torch.float32, device="cuda")
+        _, bm, bn, launch, _ = pm.pm_grouped_gemm_autotune(Mg, NK, NK, theta, n_sm, 4, A, B, C, warmup=2, reps=5)
+        t = _events_median(lambda: pm.pm_grouped_gemm_run(Mg, NK, NK, bm, bn, *launch, A, B, C))
+        flops = float(sum(2.0 * m * NK * NK for m in Mg))
+        b = float(sum(2.0 * (m * NK + NK * NK) + 4.0 * m * NK for m in Mg))
+        rows.append(_seg("grouped_G%d_NK%d" % (G, NK), t, cls=2, precision=pm.PM_BF16, flops=flops, bytes=b,
+                         working_set=b))
+        del A, B, C
+    # stencil: five-point stencil grids
+    for side in (1024, 2048, 4096, 8192, 16384):
+        x = torch.empty(side * side, dtype=torch.float32, device="cuda").uniform_(-1, 1)
+        y = torch.empty_like(x)
+        r = pm.pm_probe_run(pm.probe_args(pm.PM_PROBE_STENCIL, rows=side, cols=side), x, y, warmup=5, reps=30)
+        rows.append(_seg("stencil_%d" % side, r["median_s"], cls=3, precision=pm.PM_FP32,
+                         flops=6.0 * side * side, bytes=8.0 * side * side, working_set=8.0 * side * side))
+        del x, y
+    # multi-kernel memory segments: copy -> triad (-> copy) on shared buffers
+    for k in (20, 24, 27):
+        n = 1 << k
+        a = torch.empty(n, dtype=torch.float32, device="cuda")
+        b = torch.empty(n, dtype=torch.float32, device="cuda").uniform_(-1, 1)
+        c = torch.empty(n, dtype=torch.float32, device="cuda").uniform_(-1, 1)
+        cp = pm.probe_args(pm.PM_PROBE_COPY, n=n)
+        tr = pm.probe_args(pm.PM_PROBE_TRIAD, n=n, scalar=3.0)
+        t2 = _events_median(lambda: (pm.pm_probe_launch(cp, b, a), pm.pm_probe_launch(tr, a, b, c)))
+        t3 = _events_median(lambda: (pm.pm_probe_launch(cp, b, a), pm.pm_probe_launch(tr, a, b, c),
+                                     pm.pm_probe_launch(cp, a, c)))
+        rows.append(_seg("copy+triad_2^%d" % k, t2, cls=0, precision=pm.PM_FP32, kernels=2, flops=2.0 * n,
+                         bytes=20.0 * n, working_set=12.0 * n))
+        rows.append(_seg("copy+triad+copy_2^%d" % k, t3, cls=0, precision=pm.PM_FP32, kernels=3, flops=2.0 * n,
+                         bytes=28.0 * n, working_set=12.0 * n))
+        del a, b, c
+    # host segments: H2D of b, triad, D2H of a, one synchronisation (host clock)
+    for k in (20, 24, 27):
+        n = 1 << k
+        hb = torch.empty(n, dtype=torch.float32).pin_memory()
+        hb.uniform_(-1, 1)
+        ha = torch.empty(n, dtype=torch.float32).pin_memory()
+        a = torch.empty(n, dtype=torch.float32, device="cuda")
+        b = torch.empty(n, dtype=torch.float32, device="cuda")
+        c = torch.empty(n, dtype=torch.float32, device="cuda").uniform_(-1, 1)
+        h2d = pm.probe_args(pm.PM_PROBE_H2D, n=4 * n)
+        d2h = pm.probe_args(pm.PM_PROBE_D2H, n=4 * n)
+        tr = pm.probe_args(pm.PM_PROBE_TRIAD, n=n, scalar=3.0)
+        ts = []
+        for i in range(13):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            pm.pm_probe_launch(h2d, hb, b)
+            pm.pm_probe_launch(tr, a, b, c)
+            pm.pm_probe_launch(d2h, a, ha)
+            torch.cuda.synchronize()
+            if i >= 3:
+                ts.append(time.perf_counter() - t0)
+        rows.append(_seg("h2d+triad+d2h_2^%d" % k, float(np.median(ts)), cls=0, precision=pm.PM_FP32, flops=2.0 * n,
+                         bytes=12.0 * n, working_set=12.0 * n, h2d_bytes=4.0 * n, d2h_bytes=4.0 * n, syncs=1))
+        del ha, hb, a, b, c
+    # tau_sync: a synchronisation with nothing in flight, host clock
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(2000):
+        t0 = time.perf_counter()
+        torch.cuda.synchronize()
+        ts.append(time.perf_counter() - t0)
+    log("segments measured: %d" % len(rows))
+    return dict(rows=rows, tau_sync_s=float(np.median(ts)))
+
+
+def _seg_predict(rows, theta, psi, n_sm):
+    return pm.pm_segment_predict(pm.segment_array({f: np.array([r[f] for r in rows]) for f in SEG_FIELDS}),
+                                 theta, psi, n_sm)
+
+
+def _fit_1d(rows, theta, psi, n_sm, idx, lo=1e-3, hi=1e3):
+    """psi[idx] minimising the squared log error over rows (golden section on ln psi[idx])."""
+    t = np.array([r["t"] for r in rows])
+    a, b = math.log(lo), math.log(hi)
+    g = (math.sqrt(5.0) - 1.0) / 2.0
+
+    def f(x):
+        p = psi.copy()
+        p[idx] = math.exp(x)
+        return float(np.sum((np.log(_seg_predict(rows, theta, p, n_sm)) - np.log(t)) ** 2))
+
+    c, d = b - g * (b - a), a + g * (b - a)
+    fc, fd = f(c), f(d)
+    for _ in range(80):
+        if fc < fd:
+            b, d, fd = d, c, fc
+            c = b - g * (b - a)
+            fc = f(c)
+        else:
+            a, c, fc = c, d, fd
+            d = a + g * (b - a)
+            fd = f(d)
+    return math.exp(0.5 * (a + b))
+
+
+def fit_segments(seg_table, theta, n_sm, eq15=None) -> dict:
+    """psi of the generic path: host link from the Eq. 15 fit, tau_sync measured,
+    one scale per class and an efficiency per precision (BF16's fixed at 1)
+    fitted to the measured segments; MAE per class in-sample and leave-one-out."""
+    rows = seg_table["rows"]
+    psi = np.ones(12)
+    if eq15:
+        psi[7], psi[8] = eq15["h2d"]["B_eff"], eq15["h2d"]["tau_s"]
+        psi[9], psi[10] = eq15["d2h"]["B_eff"], eq15["d2h"]["tau_s"]
+    else:
+        psi[7], psi[8], psi[9], psi[10] = 2.0e11, 4e-6, 2.0e11, 4e-6
+    psi[11] = seg_table["tau_sync_s"]
+
+    def fit(rows_, psi_):
+        p = psi_.copy()
+        comp = [r for r in rows_ if r["cls"] == pm.PM_SEG_COMPUTE and r["precision"] == pm.PM_BF16]
+        for c in (0, 2, 3):
+            rc = [r for r in rows_ if r["cls"] == c]
+            if rc:
+                p[c] = _fit_1d(rc, theta, p, n_sm, c)
+        if comp:
+            p[1] = _fit_1d(comp, theta, p, n_sm, 1)
+        for prec in (pm.PM_FP32, pm.PM_FP8E4M3):
+            rp = [r for r in rows_ if r["cls"] == pm.PM_SEG_COMPUTE and r["precision"] == prec]
+            if rp:
+                p[4 + prec] = _fit_1d(rp, theta, p, n_sm, 4 + prec)
+        return p
+
+    psi = fit(rows, psi)
+    t = np.array([r["t"] for r in rows])
+    pred = _seg_predict(rows, theta, psi, n_sm)
+    ape = np.abs(pred - t) / t * 100.0
+    # leave-one-out: refit without each row, predict it
+    loo = np.zeros(len(rows))
+    for i in range(len(rows)):
+        p_i = fit(rows[:i] + rows[i + 1:], psi)
+        loo[i] = abs(_seg_predict([rows[i]], theta, p_i, n_sm)[0] - t[i]) / t[i] * 100.0
+    by_class = {}
+    for c, name in enumerate(SEG_CLASS_NAMES):
+        m = np.array([r["cls"] == c for r in rows])
+        if m.any():
+            by_class[name] = dict(n=int(m.sum()), mae_pct=float(ape[m].mean()), loo_mae_pct=float(loo[m].mean()))
+    extra = {}
+    for name, sel in (("multi_kernel", lambda r: r["kernels"] > 1), ("host_transfers", lambda r: r["h2d_bytes"] > 0)):
+        m = np.array([sel(r) for r in rows])
+        if m.any():
+            extra[name] = dict(n=int(m.sum()), mae_pct=float(ape[m].mean()), loo_mae_pct=float(loo[m].mean()))
+    return dict(psi=psi.tolist(), by_class=by_class, by_feature=extra, all=dict(
+        n=len(rows), mae_pct=float(ape.mean()), loo_mae_pct=float(loo.mean())),
+        rows=[dict(name=r["name"], t=r["t"], pred=float(pp)) for r, pp in zip(rows, pred)])
+
+
 def main():
     import argparse
     ap = argparse.ArgumentParser(description="measure the calibration table and fit the stage model")
@@ -494,6 +711,7 @@ def main():
     ap.add_argument("--measure-instr", action="store_true", help="re-measure only the instruction/host probes")
     ap.add_argument("--measure-tmem-b", action="store_true", help="re-measure only the strategy-B GEMM rows")
     ap.add_argument("--measure-streams", action="store_true", help="re-measure only the concurrent-stream probes")
+    ap.add_argument("--measure-segments", action="store_true", help="re-measure only the generic-path segments")
     ap.add_argument("--sweep", default=SWEEP_PATH)
     ap.add_argument("--out", default=THETA_PATH)
     ap.add_argument("--report", default=None)
@@ -514,7 +732,9 @@ def main():
             measure_tmem_b(tuple(int(s) for s in args.shapes.split(",")))
     if args.measure_streams:
         table["streams"] = measure_streams()
-    if args.measure_instr or args.measure_tmem_b or args.measure_streams:
+    if args.measure_segments:
+        table["segments"] = measure_segments(table)
+    if args.measure_instr or args.measure_tmem_b or args.measure_streams or args.measure_segments:
         with open(args.sweep, "w") as f:
             json.dump(table, f)
     rows = table["rows"]
@@ -534,8 +754,13 @@ def main():
                autotune=autotune_vs_best(rows, theta, n_sm), pchase=table.get("pchase"),
                instr=table.get("instr"), tmem_strategy=tmem_strategy_report(rows, pred),
                streams=table.get("streams"))
-    save_theta(theta, dict(device=table.get("device"), n_sm=n_sm, fitted_on=os.path.basename(args.sweep),
-                           mae_holdout=rep["mae_holdout"]), args.out)
+    if table.get("segments"):
+        rep["segments"] = fit_segments(table["segments"], theta, n_sm, (table.get("instr") or {}).get("eq15"))
+    meta = dict(device=table.get("device"), n_sm=n_sm, fitted_on=os.path.basename(args.sweep),
+                mae_holdout=rep["mae_holdout"])
+    if rep.get("segments"):
+        meta["segment_psi"] = rep["segments"]["psi"]        # generic path: class scales, efficiencies, host link
+    save_theta(theta, meta, args.out)
     if args.report:
         with open(args.report, "w") as f:
             json.dump(rep, f, indent=1)
@@ -546,6 +771,12 @@ def main():
     for a in rep["autotune"]:
         print("autotune %(M)d dt=%(dtype)d pick=%(pick)s best=%(best)s pick/best=%(pick_over_best).3f "
               "TFLOP/s pick %(tflops_pick).0f best %(tflops_best).0f" % a)
+    if rep.get("segments"):
+        sg = rep["segments"]
+        print("generic path psi %s" % ["%.3g" % v for v in sg["psi"]])
+        for name, v in list(sg["by_class"].items()) + list(sg["by_feature"].items()):
+            print("segments %-14s n=%2d MAE %.1f %% (leave-one-out %.1f %%)" % (name, v["n"], v["mae_pct"],
+                                                                            v["loo_mae_pct"]))
     for name, v in (rep.get("streams") or {}).items():
         print("streams %s: T(N_c) %s s, tau_c %.3g s (%.2f T1), additive-law MAE %.1f %%" % (
             name, ["%.3g" % x for x in v["t_s"]], v["fit"]["tau_c_s"], v["fit"]["tau_over_T1"], v["fit"]["mae_pct"]))

@@ -43,6 +43,7 @@ def test_library_exports_every_declared_symbol(pm):
 def test_struct_layouts(pm):
     assert ctypes.sizeof(pm.pm_cfg) == 24 == pm.CFG_DTYPE.itemsize
     assert ctypes.sizeof(pm.pm_params) == 64
+    assert pm.SEGMENT_DTYPE.itemsize == 64 and ctypes.sizeof(pm.pm_segment_params) == 96
     assert pm.pm_version() == 10000
 
 
@@ -112,6 +113,11 @@ def test_bad_arguments_rejected(pm):
                                       None, None) == pm.PM_EINVAL
     assert L.pm_grouped_gemm_autotune(2, Mg, 64, 64, ctypes.byref(th), 152, 4, None, None, None, 1, 1, None,
                                       o16, o16, launch, None, None) == pm.PM_EINVAL
+    ps = pm.pm_segment_params()
+    assert L.pm_segment_predict(None, 4, ctypes.byref(th), ctypes.byref(ps), 152, None, None) == pm.PM_EINVAL
+    assert L.pm_segment_predict(None, 0, ctypes.byref(th), ctypes.byref(ps), 152, None, None) == pm.PM_OK
+    assert L.pm_segment_predict(ctypes.c_void_p(12), 4, ctypes.byref(th), ctypes.byref(ps), 152, ctypes.c_void_p(16),
+                                None) == pm.PM_EINVAL                    # misaligned records
     # concurrent-stream probe: argument checks come before any CUDA call
     bufs = (ctypes.c_void_p * 8)(*([16] * 8))
     vp = ctypes.cast(bufs, ctypes.c_void_p)
