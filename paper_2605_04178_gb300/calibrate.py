@@ -755,11 +755,17 @@ def main():
                instr=table.get("instr"), tmem_strategy=tmem_strategy_report(rows, pred),
                streams=table.get("streams"))
     if table.get("segments"):
-        rep["segments"] = fit_segments(table["segments"], theta, n_sm, (table.get("instr") or {}).get("eq15"))
+        # the generic path's roofline uses the measured peak rates (instruction
+        # probe), not the stage model's fitted per-step rates
+        theta_generic = theta.copy()
+        theta_generic[6:9] = th0[6:9]
+        rep["segments"] = fit_segments(table["segments"], theta_generic, n_sm, (table.get("instr") or {}).get("eq15"))
+        rep["segments"]["theta"] = theta_generic.tolist()
     meta = dict(device=table.get("device"), n_sm=n_sm, fitted_on=os.path.basename(args.sweep),
                 mae_holdout=rep["mae_holdout"])
     if rep.get("segments"):
         meta["segment_psi"] = rep["segments"]["psi"]        # generic path: class scales, efficiencies, host link
+        meta["segment_theta"] = rep["segments"]["theta"]    # theta with the probe-measured peak rates
     save_theta(theta, meta, args.out)
     if args.report:
         with open(args.report, "w") as f:
