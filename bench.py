@@ -376,6 +376,12 @@ def run_gpu(args):
             with open(calib_rep) as f:
                 rep = json.load(f)
             line["model_mae_pct_holdout"] = {k: round(v["mae_pct"], 2) for k, v in rep["mae_holdout"].items()}
+        calib_meas = os.path.join(ROOT, "paper_2605_04178_gb300", "data", "calib_report_gb300_measured.json")
+        if os.path.exists(calib_meas):
+            with open(calib_meas) as f:
+                rep = json.load(f)
+            line["model_mae_pct_holdout_measured_reading"] = {k: round(v["mae_pct"], 2)
+                                                              for k, v in rep["mae_holdout"].items()}
         line.update(extra)
         if not args.skip_cpu:
             # the oracle on the host cores: rows 0..47 of the same product, which

@@ -77,9 +77,23 @@ typedef struct {
  *  0 T_launch   1 B_sus      2 B_peak     3 w0          4 L_TMA      5 B_TMA/SM
  *  6 R_TC tf32  7 R_TC bf16  8 R_TC fp8   9 L_mma      10 BW_TMEM_rd 11 BW_TMEM_wr
  * 12 L_mbar    13 L_alloc+L_dealloc      14 S_2SM      15 c_alpha
- * with the overlap law alpha(stages) = clamp(1 - c_alpha/(stages - 1), 0, 1)
- * (alpha = 0 for a single stage). */
+ * with the overlap law alpha(stages) = clamp(1 - c_alpha/stages, 0, 1) (the
+ * measured reading: clamp(1 - c_alpha/(stages - 1), 0, 1)). */
 typedef struct { float v[16]; } pm_params;
+
+/* Readings of the points the paper leaves open in the stage model:
+ *  PM_READING_LITERAL (default): the equations as printed -- L_mma once per
+ *    K-step (Eq. 2), alpha = 1 - c_alpha/stages, T_sync in both Eq. 7 and
+ *    Eq. 8;
+ *  PM_READING_MEASURED: readings measured on this library's kernels -- L_mma
+ *    once per tensor-pipe instruction of the K-step (BK/k_instr per 128-row
+ *    block per pass, plus strategy B's copies), alpha = 1 - c_alpha/(stages-1),
+ *    T_sync once per K-step (Eq. 8).
+ * The setting is process-wide and read by every model entry point at launch;
+ * fit theta under the reading it will be used with. */
+typedef enum { PM_READING_LITERAL = 0, PM_READING_MEASURED = 1 } pm_reading;
+pm_status pm_model_set_reading(int32_t reading);
+int32_t pm_model_reading(void);
 
 /* ------------------------------------------------------------------ probes */
 /* Calibration microbenchmarks (Sec. V-A; STREAM-style copy and triad for the

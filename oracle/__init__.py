@@ -89,6 +89,8 @@ def _load():
             lib.orc_grouped_autotune.argtypes = [ctypes.c_int, P, ctypes.c_int32, ctypes.c_int32,
                                                  ctypes.c_int, P, ctypes.c_int, P, P, P]
             lib.orc_grouped_autotune.restype = ctypes.c_double
+            lib.orc_set_reading.argtypes = [ctypes.c_int]
+            lib.orc_reading.restype = ctypes.c_int
             lib.orc_segment_predict.argtypes = [i64] + [P] * 10 + [P, P, ctypes.c_int, P]
             lib.orc_stencil5_f32.argtypes = [P, i64, i64, P]
             _lib = lib
@@ -284,9 +286,25 @@ def segment_predict(segs: dict, theta, psi, n_sm: int) -> np.ndarray:
     return t
 
 
-def prior_theta(n_sm: int, f_hz: float = 1.9e9) -> np.ndarray:
+READING_LITERAL, READING_MEASURED = 0, 1
+
+
+def set_reading(reading: int) -> None:
+    """Select the readings of the stage model's open points (process-wide):
+    0 the literal equations (L_mma per K-step, alpha = 1 - c/s, T_sync in Eqs. 7 and 8),
+    1 the readings measured on the GPU's kernels (L_mma per tensor-pipe instruction,
+    alpha = 1 - c/(s-1), T_sync once)."""
+    _load().orc_set_reading(int(reading))
+
+
+def reading() -> int:
+    return int(_load().orc_reading())
+
+
+def prior_theta(n_sm: int, f_hz: float = 1.9e9, reading: int = READING_LITERAL) -> np.ndarray:
     """Prior parameter vector built from the paper's printed values (Table "parameters",
-    Sec. II-A sustained figures); cycles are converted with the clock f_hz."""
+    Sec. II-A sustained figures); cycles are converted with the clock f_hz.  c_alpha puts
+    alpha in the printed 0.85-0.95 range under either overlap law."""
     th = np.zeros(N_PARAMS, dtype=np.float64)
     th[0] = 5e-6                      # launch overhead, 5-12 us (Sec. V-B, memory-bound class)
     th[1] = 6.8e12                    # sustained HBM (Sec. II-A)
@@ -303,7 +321,8 @@ def prior_theta(n_sm: int, f_hz: float = 1.9e9) -> np.ndarray:
     th[12] = 45.0 / f_hz              # L_mbar 40-50 cycles
     th[13] = 100e-9                   # TMEM alloc + dealloc (not printed)
     th[14] = 1.0                      # S_2SM
-    th[15] = 0.15                     # alpha(2) = 0.85, alpha(3) = 0.925 (double to triple buffering)
+    # alpha(2) = 0.85, alpha(6) = 0.95 (reading 0); alpha(2) = 0.85, alpha(3) = 0.925 (reading 1)
+    th[15] = 0.3 if reading == READING_LITERAL else 0.15
     return th
 
 

@@ -225,7 +225,7 @@ template <> inline Dual lift<Dual>(double v) { return dconst(v); }
 // 12 L_mbar        mbarrier latency                          (T_sync)
 // 13 L_alloc+L_dealloc  TMEM management                      (T_TMEM_mgmt)
 // 14 S_2SM         2-SM cooperative speedup                  (Eq. 6)
-// 15 c_alpha       overlap law alpha(s) = clamp(1 - c_alpha/(s-1), 0, 1)
+// 15 c_alpha       overlap law alpha(s) = clamp(1 - c_alpha/s, 0, 1) (reading 1: s - 1)
 // ---------------------------------------------------------------------------
 
 enum { K_GEMM = 0, K_COPY = 1, K_TRIAD = 2, K_TMA2D = 3 };
@@ -281,26 +281,37 @@ static T b_eff(const T* th, double W) {
   return th[1] + (th[2] - th[1]) * dexp(lift<T>(-W) / th[3]);
 }
 
+// Two sets of readings of the points the paper leaves open:
+//   0 (default) the literal equations: L_mma once per K-step (Eq. 2),
+//     alpha(s) = clamp(1 - c_alpha/s, 0, 1), T_sync in both Eq. 7 and Eq. 8;
+//   1 readings measured on this GPU's kernels: L_mma once per tensor-pipe
+//     instruction the K-step issues (BK/k_instr per 128-row block per pass,
+//     plus strategy B's copies), alpha(s) = clamp(1 - c_alpha/(s-1), 0, 1)
+//     (an s-stage ring keeps s-1 loads in flight), T_sync once per K-step
+//     (Eq. 8; the barrier of Eq. 7 is the same one).
+static int g_reading = 0;
+extern "C" void orc_set_reading(int r) { g_reading = r == 1 ? 1 : 0; }
+extern "C" int orc_reading() { return g_reading; }
+
 // One K-step and one tile of the stage model (Eqs. 2-8).  Returns T_step and
 // T_store through the out-arguments; shared by the GEMM and grouped models.
 template <class T>
 static void stage_terms(const Cfg& c, i64 Kt, const T* th, T& Tstep, T& Tstore) {
+  const bool measured = g_reading == 1;
   const double e = elem_bytes(c.dtype), np = mma_passes(c.dtype), l = load_mult(c.dtype);
   const T& R = th[rate_index(c.dtype)];
-  // Eq. 2: per K-step TMEM cost, D_accum = FP32 accumulator bytes of the tile.
-  // Reading: the tcgen05.mma latency L_mma is paid once per MMA instruction the
-  // K-step issues -- BK / k_instr K-slices per 128-row block, per TF32 pass --
-  // while the accumulator traffic D is counted once per K-step.
+  // Eq. 2: per K-step TMEM cost, D_accum = FP32 accumulator bytes of the tile,
+  // L_mma once per K-step (reading 0) or once per tensor-pipe instruction
+  // (reading 1: BK / k_instr K-slices per 128-row block, per TF32 pass).
   const double D = 4.0 * c.BM * c.BN;
-  double n_instr = np * (double)(c.BK / instr_k(c.dtype)) * (double)ceil_div(c.BM, 128);
+  double n_instr = measured ? np * (double)(c.BK / instr_k(c.dtype)) * (double)ceil_div(c.BM, 128) : 1.0;
   // Strategy B ("A and accumulators in TMEM", Sec. III-A.1) adds the A tile's
   // TMEM traffic: written once per K-step by the copy into TMEM (l planes),
-  // read by every tensor pass.  The copies are tensor-pipe instructions of
-  // the same K-step (one per 128-row x 32-byte slice of each plane), so under
-  // the per-instruction reading of L_mma each is charged L_mma as well.
+  // read by every tensor pass.  Under reading 1 its copies (one per 128-row x
+  // 32-byte slice of each plane) are tensor-pipe instructions charged L_mma.
   const double DA_w = c.tmem_a ? l * e * c.BM * c.BK : 0.0;
   const double DA_r = c.tmem_a ? np * e * c.BM * c.BK : 0.0;
-  if (c.tmem_a) n_instr += l * (c.BK * e / 32.0) * (double)ceil_div(c.BM, 128);
+  if (c.tmem_a && measured) n_instr += l * (c.BK * e / 32.0) * (double)ceil_div(c.BM, 128);
   const T T_tmem = (D + DA_r) / th[10] + n_instr * th[9] + (D + DA_w) / th[11];
   // T_TMEM_mgmt amortised over the K-steps (Sec. III-A.5).
   const T T_mgmt = th[13] / lift<T>((double)Kt);
@@ -313,11 +324,13 @@ static void stage_terms(const Cfg& c, i64 Kt, const T* th, T& Tstep, T& Tstore) 
   const T T_tma = th[4] + b_step / th[5];
   // T_sync = N_bar * L_mbar with N_bar = 2 (full and empty barrier per stage).
   const T T_sync = 2.0 * th[12];
-  // Eq. 7 with T_decomp = 0 and alpha from the pipeline depth: while one
-  // stage is consumed the ring keeps s - 1 loads in flight, so the exposed
-  // share of a load falls as c_alpha / (s - 1); one stage overlaps nothing.
-  const T alpha = c.s <= 1 ? lift<T>(0.0) : dclamp01(1.0 - th[15] / lift<T>((double)(c.s - 1)));
-  const T T_io = (1.0 - alpha) * T_tma + T_sync;
+  // Eq. 7 with T_decomp = 0 and alpha from the pipeline depth: reading 0
+  // alpha = 1 - c_alpha/s; reading 1 alpha = 1 - c_alpha/(s-1) (one stage
+  // overlaps nothing) and the sync is counted once, in Eq. 8.
+  T alpha = lift<T>(0.0);
+  if (measured) alpha = c.s <= 1 ? lift<T>(0.0) : dclamp01(1.0 - th[15] / lift<T>((double)(c.s - 1)));
+  else alpha = dclamp01(1.0 - th[15] / lift<T>((double)c.s));
+  const T T_io = measured ? (1.0 - alpha) * T_tma : (1.0 - alpha) * T_tma + T_sync;
   // Eq. 8, O_misc = 0.
   Tstep = dmax(T_c, T_io) + T_sync;
   // Writeback of the FP32 tile: L_store_setup + bytes(C_tile)/B (Sec. III-A.5).

@@ -21,6 +21,7 @@ LIB_PATH = os.path.join(_HERE, "lib", "libperfmodel.so")
 PM_OK, PM_EINVAL, PM_EUNSUPPORTED, PM_ECUDA, PM_ETIMEOUT, PM_ENOMEM = 0, -1, -2, -3, -4, -5
 PM_FP32, PM_BF16, PM_FP8E4M3 = 0, 1, 2
 PM_KIND_GEMM, PM_KIND_COPY, PM_KIND_TRIAD, PM_KIND_TMA2D = 0, 1, 2, 3
+PM_READING_LITERAL, PM_READING_MEASURED = 0, 1
 PM_PROBE_COPY, PM_PROBE_TRIAD, PM_PROBE_TMA2D, PM_PROBE_PCHASE = 1, 2, 3, 4
 PM_PROBE_H2D, PM_PROBE_D2H, PM_PROBE_MMA, PM_PROBE_MBAR, PM_PROBE_TMEM_LD, PM_PROBE_TMEM_ST = 5, 6, 7, 8, 9, 10
 PM_PROBE_HOST_READ, PM_PROBE_HOST_WRITE, PM_PROBE_STENCIL = 11, 12, 13
@@ -73,7 +74,7 @@ assert ctypes.sizeof(pm_cfg) == 24 and ctypes.sizeof(pm_probe_args) == 56 and ct
 # Every exported symbol of include/perfmodel.h
 EXPORTS = ("pm_probe_launch", "pm_probe_run", "pm_streams_run", "pm_gemm_operand_bytes", "pm_gemm_prepare", "pm_gemm_run",
            "pm_gemm_bench", "pm_gemm_host_workspace", "pm_gemm_host",
-           "pm_grouped_gemm_run", "pm_model_predict", "pm_model_grad_workspace", "pm_model_grad", "pm_model_grad_f64", "pm_model_grad_noalloc",
+           "pm_grouped_gemm_run", "pm_model_predict", "pm_model_set_reading", "pm_model_reading", "pm_model_grad_workspace", "pm_model_grad", "pm_model_grad_f64", "pm_model_grad_noalloc",
            "pm_autotune_pick", "pm_autotune_topk", "pm_gemm_autotune", "pm_grouped_autotune", "pm_grouped_gemm_autotune", "pm_segment_predict", "pm_last_error", "pm_device_status",
            "pm_watchdog_selftest", "pm_version")
 
@@ -124,6 +125,8 @@ def _load():
         "pm_grouped_gemm_autotune": [i32, P, i32, i32, ctypes.POINTER(pm_params), i32, i32, P, P, P, ctypes.c_int,
                                      ctypes.c_int, P, P, P, P, P, ctypes.POINTER(pm_probe_result)],
         "pm_device_status": [ctypes.c_int],
+        "pm_model_set_reading": [i32],
+        "pm_model_reading": [],
         "pm_watchdog_selftest": [i32, P],
         "pm_version": [],
         "pm_last_error": [],
@@ -402,6 +405,15 @@ def pm_segment_predict(segs: np.ndarray, theta, psi, n_sm, stream=None) -> np.nd
     _check(_lib.pm_segment_predict(_ptr(dev), int(n), ctypes.byref(params(theta)), ctypes.byref(ps), int(n_sm),
                                    _ptr(out), _stream(stream)), "pm_segment_predict")
     return out[:n].cpu().numpy()
+
+
+def pm_model_set_reading(reading: int) -> None:
+    """Process-wide reading of the stage model's open points (PM_READING_LITERAL / _MEASURED)."""
+    _check(_lib.pm_model_set_reading(int(reading)), "pm_model_set_reading")
+
+
+def pm_model_reading() -> int:
+    return int(_lib.pm_model_reading())
 
 
 # ---------------------------------------------------------------- diagnostics

@@ -10,6 +10,7 @@
 #include <math.h>
 
 #include <algorithm>
+#include <atomic>
 #include <mutex>
 #include <vector>
 
@@ -25,6 +26,7 @@ template <class F>
 struct ThetaT {
   F v[16];
   F inv[16];
+  int reading;       // PM_READING_LITERAL or PM_READING_MEASURED (see pm_model_set_reading)
 };
 using Theta = ThetaT<float>;
 
@@ -98,10 +100,13 @@ using GemmFwd = GemmFwdT<float>;
 //   T_TMEM = (D + D_A,r)/BW_rd + n_instr L_mma + (D + D_A,w)/BW_wr   (Eq. 2)
 //            D_A = 0 for TMEM strategy A; strategy B writes the A tile
 //            into TMEM (D_A,w = l e BM BK) and every pass reads it back
-//            (D_A,r = n_p e BM BK); n_instr counts its tcgen05.cp copies too
+//            (D_A,r = n_p e BM BK); n_instr = 1 (literal reading) or the
+//            tensor-pipe instructions of the K-step incl. strategy B's
+//            tcgen05.cp copies (measured reading)
 //   T_c    = n_p 2 BM BN BK / (R S) + T_TMEM + T_mgmt/K_tiles     (Eqs. 3, 6)
 //   T_tma  = L_TMA + b_step / B_TMA, b_step = l e BK (BM + BN/g) (Eq. 4, P = 1)
-//   T_io   = (1 - alpha) T_tma + T_sync, T_sync = 2 L_mbar       (Eq. 7)
+//   T_io   = (1 - alpha) T_tma + T_sync, T_sync = 2 L_mbar       (Eq. 7; the
+//            measured reading drops this T_sync: one barrier per K-step)
 //   T_step = max(T_c, T_io) + T_sync                             (Eq. 8)
 //   T_stage = T_launch + waves (K_tiles T_step + T_store)
 //   T_hat = max(T_stage, T_launch + max(FLOPs/(n_SM R S), bytes_min/B_peak))
@@ -119,13 +124,15 @@ __device__ __forceinline__ void gemm_forward(const pm_cfg& c, const ThetaT<F>& t
   f.Kt = count_to<F>(Kt);
   f.waves = count_to<F>(waves);
   f.D = F(4) * c.BM * c.BN;
-  // L_mma once per tcgen05.mma issued in the K-step: BK/k_instr per 128-row block, per pass
+  const bool measured = th.reading == PM_READING_MEASURED;
+  // L_mma once per K-step (literal) or once per tcgen05.mma the K-step
+  // issues, BK/k_instr per 128-row block per pass (measured)
   const int kin = dt == PM_FP32 ? 8 : (dt == PM_BF16 ? 16 : 32);
-  f.n_instr = np * (F)(c.BK / kin) * (F)((c.BM + 127) / 128);
+  f.n_instr = measured ? np * (F)(c.BK / kin) * (F)((c.BM + 127) / 128) : F(1);
   f.DA_w = c.tmem_a ? l * e * c.BM * c.BK : F(0);
   f.DA_r = c.tmem_a ? np * e * c.BM * c.BK : F(0);
-  // strategy B also issues one tcgen05.cp per 128-row x 32-byte A slice, each charged L_mma
-  if (c.tmem_a) f.n_instr += l * (F)(c.BK * (int)e / 32) * (F)((c.BM + 127) / 128);
+  // measured: strategy B's tcgen05.cp per 128-row x 32-byte A slice, each charged L_mma
+  if (c.tmem_a && measured) f.n_instr += l * (F)(c.BK * (int)e / 32) * (F)((c.BM + 127) / 128);
   const F T_tmem = (f.D + f.DA_r) * th.inv[10] + f.n_instr * th.v[9] + (f.D + f.DA_w) * th.inv[11];
   const F T_mgmt = th.v[13] / f.Kt;
   f.S = g == 1 ? F(1) : th.v[14];
@@ -135,12 +142,13 @@ __device__ __forceinline__ void gemm_forward(const pm_cfg& c, const ThetaT<F>& t
   f.bstep = l * e * c.BK * ((F)c.BM + (F)c.BN / (F)g);
   f.T_tma = th.v[4] + f.bstep * th.inv[5];
   const F T_sync = F(2) * th.v[12];
-  // 1 - alpha = clamp(c_alpha / (s - 1), 0, 1): s - 1 loads in flight while
-  // one stage is consumed; a single stage hides nothing
-  const F r = c.stages > 1 ? th.v[15] / (F)(c.stages - 1) : F(1);
+  // 1 - alpha = clamp(c_alpha / s, 0, 1) (literal) or clamp(c_alpha / (s - 1),
+  // 0, 1) (measured: s - 1 loads in flight while one stage is consumed; a
+  // single stage hides nothing)
+  const F r = measured ? (c.stages > 1 ? th.v[15] / (F)(c.stages - 1) : F(1)) : th.v[15] / (F)c.stages;
   f.oma_free = r > F(0) && r < F(1);
   f.oma = r <= F(0) ? F(0) : (r >= F(1) ? F(1) : r);
-  f.T_io = f.oma * f.T_tma + T_sync;
+  f.T_io = measured ? f.oma * f.T_tma : f.oma * f.T_tma + T_sync;
   f.T_step = pm_max(f.T_c, f.T_io) + T_sync;
   f.store_bytes = F(4) * c.BM * c.BN;
   f.T_store = th.v[4] + f.store_bytes * th.inv[5];
@@ -181,9 +189,10 @@ __device__ __forceinline__ void gemm_adjoint(const pm_cfg& c, const ThetaT<F>& t
   F g_c = F(0), g_io = F(0);
   if (f.T_c >= f.T_io) g_c = g_step; else g_io = g_step;
   // T_io = oma * T_tma + T_sync
-  g_sync += g_io;
+  if (th.reading != PM_READING_MEASURED) g_sync += g_io;
   const F g_tma = g_io * f.oma;
-  if (f.oma_free) d[15] += g_io * f.T_tma / (F)(c.stages - 1);
+  if (f.oma_free)
+    d[15] += g_io * f.T_tma / (F)(th.reading == PM_READING_MEASURED ? c.stages - 1 : c.stages);
   d[4] += g_tma;
   d[5] -= g_tma * (f.bstep * th.inv[5]) * th.inv[5];
   d[12] += F(2) * g_sync;
@@ -612,12 +621,15 @@ __global__ void __launch_bounds__(kGroupThreads) grouped_tune_kernel(const int32
   }
 }
 
+static std::atomic<int> g_reading{PM_READING_LITERAL};
+
 static Theta to_theta(const pm_params* p) {
   Theta t;
   for (int j = 0; j < 16; ++j) {
     t.v[j] = p->v[j];
     t.inv[j] = (float)(1.0 / (double)p->v[j]);
   }
+  t.reading = g_reading.load();
   return t;
 }
 
@@ -682,6 +694,7 @@ extern "C" pm_status pm_model_grad_f64(const pm_cfg* cfgs_dev, int64_t n, const 
     th.v[j] = theta_host[j];
     th.inv[j] = 1.0 / theta_host[j];
   }
+  th.reading = g_reading.load();
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   model_grad_kernel<double><<<blocks, kGradThreads, 0, s>>>(cfgs_dev, n, th, n_sm, t_meas_dev,
                                                             static_cast<double*>(workspace_dev));
@@ -690,6 +703,15 @@ extern "C" pm_status pm_model_grad_f64(const pm_cfg* cfgs_dev, int64_t n, const 
   model_grad_finish_kernel<<<1, 17 * 32, 0, s>>>(static_cast<const double*>(workspace_dev), blocks, n, out_dev);
   return launch_status("model_grad_finish_kernel");
 }
+
+extern "C" pm_status pm_model_set_reading(int32_t reading) {
+  PM_REQUIRE(reading == PM_READING_LITERAL || reading == PM_READING_MEASURED, PM_EINVAL,
+             "reading %d is not a pm_reading", reading);
+  g_reading.store(reading);
+  return PM_OK;
+}
+
+extern "C" int32_t pm_model_reading(void) { return g_reading.load(); }
 
 extern "C" pm_status pm_autotune_pick(const int32_t* MNK_dev, int64_t n, int32_t dtype, const pm_params* theta_host,
                                       int32_t n_sm, pm_cfg* picks_dev, float* t_pred_dev, void* stream) {

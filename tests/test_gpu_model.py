@@ -49,7 +49,7 @@ def predict_gpu(lib, c, theta):
 
 
 @pytest.mark.parametrize("n", [1, 7, 1000, 100003])
-def test_predict_matches_oracle(lib, n):
+def test_predict_matches_oracle(lib, reading, n):
     c = random_cfgs(n, seed=n, strategy_b=True)
     th = theta32()
     t_gpu = predict_gpu(lib, c, th)
@@ -57,7 +57,7 @@ def test_predict_matches_oracle(lib, n):
     assert np.all(np.abs(t_gpu - t_orc) <= 1e-5 * t_orc)
 
 
-def test_predict_probes_and_config1(lib):
+def test_predict_probes_and_config1(lib, reading):
     th = theta32()
     c = probe_cfgs()
     assert np.all(np.abs(predict_gpu(lib, c, th) - O.model_batch(c, th, N_SM)) <= 1e-5 * O.model_batch(c, th, N_SM))
@@ -94,7 +94,7 @@ def grad_gpu(lib, c, theta, t_meas):
 
 
 @pytest.mark.parametrize("n", [1, 1000, 200000])
-def test_grad_matches_oracle(lib, n):
+def test_grad_matches_oracle(lib, reading, n):
     c = random_cfgs(n, seed=17 + n, strategy_b=True)
     pc = probe_cfgs()
     c = {k: np.concatenate([c[k], pc[k]]) for k in c}
@@ -112,7 +112,7 @@ def test_grad_matches_oracle(lib, n):
     assert np.all(np.abs(g_gpu - g_orc) <= 1e-4 * scale + 1e-30), (g_gpu, g_orc, scale)
 
 
-def test_autotune_matches_oracle(lib):
+def test_autotune_matches_oracle(lib, reading):
     rng = S.splitmix64(31, 3 * 600)
     MNK = (16 * (1 + (rng >> np.uint64(40)) % np.uint64(1024))).astype(np.int32).reshape(-1, 3)
     MNK = np.concatenate([MNK, np.array([[512, 512, 512], [8192, 8192, 8192], [16384, 16384, 16384]], np.int32)])
@@ -150,7 +150,7 @@ def test_autotune_million_configs_per_launch(lib):
     assert np.all(np.abs(t.cpu().numpy()[idx] - t_o) <= 1e-5 * t_o)
 
 
-def test_grouped_autotune_matches_oracle(lib):
+def test_grouped_autotune_matches_oracle(lib, reading):
     Mg = S.grouped_m(64, 3)
     th = theta32()
     t_g, bm_g, bn_g, launch_g = lib.pm_grouped_autotune(Mg, 4096, 4096, 1, th, N_SM)
@@ -161,7 +161,7 @@ def test_grouped_autotune_matches_oracle(lib):
     assert t_check == pytest.approx(t_o, rel=1e-5)
 
 
-def test_autotune_topk_matches_oracle_order(lib):
+def test_autotune_topk_matches_oracle_order(lib, reading):
     th = theta32()
     MNK = np.array([[512, 512, 512], [1024, 2048, 4096], [8192, 8192, 8192], [300, 5000, 1000]], np.int32)
     k = 8
@@ -189,7 +189,7 @@ def test_autotune_topk_matches_oracle_order(lib):
 
 
 @pytest.mark.parametrize("n", [1, 1000, 50000])
-def test_grad_f64_matches_oracle_tightly(lib, n):
+def test_grad_f64_matches_oracle_tightly(lib, reading, n):
     # the all-FP64 objective agrees with the FP64 oracle to rounding order
     c = random_cfgs(n, seed=29 + n, strategy_b=True)
     pc = probe_cfgs()
