@@ -293,6 +293,15 @@ static int g_reading = 0;
 extern "C" void orc_set_reading(int r) { g_reading = r == 1 ? 1 : 0; }
 extern "C" int orc_reading() { return g_reading; }
 
+// Output tiles a launch runs on its CTAs: ceil(M/BM) ceil(N/BN) in the literal
+// reading; in the measured reading a CTA pair covers 2 BM x BN, so a pair
+// launch runs 2 ceil(M / 2BM) ceil(N/BN) CTA tiles (the last pair-row may be
+// half idle).
+static i64 cta_tiles(i64 M, i64 N, int BM, int BN, int g) {
+  if (g_reading == 1) return (i64)g * ceil_div(M, (i64)g * BM) * ceil_div(N, (i64)BN);
+  return ceil_div(M, (i64)BM) * ceil_div(N, (i64)BN);
+}
+
 // One K-step and one tile of the stage model (Eqs. 2-8).  Returns T_step and
 // T_store through the out-arguments; shared by the GEMM and grouped models.
 template <class T>
@@ -346,7 +355,7 @@ static void stage_terms(const Cfg& c, i64 Kt, const T* th, T& Tstep, T& Tstore) 
 template <class T>
 static T model_gemm(const Cfg& c, const T* th, int n_sm) {
   const i64 Kt = ceil_div(c.K, c.BK);
-  const i64 tiles = (i64)c.g * ceil_div(c.M, (i64)c.g * c.BM) * ceil_div(c.N, c.BN);
+  const i64 tiles = cta_tiles(c.M, c.N, c.BM, c.BN, c.g);
   const i64 n_conc = (c.g == 1) ? n_sm : 2 * (n_sm / 2);
   const i64 waves = ceil_div(tiles, n_conc);
   T Tstep, Tstore;
@@ -490,7 +499,7 @@ extern "C" double orc_grouped_predict(int G, const int32_t* Mg, int32_t N, int32
     double Tstep, Tstore;
     stage_terms<double>(c, Kt, theta, Tstep, Tstore);
     const double tau = (double)Kt * Tstep + Tstore;
-    const i64 tiles = (i64)g * ceil_div(c.M, (i64)g * c.BM) * ceil_div(N, c.BN);
+    const i64 tiles = cta_tiles(c.M, N, c.BM, c.BN, g);
     // With cta_group 2 a pair of consecutive tiles runs on a worker pair;
     // each CTA of the pair is one worker.
     for (i64 j = 0; j < tiles; ++j, ++t) busy[t % n_conc] += tau;
@@ -524,7 +533,7 @@ extern "C" double orc_grouped_autotune(int G, const int32_t* Mg, int32_t N, int3
               const i64 Kt = ceil_div(K, BK);
               double Tstep, Tstore;
               stage_terms<double>(c, Kt, theta, Tstep, Tstore);
-              const double tiles = (double)((i64)g * ceil_div(c.M, (i64)g * c.BM) * ceil_div(N, c.BN));
+              const double tiles = (double)cta_tiles(c.M, N, c.BM, c.BN, g);
               const double cost = tiles * ((double)Kt * Tstep + Tstore);
               if (cost < bq) { bq = cost; bm[q] = c.BM; bn[q] = c.BN; }
             }

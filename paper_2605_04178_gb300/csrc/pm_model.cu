@@ -112,19 +112,21 @@ using GemmFwd = GemmFwdT<float>;
 //   T_hat = max(T_stage, T_launch + max(FLOPs/(n_SM R S), bytes_min/B_peak))
 template <class F>
 __device__ __forceinline__ void gemm_forward(const pm_cfg& c, const ThetaT<F>& th, int n_sm, GemmFwdT<F>& f) {
+  const bool measured = th.reading == PM_READING_MEASURED;
   const int dt = c.dtype, g = c.cta_group;
   const F e = dt_bytes(dt), np = dt_passes(dt), l = dt_loads(dt);
   f.ri = dt_rate(dt);
   f.R = th.v[f.ri];
   f.invR = th.inv[f.ri];
   const int64_t Kt = cdiv(c.K, c.BK);
-  const int64_t tiles = (int64_t)g * cdiv(c.M, (int64_t)g * c.BM) * cdiv(c.N, c.BN);
+  // CTA tiles: ceil(M/BM) ceil(N/BN) (literal); a pair covers 2 BM x BN (measured)
+  const int64_t tiles = measured ? (int64_t)g * cdiv(c.M, (int64_t)g * c.BM) * cdiv(c.N, c.BN)
+                                 : cdiv(c.M, c.BM) * cdiv(c.N, c.BN);
   const int64_t n_conc = g == 1 ? n_sm : 2 * (n_sm / 2);
   const int64_t waves = cdiv(tiles, n_conc);
   f.Kt = count_to<F>(Kt);
   f.waves = count_to<F>(waves);
   f.D = F(4) * c.BM * c.BN;
-  const bool measured = th.reading == PM_READING_MEASURED;
   // L_mma once per K-step (literal) or once per tcgen05.mma the K-step
   // issues, BK/k_instr per 128-row block per pass (measured)
   const int kin = dt == PM_FP32 ? 8 : (dt == PM_BF16 ? 16 : 32);
@@ -584,7 +586,8 @@ __global__ void __launch_bounds__(kGroupThreads) grouped_tune_kernel(const int32
         GemmFwd f;
         gemm_forward(c, th, n_sm, f);
         const float tq = f.Kt * f.T_step + f.T_store;   // one tile of this group
-        const int64_t nt = (int64_t)g * cdiv(c.M, (int64_t)g * BM) * cdiv(N, BN);
+        const int64_t nt = th.reading == PM_READING_MEASURED ? (int64_t)g * cdiv(c.M, (int64_t)g * BM) * cdiv(N, BN)
+                                                             : cdiv(c.M, BM) * cdiv(N, BN);
         const float cost = (float)nt * tq;
         if (cost < best) { best = cost; bm = BM; bn = BN; btau = tq; btiles = nt; }
       }

@@ -312,3 +312,19 @@ def test_grouped_autotune_brute_force(reading):
         if best is None or v < best[0]:
             best = (v, [x[1] for x in sel], [x[2] for x in sel], (bk, s, g))
     assert t == best[0] and list(bm) == best[1] and list(bn) == best[2] and launch == best[3]
+
+
+def test_pair_tile_count_per_reading(reading):
+    # ceil(M/BM) ceil(N/BN) CTA tiles (literal) against 2 ceil(M/2BM) ceil(N/BN)
+    # (measured: the pair covers 2 BM rows).  With 152 SMs (76 pairs) and
+    # N = 50 BN: M = 3 BM gives 150 tiles = one wave (literal) or 200 = two
+    # waves (measured); M = 2 BM gives 100 tiles, one wave, either way.
+    th = PRIOR160.copy()
+    base = dict(N=128 * 50, K=4096, BM=128, BN=128, BK=64, stages=4, cta_group=2, dtype=1)
+    t3 = float(O.model_batch(cfgs([dict(M=384, **base)]), th, 152)[0])
+    t2 = float(O.model_batch(cfgs([dict(M=256, **base)]), th, 152)[0])
+    step_part = t2 - th[0]                                  # one wave of K-steps + store
+    if reading == 0:
+        assert t3 == pytest.approx(t2, rel=1e-12)
+    else:
+        assert t3 - th[0] == pytest.approx(2 * step_part, rel=1e-12)
