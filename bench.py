@@ -17,6 +17,7 @@ from __future__ import annotations
 import argparse
 import json
 import os
+import platform
 import statistics
 import subprocess
 import sys
@@ -149,7 +150,8 @@ def run_reference(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": "gemm_8192^3_rows_sample", "M": M, "N": N, "K": K, "rows_per_step": rows_per_step},
         "cpu_baseline": {"value": tflops, "unit": "TFLOP/s", "cores": cores, "kind": "oracle",
-                         "sample": "%d rows x 8192 x 8192 FP64 per step (C = A.B definition, OpenMP)" % rows_per_step},
+                         "sample": "%d rows x 8192 x 8192 FP64 per step (C = A.B definition, OpenMP)" % rows_per_step,
+                         "cpu_model": _cpu_model()},
         "e2e": {"value": tflops, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
         "gpu_launches": 0,
     }
@@ -389,7 +391,8 @@ def run_gpu(args):
             tfl, dt, rows, ref = _cpu_gemm_rate(A_h[:64], B_h, 8, 6, 1)
             err = float(np.linalg.norm(C_h[:48] - ref) / np.linalg.norm(ref))
             line["cpu_baseline"] = {"value": tfl, "unit": "TFLOP/s", "cores": os.cpu_count(), "kind": "oracle",
-                                    "sample": "6 x 8 rows of the 8192^3 GEMM in FP64 (%.1f s)" % dt}
+                                    "sample": "6 x 8 rows of the 8192^3 GEMM in FP64 (%.1f s)" % dt,
+                                    "cpu_model": _cpu_model()}
             line["bf16_rel_frobenius_error_rows0_47"] = err
         line["roofline"]["traffic"] = _traffic_from_profile(pick)
         print(json.dumps(line))
@@ -397,6 +400,20 @@ def run_gpu(args):
     if dist is not None:
         dist.barrier()
         dist.destroy_process_group()
+
+
+def _cpu_model() -> str:
+    """The host CPU as /proc/cpuinfo names it (model name, else implementer/part)."""
+    try:
+        with open("/proc/cpuinfo") as f:
+            info = f.read()
+    except OSError:
+        return platform.machine()
+    for key in ("model name", "Model", "CPU part"):
+        for line in info.splitlines():
+            if line.startswith(key) and ":" in line:
+                return "%s %s" % (platform.machine(), line.split(":", 1)[1].strip())
+    return platform.machine()
 
 
 def _kernel_source_sha() -> str:
@@ -505,10 +522,26 @@ def secondary(pm, S, theta, n_sm, peaks):
                       "roofline_frac": max(gflops / (float(peaks.get("bf16_tflops", 1900.0)) * 1e12),
                                            gbytes / (float(peaks.get("hbm_gbs", 6800.0)) * 1e9)) / t_grp}
     del A_g, B_g, C_g, graph
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
     out["model"] = {"configs": nc, "forward_Mcfg_per_s": nc / t_f / 1e6, "forward_us": t_f * 1e6,
                     "adjoint_Mcfg_per_s": nc / t_g / 1e6, "adjoint_us": t_g * 1e6,
                     "autotune_Mcfg_per_s": (nc // 180) * 180 / t_a / 1e6, "autotune_us": t_a * 1e6,
                     "forward_GBps": 28.0 * nc / t_f / 1e9}
+    # 10^8 configurations (the 10^6 batch repeated on the device): the asymptotic
+    # rates, and the forward's fraction of the 28 B/configuration HBM floor
+    big = 100
+    dev_big = dev.repeat(big)
+    nb = nc * big
+    t_big = torch.empty(nb, dtype=torch.float32, device="cuda")
+    tm_big = torch.full((nb,), 1e-3, dtype=torch.float32, device="cuda")
+    ws_big = torch.empty(pm.pm_model_grad_workspace(nb) // 8, dtype=torch.float64, device="cuda")
+    t_fb = timeit(lambda: pm.pm_model_predict(dev_big, nb, theta, n_sm, t_big), reps=10)
+    t_gb = timeit(lambda: pm.pm_model_grad(dev_big, nb, theta, n_sm, tm_big, ws_big, go), reps=10)
+    out["model"].update({"configs_large": nb, "forward_large_Mcfg_per_s": nb / t_fb / 1e6,
+                         "adjoint_large_Mcfg_per_s": nb / t_gb / 1e6,
+                         "forward_large_hbm_frac": 28.0 * nb / t_fb / 1e9 / hbm,
+                         "adjoint_large_hbm_frac": 28.0 * nb / t_gb / 1e9 / hbm})
+    del dev_big, t_big, tm_big, ws_big
     return out
 
 
