@@ -321,6 +321,15 @@ pm_status pm_model_grad_noalloc(const pm_cfg* cfgs_dev, int64_t n, const pm_para
 pm_status pm_autotune_pick(const int32_t* MNK_dev, int64_t n, int32_t dtype, const pm_params* theta_host,
                            int32_t n_sm, pm_cfg* picks_dev, float* t_pred_dev, void* stream);
 
+/* Stage-model makespan of one grouped launch with given per-group tiles
+ * (the C9 reading of the grouped GEMM: per group tau_g = K_tiles T_step_g +
+ * T_store_g, tiles listed group by group, tile t on worker t mod n_conc,
+ * T_hat = T_launch + max_w sum tau).  Host arrays of G entries; *t_pred_host
+ * in seconds.  Synchronises. */
+pm_status pm_grouped_predict(int32_t G, const int32_t* M_host, int32_t N, int32_t K, const int16_t* BM_host,
+                             const int16_t* BN_host, int32_t BK, int32_t stages, int32_t cta_group, int32_t dtype,
+                             const pm_params* theta_host, int32_t n_sm, float* t_pred_host, void* stream);
+
 /* Grouped autotuner: for each launch-level (BK, stages, cta_group), each
  * group takes the (BM, BN) minimising tiles_g * (K_tiles T_step_g + T_store_g);
  * the launch whose static schedule has the smallest makespan

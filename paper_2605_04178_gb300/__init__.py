@@ -75,7 +75,7 @@ assert ctypes.sizeof(pm_cfg) == 24 and ctypes.sizeof(pm_probe_args) == 56 and ct
 EXPORTS = ("pm_probe_launch", "pm_probe_run", "pm_streams_run", "pm_gemm_operand_bytes", "pm_gemm_prepare", "pm_gemm_run",
            "pm_gemm_bench", "pm_gemm_host_workspace", "pm_gemm_host",
            "pm_grouped_gemm_run", "pm_model_predict", "pm_model_set_reading", "pm_model_reading", "pm_model_grad_workspace", "pm_model_grad", "pm_model_grad_f64", "pm_model_grad_noalloc",
-           "pm_autotune_pick", "pm_autotune_topk", "pm_gemm_autotune", "pm_grouped_autotune", "pm_grouped_gemm_autotune", "pm_segment_predict", "pm_last_error", "pm_device_status",
+           "pm_autotune_pick", "pm_autotune_topk", "pm_gemm_autotune", "pm_grouped_predict", "pm_grouped_autotune", "pm_grouped_gemm_autotune", "pm_segment_predict", "pm_last_error", "pm_device_status",
            "pm_watchdog_selftest", "pm_version")
 
 
@@ -121,6 +121,7 @@ def _load():
         "pm_gemm_autotune": [ctypes.POINTER(pm_cfg), i32, ctypes.POINTER(pm_params), i32, P, P, P, P, ctypes.c_int,
                              ctypes.c_int, P, ctypes.POINTER(pm_cfg), ctypes.POINTER(pm_probe_result)],
         "pm_grouped_autotune": [i32, P, i32, i32, i32, ctypes.POINTER(pm_params), i32, P, P, P, P, P],
+        "pm_grouped_predict": [i32, P, i32, i32, P, P, i32, i32, i32, i32, ctypes.POINTER(pm_params), i32, P, P],
         "pm_segment_predict": [P, i64, ctypes.POINTER(pm_params), ctypes.POINTER(pm_segment_params), i32, P, P],
         "pm_grouped_gemm_autotune": [i32, P, i32, i32, ctypes.POINTER(pm_params), i32, i32, P, P, P, ctypes.c_int,
                                      ctypes.c_int, P, P, P, P, P, ctypes.POINTER(pm_probe_result)],
@@ -352,6 +353,19 @@ def pm_gemm_autotune(shape: pm_cfg, k, theta, n_sm, A_op, B_op, C, scales=None, 
                                  _ptr(B_op), _ptr(C), _ptr(scales), int(warmup), int(reps), _stream(stream),
                                  ctypes.byref(pick), ctypes.byref(res)), "pm_gemm_autotune")
     return pick, dict(median_s=res.median_s, p25_s=res.p25_s, p75_s=res.p75_s, min_s=res.min_s)
+
+
+def pm_grouped_predict(M_list, N, K, BM_list, BN_list, BK, stages, cta_group, dtype, theta, n_sm, stream=None):
+    """Stage-model makespan (s) of one grouped launch with the given per-group tiles."""
+    G = len(M_list)
+    Mh = (ctypes.c_int32 * G)(*[int(m) for m in M_list])
+    bm = (ctypes.c_int16 * G)(*[int(v) for v in BM_list])
+    bn = (ctypes.c_int16 * G)(*[int(v) for v in BN_list])
+    t = ctypes.c_float()
+    _check(_lib.pm_grouped_predict(G, Mh, int(N), int(K), bm, bn, int(BK), int(stages), int(cta_group), int(dtype),
+                                   ctypes.byref(params(theta)), int(n_sm), ctypes.byref(t), _stream(stream)),
+           "pm_grouped_predict")
+    return float(t.value)
 
 
 def pm_grouped_autotune(M_list, N, K, dtype, theta, n_sm, stream=None):

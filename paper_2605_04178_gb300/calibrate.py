@@ -561,7 +561,8 @@ def measure_segments(table, log=print) -> dict:
         flops = float(sum(2.0 * m * NK * NK for m in Mg))
         b = float(sum(2.0 * (m * NK + NK * NK) + 4.0 * m * NK for m in Mg))
         rows.append(_seg("grouped_G%d_NK%d" % (G, NK), t, cls=2, precision=pm.PM_BF16, flops=flops, bytes=b,
-                         working_set=b))
+                         working_set=b, grouped=dict(M=[int(m) for m in Mg], NK=NK, bm=[int(v) for v in bm],
+                                                     bn=[int(v) for v in bn], launch=[int(v) for v in launch])))
         del A, B, C
     # stencil: five-point stencil grids
     for side in (1024, 2048, 4096, 8192, 16384):
@@ -621,6 +622,22 @@ def measure_segments(table, log=print) -> dict:
         ts.append(time.perf_counter() - t0)
     log("segments measured: %d" % len(rows))
     return dict(rows=rows, tau_sync_s=float(np.median(ts)))
+
+
+def grouped_family(seg_table, theta, n_sm) -> dict:
+    """Family 4 (grouped GEMM): the stage model's makespan (pm_grouped_predict)
+    of each measured grouped launch against its time."""
+    out = []
+    for r in seg_table["rows"]:
+        gq = r.get("grouped")
+        if not gq:
+            continue
+        t_pred = pm.pm_grouped_predict(gq["M"], gq["NK"], gq["NK"], gq["bm"], gq["bn"], *gq["launch"], pm.PM_BF16,
+                                       theta, n_sm)
+        out.append(dict(name=r["name"], t=r["t"], pred=t_pred, ape_pct=abs(t_pred - r["t"]) / r["t"] * 100.0))
+    if not out:
+        return {}
+    return dict(n=len(out), mae_pct=float(np.mean([x["ape_pct"] for x in out])), rows=out)
 
 
 def _seg_predict(rows, theta, psi, n_sm):
@@ -765,6 +782,7 @@ def main():
         theta_generic[6:9] = th0[6:9]
         rep["segments"] = fit_segments(table["segments"], theta_generic, n_sm, (table.get("instr") or {}).get("eq15"))
         rep["segments"]["theta"] = theta_generic.tolist()
+        rep["grouped_family"] = grouped_family(table["segments"], theta, n_sm)
     meta = dict(device=table.get("device"), n_sm=n_sm, fitted_on=os.path.basename(args.sweep),
                 reading=args.reading, mae_holdout=rep["mae_holdout"])
     if rep.get("segments"):
@@ -781,6 +799,10 @@ def main():
     for a in rep["autotune"]:
         print("autotune %(M)d dt=%(dtype)d pick=%(pick)s best=%(best)s pick/best=%(pick_over_best).3f "
               "TFLOP/s pick %(tflops_pick).0f best %(tflops_best).0f" % a)
+    if rep.get("grouped_family"):
+        gf = rep["grouped_family"]
+        print("family 4 grouped GEMM: n=%d MAE %.1f %% (%s)" % (gf["n"], gf["mae_pct"], ", ".join(
+            "%s %.1f%%" % (x["name"], x["ape_pct"]) for x in gf["rows"])))
     if rep.get("segments"):
         sg = rep["segments"]
         print("generic path psi %s" % ["%.3g" % v for v in sg["psi"]])

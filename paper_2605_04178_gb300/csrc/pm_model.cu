@@ -557,6 +557,35 @@ __device__ __forceinline__ int64_t count_congruent(int64_t X, int64_t w, int64_t
   return X < w ? 0 : (X - w) / n + 1;
 }
 
+// Makespan of the static schedule: tiles listed group by group, tile t on
+// worker t mod n_conc, each tile of group q taking tau[q]; max over workers.
+// Called by all threads of a block; the result is valid in every thread.
+__device__ float grouped_makespan(const float* tau, const int64_t* tiles, int64_t* off, float* red, int G,
+                                  int64_t n_conc) {
+  if (threadIdx.x == 0) {
+    off[0] = 0;
+    for (int q = 0; q < G; ++q) off[q + 1] = off[q] + tiles[q];
+  }
+  __syncthreads();
+  float mx = 0.f;
+  for (int64_t w = threadIdx.x; w < n_conc; w += blockDim.x) {
+    float busy = 0.f;
+    for (int q = 0; q < G; ++q) {
+      const int64_t cnt = count_congruent(off[q + 1] - 1, w, n_conc) - count_congruent(off[q] - 1, w, n_conc);
+      busy += (float)cnt * tau[q];
+    }
+    mx = fmaxf(mx, busy);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+  __syncthreads();
+  float m = red[0];
+  for (int w = 1; w < (int)(blockDim.x / 32); ++w) m = fmaxf(m, red[w]);
+  __syncthreads();
+  return m;
+}
+
 __global__ void __launch_bounds__(kGroupThreads) grouped_tune_kernel(const int32_t* __restrict__ Mg, int G, int N,
                                                                      int K, int dt, Theta th, int n_sm,
                                                                      float* __restrict__ out_t,
@@ -598,30 +627,35 @@ __global__ void __launch_bounds__(kGroupThreads) grouped_tune_kernel(const int32
     out_bn[combo * G + q] = (int16_t)bn;
   }
   any_invalid = __syncthreads_or(any_invalid);
-  if (threadIdx.x == 0) {
-    off[0] = 0;
-    for (int q = 0; q < G; ++q) off[q + 1] = off[q] + tiles[q];
+  const float t = grouped_makespan(tau, tiles, off, red, G, g == 1 ? n_sm : 2 * (n_sm / 2));
+  if (threadIdx.x == 0) out_t[combo] = any_invalid ? INFINITY : th.v[0] + t;
+}
+
+// Stage-model makespan of one grouped launch with given per-group tiles
+// (the schedule of pm_grouped_gemm_run; same terms as the grouped autotuner).
+__global__ void __launch_bounds__(kGroupThreads) grouped_predict_kernel(const int32_t* __restrict__ Mg,
+                                                                        const int16_t* __restrict__ BMg,
+                                                                        const int16_t* __restrict__ BNg, int G, int N,
+                                                                        int K, int BK, int s, int g, int dt,
+                                                                        Theta th, int n_sm,
+                                                                        float* __restrict__ out_t) {
+  __shared__ float tau[kMaxGroups];
+  __shared__ int64_t tiles[kMaxGroups];
+  __shared__ int64_t off[kMaxGroups + 1];
+  __shared__ float red[kGroupThreads / 32];
+  for (int q = threadIdx.x; q < G; q += blockDim.x) {
+    pm_cfg c;
+    c.M = Mg[q]; c.N = N; c.K = K; c.BM = BMg[q]; c.BN = BNg[q]; c.BK = (int16_t)BK;
+    c.stages = (int8_t)s; c.cta_group = (int8_t)g; c.dtype = (int8_t)dt; c.kind = 0; c.tmem_a = 0;
+    GemmFwd f;
+    gemm_forward(c, th, n_sm, f);
+    tau[q] = f.Kt * f.T_step + f.T_store;
+    tiles[q] = th.reading == PM_READING_MEASURED ? (int64_t)g * cdiv(c.M, (int64_t)g * c.BM) * cdiv(N, c.BN)
+                                                 : cdiv(c.M, c.BM) * cdiv(N, c.BN);
   }
   __syncthreads();
-  const int64_t n_conc = g == 1 ? n_sm : 2 * (n_sm / 2);
-  float mx = 0.f;
-  for (int64_t w = threadIdx.x; w < n_conc; w += blockDim.x) {
-    float busy = 0.f;
-    for (int q = 0; q < G; ++q) {
-      const int64_t cnt = count_congruent(off[q + 1] - 1, w, n_conc) - count_congruent(off[q] - 1, w, n_conc);
-      busy += (float)cnt * tau[q];
-    }
-    mx = fmaxf(mx, busy);
-  }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    float m = red[0];
-    for (int w = 1; w < kGroupThreads / 32; ++w) m = fmaxf(m, red[w]);
-    out_t[combo] = any_invalid ? INFINITY : th.v[0] + m;
-  }
+  const float t = grouped_makespan(tau, tiles, off, red, G, g == 1 ? n_sm : 2 * (n_sm / 2));
+  if (threadIdx.x == 0) out_t[0] = th.v[0] + t;
 }
 
 static std::atomic<int> g_reading{PM_READING_LITERAL};
@@ -788,6 +822,45 @@ static void grouped_launch_of(int i, int dtype, int32_t* launch) {
 }
 
 }  // namespace pm
+
+extern "C" pm_status pm_grouped_predict(int32_t G, const int32_t* M_host, int32_t N, int32_t K,
+                                        const int16_t* BM_host, const int16_t* BN_host, int32_t BK, int32_t stages,
+                                        int32_t cta_group, int32_t dtype, const pm_params* theta_host, int32_t n_sm,
+                                        float* t_pred_host, void* stream) {
+  PM_REQUIRE(G > 0 && G <= kMaxGroups, PM_EINVAL, "G must be in [1, %d]", kMaxGroups);
+  PM_REQUIRE(M_host && BM_host && BN_host && theta_host && t_pred_host && n_sm > 0, PM_EINVAL,
+             "null pointer or n_sm <= 0");
+  PM_REQUIRE(N > 0 && K > 0 && dtype >= 0 && dtype <= 2, PM_EINVAL, "bad N, K or dtype");
+  for (int q = 0; q < G; ++q) {
+    PM_REQUIRE(M_host[q] > 0, PM_EINVAL, "M[%d] <= 0", q);
+    PM_REQUIRE(tile_valid(BM_host[q], BN_host[q], BK, stages, cta_group, dtype), PM_EUNSUPPORTED,
+               "group %d: tile %dx%dx%d stages=%d cta_group=%d outside the valid space", q, BM_host[q], BN_host[q],
+               BK, stages, cta_group);
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  char* buf = nullptr;
+  const size_t bytes = 256 + (size_t)G * 8 + 16;
+  PM_CUDA(cudaMallocAsync((void**)&buf, bytes, s));
+  int32_t* dM = (int32_t*)buf;
+  int16_t* dbm = (int16_t*)(buf + ((G * 4 + 15) & ~15));
+  int16_t* dbn = dbm + ((G + 7) & ~7);
+  float* dt = (float*)(dbn + ((G + 7) & ~7));
+  pm_status st = PM_OK;
+  cudaError_t e = cudaMemcpyAsync(dM, M_host, G * 4, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(dbm, BM_host, G * 2, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(dbn, BN_host, G * 2, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) {
+    grouped_predict_kernel<<<1, kGroupThreads, 0, s>>>(dM, dbm, dbn, G, N, K, BK, stages, cta_group, dtype,
+                                                        to_theta(theta_host), n_sm, dt);
+    st = launch_status("grouped_predict_kernel");
+    if (st == PM_OK) e = cudaMemcpyAsync(t_pred_host, dt, 4, cudaMemcpyDeviceToHost, s);
+  }
+  cudaFreeAsync(buf, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (st != PM_OK) return st;
+  if (e != cudaSuccess) return cuda_fail(e, "grouped predict copies");
+  return PM_OK;
+}
 
 extern "C" pm_status pm_grouped_autotune(int32_t G, const int32_t* M_host, int32_t N, int32_t K, int32_t dtype,
                                          const pm_params* theta_host, int32_t n_sm, int16_t* BM_out_host,

@@ -114,6 +114,12 @@ def test_bad_arguments_rejected(pm):
                                  None) == pm.PM_EINVAL
     assert L.pm_watchdog_selftest(0, None) == pm.PM_EINVAL
     Mg = (ctypes.c_int32 * 2)(16, 32)
+    bad16 = (ctypes.c_int16 * 2)(96, 96)
+    tf = ctypes.c_float()
+    assert L.pm_grouped_predict(2, Mg, 64, 64, bad16, bad16, 64, 4, 1, 1, ctypes.byref(th), 152, ctypes.byref(tf),
+                                None) == pm.PM_EUNSUPPORTED
+    assert L.pm_grouped_predict(0, Mg, 64, 64, bad16, bad16, 64, 4, 1, 1, ctypes.byref(th), 152, ctypes.byref(tf),
+                                None) == pm.PM_EINVAL
     assert L.pm_grouped_gemm_autotune(2, Mg, 64, 64, ctypes.byref(th), 152, 0, ctypes.c_void_p(16),
                                       ctypes.c_void_p(16), ctypes.c_void_p(16), 1, 1, None, o16, o16, launch,
                                       None, None) == pm.PM_EINVAL

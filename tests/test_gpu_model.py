@@ -209,3 +209,15 @@ def test_grad_f64_matches_oracle_tightly(lib, reading, n):
     r = np.log(t_true) - np.log(t_meas)
     scale = (2.0 / len(r)) * np.sum(np.abs(r[:, None] * gi / t_true[:, None]), axis=0)
     assert np.all(np.abs(o[1:] - g_orc) <= 1e-10 * scale + 1e-300), (o[1:], g_orc)
+
+
+def test_grouped_predict_matches_oracle(lib, reading):
+    Mg = S.grouped_m(64, 3)
+    th = theta32()
+    G = len(Mg)
+    bm = [(64, 128, 256)[q % 3] for q in range(G)]
+    bn = [(128, 256, 64)[q % 3] for q in range(G)]
+    for launch in ((64, 4, 1), (128, 3, 2), (128, 2, 2)):
+        t_g = lib.pm_grouped_predict(Mg, 4096, 4096, bm, bn, *launch, 1, th, N_SM)
+        t_o = O.grouped_predict(Mg, 4096, 4096, bm, bn, *launch, 1, th, N_SM)
+        assert t_g == pytest.approx(t_o, rel=1e-5)
