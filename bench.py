@@ -360,6 +360,7 @@ def run_gpu(args):
                        "theta": theta_src, "l2": "operands 256 MB > 129 MB L2, no flush",
                        "parallelism": "replicas" if world > 1 else "single"},
             "pct_of_peak": 100.0 * achieved / peak,
+            "pct_of_datasheet_dense_bf16": 100.0 * achieved / 2250.0,
             "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                          "frac": achieved / peak, "traffic": None,
                          "peak_source": "%s bf16 burst (cuBLAS 8192^3)" % peak_src,
@@ -519,6 +520,8 @@ def secondary(pm, S, theta, n_sm, peaks):
                       "model_only_launch": dict(zip(("BK", "stages", "cta_group"), model_launch)),
                       "ms": t_grp * 1e3, "TFLOPps": gflops / t_grp / 1e12, "GBps": gbytes / t_grp / 1e9,
                       "predicted_ms": t_gp * 1e3, "ape_pct": abs(t_gp - t_grp) / t_grp * 100,
+                      "flop_frac": gflops / (float(peaks.get("bf16_tflops", 1900.0)) * 1e12) / t_grp,
+                      "byte_frac": gbytes / (float(peaks.get("hbm_gbs", 6800.0)) * 1e9) / t_grp,
                       "roofline_frac": max(gflops / (float(peaks.get("bf16_tflops", 1900.0)) * 1e12),
                                            gbytes / (float(peaks.get("hbm_gbs", 6800.0)) * 1e9)) / t_grp}
     del A_g, B_g, C_g, graph

@@ -245,6 +245,20 @@ def measure_instructions() -> dict:
 STREAM_COUNTS = (1, 2, 3, 4, 6, 8)
 
 
+def pchase_levels(pchase, l1_bytes: float, l2_bytes: float) -> dict:
+    """Three-level latency step L(W) from the pointer chase: the median ns/hop
+    of the working sets well inside each level (W <= L1/2; 2 L1 <= W <= L2/2;
+    W >= 4 L2), with the capacities of the device."""
+    W = np.array([p["W"] for p in pchase], dtype=np.float64)
+    ns = np.array([p["ns_per_hop"] for p in pchase], dtype=np.float64)
+    out = dict(l1_bytes=float(l1_bytes), l2_bytes=float(l2_bytes))
+    for name, m in (("l1_ns", W <= l1_bytes / 2), ("l2_ns", (W >= 2 * l1_bytes) & (W <= l2_bytes / 2)),
+                    ("dram_ns", W >= 4 * l2_bytes)):
+        out[name] = float(np.median(ns[m])) if m.any() else None
+        out[name.replace("_ns", "_points")] = int(m.sum())
+    return out
+
+
 def fit_tau_c(counts, times) -> dict:
     """Least-squares tau_c of T(N_c) = T(1) + (N_c - 1) tau_c (Sec. III-A.6),
     with T(1) the measured single-stream time, and the MAE of that law over
@@ -775,6 +789,11 @@ def main():
                autotune=autotune_vs_best(rows, theta, n_sm), pchase=table.get("pchase"),
                instr=table.get("instr"), tmem_strategy=tmem_strategy_report(rows, pred),
                streams=table.get("streams"))
+    if table.get("pchase"):
+        props = torch.cuda.get_device_properties(0)
+        rep["pchase_levels"] = pchase_levels(table["pchase"],
+                                             getattr(props, "shared_memory_per_multiprocessor", 0) or 256 * 1024,
+                                             getattr(props, "L2_cache_size", 0) or 128 * 2 ** 20)
     if table.get("segments"):
         # the generic path's roofline uses the measured peak rates (instruction
         # probe), not the stage model's fitted per-step rates
@@ -799,6 +818,10 @@ def main():
     for a in rep["autotune"]:
         print("autotune %(M)d dt=%(dtype)d pick=%(pick)s best=%(best)s pick/best=%(pick_over_best).3f "
               "TFLOP/s pick %(tflops_pick).0f best %(tflops_best).0f" % a)
+    if rep.get("pchase_levels"):
+        pl = rep["pchase_levels"]
+        print("pointer chase levels: L1 %s ns, L2 %s ns, DRAM %s ns (capacities %.0f KB, %.0f MB)" % (
+            pl["l1_ns"], pl["l2_ns"], pl["dram_ns"], pl["l1_bytes"] / 1024, pl["l2_bytes"] / 2 ** 20))
     if rep.get("grouped_family"):
         gf = rep["grouped_family"]
         print("family 4 grouped GEMM: n=%d MAE %.1f %% (%s)" % (gf["n"], gf["mae_pct"], ", ".join(

@@ -117,3 +117,12 @@ def test_tau_c_fit_recovers_additive_law():
     # perfect overlap gives tau_c = 0; full serialisation gives tau_c = T1
     assert C.fit_tau_c(counts, [3e-5] * len(counts))["tau_c_s"] == pytest.approx(0.0, abs=1e-18)
     assert C.fit_tau_c(counts, [3e-5 * n for n in counts])["tau_over_T1"] == pytest.approx(1.0, rel=1e-12)
+
+
+def test_pchase_levels_takes_medians_inside_each_level():
+    W = [16384 * 2 ** k for k in range(17)]
+    ns = [20.0 if w <= 128 * 1024 else (140.0 if w <= 64 * 2 ** 20 else 400.0) for w in W]
+    ns[3] = 25.0                                   # one noisy L1 point: the median ignores it
+    lv = C.pchase_levels([dict(W=w, ns_per_hop=v) for w, v in zip(W, ns)], 256 * 1024, 128 * 2 ** 20)
+    assert lv["l1_ns"] == 20.0 and lv["l2_ns"] == 140.0 and lv["dram_ns"] == 400.0
+    assert lv["l1_points"] == 4 and lv["dram_points"] == 2
