@@ -17,7 +17,9 @@
 // copies each A K-slice of the stage into tensor memory with tcgen05.cp and
 // the MMAs read A from there (Sec. III-A.1, "two TMEM strategies").
 // Two TMEM accumulator buffers when they fit, so the epilogue of tile i
-// overlaps the main loop of tile i+1.  Each CTA of a pair loads its own A
+// overlaps the main loop of tile i+1.  When one accumulator fills TMEM (two
+// 128-row blocks of 256 columns) the two row blocks are released separately:
+// tile i+1 starts on row block 0 while the epilogue still drains row block 1.  Each CTA of a pair loads its own A
 // rows and half of B (traffic 2 M_A + M_B per pair, no multicast); the pair
 // leader issues the cta_group::2 MMAs.
 #include <cuda_bf16.h>
@@ -65,6 +67,7 @@ struct GemmParams {
   int sw;                          // swizzle span in bytes (64 or 128)
   int n_atoms;                     // swizzle atoms along K per stage
   int acc_cols, nbuf, alloc_cols;  // TMEM columns per accumulator buffer (largest tile)
+  int split;                       // one buffer of two 128-row blocks, released block by block
   int a_col0, a_cols;              // strategy B: first TMEM column of the A ring, columns per stage
   uint32_t stage_bytes;            // ring stride (largest tile)
   uint32_t ab_fmt;                 // tcgen05 operand format code
@@ -287,6 +290,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
         decode_tile<CG, L>(t, p, g, 0, T);
         const int buf = it % p.nbuf;
         const uint32_t use = (uint32_t)(it / p.nbuf);
+        // split release: acce_bar[0] / [1] guard row blocks 0 / 1 of the single buffer
         if (!mbar_wait(smem_u32(&acce_bar[buf]), (use & 1u) ^ 1u, p.wd, abort_p, SITE_GEMM_MMA)) {
           ok = false;
           break;
@@ -306,19 +310,38 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
           const bool first = kt == 0;
           const uint32_t bn = (uint32_t)T.BN;
           const uint32_t a_tm = TA ? tmem_base + (uint32_t)(p.a_col0 + stage * p.a_cols) : 0u;
-#define PM_ISSUE(NA, NK, NM) \
-  issue_stage<CG, KIND, NA, NK, NM, TA>(d0, a0, b0, a16, b16, m16, T.idesc, bn, first, a_tm)
-          if (p.sw == 128) {
-            if (p.n_atoms == 1) {
-              if (T.n_mblk == 1) PM_ISSUE(1, 4, 1);
-              else PM_ISSUE(1, 4, 2);
+#define PM_ISSUE(NA, NK, NM, D0, A0) \
+  issue_stage<CG, KIND, NA, NK, NM, TA>(D0, A0, b0, a16, b16, m16, T.idesc, bn, first, a_tm)
+          if (p.split && first) {
+            // first K-step of a tile under split release: row block 0 now, row
+            // block 1 once the epilogue has drained it from the previous tile
+            const uint64_t a1 = a0 + (uint64_t)m16;
+            if (p.sw == 128) {
+              if (p.n_atoms == 1) PM_ISSUE(1, 4, 1, d0, a0); else PM_ISSUE(2, 4, 1, d0, a0);
             } else {
-              if (T.n_mblk == 1) PM_ISSUE(2, 4, 1);
-              else PM_ISSUE(2, 4, 2);
+              PM_ISSUE(1, 2, 1, d0, a0);
+            }
+            if (!mbar_wait(smem_u32(&acce_bar[1]), (use & 1u) ^ 1u, p.wd, abort_p, SITE_GEMM_MMA)) {
+              ok = false;
+              break;
+            }
+            tc_fence_after();
+            if (p.sw == 128) {
+              if (p.n_atoms == 1) PM_ISSUE(1, 4, 1, d0 + bn, a1); else PM_ISSUE(2, 4, 1, d0 + bn, a1);
+            } else {
+              PM_ISSUE(1, 2, 1, d0 + bn, a1);
+            }
+          } else if (p.sw == 128) {
+            if (p.n_atoms == 1) {
+              if (T.n_mblk == 1) PM_ISSUE(1, 4, 1, d0, a0);
+              else PM_ISSUE(1, 4, 2, d0, a0);
+            } else {
+              if (T.n_mblk == 1) PM_ISSUE(2, 4, 1, d0, a0);
+              else PM_ISSUE(2, 4, 2, d0, a0);
             }
           } else {
-            if (T.n_mblk == 1) PM_ISSUE(1, 2, 1);
-            else PM_ISSUE(1, 2, 2);
+            if (T.n_mblk == 1) PM_ISSUE(1, 2, 1, d0, a0);
+            else PM_ISSUE(1, 2, 2, d0, a0);
           }
 #undef PM_ISSUE
           if constexpr (CG == 1) umma_commit(smem_u32(&empty_bar[stage]));
@@ -414,13 +437,25 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
             }
           }
         }
+        if (p.split) {
+          // this row block is drained: the next tile may start writing it
+          tc_fence_before();
+          __syncwarp();
+          if (lane == 0) {
+            const uint32_t eb = smem_u32(&acce_bar[m]);
+            if constexpr (CG == 1) mbar_arrive(eb);
+            else mbar_arrive_cluster(mapa_shared(eb, 0));
+          }
+        }
       }
-      tc_fence_before();
-      __syncwarp();
-      if (lane == 0) {
-        const uint32_t eb = smem_u32(&acce_bar[buf]);
-        if constexpr (CG == 1) mbar_arrive(eb);
-        else mbar_arrive_cluster(mapa_shared(eb, 0));
+      if (!p.split) {
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) {
+          const uint32_t eb = smem_u32(&acce_bar[buf]);
+          if constexpr (CG == 1) mbar_arrive(eb);
+          else mbar_arrive_cluster(mapa_shared(eb, 0));
+        }
       }
     }
     if (lane == 0) bulk_wait_all();                       // staged stores complete before exit
@@ -690,6 +725,11 @@ static pm_status plan_launch(int dt, int cg, int BK, int stages, int tmem_a, int
   p.a_cols = tmem_a ? L * (BK * e / 4) * max_mblk : 0;
   const int a_ring = stages * p.a_cols;
   p.nbuf = (2 * acc + a_ring <= 512) ? 2 : 1;
+  // split release when one buffer of two 128-row blocks holds the whole tile
+  // (every group: BM = 256 per CTA) and nothing else lives in TMEM
+  bool all_two_blocks = true;
+  for (int q = 0; q < G; ++q) all_two_blocks = all_two_blocks && BMv[q] == 256;
+  p.split = (p.nbuf == 1 && all_two_blocks && tmem_a == 0) ? 1 : 0;
   p.a_col0 = p.nbuf * acc;
   int cols = 32;
   while (cols < p.nbuf * acc + a_ring) cols <<= 1;

@@ -240,3 +240,20 @@ def test_gemm_host_pipeline_exact(lib, dt, chunks, t):
             assert np.all(np.abs(C - ref) <= 2.0 ** -23 * np.abs(ref))
         else:
             assert np.array_equal(C, ref)
+
+
+@pytest.mark.parametrize("dt,t", [(1, (256, 256, 64, 3, 1)), (1, (256, 256, 64, 4, 2)), (2, (256, 256, 128, 3, 1)),
+                                  (2, (256, 256, 128, 4, 2)), (0, (256, 256, 32, 2, 1))])
+def test_split_accumulator_release_many_tiles_per_cta(lib, dt, t):
+    # 256 x 256 tiles fill TMEM with one accumulator, so its two row blocks are
+    # released separately; 8192 x 8192 outputs give every CTA several tiles
+    M = N = 8192
+    K = 256 if dt else 64
+    A, B = S.integer_matrix(31, M, K), S.integer_matrix(32, K, N)
+    C, _ = run_gemm(lib, A, B, lib.cfg(M, N, K, *t, dtype=dt), dt)
+    rows = S.sampled_rows(33, M, 96)
+    ref = O.gemm_f64(A[rows], B)
+    if dt == 2:
+        assert np.all(np.abs(C[rows] - ref) <= 2.0 ** -23 * np.abs(ref))
+    else:
+        assert np.array_equal(C[rows].astype(np.float64), ref)

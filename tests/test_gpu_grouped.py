@@ -113,3 +113,17 @@ def test_grouped_measured_autotune_picks_from_model_shortlist(lib):
     for A, B in zip(A_list, B_list):
         assert np.array_equal(C[row0:row0 + A.shape[0]].astype(np.float64), O.gemm_f64(A, B))
         row0 += A.shape[0]
+
+
+@pytest.mark.parametrize("launch", [(64, 3, 1), (64, 3, 2)])
+def test_grouped_exact_integer_split_release(lib, launch):
+    # every group in 256 x 256 tiles: one TMEM accumulator released by row block
+    Ms = [300, 600, 900, 257, 1024, 2048, 513, 4096]
+    N, K = 1024, 192
+    A_list, B_list = int_groups(Ms, N, K, seed=61)
+    G = len(Ms)
+    C = run_grouped(lib, A_list, B_list, N, K, [256] * G, [256] * G, launch, graph=True)
+    row0 = 0
+    for A, B in zip(A_list, B_list):
+        assert np.array_equal(C[row0:row0 + A.shape[0]].astype(np.float64), O.gemm_f64(A, B))
+        row0 += A.shape[0]
