@@ -398,6 +398,13 @@ pm_status pm_segment_predict(const pm_segment* segs_dev, int64_t n, const pm_par
 /* Text of the last error on this host thread (valid until the next call). */
 const char* pm_last_error(void);
 
+/* Releases what the library holds beyond the static watchdog word: its pool
+ * of concurrent-probe streams on every device, and the calling thread's
+ * host-transfer pipeline (streams, events) and TMA descriptor caches.  Work
+ * already queued on those streams completes.  Any later call re-creates what
+ * it needs.  Always PM_OK. */
+pm_status pm_shutdown(void);
+
 /* Reads (and with clear != 0, clears) the device watchdog word of the current
  * device: PM_OK or PM_ETIMEOUT.  Synchronises the device. */
 pm_status pm_device_status(int clear);

@@ -75,7 +75,7 @@ assert ctypes.sizeof(pm_cfg) == 24 and ctypes.sizeof(pm_probe_args) == 56 and ct
 EXPORTS = ("pm_probe_launch", "pm_probe_run", "pm_streams_run", "pm_gemm_operand_bytes", "pm_gemm_prepare", "pm_gemm_run",
            "pm_gemm_bench", "pm_gemm_host_workspace", "pm_gemm_host",
            "pm_grouped_gemm_run", "pm_model_predict", "pm_model_set_reading", "pm_model_reading", "pm_model_grad_workspace", "pm_model_grad", "pm_model_grad_f64", "pm_model_grad_noalloc",
-           "pm_autotune_pick", "pm_autotune_topk", "pm_gemm_autotune", "pm_grouped_predict", "pm_grouped_autotune", "pm_grouped_gemm_autotune", "pm_segment_predict", "pm_last_error", "pm_device_status",
+           "pm_autotune_pick", "pm_autotune_topk", "pm_gemm_autotune", "pm_grouped_predict", "pm_grouped_autotune", "pm_grouped_gemm_autotune", "pm_segment_predict", "pm_last_error", "pm_device_status", "pm_shutdown",
            "pm_watchdog_selftest", "pm_version")
 
 
@@ -126,6 +126,7 @@ def _load():
         "pm_grouped_gemm_autotune": [i32, P, i32, i32, ctypes.POINTER(pm_params), i32, i32, P, P, P, ctypes.c_int,
                                      ctypes.c_int, P, P, P, P, P, ctypes.POINTER(pm_probe_result)],
         "pm_device_status": [ctypes.c_int],
+        "pm_shutdown": [],
         "pm_model_set_reading": [i32],
         "pm_model_reading": [],
         "pm_watchdog_selftest": [i32, P],
@@ -433,6 +434,11 @@ def pm_model_reading() -> int:
 # ---------------------------------------------------------------- diagnostics
 def pm_last_error() -> str:
     return _lib.pm_last_error().decode(errors="replace")
+
+
+def pm_shutdown() -> None:
+    """Release the library's streams, host pipeline and descriptor caches (re-created on demand)."""
+    _check(_lib.pm_shutdown(), "pm_shutdown")
 
 
 def pm_device_status(clear=True) -> int:

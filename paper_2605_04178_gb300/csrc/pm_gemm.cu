@@ -600,6 +600,12 @@ struct TmapEntry {
 static thread_local TmapEntry g_tmaps[16];
 static thread_local int g_tmap_next = 0;
 
+void clear_tmap_caches_this_thread() {
+  for (auto& e : g_tmaps) e.used = false;
+  g_tmap_next = 0;
+  clear_probe_tmap_cache_this_thread();
+}
+
 pm_status cached_tmap(CUtensorMap* out, const void* ptr, int dtcode, uint64_t rows, uint64_t cols, uint32_t box_rows,
                       uint32_t box_cols, int sw) {
   TmapKey k{ptr, rows, cols, box_rows, box_cols, dtcode, sw};
@@ -880,6 +886,7 @@ extern "C" pm_status pm_gemm_bench(const pm_cfg* cfg, const void* A_op_dev, cons
                                    const float* scales_dev, int warmup, int reps, void* stream,
                                    pm_probe_result* out) {
   PM_REQUIRE(cfg != nullptr && out != nullptr, PM_EINVAL, "cfg or out is NULL");
+  pm::NvtxRange nvtx("pm_gemm_bench");
   PM_REQUIRE(warmup >= 0 && reps >= 1 && reps <= 100000, PM_EINVAL, "warmup >= 0 and 1 <= reps <= 1e5 required");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   for (int i = 0; i < warmup; ++i) {
@@ -936,6 +943,7 @@ extern "C" pm_status pm_gemm_autotune(const pm_cfg* shape, int32_t k, const pm_p
                                       pm_cfg* pick_out, pm_probe_result* pick_time_out) {
   PM_REQUIRE(shape && theta_host && pick_out, PM_EINVAL, "null argument");
   PM_REQUIRE(k >= 1 && k <= 16, PM_EINVAL, "k must be in [1, 16]");
+  pm::NvtxRange nvtx("pm_gemm_autotune");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   // model shortlist on the GPU
   char* buf = nullptr;
@@ -987,6 +995,23 @@ struct HostPipe {
   cudaEvent_t start, b_ready, done, a_loaded[2], a_free[2], c_ready[2], c_free[2];
 };
 static thread_local HostPipe g_pipe;
+
+void release_host_pipe_this_thread() {
+  HostPipe& P = g_pipe;
+  if (P.dev < 0) return;
+  int cur = -1;
+  cudaGetDevice(&cur);
+  if (cudaSetDevice(P.dev) == cudaSuccess) {
+    cudaEvent_t evs[] = {P.start, P.b_ready, P.done, P.a_loaded[0], P.a_loaded[1], P.a_free[0],
+                         P.a_free[1], P.c_ready[0], P.c_ready[1], P.c_free[0], P.c_free[1]};
+    for (cudaEvent_t e : evs) cudaEventDestroy(e);
+    cudaStreamDestroy(P.s_in);
+    cudaStreamDestroy(P.s_comp);
+    cudaStreamDestroy(P.s_out);
+  }
+  P = HostPipe();
+  if (cur >= 0) cudaSetDevice(cur);
+}
 
 static pm_status host_pipe() {
   int dev = 0;
@@ -1055,6 +1080,7 @@ extern "C" pm_status pm_gemm_host(const pm_cfg* cfg, const float* A_host, const 
   const HostLayout Lh = host_layout(*cfg, chunks);
   PM_REQUIRE(ws_bytes >= Lh.total, PM_ENOMEM, "workspace of %zu bytes is smaller than the %zu needed", ws_bytes,
              Lh.total);
+  NvtxRange nvtx("pm_gemm_host");
   pm_status st = host_pipe();
   if (st != PM_OK) return st;
   HostPipe& P = g_pipe;

@@ -8,6 +8,7 @@
 
 #include <cuda.h>
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stdint.h>
 
 #include "../../include/perfmodel.h"
@@ -23,6 +24,21 @@ unsigned int* watchdog_word();
 unsigned long long watchdog_limit_ns();
 // Number of SMs of the current device.
 int sm_count();
+// Resources pm_shutdown releases: the library's stream pool (all devices), and
+// the calling thread's host-transfer pipeline and tensor-map caches.
+void release_stream_pool();
+void release_host_pipe_this_thread();
+void clear_tmap_caches_this_thread();
+void clear_probe_tmap_cache_this_thread();
+
+// Named NVTX range over a scope (timing harnesses and pipelines); free when
+// no profiler is attached.
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
 // 2D tiled tensor map over a row-major [rows, cols] matrix of elem_bytes-wide
 // elements, box box_cols x box_rows, swizzle 0/32/64/128 bytes.
 pm_status make_tmap_2d(CUtensorMap* map, const void* base, int dtype_code, uint64_t rows, uint64_t cols,

@@ -895,6 +895,7 @@ extern "C" pm_status pm_grouped_gemm_autotune(int32_t G, const int32_t* M_host, 
   PM_REQUIRE(k >= 1 && k <= 20, PM_EINVAL, "k must be in [1, 20]");
   PM_REQUIRE(warmup >= 0 && reps >= 1 && reps <= 100000, PM_EINVAL, "warmup >= 0 and 1 <= reps <= 1e5 required");
   PM_REQUIRE(A_op_dev && B_op_dev && C_dev, PM_EINVAL, "null operand or output pointer");
+  NvtxRange nvtx("pm_grouped_gemm_autotune");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   float ht[20];
   std::vector<int16_t> hbm, hbn;

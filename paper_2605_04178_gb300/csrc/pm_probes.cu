@@ -352,6 +352,7 @@ struct TmaProbeCache {
   CUtensorMap ms, md;
 };
 static thread_local TmaProbeCache g_tma_cache;
+void clear_probe_tmap_cache_this_thread() { g_tma_cache = TmaProbeCache(); }
 
 static pm_status probe_launch(const pm_probe_args* a, void* buf0, void* buf1, void* buf2, cudaStream_t s) {
   switch (a->kind) {
@@ -544,6 +545,7 @@ extern "C" pm_status pm_probe_launch(const pm_probe_args* args, void* buf0, void
 extern "C" pm_status pm_probe_run(const pm_probe_args* args, void* buf0, void* buf1, void* buf2, int warmup,
                                   int reps, void* stream, pm_probe_result* out) {
   PM_REQUIRE(args != nullptr && out != nullptr, PM_EINVAL, "args or out is NULL");
+  NvtxRange nvtx("pm_probe_run");
   PM_REQUIRE(warmup >= 0 && reps >= 1 && reps <= 100000, PM_EINVAL, "warmup >= 0 and 1 <= reps <= 1e5 required");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   // pointer chase: every launch after the first continues the walk
@@ -620,6 +622,20 @@ struct ConcStreams {
 static std::mutex g_conc_mu;
 static ConcStreams g_conc[64];
 
+void release_stream_pool() {
+  std::lock_guard<std::mutex> lk(g_conc_mu);
+  int cur = -1;
+  cudaGetDevice(&cur);
+  for (int dev = 0; dev < 64; ++dev) {
+    ConcStreams& c = g_conc[dev];
+    if (!c.made) continue;
+    if (cudaSetDevice(dev) == cudaSuccess)
+      for (int i = 0; i < kMaxConcStreams; ++i) cudaStreamDestroy(c.s[i]);
+    c.made = false;
+  }
+  if (cur >= 0) cudaSetDevice(cur);
+}
+
 static pm_status conc_streams(cudaStream_t** out) {
   int dev = 0;
   PM_CUDA(cudaGetDevice(&dev));
@@ -648,6 +664,7 @@ extern "C" pm_status pm_streams_run(const pm_probe_args* per_stream, int32_t n_s
   PM_REQUIRE(k == PM_PROBE_MMA || buf1 != nullptr, PM_EINVAL, "copy/triad need buf1 arrays");
   PM_REQUIRE(k != PM_PROBE_TRIAD || buf2 != nullptr, PM_EINVAL, "triad needs buf2 arrays");
   PM_REQUIRE(warmup >= 0 && reps >= 1 && reps <= 100000, PM_EINVAL, "warmup >= 0 and 1 <= reps <= 1e5 required");
+  NvtxRange nvtx("pm_streams_run");
   cudaStream_t* cs = nullptr;
   pm_status st = conc_streams(&cs);
   if (st != PM_OK) return st;

@@ -174,3 +174,10 @@ extern "C" pm_status pm_watchdog_selftest(int32_t limit_us, void* stream) {
   }
   return PM_OK;
 }
+
+extern "C" pm_status pm_shutdown(void) {
+  pm::release_stream_pool();
+  pm::release_host_pipe_this_thread();
+  pm::clear_tmap_caches_this_thread();
+  return PM_OK;
+}

@@ -45,6 +45,7 @@ def test_struct_layouts(pm):
     assert ctypes.sizeof(pm.pm_params) == 64
     assert pm.SEGMENT_DTYPE.itemsize == 64 and ctypes.sizeof(pm.pm_segment_params) == 96
     assert pm.pm_version() == 10000
+    assert pm._lib.pm_shutdown() == pm.PM_OK                 # nothing created yet: nothing to release
     # reading switch: default literal, round trip, bad value refused
     assert pm.pm_model_reading() == pm.PM_READING_LITERAL
     pm.pm_model_set_reading(pm.PM_READING_MEASURED)

@@ -44,3 +44,22 @@ def test_mma_on_concurrent_streams_exact(lib, ctas):
         assert np.all(o.cpu().numpy().view(np.float32) == O.mma_probe_value(n, 1))
     assert r["bytes"] == k * ctas * n * 2.0 * 128 * 256 * 16
     assert lib.pm_device_status(True) == lib.PM_OK
+
+
+def test_shutdown_releases_and_recreates(lib):
+    # streams, host pipeline and descriptor caches are released and re-created on demand
+    n = 4099
+    src = [torch.from_numpy(S.uniform_pm1(70 + i, n)).cuda() for i in range(3)]
+    for _ in range(2):
+        dst = [torch.full_like(x, float("nan")) for x in src]
+        lib.pm_streams_run(lib.probe_args(lib.PM_PROBE_COPY, n=n), src, dst, warmup=0, reps=1)
+        for a, b in zip(src, dst):
+            assert torch.equal(a, b)
+        A, B = S.integer_matrix(71, 200, 64), S.integer_matrix(72, 64, 96)
+        c = lib.cfg(200, 96, 64, 128, 128, 64, 2, 1, lib.PM_BF16)
+        ws = torch.empty(lib.pm_gemm_host_workspace(c, 2), dtype=torch.uint8, device="cuda")
+        Ch = torch.empty(200, 96, dtype=torch.float32).pin_memory()
+        lib.pm_gemm_host(c, torch.from_numpy(A).pin_memory(), torch.from_numpy(B).pin_memory(), Ch, ws, 2)
+        torch.cuda.synchronize()
+        assert np.array_equal(Ch.numpy().astype(np.float64), O.gemm_f64(A, B))
+        lib.pm_shutdown()
