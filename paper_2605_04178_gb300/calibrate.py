@@ -91,6 +91,7 @@ def _valid(dt, t, tmem_a=0):
 
 def measure_sweep(shapes=(1024, 2048, 4096, 8192, 16384), dtypes=(1, 2), log=print) -> dict:
     """Device-timed calibration table (list of records) plus pointer-chase latencies."""
+    torch.cuda.nvtx.range_push("measure_sweep")
     rows = []
     t0 = time.time()
     # config 1: FP32 (three-pass TF32) 512^3 over the FP32 tile space
@@ -175,7 +176,8 @@ def measure_sweep(shapes=(1024, 2048, 4096, 8192, 16384), dtypes=(1, 2), log=pri
     rows += measure_tmem_b(shapes, dtypes, log)
     props = torch.cuda.get_device_properties(0)
     segments = measure_segments(dict(rows=rows), log)
-    return dict(device=props.name, n_sm=props.multi_processor_count, rows=rows, pchase=pchase, instr=instr,
+    torch.cuda.nvtx.range_pop()
+    return dict(environment=environment(), device=props.name, n_sm=props.multi_processor_count, rows=rows, pchase=pchase, instr=instr,
                 streams=streams, segments=segments, protocol="10 warm-ups; 100 timed runs (20-40 at 8192-16384, 20 for TMA), median of CUDA-event times")
 
 
@@ -473,6 +475,43 @@ def autotune_vs_best(rows, theta, n_sm) -> list:
                         t_pred=float(tp.item()), pick_over_best=cand.get(pick, math.inf) / cand[best],
                         tflops_pick=flops / cand.get(pick, math.inf) / 1e12, tflops_best=flops / cand[best] / 1e12))
     return out
+
+
+def two_sm_report(rows) -> dict:
+    """Measured CTA-pair speedup (Sec. V reports 1.28-1.30x on B200): per GEMM
+    shape and dtype, the fastest one-SM tile's time over the fastest pair
+    tile's, and the median over tiles that exist in both forms."""
+    out = {}
+    gem = [r for r in rows if r["kind"] == pm.PM_KIND_GEMM and not r.get("tmem_a", 0)]
+    for dt in sorted(set(r["dtype"] for r in gem)):
+        best_ratio, same = [], []
+        for M in sorted(set(r["M"] for r in gem if r["dtype"] == dt)):
+            cand = [r for r in gem if r["dtype"] == dt and r["M"] == M]
+            t1 = [r["t"] for r in cand if r["cta_group"] == 1]
+            t2 = [r["t"] for r in cand if r["cta_group"] == 2]
+            if t1 and t2:
+                best_ratio.append(min(t1) / min(t2))
+            by_tile = {(r["BM"], r["BN"], r["BK"], r["stages"], r["cta_group"]): r["t"] for r in cand}
+            same += [by_tile[k[:4] + (1,)] / v for k, v in by_tile.items() if k[4] == 2 and k[:4] + (1,) in by_tile]
+        if best_ratio:
+            out[("fp32", "bf16", "fp8")[dt]] = dict(best_single_over_best_pair=[round(x, 3) for x in best_ratio],
+                                                    median_same_tile_speedup=float(np.median(same)) if same else None)
+    return out
+
+
+def environment() -> dict:
+    """Where the measurements and the fit ran: GPU, driver and runtime versions, host."""
+    import subprocess
+    props = torch.cuda.get_device_properties(0)
+    driver = None
+    try:
+        driver = subprocess.run(["nvidia-smi", "--query-gpu=driver_version", "--format=csv,noheader", "-i", "0"],
+                                capture_output=True, text=True, timeout=30).stdout.strip() or None
+    except (OSError, subprocess.SubprocessError):
+        pass
+    return dict(gpu=props.name, sm_count=props.multi_processor_count, total_memory=props.total_memory,
+                driver=driver, torch=torch.__version__, torch_cuda=torch.version.cuda,
+                host_cores=os.cpu_count(), host_machine=os.uname().machine)
 
 
 def tmem_strategy_report(rows, t_pred) -> list:
@@ -781,7 +820,10 @@ def main():
     allobj = GpuObjective(rows, n_sm)
     pred0, pred = allobj.predict(th0), allobj.predict(theta)
     rep = dict(reading=args.reading, n_rows=len(rows), n_train=int(train.sum()), n_holdout=int(hold.sum()),
-               loss_trace=[trace[0], trace[-1]], theta=theta.tolist(), prior=th0.tolist(),
+               loss_trace=[float(x) for x in trace], theta=theta.tolist(), prior=th0.tolist(),
+               environment=environment(), two_sm=two_sm_report(rows),
+               per_config=[dict(family=family_of(r), cfg=[r.get(f, 0) for f in FIELDS], t=r["t"], pred=float(p),
+                                holdout=bool(h)) for r, p, h in zip(rows, pred, hold)],
                mae_paper_prior=mae_by_family(rows, allobj.predict(th_paper)),
                mae_prior=mae_by_family(rows, pred0), mae_train=mae_by_family(rows, pred, train),
                mae_holdout=mae_by_family(rows, pred, hold), mae_all=mae_by_family(rows, pred),
