@@ -40,6 +40,24 @@ def _dist_env():
     return rank, world, local
 
 
+def max_over_ranks(x: float, dist=None, device: str = "cpu") -> float:
+    """The largest of one value per rank (the job's time is its slowest replica)."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_throughput(units_per_rank: float, seconds: float, world: int, dist=None, device: str = "cpu"):
+    """Whole-job rate of independent replicas: every rank does units_per_rank
+    in its own time; the job takes the slowest rank's time (max over ranks)
+    and does world x units.  Returns (rate in units/s, max seconds)."""
+    t = max_over_ranks(seconds, dist, device)
+    return world * units_per_rank / t, t
+
+
 def _measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -185,13 +203,6 @@ def run_gpu(args):
             dist.barrier()
         torch.cuda.synchronize()
 
-    def max_over_ranks(x: float) -> float:
-        if dist is None:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
-
     peaks, peak_src = _measured_peaks()
     n_sm = pm.sm_count()
     theta = prior_theta(n_sm).astype(np.float32).astype(np.float64)
@@ -253,9 +264,10 @@ def run_gpu(args):
     clocks.stop()
     ms_total = start.elapsed_time(end)
     per_launch = [ev[2 * i].elapsed_time(ev[2 * i + 1]) for i in range(args.steps)]
-    ms_total = max_over_ranks(ms_total)
+    rate, t_max = replica_throughput(flops * args.steps, ms_total * 1e-3, world, dist, "cuda")
+    ms_total = t_max * 1e3
     ms_step = ms_total / args.steps
-    value = world * flops * args.steps / (ms_total * 1e-3) / 1e12
+    value = rate / 1e12
     kern_ms = statistics.mean(per_launch)
     achieved = flops / (kern_ms * 1e-3) / 1e12
     peak = float(peaks.get("bf16_tflops", 1900.0))
@@ -280,8 +292,8 @@ def run_gpu(args):
     for _ in range(e2e_steps):
         e2e_step()
     barrier()
-    e2e_s = max_over_ranks(time.perf_counter() - t0)
-    e2e_value = world * flops * e2e_steps / e2e_s / 1e12
+    e2e_rate, e2e_s = replica_throughput(flops * e2e_steps, time.perf_counter() - t0, world, dist, "cuda")
+    e2e_value = e2e_rate / 1e12
 
     # exhaustive search at this shape (every valid BF16 tile, same protocol for
     # all, including the model's pick) and the model's error on those times
