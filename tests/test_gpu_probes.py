@@ -95,8 +95,10 @@ def test_host_link_probe_refuses_unpinned_memory(lib):
     assert e.value.status == lib.PM_EINVAL
 
 
-@pytest.mark.parametrize("shape", [(1, 1), (2, 7), (3, 3), (37, 1000), (1000, 37), (1024, 1024), (4099, 2053)])
+@pytest.mark.parametrize("shape", [(1, 1), (2, 7), (3, 3), (37, 1000), (1000, 37), (1024, 1024), (4099, 2053),
+                                   (5, 8), (9, 132), (17, 4100), (3, 256), (1, 64)])
 def test_stencil_bit_exact(lib, shape):
+    # widths that are multiples of 4 take the four-points-per-thread kernel
     rows, cols = shape
     x = S.uniform_pm1(21, rows * cols).reshape(rows, cols)
     src = torch.from_numpy(x).cuda()
