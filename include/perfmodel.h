@@ -99,10 +99,7 @@ int32_t pm_model_reading(void);
 /* Calibration microbenchmarks (Sec. V-A; STREAM-style copy and triad for the
  * memory-bound class; TMA copy latency and bandwidth by tile size; pointer
  * chase after Mei & Chu as cited in Sec. III-B).
- *  PM_PROBE_COPY  : buf1[i] = buf0[i], n FP32 elements (16-byte aligned buffers);
- *                   from 64 MB up by the bulk-copy engine (1-D cp.async.bulk
- *                   through a shared-memory ring, one CTA per SM), the bytes
- *                   past the last 32 KB chunk and smaller copies by the SMs.
+ *  PM_PROBE_COPY  : buf1[i] = buf0[i], n FP32 elements (16-byte aligned buffers).
  *  PM_PROBE_TRIAD : buf0[i] = fmaf(scalar, buf2[i], buf1[i]) (one rounding).
  *  PM_PROBE_TMA2D : buf1 = buf0, an rows x cols FP32 matrix moved in
  *                   tile_r x tile_c tiles by TMA loads and TMA stores through

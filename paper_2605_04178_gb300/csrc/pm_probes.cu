@@ -39,65 +39,6 @@ __global__ void __launch_bounds__(kStreamThreads) copy_kernel(const float4* __re
   if (blockIdx.x == 0 && threadIdx.x < tail) dst_tail[threadIdx.x] = src_tail[threadIdx.x];
 }
 
-// Large copies by the bulk-copy engine (1-D cp.async.bulk, no tensor map):
-// one CTA per SM, one issuing thread, a ring of kBulkRing 32 KB shared-memory
-// buffers; chunk c (32 KB) goes to CTA c mod grid.  Each chunk is loaded into
-// a buffer (completion on that buffer's mbarrier, bounded wait) and stored
-// back from it; a buffer is reloaded once the store two chunks back has
-// finished reading it.  The bytes past the last whole chunk go through
-// copy_kernel.
-constexpr int kBulkChunk = 32768;
-constexpr int kBulkRing = 6;
-
-__device__ __forceinline__ void bulk_load_1d(uint32_t dst_smem, const void* src, uint32_t bytes, uint32_t bar) {
-  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
-               ::"r"(dst_smem), "l"(src), "r"(bytes), "r"(bar)
-               : "memory");
-}
-
-__device__ __forceinline__ void bulk_store_1d(void* dst, uint32_t src_smem, uint32_t bytes) {
-  asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst), "r"(src_smem), "r"(bytes)
-               : "memory");
-}
-
-__global__ void __launch_bounds__(32, 1) copy_bulk_kernel(const char* __restrict__ src, char* __restrict__ dst,
-                                                          int64_t chunks, Watchdog wd) {
-  extern __shared__ __align__(128) uint8_t smb[];
-  __shared__ __align__(8) uint64_t full[kBulkRing];
-  if (threadIdx.x != 0) return;
-  const uint32_t base = (smem_u32(smb) + 127u) & ~127u;
-  for (int r = 0; r < kBulkRing; ++r) mbar_init(smem_u32(&full[r]), 1);
-  fence_mbar_init();
-  const int64_t mine = chunks > (int64_t)blockIdx.x ? (chunks - 1 - blockIdx.x) / gridDim.x + 1 : 0;
-  auto load = [&](int64_t k) {
-    const int slot = (int)(k % kBulkRing);
-    const uint32_t bar = smem_u32(&full[slot]);
-    mbar_arrive_expect_tx(bar, (uint32_t)kBulkChunk);
-    bulk_load_1d(base + (uint32_t)slot * kBulkChunk, src + ((int64_t)blockIdx.x + k * gridDim.x) * kBulkChunk,
-                 (uint32_t)kBulkChunk, bar);
-  };
-  const int64_t pre = mine < kBulkRing - 1 ? mine : kBulkRing - 1;
-  for (int64_t k = 0; k < pre; ++k) load(k);
-  int64_t issued = pre, done = 0;
-  for (int64_t k = 0; k < mine; ++k) {
-    const int slot = (int)(k % kBulkRing);
-    if (!mbar_wait(smem_u32(&full[slot]), (uint32_t)((k / kBulkRing) & 1), wd, nullptr, SITE_TMA_PROBE)) break;
-    done = k + 1;
-    bulk_store_1d(dst + ((int64_t)blockIdx.x + k * gridDim.x) * kBulkChunk, base + (uint32_t)slot * kBulkChunk,
-                  (uint32_t)kBulkChunk);
-    bulk_commit();
-    if (issued < mine) {
-      bulk_wait_read<1>();          // the store of chunk k - 1 (the slot of chunk `issued`) has read it
-      load(issued++);
-    }
-  }
-  // after an expired wait, let the loads still in flight land before the
-  // shared memory goes away (bounded as well)
-  for (int64_t k = done; k < issued; ++k)
-    mbar_wait(smem_u32(&full[k % kBulkRing]), (uint32_t)((k / kBulkRing) & 1), wd, nullptr, SITE_TMA_PROBE);
-  bulk_wait_all();
-}
-
 __global__ void __launch_bounds__(kStreamThreads) triad_kernel(float4* __restrict__ a, const float4* __restrict__ b,
                                                                const float4* __restrict__ c, float s, int64_t n4,
                                                                float* __restrict__ a_tail,
@@ -459,34 +400,10 @@ static pm_status probe_launch(const pm_probe_args* a, void* buf0, void* buf1, vo
       PM_REQUIRE(buf0 && buf1 && a->n > 0, PM_EINVAL, "copy probe: null buffer or n <= 0");
       PM_REQUIRE(((uintptr_t)buf0 & 15) == 0 && ((uintptr_t)buf1 & 15) == 0, PM_EINVAL,
                  "copy probe: buffers must be 16-byte aligned");
-      int64_t done_elems = 0;
-      if (a->n * 4 >= ((int64_t)64 << 20)) {
-        // large copies: the bulk-copy engine, then the remainder below
-        const int64_t chunks = a->n * 4 / kBulkChunk;
-        const int smem = kBulkRing * kBulkChunk + 128;
-        static std::once_flag once;
-        static cudaError_t attr = cudaSuccess;
-        std::call_once(once, [&] {
-          attr = cudaFuncSetAttribute(copy_bulk_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        });
-        if (attr != cudaSuccess) return cuda_fail(attr, "cudaFuncSetAttribute(copy_bulk_kernel)");
-        unsigned int* w = watchdog_word();
-        PM_REQUIRE(w != nullptr, PM_ECUDA, "watchdog word unavailable");
-        const int grid = (int)std::min<int64_t>(chunks, std::max(1, sm_count()));
-        copy_bulk_kernel<<<grid, 32, smem, s>>>((const char*)buf0, (char*)buf1, chunks,
-                                                Watchdog{w, watchdog_limit_ns()});
-        pm_status st = launch_status("copy_bulk_kernel");
-        if (st != PM_OK) return st;
-        done_elems = chunks * (kBulkChunk / 4);
-        if (done_elems == a->n) return PM_OK;
-      }
-      const float* src = (const float*)buf0 + done_elems;
-      float* dst = (float*)buf1 + done_elems;
-      const int64_t rest = a->n - done_elems;
-      const int64_t n4 = rest / 4;
-      const int tail = (int)(rest - n4 * 4);
-      copy_kernel<<<stream_grid(n4), kStreamThreads, 0, s>>>((const float4*)src, (float4*)dst, n4, src + n4 * 4,
-                                                             dst + n4 * 4, tail);
+      const int64_t n4 = a->n / 4;
+      const int tail = (int)(a->n - n4 * 4);
+      copy_kernel<<<stream_grid(n4), kStreamThreads, 0, s>>>(
+          (const float4*)buf0, (float4*)buf1, n4, (const float*)buf0 + n4 * 4, (float*)buf1 + n4 * 4, tail);
       return launch_status("copy_kernel");
     }
     case PM_PROBE_TRIAD: {
@@ -722,8 +639,7 @@ extern "C" pm_status pm_probe_run(const pm_probe_args* args, void* buf0, void* b
     PM_CUDA(cudaMemcpy(&fi, args->kind == PM_PROBE_PCHASE ? buf1 : buf0, 4, cudaMemcpyDeviceToHost));
     out->final_index = fi;
   }
-  if (args->kind == PM_PROBE_TMA2D || args->kind == PM_PROBE_MMA || args->kind == PM_PROBE_MBAR ||
-      args->kind == PM_PROBE_COPY) {
+  if (args->kind == PM_PROBE_TMA2D || args->kind == PM_PROBE_MMA || args->kind == PM_PROBE_MBAR) {
     unsigned int* w = watchdog_word();
     unsigned int h[2] = {0, 0};
     PM_CUDA(cudaMemcpy(h, w, sizeof(h), cudaMemcpyDeviceToHost));

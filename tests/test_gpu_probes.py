@@ -11,7 +11,6 @@ pytestmark = pytest.mark.gpu
 
 @pytest.mark.parametrize("n", [1, 3, 4, 1000, 2 ** 20 + 3, 2 ** 24, 2 ** 24 + 3, 2 ** 24 + 8195, 5 * 2 ** 23 + 1])
 def test_copy_bit_exact(lib, n):
-    # from 64 MB up the copy runs on the bulk-copy engine, the rest on the SMs
     a = torch.from_numpy(S.uniform_pm1(1, n)).cuda()
     b = torch.full_like(a, float("nan"))
     r = lib.pm_probe_run(lib.probe_args(lib.PM_PROBE_COPY, n=n), a, b, warmup=1, reps=3)
