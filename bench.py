@@ -270,12 +270,15 @@ def run_gpu(args):
     value = rate / 1e12
     kern_ms = statistics.mean(per_launch)
     achieved = flops / (kern_ms * 1e-3) / 1e12
-    peak = float(peaks.get("bf16_tflops", 1900.0))
+    # the timed loop runs the GEMM back to back for seconds under the power cap,
+    # so its peak is cuBLAS's sustained figure (the burst figure is reported too)
+    peak_burst = float(peaks.get("bf16_tflops", 1900.0))
+    peak = float(peaks.get("bf16_tflops_sustained", 1700.0))
     C_h = C.cpu().numpy()
 
     # ------------------------------------------------------ end-to-end steps
     C_pin = torch.empty(M, N, dtype=torch.float32).pin_memory()
-    e2e_steps = max(3, args.steps // 50)
+    e2e_steps = max(3, min(100, args.steps // 50))
 
     ws_host = torch.empty(pm.pm_gemm_host_workspace(cfg, args.e2e_chunks), dtype=torch.uint8, device="cuda")
 
@@ -375,7 +378,8 @@ def run_gpu(args):
             "pct_of_datasheet_dense_bf16": 100.0 * achieved / 2250.0,
             "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                          "frac": achieved / peak, "traffic": None,
-                         "peak_source": "%s bf16 burst (cuBLAS 8192^3)" % peak_src,
+                         "peak_source": "%s bf16 sustained (cuBLAS 8192^3 back to back for 4 s)" % peak_src,
+                         "peak_burst": peak_burst, "frac_vs_burst": achieved / peak_burst,
                          "kernel": "gemm_kernel<1 or 2, bf16>", "kernel_ms": kern_ms},
             "e2e": {"value": e2e_value, "unit": "TFLOP/s", "h2d_bytes_per_step": 4 * (M * K + K * N),
                     "d2h_bytes_per_step": 4 * M * N, "call": "pm_gemm_host, %d row chunks" % args.e2e_chunks,
@@ -563,7 +567,7 @@ def secondary(pm, S, theta, n_sm, peaks):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--steps", type=int, default=6000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cfg", default=None, help="override the tile: BM,BN,BK,stages,cta_group")
