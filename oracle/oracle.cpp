@@ -288,7 +288,8 @@ static T b_eff(const T* th, double W) {
 //     instruction the K-step issues (BK/k_instr per 128-row block per pass,
 //     plus strategy B's copies), alpha(s) = clamp(1 - c_alpha/(s-1), 0, 1)
 //     (an s-stage ring keeps s-1 loads in flight), T_sync once per K-step
-//     (Eq. 8; the barrier of Eq. 7 is the same one).
+//     (Eq. 8; the barrier of Eq. 7 is the same one), and B_TMA scaled by the
+//     working-set ratio B_eff(W)/B_sus of Eq. 16 (L2 residency of the loads).
 static int g_reading = 0;
 extern "C" void orc_set_reading(int r) { g_reading = r == 1 ? 1 : 0; }
 extern "C" int orc_reading() { return g_reading; }
@@ -304,8 +305,10 @@ static i64 cta_tiles(i64 M, i64 N, int BM, int BN, int g) {
 
 // One K-step and one tile of the stage model (Eqs. 2-8).  Returns T_step and
 // T_store through the out-arguments; shared by the GEMM and grouped models.
+// W is the launch's working set in bytes (operands and C), used by the
+// measured reading's L2 residency of the TMA loads.
 template <class T>
-static void stage_terms(const Cfg& c, i64 Kt, const T* th, T& Tstep, T& Tstore) {
+static void stage_terms(const Cfg& c, i64 Kt, const T* th, double W, T& Tstep, T& Tstore) {
   const bool measured = g_reading == 1;
   const double e = elem_bytes(c.dtype), np = mma_passes(c.dtype), l = load_mult(c.dtype);
   const T& R = th[rate_index(c.dtype)];
@@ -330,7 +333,13 @@ static void stage_terms(const Cfg& c, i64 Kt, const T* th, T& Tstep, T& Tstore) 
   // Eq. 4 with P = 1 (no multicast); the CTA pair loads 2 M_A + M_B per
   // K-step, i.e. each CTA its own A rows and half of B (Sec. III-A.4).
   const double b_step = l * e * c.BK * (c.BM + (double)c.BN / c.g);
-  const T T_tma = th[4] + b_step / th[5];
+  // B_TMA depends on how many of the loads hit in L2 (Sec. III-A.2).  The
+  // measured reading takes the working-set law of Eq. 16 for it: B_TMA is
+  // scaled by B_eff(W) / B_sus, which falls from B_peak / B_sus for a launch
+  // whose operands stay in L2 to 1 for one streaming from HBM.  The literal
+  // reading keeps B_TMA constant.
+  const T B_tma = measured ? th[5] * (b_eff<T>(th, W) / th[1]) : th[5];
+  const T T_tma = th[4] + b_step / B_tma;
   // T_sync = N_bar * L_mbar with N_bar = 2 (full and empty barrier per stage).
   const T T_sync = 2.0 * th[12];
   // Eq. 7 with T_decomp = 0 and alpha from the pipeline depth: reading 0
@@ -358,14 +367,16 @@ static T model_gemm(const Cfg& c, const T* th, int n_sm) {
   const i64 tiles = cta_tiles(c.M, c.N, c.BM, c.BN, c.g);
   const i64 n_conc = (c.g == 1) ? n_sm : 2 * (n_sm / 2);
   const i64 waves = ceil_div(tiles, n_conc);
-  T Tstep, Tstore;
-  stage_terms<T>(c, Kt, th, Tstep, Tstore);
-  const T T_stage = th[0] + lift<T>((double)waves) * (lift<T>((double)Kt) * Tstep + Tstore);
   const double e = elem_bytes(c.dtype), np = mma_passes(c.dtype), l = load_mult(c.dtype);
+  // bytes the launch must move at least: both operands once, C written once;
+  // also its working set
+  const double bytes_min = l * e * ((double)c.M * c.K + (double)c.N * c.K) + 4.0 * (double)c.M * c.N;
+  T Tstep, Tstore;
+  stage_terms<T>(c, Kt, th, bytes_min, Tstep, Tstore);
+  const T T_stage = th[0] + lift<T>((double)waves) * (lift<T>((double)Kt) * Tstep + Tstore);
   const T& R = th[rate_index(c.dtype)];
   const T S = (c.g == 1) ? lift<T>(1.0) : th[14];
   const double flops = np * 2.0 * (double)c.M * (double)c.N * (double)c.K;
-  const double bytes_min = l * e * ((double)c.M * c.K + (double)c.N * c.K) + 4.0 * (double)c.M * c.N;
   const T T_rl = th[0] + dmax(lift<T>(flops) / (lift<T>((double)n_sm) * R * S), lift<T>(bytes_min) / th[2]);
   return dmax(T_stage, T_rl);
 }
@@ -485,11 +496,20 @@ extern "C" void orc_autotune(i64 n, const int32_t* MNK, int dtype, const double*
 // and the launch ends with its busiest worker:
 //   T_hat = T_launch + max_w sum_{t = w mod n_conc} tau(t).
 // ---------------------------------------------------------------------------
+// Working set of a grouped launch: every group's A rows, its own B and its C.
+static double grouped_working_set(int G, const int32_t* Mg, int32_t N, int32_t K, int dtype) {
+  const double le = load_mult(dtype) * elem_bytes(dtype);
+  double W = 0.0;
+  for (int q = 0; q < G; ++q) W += le * ((double)Mg[q] * K + (double)N * K) + 4.0 * (double)Mg[q] * N;
+  return W;
+}
+
 extern "C" double orc_grouped_predict(int G, const int32_t* Mg, int32_t N, int32_t K,
                                       const int32_t* BMg, const int32_t* BNg, int BK, int s, int g,
                                       int dtype, const double* theta, int n_sm) {
   const i64 n_conc = (g == 1) ? n_sm : 2 * (n_sm / 2);
   std::vector<double> busy(n_conc, 0.0);
+  const double W = grouped_working_set(G, Mg, N, K, dtype);
   i64 t = 0;
   for (int q = 0; q < G; ++q) {
     Cfg c;
@@ -497,7 +517,7 @@ extern "C" double orc_grouped_predict(int G, const int32_t* Mg, int32_t N, int32
     c.dtype = dtype; c.kind = K_GEMM;
     const i64 Kt = ceil_div(K, BK);
     double Tstep, Tstore;
-    stage_terms<double>(c, Kt, theta, Tstep, Tstore);
+    stage_terms<double>(c, Kt, theta, W, Tstep, Tstore);
     const double tau = (double)Kt * Tstep + Tstore;
     const i64 tiles = cta_tiles(c.M, N, c.BM, c.BN, g);
     // With cta_group 2 a pair of consecutive tiles runs on a worker pair;
@@ -517,6 +537,7 @@ extern "C" double orc_grouped_autotune(int G, const int32_t* Mg, int32_t N, int3
                                        int32_t* launch /* BK, s, g */) {
   double best = INFINITY;
   std::vector<int32_t> bm(G), bn(G);
+  const double W = grouped_working_set(G, Mg, N, K, dtype);
   for (int k = 0; k < 2; ++k)
     for (int s = 2; s <= 6; ++s)
       for (int g = 1; g <= 2; ++g) {
@@ -532,7 +553,7 @@ extern "C" double orc_grouped_autotune(int G, const int32_t* Mg, int32_t N, int3
               c.g = g; c.dtype = dtype; c.kind = K_GEMM;
               const i64 Kt = ceil_div(K, BK);
               double Tstep, Tstore;
-              stage_terms<double>(c, Kt, theta, Tstep, Tstore);
+              stage_terms<double>(c, Kt, theta, W, Tstep, Tstore);
               const double tiles = (double)cta_tiles(c.M, N, c.BM, c.BN, g);
               const double cost = tiles * ((double)Kt * Tstep + Tstore);
               if (cost < bq) { bq = cost; bm[q] = c.BM; bn[q] = c.BN; }

@@ -91,8 +91,9 @@ struct GemmFwdT {
   F T_c, T_io, T_tma, oma, X, R, S, invR, invS, T_step, T_store;
   F D, DA_r, DA_w, bstep, store_bytes, n_instr;
   F waves, Kt;
+  F W, E, rho;          // L2 residency of the TMA loads (measured reading)
   int ri;
-  bool oma_free;
+  bool oma_free, blend;
 };
 using GemmFwd = GemmFwdT<float>;
 
@@ -104,17 +105,24 @@ using GemmFwd = GemmFwdT<float>;
 //            tensor-pipe instructions of the K-step incl. strategy B's
 //            tcgen05.cp copies (measured reading)
 //   T_c    = n_p 2 BM BN BK / (R S) + T_TMEM + T_mgmt/K_tiles     (Eqs. 3, 6)
-//   T_tma  = L_TMA + b_step / B_TMA, b_step = l e BK (BM + BN/g) (Eq. 4, P = 1)
+//   T_tma  = L_TMA + b_step / (B_TMA rho), b_step = l e BK (BM + BN/g) (Eq. 4,
+//            P = 1); rho = 1 (literal reading) or the L2-residency factor
+//            B_eff(W)/B_sus of Eq. 16 over the launch's working set W
+//            (measured reading)
 //   T_io   = (1 - alpha) T_tma + T_sync, T_sync = 2 L_mbar       (Eq. 7; the
 //            measured reading drops this T_sync: one barrier per K-step)
 //   T_step = max(T_c, T_io) + T_sync                             (Eq. 8)
 //   T_stage = T_launch + waves (K_tiles T_step + T_store)
 //   T_hat = max(T_stage, T_launch + max(FLOPs/(n_SM R S), bytes_min/B_peak))
+// W_launch > 0 overrides the working set (a grouped launch passes its own);
+// otherwise W = bytes_min of this GEMM (operands once, C once).
 template <class F>
-__device__ __forceinline__ void gemm_forward(const pm_cfg& c, const ThetaT<F>& th, int n_sm, GemmFwdT<F>& f) {
+__device__ __forceinline__ void gemm_forward(const pm_cfg& c, const ThetaT<F>& th, int n_sm, GemmFwdT<F>& f,
+                                             F W_launch = F(-1)) {
   const bool measured = th.reading == PM_READING_MEASURED;
   const int dt = c.dtype, g = c.cta_group;
   const F e = dt_bytes(dt), np = dt_passes(dt), l = dt_loads(dt);
+  const F bytes_min = l * e * ((F)c.M * c.K + (F)c.N * c.K) + F(4) * (F)c.M * (F)c.N;
   f.ri = dt_rate(dt);
   f.R = th.v[f.ri];
   f.invR = th.inv[f.ri];
@@ -142,7 +150,13 @@ __device__ __forceinline__ void gemm_forward(const pm_cfg& c, const ThetaT<F>& t
   f.X = (np * F(2) * c.BM * c.BN * c.BK) * (f.invR * f.invS);
   f.T_c = f.X + T_tmem + T_mgmt;
   f.bstep = l * e * c.BK * ((F)c.BM + (F)c.BN / (F)g);
-  f.T_tma = th.v[4] + f.bstep * th.inv[5];
+  // measured: B_TMA x B_eff(W)/B_sus (Eq. 16; loads that hit in L2 arrive
+  // faster, Sec. III-A.2); w0 <= 0 switches the blend off
+  f.W = W_launch > F(0) ? W_launch : bytes_min;
+  f.blend = measured && th.v[3] > F(0);
+  f.E = f.blend ? pm_exp(-f.W / th.v[3]) : F(0);
+  f.rho = f.blend ? F(1) + (th.v[2] * th.inv[1] - F(1)) * f.E : F(1);
+  f.T_tma = th.v[4] + f.bstep * th.inv[5] / f.rho;
   const F T_sync = F(2) * th.v[12];
   // 1 - alpha = clamp(c_alpha / s, 0, 1) (literal) or clamp(c_alpha / (s - 1),
   // 0, 1) (measured: s - 1 loads in flight while one stage is consumed; a
@@ -156,7 +170,6 @@ __device__ __forceinline__ void gemm_forward(const pm_cfg& c, const ThetaT<F>& t
   f.T_store = th.v[4] + f.store_bytes * th.inv[5];
   f.T_stage = th.v[0] + f.waves * (f.Kt * f.T_step + f.T_store);
   const F flops = np * F(2) * (F)c.M * (F)c.N * (F)c.K;
-  const F bytes_min = l * e * ((F)c.M * c.K + (F)c.N * c.K) + F(4) * (F)c.M * (F)c.N;
   f.A_rl = flops * (f.invR * f.invS) / (F)n_sm;
   f.B_rl = bytes_min * th.inv[2];
   f.T_rl = th.v[0] + (f.A_rl >= f.B_rl ? f.A_rl : f.B_rl);
@@ -196,7 +209,16 @@ __device__ __forceinline__ void gemm_adjoint(const pm_cfg& c, const ThetaT<F>& t
   if (f.oma_free)
     d[15] += g_io * f.T_tma / (F)(th.reading == PM_READING_MEASURED ? c.stages - 1 : c.stages);
   d[4] += g_tma;
-  d[5] -= g_tma * (f.bstep * th.inv[5]) * th.inv[5];
+  const F t_bw = f.bstep * th.inv[5] / f.rho;         // b_step / (B_TMA rho)
+  d[5] -= g_tma * t_bw * th.inv[5];
+  if (f.blend) {
+    // rho = 1 + (B_peak/B_sus - 1) E, E = exp(-W/w0)
+    const F g_rho = -g_tma * t_bw / f.rho;
+    const F q = th.v[2] * th.inv[1];
+    d[1] -= g_rho * q * f.E * th.inv[1];
+    d[2] += g_rho * f.E * th.inv[1];
+    d[3] += g_rho * (q - F(1)) * f.E * (f.W * th.inv[3]) * th.inv[3];
+  }
   d[12] += F(2) * g_sync;
   // T_c = X + (D + D_A,r)/BW_rd + n_instr L_mma + (D + D_A,w)/BW_wr + L_mgmt/K_tiles
   gR -= g_c * f.X * f.invR;
@@ -557,6 +579,21 @@ __device__ __forceinline__ int64_t count_congruent(int64_t X, int64_t w, int64_t
   return X < w ? 0 : (X - w) / n + 1;
 }
 
+// Working set of a grouped launch (every group's A rows, its B and its C),
+// for the L2 residency of the TMA loads; called by all threads of a block.
+__device__ float grouped_working_set(const int32_t* Mg, int G, int N, int K, int dt) {
+  __shared__ unsigned long long sum_m;
+  if (threadIdx.x == 0) sum_m = 0ull;
+  __syncthreads();
+  unsigned long long mine = 0ull;
+  for (int q = threadIdx.x; q < G; q += blockDim.x) mine += (unsigned long long)Mg[q];
+  atomicAdd(&sum_m, mine);
+  __syncthreads();
+  const float sm = (float)sum_m;
+  __syncthreads();
+  return dt_loads(dt) * dt_bytes(dt) * (sm * (float)K + (float)G * (float)N * (float)K) + 4.f * sm * (float)N;
+}
+
 // Makespan of the static schedule: tiles listed group by group, tile t on
 // worker t mod n_conc, each tile of group q taking tau[q]; max over workers.
 // Called by all threads of a block; the result is valid in every thread.
@@ -599,6 +636,7 @@ __global__ void __launch_bounds__(kGroupThreads) grouped_tune_kernel(const int32
   const int BK = kBK[dt][combo / 10];
   const int s = 2 + (combo / 2) % 5;
   const int g = 1 + combo % 2;
+  const float W = grouped_working_set(Mg, G, N, K, dt);
   bool any_invalid = false;
   for (int q = threadIdx.x; q < G; q += blockDim.x) {
     float best = INFINITY;
@@ -613,7 +651,7 @@ __global__ void __launch_bounds__(kGroupThreads) grouped_tune_kernel(const int32
         c.M = Mg[q]; c.N = N; c.K = K; c.BM = (int16_t)BM; c.BN = (int16_t)BN; c.BK = (int16_t)BK;
         c.stages = (int8_t)s; c.cta_group = (int8_t)g; c.dtype = (int8_t)dt; c.kind = 0; c.tmem_a = 0;
         GemmFwd f;
-        gemm_forward(c, th, n_sm, f);
+        gemm_forward(c, th, n_sm, f, W);
         const float tq = f.Kt * f.T_step + f.T_store;   // one tile of this group
         const int64_t nt = th.reading == PM_READING_MEASURED ? (int64_t)g * cdiv(c.M, (int64_t)g * BM) * cdiv(N, BN)
                                                              : cdiv(c.M, BM) * cdiv(N, BN);
@@ -643,12 +681,13 @@ __global__ void __launch_bounds__(kGroupThreads) grouped_predict_kernel(const in
   __shared__ int64_t tiles[kMaxGroups];
   __shared__ int64_t off[kMaxGroups + 1];
   __shared__ float red[kGroupThreads / 32];
+  const float W = grouped_working_set(Mg, G, N, K, dt);
   for (int q = threadIdx.x; q < G; q += blockDim.x) {
     pm_cfg c;
     c.M = Mg[q]; c.N = N; c.K = K; c.BM = BMg[q]; c.BN = BNg[q]; c.BK = (int16_t)BK;
     c.stages = (int8_t)s; c.cta_group = (int8_t)g; c.dtype = (int8_t)dt; c.kind = 0; c.tmem_a = 0;
     GemmFwd f;
-    gemm_forward(c, th, n_sm, f);
+    gemm_forward(c, th, n_sm, f, W);
     tau[q] = f.Kt * f.T_step + f.T_store;
     tiles[q] = th.reading == PM_READING_MEASURED ? (int64_t)g * cdiv(c.M, (int64_t)g * c.BM) * cdiv(N, c.BN)
                                                  : cdiv(c.M, c.BM) * cdiv(N, c.BN);

@@ -56,9 +56,15 @@ def test_hand_evaluated_rows(reading, i):
 
 # Load-bound rows (T_io > T_c) that pin the overlap law of Eq. 7: hand
 # evaluated as above with c_alpha = 0.9, so 1 - alpha = 0.225 / 0.15 at 4 / 6
-# stages (literal) and 0.3 / 0.18 (measured).
+# stages (literal) and 0.3 / 0.18 (measured).  Under the measured reading the
+# TMA bandwidth carries the L2-residency factor rho = B_eff(W)/B_sus of
+# Eq. 16: the working set W = 2 (4096^2 x 2 B) + 4096^2 x 4 B = 2 w0, so
+# rho = 1 + (8/6.8 - 1) e^-2 = 1.023882697, T_tma = 9.7408007e-07 s and
+# T_step = 3.3959244e-07 s (4 stages) / 2.2270283e-07 s (6 stages); with the
+# blend switched off (w0 <= 0, rho = 1) the same rows take the second values.
 LOAD_BOUND_ROWS = [dict(M=4096, N=4096, K=4096, BM=64, BN=64, BK=128, stages=s, cta_group=1, dtype=1) for s in (4, 6)]
-HAND_LOAD_BOUND = {0: [2.853060e-04, 2.234012e-04], 1: [3.078003e-04, 2.087526e-04]}
+HAND_LOAD_BOUND = {0: [2.853060e-04, 2.234012e-04], 1: [3.033114e-04, 2.060593e-04]}
+HAND_LOAD_BOUND_NO_BLEND = {0: [2.853060e-04, 2.234012e-04], 1: [3.078003e-04, 2.087526e-04]}
 
 
 @pytest.mark.parametrize("i", range(2))
@@ -66,6 +72,46 @@ def test_hand_evaluated_load_bound_rows(reading, i):
     th = (PRIOR160 if reading == 0 else PRIOR160_MEASURED).copy()
     th[15] = 0.9
     assert one(th, **LOAD_BOUND_ROWS[i]) == pytest.approx(HAND_LOAD_BOUND[reading][i], rel=2e-6)
+    th[3] = 0.0
+    assert one(th, **LOAD_BOUND_ROWS[i]) == pytest.approx(HAND_LOAD_BOUND_NO_BLEND[reading][i], rel=2e-6)
+
+
+def test_l2_residency_of_tma_loads_closed_form(reading):
+    # Load-bound K-steps (alpha = 0 through c_alpha = 10, compute and barriers
+    # free).  Measured reading: an L2-resident launch (w0 -> infinity) loads at
+    # B_TMA B_peak/B_sus, a streaming one (w0 <= 0) at B_TMA, so per K-step the
+    # difference is b_step / B_TMA (1 - B_sus/B_peak).  The literal reading has
+    # no such term: both give the same time.
+    th = PRIOR160.copy()
+    th[15] = 10.0
+    th[6] = th[7] = th[8] = 1e30
+    th[9] = th[12] = th[13] = 0.0
+    th[10] = th[11] = 1e30
+    th[2] = 2.0 * th[1]                                # B_peak / B_sus = 2
+    base = dict(M=128, N=128, BM=128, BN=128, BK=64, stages=3, cta_group=1, dtype=1)
+    b_step = 2 * 64 * (128 + 128)
+
+    def per_step(w0):
+        t = th.copy()
+        t[3] = w0
+        return (one(t, K=64 * 400, **base) - one(t, K=64 * 200, **base)) / 200
+
+    resident, streaming = per_step(1e30), per_step(0.0)
+    assert streaming == pytest.approx(th[4] + b_step / th[5], rel=1e-9)
+    if reading == 1:
+        assert resident == pytest.approx(th[4] + b_step / (2.0 * th[5]), rel=1e-9)
+        assert streaming - resident == pytest.approx(b_step / th[5] * 0.5, rel=1e-9)
+        # a larger working-set scale w0 keeps more of the launch in L2: the
+        # time falls monotonically from the streaming to the resident limit
+        r = dict(base, M=1024, N=1024, K=64 * 64)
+        ts = []
+        for w0 in (0.0, 3e6, 1e7, 3e7, 1e8, 1e30):    # W = 21 MB
+            t = th.copy()
+            t[3] = w0
+            ts.append(one(t, **r))
+        assert all(a > b for a, b in zip(ts, ts[1:]))
+    else:
+        assert resident == pytest.approx(streaming, rel=1e-12)
 
 
 def test_valid_config_counts():
