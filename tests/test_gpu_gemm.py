@@ -8,6 +8,8 @@ the FP64 CPU oracle.
   * real-valued operands: FP32 normwise-max error <= 1e-5, BF16 relative
     Frobenius <= 2e-2, FP8 e4m3 <= 6e-2 against C = A.B in FP64.
 """
+import functools
+
 import numpy as np
 import pytest
 
@@ -182,11 +184,17 @@ def test_lowp_frobenius(lib, dt, tol, t):
     assert err <= tol, err
 
 
+@functools.lru_cache(maxsize=2)
+def normal_operands(n):
+    # generated once per size (a 16384^3 pair takes about a minute on the host)
+    return S.gemm_operands(n, n, n, seed=2, dist="normal")
+
+
 @pytest.mark.parametrize("dt", [1, 2])
 def test_large_sampled_rows(lib, dt):
     # full 8192^3 launch in the configuration the model picks; 128 sampled rows
     M = N = K = 8192
-    A, B = S.gemm_operands(M, N, K, seed=2, dist="normal")
+    A, B = normal_operands(M)
     th = O.prior_theta(lib.sm_count())
     pick, _ = O.autotune(np.array([[M, N, K]], np.int32), dt, th, lib.sm_count())
     C, _ = run_gemm(lib, A, B, lib.cfg(M, N, K, *pick[0], dtype=dt), dt)
@@ -194,6 +202,41 @@ def test_large_sampled_rows(lib, dt):
     ref = O.gemm_f64(A[rows], B)
     err = np.linalg.norm(C[rows] - ref) / np.linalg.norm(ref)
     assert err <= (2e-2 if dt == 1 else 6e-2), err
+
+
+# The launch configurations the bench and the sweep's exhaustive search time
+# at full size (8192^3 and 16384^3), checked on seeded sampled rows.
+FULL_SIZE = [(1, 8192, (256, 256, 64, 4, 2)), (2, 8192, (256, 256, 128, 3, 1)),
+             (1, 16384, (256, 256, 64, 3, 2)), (2, 16384, (256, 256, 128, 4, 2))]
+
+
+@pytest.mark.parametrize("dt,n,t", FULL_SIZE, ids=["%s-%d" % (DT_NAMES[d], n) for d, n, _ in FULL_SIZE])
+def test_full_size_sampled_rows(lib, dt, n, t):
+    A, B = normal_operands(n)
+    C, _ = run_gemm(lib, A, B, lib.cfg(n, n, n, *t, dtype=dt), dt)
+    rows = S.sampled_rows(10, n, 128)
+    ref = O.gemm_f64(A[rows], B)
+    err = np.linalg.norm(C[rows] - ref) / np.linalg.norm(ref)
+    assert err <= (2e-2 if dt == 1 else 6e-2), err
+    assert np.isfinite(C).all()
+
+
+def test_gemm_host_full_size_sampled_rows(lib):
+    # the end-to-end call of the bench: host FP32 in and out, 8 row chunks
+    n, t = 8192, (256, 256, 64, 4, 2)
+    A, B = normal_operands(n)
+    Ah = torch.from_numpy(A).pin_memory()
+    Bh = torch.from_numpy(B).pin_memory()
+    Ch = torch.full((n, n), float("nan"), dtype=torch.float32).pin_memory()
+    c = lib.cfg(n, n, n, *t, dtype=1)
+    ws = torch.empty(lib.pm_gemm_host_workspace(c, 8), dtype=torch.uint8, device="cuda")
+    lib.pm_gemm_host(c, Ah, Bh, Ch, ws, 8)
+    torch.cuda.synchronize()
+    C = Ch.numpy()
+    assert np.isfinite(C).all()
+    rows = S.sampled_rows(11, n, 128)
+    ref = O.gemm_f64(A[rows], B)
+    assert np.linalg.norm(C[rows] - ref) / np.linalg.norm(ref) <= 2e-2
 
 
 def test_gemm_autotune_picks_fastest_of_model_shortlist(lib):
