@@ -88,9 +88,11 @@ typedef struct { float v[16]; } pm_params;
  *  PM_READING_MEASURED: readings measured on this library's kernels -- L_mma
  *    once per tensor-pipe instruction of the K-step (BK/k_instr per 128-row
  *    block per pass, plus strategy B's copies), alpha = 1 - c_alpha/(stages-1),
- *    T_sync once per K-step (Eq. 8), and the TMA bandwidth scaled by the
- *    L2-residency factor B_eff(W)/B_sus of Eq. 16 over the launch's working
- *    set W (operands and C; Sec. III-A.2 notes that L2 hits change B_TMA).
+ *    T_sync once per K-step (Eq. 8), O_misc of Eq. 8 = the bubble of the
+ *    s-deep ring (T_step >= (T_tma + T_c + T_sync)/s), and the TMA bandwidth
+ *    scaled by the L2-residency factor B_eff(W)/B_sus of Eq. 16 over the
+ *    launch's working set W (operands and C; Sec. III-A.2 notes that L2 hits
+ *    change B_TMA).
  * The setting is process-wide and read by every model entry point at launch;
  * fit theta under the reading it will be used with. */
 typedef enum { PM_READING_LITERAL = 0, PM_READING_MEASURED = 1 } pm_reading;

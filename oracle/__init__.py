@@ -293,7 +293,8 @@ def set_reading(reading: int) -> None:
     """Select the readings of the stage model's open points (process-wide):
     0 the literal equations (L_mma per K-step, alpha = 1 - c/s, T_sync in Eqs. 7 and 8),
     1 the readings measured on the GPU's kernels (L_mma per tensor-pipe instruction,
-    alpha = 1 - c/(s-1), T_sync once, B_TMA scaled by the L2-residency factor
+    alpha = 1 - c/(s-1), T_sync once, the ring bubble (T_tma + T_c + T_sync)/s as a
+    lower bound of T_step, B_TMA scaled by the L2-residency factor
     B_eff(W)/B_sus of Eq. 16 over the launch's working set W)."""
     _load().orc_set_reading(int(reading))
 

@@ -288,8 +288,10 @@ static T b_eff(const T* th, double W) {
 //     instruction the K-step issues (BK/k_instr per 128-row block per pass,
 //     plus strategy B's copies), alpha(s) = clamp(1 - c_alpha/(s-1), 0, 1)
 //     (an s-stage ring keeps s-1 loads in flight), T_sync once per K-step
-//     (Eq. 8; the barrier of Eq. 7 is the same one), and B_TMA scaled by the
-//     working-set ratio B_eff(W)/B_sus of Eq. 16 (L2 residency of the loads).
+//     (Eq. 8; the barrier of Eq. 7 is the same one), O_misc of Eq. 8 = the
+//     bubble of the s-deep ring (T_step >= (T_tma + T_c + T_sync)/s), and
+//     B_TMA scaled by the working-set ratio B_eff(W)/B_sus of Eq. 16 (L2
+//     residency of the loads).
 static int g_reading = 0;
 extern "C" void orc_set_reading(int r) { g_reading = r == 1 ? 1 : 0; }
 extern "C" int orc_reading() { return g_reading; }
@@ -349,8 +351,13 @@ static void stage_terms(const Cfg& c, i64 Kt, const T* th, double W, T& Tstep, T
   if (measured) alpha = c.s <= 1 ? lift<T>(0.0) : dclamp01(1.0 - th[15] / lift<T>((double)(c.s - 1)));
   else alpha = dclamp01(1.0 - th[15] / lift<T>((double)c.s));
   const T T_io = measured ? (1.0 - alpha) * T_tma : (1.0 - alpha) * T_tma + T_sync;
-  // Eq. 8, O_misc = 0.
+  // Eq. 8.  Literal reading: O_misc = 0.  Measured reading: O_misc is the
+  // pipeline bubble of the s-deep ring (Sec. III-A.5 counts pipeline bubbles
+  // in O_misc): every stage cycles through its load, its MMAs and its full
+  // and empty barriers, so s stages complete at most one K-step per
+  // (T_tma + T_c + T_sync) / s, and T_step is the larger of that and Eq. 8.
   Tstep = dmax(T_c, T_io) + T_sync;
+  if (measured) Tstep = dmax(Tstep, (T_tma + T_c + T_sync) / lift<T>((double)c.s));
   // Writeback of the FP32 tile: L_store_setup + bytes(C_tile)/B (Sec. III-A.5).
   Tstore = th[4] + (4.0 * c.BM * c.BN) / th[5];
 }

@@ -92,8 +92,9 @@ struct GemmFwdT {
   F D, DA_r, DA_w, bstep, store_bytes, n_instr;
   F waves, Kt;
   F W, E, rho;          // L2 residency of the TMA loads (measured reading)
+  F T_eq8, T_ring;       // Eq. 8 and the ring bound (measured reading)
   int ri;
-  bool oma_free, blend;
+  bool oma_free, blend, ring;
 };
 using GemmFwd = GemmFwdT<float>;
 
@@ -111,7 +112,9 @@ using GemmFwd = GemmFwdT<float>;
 //            (measured reading)
 //   T_io   = (1 - alpha) T_tma + T_sync, T_sync = 2 L_mbar       (Eq. 7; the
 //            measured reading drops this T_sync: one barrier per K-step)
-//   T_step = max(T_c, T_io) + T_sync                             (Eq. 8)
+//   T_step = max(T_c, T_io) + T_sync                             (Eq. 8; the
+//            measured reading adds the bubble of the s-deep ring as O_misc:
+//            T_step = max(Eq. 8, (T_tma + T_c + T_sync) / s))
 //   T_stage = T_launch + waves (K_tiles T_step + T_store)
 //   T_hat = max(T_stage, T_launch + max(FLOPs/(n_SM R S), bytes_min/B_peak))
 // W_launch > 0 overrides the working set (a grouped launch passes its own);
@@ -165,7 +168,12 @@ __device__ __forceinline__ void gemm_forward(const pm_cfg& c, const ThetaT<F>& t
   f.oma_free = r > F(0) && r < F(1);
   f.oma = r <= F(0) ? F(0) : (r >= F(1) ? F(1) : r);
   f.T_io = measured ? f.oma * f.T_tma : f.oma * f.T_tma + T_sync;
-  f.T_step = pm_max(f.T_c, f.T_io) + T_sync;
+  f.T_eq8 = pm_max(f.T_c, f.T_io) + T_sync;
+  // measured: each stage cycles through its load, its MMAs and its full and
+  // empty barriers, so s stages finish at most one K-step per cycle / s
+  f.T_ring = measured ? (f.T_tma + f.T_c + T_sync) / (F)c.stages : F(0);
+  f.ring = measured && f.T_ring > f.T_eq8;
+  f.T_step = f.ring ? f.T_ring : f.T_eq8;
   f.store_bytes = F(4) * c.BM * c.BN;
   f.T_store = th.v[4] + f.store_bytes * th.inv[5];
   f.T_stage = th.v[0] + f.waves * (f.Kt * f.T_step + f.T_store);
@@ -200,12 +208,15 @@ __device__ __forceinline__ void gemm_adjoint(const pm_cfg& c, const ThetaT<F>& t
   const F g_store = g_stage * f.waves;
   d[4] += g_store;
   d[5] -= g_store * (f.store_bytes * th.inv[5]) * th.inv[5];
-  F g_sync = g_step;
-  F g_c = F(0), g_io = F(0);
-  if (f.T_c >= f.T_io) g_c = g_step; else g_io = g_step;
+  // T_step = max(T_eq8, T_ring); ties to Eq. 8
+  const F g_eq8 = f.ring ? F(0) : g_step;
+  const F g_ring = f.ring ? g_step / (F)c.stages : F(0);   // per term of the ring's cycle
+  F g_sync = g_eq8 + g_ring;
+  F g_c = g_ring, g_io = F(0);
+  if (f.T_c >= f.T_io) g_c += g_eq8; else g_io = g_eq8;
   // T_io = oma * T_tma + T_sync
   if (th.reading != PM_READING_MEASURED) g_sync += g_io;
-  const F g_tma = g_io * f.oma;
+  const F g_tma = g_io * f.oma + g_ring;
   if (f.oma_free)
     d[15] += g_io * f.T_tma / (F)(th.reading == PM_READING_MEASURED ? c.stages - 1 : c.stages);
   d[4] += g_tma;

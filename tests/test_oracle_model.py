@@ -43,8 +43,13 @@ CONFIG_ROWS = [
 # and 8): config 1 has T_c = 4.290643e-07 s and T_io = 3.118298e-07 s per step.
 HAND_LITERAL = [1.438600e-05, 6.278955e-04, 3.385809e-04, 6.608431e-03, 1.268226e-03, 1.899839e-03, 6.067389e-06]
 # Measured reading (L_mma per instruction: 12, 4 and 4 per K-step in the first
-# three rows; alpha = 1 - 0.15/(s-1); T_sync once).
-HAND_MEASURED = [1.549758e-05, 6.594239e-04, 3.543451e-04, 5.988797e-03, 1.268226e-03, 1.899839e-03, 6.067389e-06]
+# three rows; alpha = 1 - 0.15/(s-1); T_sync once; B_TMA x rho(W); O_misc =
+# the ring bubble, T_step >= (T_tma + T_c + T_sync)/s).  With the prior's
+# per-SM B_TMA the ring binds in all four GEMM rows: config 1 has T_c =
+# 4.98538e-07 s, rho = 1.163209, T_tma = 1.546716e-06 s, Eq. 8 5.459064e-07 s
+# and the ring 1.046311e-06 s per K-step; the 8192^3 BF16 row 3.674625e-07 s
+# (Eq. 8) against 4.362411e-07 s (ring).
+HAND_MEASURED = [2.350406e-05, 7.738715e-04, 4.109904e-04, 1.616707e-02, 1.268226e-03, 1.899839e-03, 6.067389e-06]
 
 
 @pytest.mark.parametrize("i", range(len(CONFIG_ROWS)))
@@ -60,7 +65,8 @@ def test_hand_evaluated_rows(reading, i):
 # TMA bandwidth carries the L2-residency factor rho = B_eff(W)/B_sus of
 # Eq. 16: the working set W = 2 (4096^2 x 2 B) + 4096^2 x 4 B = 2 w0, so
 # rho = 1 + (8/6.8 - 1) e^-2 = 1.023882697, T_tma = 9.7408007e-07 s and
-# T_step = 3.3959244e-07 s (4 stages) / 2.2270283e-07 s (6 stages); with the
+# T_step = 3.3959244e-07 s (4 stages) / 2.2270283e-07 s (6 stages), above the
+# ring bound (2.863851e-07 / 1.909234e-07 s), so Eq. 7 sets the step; with the
 # blend switched off (w0 <= 0, rho = 1) the same rows take the second values.
 LOAD_BOUND_ROWS = [dict(M=4096, N=4096, K=4096, BM=64, BN=64, BK=128, stages=s, cta_group=1, dtype=1) for s in (4, 6)]
 HAND_LOAD_BOUND = {0: [2.853060e-04, 2.234012e-04], 1: [3.033114e-04, 2.060593e-04]}
@@ -152,9 +158,12 @@ def test_eq16_small_working_set_sees_peak():
 def test_full_overlap_leaves_only_sync(reading):
     # c_alpha = 0 gives alpha = 1 (Eq. 7): T_io = T_sync (literal) or 0
     # (measured) and the K-step is compute + sync when compute dominates;
-    # isolate by differencing in K.
+    # isolate by differencing in K.  The measured reading's ring bound still
+    # holds: three stages complete at most one K-step per (T_tma + T_c +
+    # T_sync)/3, which an absurdly slow TMA makes the step time.
     th = PRIOR160.copy()
     th[15] = 0.0
+    th[3] = 0.0                                        # rho = 1
     th[5] = 1e3                                        # absurdly slow TMA: would dominate if not hidden
     base = dict(M=128, N=128, BM=128, BN=128, BK=64, stages=3, cta_group=1, dtype=1)
     d = one(th, K=64 * 200, **base) - one(th, K=64 * 100, **base)
@@ -162,8 +171,17 @@ def test_full_overlap_leaves_only_sync(reading):
     # L_mma once per K-step (literal) or per each of its BK/16 = 4 MMAs
     n_mma = 1 if reading == 0 else 4
     Tc_noamort = 2 * 128 * 128 * 64 / th[7] + 4 * 128 * 128 / th[10] + n_mma * th[9] + 4 * 128 * 128 / th[11]
-    expect = 100 * (Tc_noamort + 2 * th[12])
+    if reading == 0:
+        expect = 100 * (Tc_noamort + 2 * th[12])
+    else:
+        T_tma = th[4] + 2 * 64 * (128 + 128) / th[5]
+        expect = 100 * (T_tma + Tc_noamort + 2 * th[12]) / 3
     assert d == pytest.approx(expect, rel=1e-9)
+    if reading == 1:
+        # with a fast TMA the ring does not bind and the step is T_c + T_sync
+        th[4], th[5] = 0.0, 1e30
+        d = one(th, K=64 * 200, **base) - one(th, K=64 * 100, **base)
+        assert d == pytest.approx(100 * (Tc_noamort + 2 * th[12]), rel=1e-9)
 
 
 def test_two_sm_traffic_ratio_square_tiles():
@@ -319,7 +337,10 @@ def test_grouped_single_group_reduces_to_stage_model(reading):
 
 
 def test_grouped_makespan_brute_force(reading):
-    th = PRIOR160
+    # w0 = 0: the single-tile GEMMs below have another working set than the
+    # launch, and the schedule, not the L2 factor, is under test here
+    th = PRIOR160.copy()
+    th[3] = 0.0
     Mg = S.grouped_m(6, 3, 16, 600)
     n_sm = 8
     t = O.grouped_predict(Mg, 256, 512, [64] * 6, [128] * 6, 64, 3, 1, 1, th, n_sm)
@@ -364,8 +385,10 @@ def test_pair_tile_count_per_reading(reading):
     # ceil(M/BM) ceil(N/BN) CTA tiles (literal) against 2 ceil(M/2BM) ceil(N/BN)
     # (measured: the pair covers 2 BM rows).  With 152 SMs (76 pairs) and
     # N = 50 BN: M = 3 BM gives 150 tiles = one wave (literal) or 200 = two
-    # waves (measured); M = 2 BM gives 100 tiles, one wave, either way.
+    # waves (measured); M = 2 BM gives 100 tiles, one wave, either way.  w0 = 0
+    # keeps the two shapes' K-steps identical (no working-set factor).
     th = PRIOR160.copy()
+    th[3] = 0.0
     base = dict(N=128 * 50, K=4096, BM=128, BN=128, BK=64, stages=4, cta_group=2, dtype=1)
     t3 = float(O.model_batch(cfgs([dict(M=384, **base)]), th, 152)[0])
     t2 = float(O.model_batch(cfgs([dict(M=256, **base)]), th, 152)[0])

@@ -69,13 +69,16 @@ def test_strategy_b_space_is_a_subset_of_a():
 @pytest.mark.parametrize("dt,bk,e,n_p,l", [(1, 64, 2, 1, 1), (2, 128, 1, 1, 1), (0, 32, 4, 3, 2)])
 def test_strategy_b_adds_a_tile_traffic_when_compute_bound(reading, dt, bk, e, n_p, l):
     # alpha = 1 (c_alpha = 0) leaves T_io = T_sync, so every K-step costs
-    # T_c + T_sync and the two strategies differ only in T_TMEM:
+    # T_c + T_sync (instant loads keep the measured reading's ring bound
+    # (T_tma + T_c + T_sync)/s below it) and the two strategies differ only
+    # in T_TMEM:
     #   per K-step   n_p e BM BK / BW_rd  (every pass reads A from TMEM)
     #              + l e BM BK / BW_wr    (the A planes are copied in)
     #              + n_cp L_mma           (measured reading: one tcgen05.cp per
     #                                      128 x 32-byte slice, l * BK e / 32)
     th = PRIOR160.copy()
     th[15] = 0.0
+    th[4], th[5] = 0.0, 1e30           # instant loads: the ring bound of the measured reading stays below
     M = N = 1024                       # 8 x 8 = 64 tiles of 128 x 128: one wave on 160 SMs
     K = bk * 50
     base = dict(M=M, N=N, K=K, BM=128, BN=128, BK=bk, stages=2, cta_group=1, dtype=dt)
