@@ -328,6 +328,26 @@ def run_gpu(args):
                       "model_only_over_best_time": meas[model_pick] / meas[best],
                       "model_mae_pct": float(np.mean(np.abs(pred - tm) / tm) * 100.0),
                       "protocol": "3 warm-ups, median of 15 CUDA-event timed launches per tile"}
+        # the same under the measured reading with its own calibration
+        calib_m = os.path.join(ROOT, "paper_2605_04178_gb300", "theta_gb300_measured.json")
+        if os.path.exists(calib_m):
+            with open(calib_m) as f:
+                theta_m = np.array(json.load(f)["theta"], dtype=np.float64)
+            pred_m = torch.empty(len(tiles), dtype=torch.float32, device="cuda")
+            pm.pm_model_set_reading(pm.PM_READING_MEASURED)
+            try:
+                pm.pm_autotune_pick(MNK, 1, pm.PM_BF16, theta_m, n_sm, picks, t_pred)
+                pm.pm_model_predict(pm.cfg_tensor(cols), len(tiles), theta_m, n_sm, pred_m)
+                torch.cuda.synchronize()
+            finally:
+                pm.pm_model_set_reading(pm.PM_READING_LITERAL)
+            pq = picks.cpu().numpy().view(pm.CFG_DTYPE)[0]
+            mp = tuple(int(pq[k]) for k in ("BM", "BN", "BK", "stages", "cta_group"))
+            pm_np = pred_m.cpu().numpy().astype(np.float64)
+            exhaustive["measured_reading"] = {
+                "model_only_tile": dict(zip(("BM", "BN", "BK", "stages", "cta_group"), mp)),
+                "model_only_over_best_time": meas[mp] / meas[best] if mp in meas else None,
+                "model_mae_pct": float(np.mean(np.abs(pm_np - tm) / tm) * 100.0)}
         # TMEM strategy B (A operand copied into tensor memory) over its tile
         # space at the same shape: fastest of each strategy, measured and predicted
         measB = {}
