@@ -431,12 +431,81 @@ def run_gpu(args):
                                     "sample": "6 x 8 rows of the 8192^3 GEMM in FP64 (%.1f s)" % dt,
                                     "cpu_model": _cpu_model()}
             line["bf16_rel_frobenius_error_rows0_47"] = err
+            line["cpu_baseline"]["per_config"] = _cpu_per_config()
         line["roofline"]["traffic"] = _traffic_from_profile(pick)
         print(json.dumps(line))
         sys.stdout.flush()
     if dist is not None:
         dist.barrier()
         dist.destroy_process_group()
+
+
+def _cpu_per_config() -> dict:
+    """The oracle, as it stands, timed on the host cores on a bounded sample of
+    each workload the bench reports on the GPU (a few seconds in all)."""
+    import ctypes
+
+    import numpy as np
+
+    import oracle as O
+    import synthetic as S
+
+    def best(fn, reps=3):
+        ts = []
+        for _ in range(reps):
+            t0 = time.perf_counter()
+            fn()
+            ts.append(time.perf_counter() - t0)
+        return min(ts)
+
+    out = {}
+    # config 1: FP64 GEMM 512^3 (the definition), all host cores and one thread
+    A, B = S.gemm_operands(512, 512, 512, seed=0)
+    O.gemm_f64(A, B)
+    t_all = best(lambda: O.gemm_f64(A, B))
+    c1 = {"GFLOPps_all_cores": 2 * 512 ** 3 / t_all / 1e9, "ms_all_cores": t_all * 1e3}
+    try:
+        gomp = ctypes.CDLL("libgomp.so.1")
+        gomp.omp_set_num_threads(1)
+        try:
+            t_one = best(lambda: O.gemm_f64(A, B), 1)
+        finally:
+            gomp.omp_set_num_threads(os.cpu_count() or 1)
+        c1.update(GFLOPps_one_thread=2 * 512 ** 3 / t_one / 1e9, ms_one_thread=t_one * 1e3)
+    except OSError:
+        pass
+    out["config1_fp64_gemm_512"] = c1
+    # config 2a: triad (one rounding, one thread) and copy over 2^26 FP32
+    n = 2 ** 26
+    b = S.uniform_pm1(1, n)
+    c = S.uniform_pm1(1, n, offset=n)
+    t_tr = best(lambda: O.triad_f32(b, c, 3.0))
+    dst = np.empty_like(b)
+    t_cp = best(lambda: np.copyto(dst, b))
+    out["config2a_stream"] = {"n": n, "triad_GBps_one_thread": 12.0 * n / t_tr / 1e9,
+                              "copy_GBps": 8.0 * n / t_cp / 1e9}
+    # config 2c: pointer chase over 256 MB, 2^20 dependent loads
+    nodes = (256 << 20) // 64
+    buf = S.pchase_buffer(nodes, seed=1)
+    hops = 2 ** 20
+    t_pc = best(lambda: O.pchase(buf, 16, 0, hops), 2)
+    out["config2c_pchase_256MB"] = {"ns_per_hop": t_pc / hops * 1e9}
+    del b, c, dst, buf
+    # config 4: per-group sampled rows of the grouped GEMM (8 groups x 8 rows, N = K = 4096)
+    Bg = S.matrix(3, 4096, 4096, "normal", 0)
+    Ag = S.matrix(3, 8, 4096, "normal", 4096 * 4096)
+    t_g = best(lambda: [O.gemm_f64(Ag, Bg) for _ in range(8)], 2)
+    out["config4_grouped_rows"] = {"GFLOPps": 8 * 2 * 8 * 4096 * 4096 / t_g / 1e9, "sample": "8 groups x 8 rows"}
+    # config 5: FP64 model with its dual-number gradient over 2e5 configurations
+    nc = 200000
+    cf = S.model_config_batch(nc, seed=4)
+    cf["kind"] = np.zeros(nc, dtype=np.int32)
+    th = O.prior_theta(152)
+    t_m = best(lambda: O.model_batch(cf, th, 152), 2)
+    t_mg = best(lambda: O.model_batch(cf, th, 152, grad=True), 2)
+    out["config5_model"] = {"forward_Mcfg_per_s": nc / t_m / 1e6, "forward_grad_Mcfg_per_s": nc / t_mg / 1e6,
+                            "sample": "%d configurations" % nc}
+    return out
 
 
 def _cpu_model() -> str:
@@ -497,7 +566,39 @@ def secondary(pm, S, theta, n_sm, peaks):
     }
     out["probes"]["copy_frac"] = out["probes"]["copy_GBps"] / hbm
     out["probes"]["triad_frac"] = out["probes"]["triad_GBps"] / hbm
-    del a, b, c
+    # TMA 2D tile copy of a 1 GiB FP32 matrix (64 x 64 tiles): 2 GiB moved
+    src = a[: 16384 * 16384].view(16384, 16384)
+    dst = b[: 16384 * 16384].view(16384, 16384)
+    r_tma = pm.pm_probe_run(pm.probe_args(pm.PM_PROBE_TMA2D, rows=16384, cols=16384, tile_r=64, tile_c=64),
+                            src, dst, warmup=3, reps=20)
+    out["probes"]["tma2d_64x64_GBps"] = r_tma["bytes"] / r_tma["median_s"] / 1e9
+    out["probes"]["tma2d_frac"] = out["probes"]["tma2d_64x64_GBps"] / hbm
+    del a, b, c, src, dst
+    # pointer chase over a 256 MB working set (DRAM level), 64-byte node stride
+    nodes = (256 << 20) // 64
+    buf = torch.from_numpy(S.pchase_buffer(nodes, seed=1).view(np.int32)).cuda()
+    res = torch.zeros(1, dtype=torch.int32, device="cuda")
+    hops = 2 ** 18
+    r_pc = pm.pm_probe_run(pm.probe_args(pm.PM_PROBE_PCHASE, n=nodes, hops=hops, start=0), buf, res, warmup=2, reps=3)
+    out["probes"]["pchase_256MB_ns_per_hop"] = 1e9 * r_pc["median_s"] / hops
+    del buf
+    # config 1: FP32 (three-pass TF32) GEMM 512^3 in its fixed tile, and the
+    # stage model's prediction for that launch (calibrated literal theta)
+    A1 = torch.from_numpy(S.matrix(0, 512, 512, "uniform", 0)).cuda()
+    B1 = torch.from_numpy(S.matrix(0, 512, 512, "uniform", 512 * 512)).cuda()
+    ops1 = pm.GemmOperands(pm.PM_FP32, 512, 512, 512)
+    ops1.prepare(A1, B1)
+    C1 = torch.empty(512, 512, dtype=torch.float32, device="cuda")
+    c1 = pm.cfg(512, 512, 512, 128, 128, 32, 2, 1, dtype=pm.PM_FP32)
+    r1 = ops1.bench(c1, C1, warmup=10, reps=100)
+    p1 = torch.empty(1, dtype=torch.float32, device="cuda")
+    pm.pm_model_predict(pm.cfg_tensor({k: np.array([v]) for k, v in dict(
+        M=512, N=512, K=512, BM=128, BN=128, BK=32, stages=2, cta_group=1, dtype=0, kind=0).items()}),
+        1, theta, n_sm, p1)
+    out["config1"] = {"workload": "fp32_gemm_512^3_128x128x32_s2_g1", "gpu_us": r1["median_s"] * 1e6,
+                      "TFLOPps": 2 * 512 ** 3 / r1["median_s"] / 1e12, "model_pred_us": float(p1.item()) * 1e6,
+                      "model_ape_pct": abs(float(p1.item()) - r1["median_s"]) / r1["median_s"] * 100}
+    del A1, B1, C1, ops1
     # batched model over 1e6 configurations: forward and adjoint
     nc = 10 ** 6
     cf = S.model_config_batch(nc, seed=4)
