@@ -176,6 +176,72 @@ __device__ __forceinline__ void issue_stage(uint32_t d0, uint64_t a0, uint64_t b
   }
 }
 
+// Barriers and buffers the MMA issuer's K-loop works with.
+struct MmaRing {
+  uint64_t* full;
+  uint64_t* empty;
+  uint64_t* acce;
+  int stage;
+  uint32_t phase;
+};
+
+// One K-step's MMAs and the commit that frees its ring stage.
+template <int CG, int KIND, int NA, int NK, int NM, int TA>
+__device__ __forceinline__ void mma_step(MmaRing& r, const GemmParams& p, uint32_t d0, uint64_t a0, uint64_t b0,
+                                         uint32_t a16, uint32_t b16, uint32_t m16, uint32_t idesc, uint32_t bn,
+                                         bool first, uint32_t a_tm) {
+  issue_stage<CG, KIND, NA, NK, NM, TA>(d0, a0, b0, a16, b16, m16, idesc, bn, first, a_tm);
+  if constexpr (CG == 1) umma_commit(smem_u32(&r.empty[r.stage]));
+  else umma_commit_pair(smem_u32(&r.empty[r.stage]), (uint16_t)3);
+  if (++r.stage == p.stages) { r.stage = 0; r.phase ^= 1u; }
+}
+
+// The MMA issuer's K-loop for one tile, specialised on the stage's shape
+// (NA swizzle atoms along K, NK k-steps per atom, NM 128-row blocks) so the
+// per-K-step path is a barrier wait, descriptor additions, the unrolled MMAs
+// and a commit: the issuing thread is then never the bottleneck of the tensor
+// pipe (a shape switch inside the loop cost a quarter of the throughput of
+// four-MMA K-steps).  The first K-step is peeled off for the split release of
+// 256 x 256 tiles.  Returns false if a wait gave up.
+template <int CG, int KIND, int TA, int NA, int NK, int NM>
+__device__ __forceinline__ bool mma_tile(MmaRing& r, const GemmParams& p, const Tile& T, uint32_t d0, uint32_t base,
+                                         uint32_t tmem_base, uint32_t use, volatile int* abort_p) {
+  constexpr int L = (KIND == 1) ? 2 : 1;
+  const uint32_t swcode = p.sw == 128 ? 2u : 4u;
+  const uint64_t desc0 = smem_desc(base, 8u * (uint32_t)p.sw, swcode);    // stage 0, first A atom
+  const uint32_t stage16 = p.stage_bytes >> 4;                              // descriptor units (16 B)
+  const uint32_t a16 = T.a_part >> 4, b16 = T.b_part >> 4, m16 = (uint32_t)(128 * p.sw) >> 4;
+  const uint32_t boff16 = (uint32_t)(L * NA) * a16;                         // B follows the A atoms
+  const uint32_t bn = (uint32_t)T.BN;
+  // first K-step
+  if (!mbar_wait(smem_u32(&r.full[r.stage]), r.phase, p.wd, abort_p, SITE_GEMM_MMA)) return false;
+  tc_fence_after();
+  {
+    const uint64_t a0 = desc0 + (uint64_t)((uint32_t)r.stage * stage16);
+    const uint64_t b0 = a0 + (uint64_t)boff16;
+    const uint32_t a_tm = TA ? tmem_base + (uint32_t)(p.a_col0 + r.stage * p.a_cols) : 0u;
+    if (NM == 2 && !TA && p.split) {
+      // split release: row block 0 now, row block 1 once the epilogue has
+      // drained it from the previous tile
+      issue_stage<CG, KIND, NA, NK, 1, TA>(d0, a0, b0, a16, b16, m16, T.idesc, bn, true, a_tm);
+      if (!mbar_wait(smem_u32(&r.acce[1]), (use & 1u) ^ 1u, p.wd, abort_p, SITE_GEMM_MMA)) return false;
+      tc_fence_after();
+      mma_step<CG, KIND, NA, NK, 1, TA>(r, p, d0 + bn, a0 + (uint64_t)m16, b0, a16, b16, m16, T.idesc, bn, true,
+                                        a_tm);
+    } else {
+      mma_step<CG, KIND, NA, NK, NM, TA>(r, p, d0, a0, b0, a16, b16, m16, T.idesc, bn, true, a_tm);
+    }
+  }
+  for (int kt = 1; kt < p.Kt; ++kt) {
+    if (!mbar_wait(smem_u32(&r.full[r.stage]), r.phase, p.wd, abort_p, SITE_GEMM_MMA)) return false;
+    tc_fence_after();
+    const uint64_t a0 = desc0 + (uint64_t)((uint32_t)r.stage * stage16);
+    const uint32_t a_tm = TA ? tmem_base + (uint32_t)(p.a_col0 + r.stage * p.a_cols) : 0u;
+    mma_step<CG, KIND, NA, NK, NM, TA>(r, p, d0, a0, a0 + (uint64_t)boff16, a16, b16, m16, T.idesc, bn, false, a_tm);
+  }
+  return true;
+}
+
 template <int CG, int KIND, int TA>
 __global__ void __launch_bounds__(kGemmThreads, 1)
     gemm_kernel(const __grid_constant__ TensorMaps maps, const __grid_constant__ GroupTable g,
@@ -197,7 +263,6 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
   const int n_ctas = (CG == 2) ? (int)(gridDim.x >> 1) : (int)gridDim.x;
   const int n_tiles = g.tile_off[g.n_groups];
   const uint32_t base = (smem_u32(dsmem) + 1023u) & ~1023u;
-  const uint32_t swcode = p.sw == 128 ? 2u : 4u;
   volatile int* abort_p = &abort_flag;
 
   if (threadIdx.x == 0) {
@@ -280,10 +345,8 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
   } else if (warp == 1) {
     // ------------------------------------------------------------- MMA issuer
     if (lane == 0 && rank == 0) {
-      int stage = 0;
-      uint32_t phase = 0;
+      MmaRing r{full_bar, empty_bar, acce_bar, 0, 0u};
       bool ok = true;
-      const uint32_t sbo = 8u * (uint32_t)p.sw;
       int it = 0;
       for (int t = cta; t < n_tiles && ok; t += n_ctas, ++it) {
         Tile T;
@@ -297,56 +360,17 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
         }
         tc_fence_after();
         const uint32_t d0 = tmem_base + (uint32_t)(buf * p.acc_cols);
-        for (int kt = 0; kt < p.Kt; ++kt) {
-          if (!mbar_wait(smem_u32(&full_bar[stage]), phase, p.wd, abort_p, SITE_GEMM_MMA)) {
-            ok = false;
-            break;
-          }
-          tc_fence_after();
-          const uint32_t sbase = base + (uint32_t)stage * p.stage_bytes;
-          const uint64_t a0 = smem_desc(sbase, sbo, swcode);
-          const uint64_t b0 = smem_desc(sbase + (uint32_t)(L * p.n_atoms) * T.a_part, sbo, swcode);
-          const uint32_t a16 = T.a_part >> 4, b16 = T.b_part >> 4, m16 = (uint32_t)(128 * p.sw) >> 4;
-          const bool first = kt == 0;
-          const uint32_t bn = (uint32_t)T.BN;
-          const uint32_t a_tm = TA ? tmem_base + (uint32_t)(p.a_col0 + stage * p.a_cols) : 0u;
-#define PM_ISSUE(NA, NK, NM, D0, A0) \
-  issue_stage<CG, KIND, NA, NK, NM, TA>(D0, A0, b0, a16, b16, m16, T.idesc, bn, first, a_tm)
-          if (p.split && first) {
-            // first K-step of a tile under split release: row block 0 now, row
-            // block 1 once the epilogue has drained it from the previous tile
-            const uint64_t a1 = a0 + (uint64_t)m16;
-            if (p.sw == 128) {
-              if (p.n_atoms == 1) PM_ISSUE(1, 4, 1, d0, a0); else PM_ISSUE(2, 4, 1, d0, a0);
-            } else {
-              PM_ISSUE(1, 2, 1, d0, a0);
-            }
-            if (!mbar_wait(smem_u32(&acce_bar[1]), (use & 1u) ^ 1u, p.wd, abort_p, SITE_GEMM_MMA)) {
-              ok = false;
-              break;
-            }
-            tc_fence_after();
-            if (p.sw == 128) {
-              if (p.n_atoms == 1) PM_ISSUE(1, 4, 1, d0 + bn, a1); else PM_ISSUE(2, 4, 1, d0 + bn, a1);
-            } else {
-              PM_ISSUE(1, 2, 1, d0 + bn, a1);
-            }
-          } else if (p.sw == 128) {
-            if (p.n_atoms == 1) {
-              if (T.n_mblk == 1) PM_ISSUE(1, 4, 1, d0, a0);
-              else PM_ISSUE(1, 4, 2, d0, a0);
-            } else {
-              if (T.n_mblk == 1) PM_ISSUE(2, 4, 1, d0, a0);
-              else PM_ISSUE(2, 4, 2, d0, a0);
-            }
-          } else {
-            if (T.n_mblk == 1) PM_ISSUE(1, 2, 1, d0, a0);
-            else PM_ISSUE(1, 2, 2, d0, a0);
-          }
-#undef PM_ISSUE
-          if constexpr (CG == 1) umma_commit(smem_u32(&empty_bar[stage]));
-          else umma_commit_pair(smem_u32(&empty_bar[stage]), (uint16_t)3);
-          if (++stage == p.stages) { stage = 0; phase ^= 1u; }
+        // the stage's MMA shape is fixed for the whole tile: dispatch once
+        if (p.sw == 128) {
+          if (p.n_atoms == 1)
+            ok = T.n_mblk == 1 ? mma_tile<CG, KIND, TA, 1, 4, 1>(r, p, T, d0, base, tmem_base, use, abort_p)
+                               : mma_tile<CG, KIND, TA, 1, 4, 2>(r, p, T, d0, base, tmem_base, use, abort_p);
+          else
+            ok = T.n_mblk == 1 ? mma_tile<CG, KIND, TA, 2, 4, 1>(r, p, T, d0, base, tmem_base, use, abort_p)
+                               : mma_tile<CG, KIND, TA, 2, 4, 2>(r, p, T, d0, base, tmem_base, use, abort_p);
+        } else {
+          ok = T.n_mblk == 1 ? mma_tile<CG, KIND, TA, 1, 2, 1>(r, p, T, d0, base, tmem_base, use, abort_p)
+                             : mma_tile<CG, KIND, TA, 1, 2, 2>(r, p, T, d0, base, tmem_base, use, abort_p);
         }
         if (!ok) break;
         if constexpr (CG == 1) umma_commit(smem_u32(&accf_bar[buf]));
