@@ -201,8 +201,9 @@ __device__ __forceinline__ void mma_step(MmaRing& r, const GemmParams& p, uint32
 // per-K-step path is a barrier wait, descriptor additions, the unrolled MMAs
 // and a commit: the issuing thread is then never the bottleneck of the tensor
 // pipe (a shape switch inside the loop cost a quarter of the throughput of
-// four-MMA K-steps).  The first K-step is peeled off for the split release of
-// 256 x 256 tiles.  Returns false if a wait gave up.
+// four-MMA K-steps).  Under split release (256 x 256 tiles) the first K-step
+// is peeled off; elsewhere it stays in the loop to keep the code small.
+// Returns false if a wait gave up.
 template <int CG, int KIND, int TA, int NA, int NK, int NM>
 __device__ __forceinline__ bool mma_tile(MmaRing& r, const GemmParams& p, const Tile& T, uint32_t d0, uint32_t base,
                                          uint32_t tmem_base, uint32_t use, volatile int* abort_p) {
@@ -213,31 +214,29 @@ __device__ __forceinline__ bool mma_tile(MmaRing& r, const GemmParams& p, const 
   const uint32_t a16 = T.a_part >> 4, b16 = T.b_part >> 4, m16 = (uint32_t)(128 * p.sw) >> 4;
   const uint32_t boff16 = (uint32_t)(L * NA) * a16;                         // B follows the A atoms
   const uint32_t bn = (uint32_t)T.BN;
-  // first K-step
-  if (!mbar_wait(smem_u32(&r.full[r.stage]), r.phase, p.wd, abort_p, SITE_GEMM_MMA)) return false;
-  tc_fence_after();
-  {
-    const uint64_t a0 = desc0 + (uint64_t)((uint32_t)r.stage * stage16);
-    const uint64_t b0 = a0 + (uint64_t)boff16;
-    const uint32_t a_tm = TA ? tmem_base + (uint32_t)(p.a_col0 + r.stage * p.a_cols) : 0u;
-    if (NM == 2 && !TA && p.split) {
-      // split release: row block 0 now, row block 1 once the epilogue has
-      // drained it from the previous tile
-      issue_stage<CG, KIND, NA, NK, 1, TA>(d0, a0, b0, a16, b16, m16, T.idesc, bn, true, a_tm);
+  int kt0 = 0;
+  if constexpr (NM == 2 && !TA) {
+    if (p.split) {
+      // row block 0 now, row block 1 once the epilogue has drained it from
+      // the previous tile
+      if (!mbar_wait(smem_u32(&r.full[r.stage]), r.phase, p.wd, abort_p, SITE_GEMM_MMA)) return false;
+      tc_fence_after();
+      const uint64_t a0 = desc0 + (uint64_t)((uint32_t)r.stage * stage16);
+      const uint64_t b0 = a0 + (uint64_t)boff16;
+      issue_stage<CG, KIND, NA, NK, 1, TA>(d0, a0, b0, a16, b16, m16, T.idesc, bn, true, 0u);
       if (!mbar_wait(smem_u32(&r.acce[1]), (use & 1u) ^ 1u, p.wd, abort_p, SITE_GEMM_MMA)) return false;
       tc_fence_after();
-      mma_step<CG, KIND, NA, NK, 1, TA>(r, p, d0 + bn, a0 + (uint64_t)m16, b0, a16, b16, m16, T.idesc, bn, true,
-                                        a_tm);
-    } else {
-      mma_step<CG, KIND, NA, NK, NM, TA>(r, p, d0, a0, b0, a16, b16, m16, T.idesc, bn, true, a_tm);
+      mma_step<CG, KIND, NA, NK, 1, TA>(r, p, d0 + bn, a0 + (uint64_t)m16, b0, a16, b16, m16, T.idesc, bn, true, 0u);
+      kt0 = 1;
     }
   }
-  for (int kt = 1; kt < p.Kt; ++kt) {
+  for (int kt = kt0; kt < p.Kt; ++kt) {
     if (!mbar_wait(smem_u32(&r.full[r.stage]), r.phase, p.wd, abort_p, SITE_GEMM_MMA)) return false;
     tc_fence_after();
     const uint64_t a0 = desc0 + (uint64_t)((uint32_t)r.stage * stage16);
     const uint32_t a_tm = TA ? tmem_base + (uint32_t)(p.a_col0 + r.stage * p.a_cols) : 0u;
-    mma_step<CG, KIND, NA, NK, NM, TA>(r, p, d0, a0, a0 + (uint64_t)boff16, a16, b16, m16, T.idesc, bn, false, a_tm);
+    mma_step<CG, KIND, NA, NK, NM, TA>(r, p, d0, a0, a0 + (uint64_t)boff16, a16, b16, m16, T.idesc, bn, kt == 0,
+                                       a_tm);
   }
   return true;
 }
