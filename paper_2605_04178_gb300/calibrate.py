@@ -89,6 +89,18 @@ def _valid(dt, t, tmem_a=0):
     return True
 
 
+SETTLE_S = 5.0
+
+
+def settle(seconds: float = SETTLE_S) -> None:
+    """Leave the GPU idle for a few seconds.  After seconds of full-power work
+    the SM clock stays capped for a while; short kernels timed in that window
+    ran up to 30 % slow, so every block of short kernels that follows heavy
+    work starts after this pause."""
+    torch.cuda.synchronize()
+    time.sleep(seconds)
+
+
 def measure_sweep(shapes=(1024, 2048, 4096, 8192, 16384), dtypes=(1, 2), log=print) -> dict:
     """Device-timed calibration table (list of records) plus pointer-chase latencies."""
     torch.cuda.nvtx.range_push("measure_sweep")
@@ -152,6 +164,7 @@ def measure_sweep(shapes=(1024, 2048, 4096, 8192, 16384), dtypes=(1, 2), log=pri
     instr = measure_instructions()
     log("instruction and host-link probes done (%.0f s)" % (time.time() - t0))
     streams = measure_streams()
+    settle()
     log("concurrent-stream probes done (%.0f s)" % (time.time() - t0))
     # config 3: every valid BF16 / FP8 configuration at M = N = K = s
     for s in shapes:
@@ -173,7 +186,9 @@ def measure_sweep(shapes=(1024, 2048, 4096, 8192, 16384), dtypes=(1, 2), log=pri
         del Ad, Bd, C
         torch.cuda.empty_cache()
         log("config 3 shape %d done (%d rows, %.0f s)" % (s, len(rows), time.time() - t0))
+    settle()
     rows += measure_tmem_b(shapes, dtypes, log)
+    settle()
     props = torch.cuda.get_device_properties(0)
     segments = measure_segments(dict(rows=rows), log)
     torch.cuda.nvtx.range_pop()
@@ -625,6 +640,7 @@ def measure_segments(table, log=print) -> dict:
         rows.append(_seg("stencil_%d" % side, r["median_s"], cls=3, precision=pm.PM_FP32,
                          flops=6.0 * side * side, bytes=8.0 * side * side, working_set=8.0 * side * side))
         del x, y
+    settle()
     # multi-kernel memory segments: copy -> triad (-> copy) on shared buffers
     for k in (20, 24, 27):
         n = 1 << k
@@ -802,11 +818,13 @@ def main():
     if args.measure_instr:
         table["instr"] = measure_instructions()
     if args.measure_tmem_b:
+        settle()
         table["rows"] = [r for r in table["rows"] if not r.get("tmem_a", 0)] + \
             measure_tmem_b(tuple(int(s) for s in args.shapes.split(",")))
     if args.measure_streams:
         table["streams"] = measure_streams()
     if args.measure_segments:
+        settle()
         table["segments"] = measure_segments(table)
     if args.measure_instr or args.measure_tmem_b or args.measure_streams or args.measure_segments:
         with open(args.sweep, "w") as f:
