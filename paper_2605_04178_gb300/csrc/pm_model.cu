@@ -37,11 +37,15 @@ __device__ __forceinline__ double pm_log(double x) { return log(x); }
 __device__ __forceinline__ float pm_max(float a, float b) { return fmaxf(a, b); }
 __device__ __forceinline__ double pm_max(double a, double b) { return fmax(a, b); }
 
-// ceil(a / b) for a >= 0, b > 0: 32-bit unsigned division whenever both fit
-// (64-bit division is a long software sequence), exact either way.
+// ceil(a / b) for a >= 0, b > 0: a shift when b is a power of two (every tile
+// extent of the search space), else 32-bit unsigned division whenever both fit
+// (64-bit division is a long software sequence); exact either way.
 __device__ __forceinline__ int64_t cdiv(int64_t a, int64_t b) {
-  if (((uint64_t)a | (uint64_t)b) < 0x80000000ull)
-    return (int64_t)(((uint32_t)a + (uint32_t)b - 1u) / (uint32_t)b);
+  if (((uint64_t)a | (uint64_t)b) < 0x80000000ull) {
+    const uint32_t ua = (uint32_t)a, ub = (uint32_t)b;
+    if ((ub & (ub - 1u)) == 0u) return (int64_t)((ua + ub - 1u) >> (__ffs((int)ub) - 1));
+    return (int64_t)((ua + ub - 1u) / ub);
+  }
   return (a + b - 1) / b;
 }
 
