@@ -1,0 +1,86 @@
+"""The oracle's prior parameters and derived quantities against the values the
+paper prints (tests/golden/paper_printed_values.json, each with its
+citation).  The priors are the paper's printed values converted to SI units
+with a 1.9 GHz clock; these tests check the conversion and every range."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle as O
+
+GOLDEN = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_printed_values.json")))
+F = 1.9e9
+
+
+@pytest.mark.parametrize("reading", [0, 1])
+def test_priors_are_the_printed_parameters(reading):
+    th = O.prior_theta(160, F, reading)
+    tp = GOLDEN["table_parameters"]
+    assert th[10] == pytest.approx(tp["tmem_bw_read_TBps"] * 1e12)
+    assert th[11] == pytest.approx(tp["tmem_bw_write_TBps"] * 1e12)
+    assert th[4] * F == pytest.approx(tp["L_TMA_cycles"])
+    lo, hi = tp["L_mma_cycles_range"]
+    assert lo <= th[9] * F <= hi
+    lo, hi = tp["L_mbar_cycles_range"]
+    assert lo <= th[12] * F <= hi
+    lo, hi = GOLDEN["launch_overhead_us_range"]["range"]
+    assert lo <= th[0] * 1e6 <= hi
+    assert th[2] == pytest.approx(GOLDEN["table_arch_params_b200"]["hbm_peak_TBps"] * 1e12)
+
+
+def test_prior_tensor_rates_reproduce_the_printed_chip_peaks():
+    # per-SM rates x the B200's SM count at the conversion clock against the
+    # printed chip peaks (within the 2 % the per-cycle rounding leaves)
+    a = GOLDEN["table_arch_params_b200"]
+    n = GOLDEN["worked_example_b200"]["n_sm_b200"]
+    th = O.prior_theta(n, F)
+    assert th[7] * n / 1e12 == pytest.approx(a["tensor_peak_TFLOPS_fp16"], rel=0.05)
+    assert th[8] * n / 1e12 == pytest.approx(a["tensor_peak_TFLOPS_fp8"], rel=0.05)
+    assert th[8] / th[7] == pytest.approx(a["tensor_peak_TFLOPS_fp8"] / a["tensor_peak_TFLOPS_fp16"])
+
+
+@pytest.mark.parametrize("reading", [0, 1])
+def test_prior_overlap_in_the_printed_alpha_range(reading):
+    # alpha(s) = 1 - c/s (literal) or 1 - c/(s-1) (measured) at double and
+    # triple buffering lies in the printed range
+    c = O.prior_theta(160, F, reading)[15]
+    lo, hi = GOLDEN["overlap_alpha_range"]["range"]
+    for s in (2, 3):
+        a = 1 - c / s if reading == 0 else 1 - c / (s - 1)
+        assert lo - 1e-12 <= a <= hi + 1e-12
+    a2 = 1 - c / 2 if reading == 0 else 1 - c
+    assert a2 == pytest.approx(lo)
+
+
+def test_cta_pair_traffic_reduction_matches_the_printed_factor():
+    # per-K-step bytes of one CTA, b_step = l e BK (BM + BN/g): a square tile in
+    # a pair loads 3/4 of what it loads alone, the printed ~1.33x reduction
+    th = O.prior_theta(160, F)
+    th[15] = 10.0                      # loads fully exposed
+    th[4] = th[12] = th[9] = th[13] = 0.0
+    th[6] = th[7] = th[8] = th[10] = th[11] = th[2] = 1e30
+    th[14] = 1.0
+    base = dict(M=256, N=128, BM=128, BN=128, BK=64, stages=2, dtype=1, kind=0)
+
+    def per_step(g):
+        one = lambda K: float(O.model_batch({k: np.array([v]) for k, v in dict(base, K=K, cta_group=g).items()},
+                                            th, 160)[0])
+        return one(64 * 40) - one(64 * 20)
+
+    assert per_step(1) / per_step(2) == pytest.approx(GOLDEN["cta_pair_traffic_reduction"]["max_factor"], abs=0.01)
+
+
+def test_worked_example_is_only_banded():
+    # the printed prediction is not reproducible from the printed parameters
+    # (parity unpinned for this row): the oracle with the printed priors on the
+    # B200's 148 SMs gives 10.5 ms, within a factor-of-three band of the
+    # printed measurement
+    w = GOLDEN["worked_example_b200"]
+    th = O.prior_theta(w["n_sm_b200"], F)
+    cfg = {k: np.array([v]) for k, v in dict(M=w["M"], N=w["N"], K=w["K"], BM=w["BM"], BN=w["BN"], BK=w["BK"],
+                                                stages=2, cta_group=1, dtype=1, kind=0).items()}
+    t = float(O.model_batch(cfg, th, w["n_sm_b200"])[0]) * 1e3
+    assert w["measured_ms"] / 3 < t < w["measured_ms"] * 3
+    assert abs(w["predicted_ms"] / w["measured_ms"] - 1) < 0.02       # the printed 1.8 % error
