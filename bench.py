@@ -598,6 +598,21 @@ def secondary(pm, S, theta, n_sm, peaks):
     out["config1"] = {"workload": "fp32_gemm_512^3_128x128x32_s2_g1", "gpu_us": r1["median_s"] * 1e6,
                       "TFLOPps": 2 * 512 ** 3 / r1["median_s"] / 1e12, "model_pred_us": float(p1.item()) * 1e6,
                       "model_ape_pct": abs(float(p1.item()) - r1["median_s"]) / r1["median_s"] * 100}
+    # the same launch under the measured reading with its own calibration
+    calib_m = os.path.join(ROOT, "paper_2605_04178_gb300", "theta_gb300_measured.json")
+    if os.path.exists(calib_m):
+        with open(calib_m) as f:
+            theta_m = np.array(json.load(f)["theta"], dtype=np.float64)
+        pm.pm_model_set_reading(pm.PM_READING_MEASURED)
+        try:
+            pm.pm_model_predict(pm.cfg_tensor({k: np.array([v]) for k, v in dict(
+                M=512, N=512, K=512, BM=128, BN=128, BK=32, stages=2, cta_group=1, dtype=0, kind=0).items()}),
+                1, theta_m, n_sm, p1)
+            torch.cuda.synchronize()
+        finally:
+            pm.pm_model_set_reading(pm.PM_READING_LITERAL)
+        out["config1"]["model_pred_us_measured_reading"] = float(p1.item()) * 1e6
+        out["config1"]["model_ape_pct_measured_reading"] = abs(float(p1.item()) - r1["median_s"]) / r1["median_s"] * 100
     del A1, B1, C1, ops1
     # batched model over 1e6 configurations: forward and adjoint
     nc = 10 ** 6
