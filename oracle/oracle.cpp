@@ -370,6 +370,10 @@ static void stage_terms(const Cfg& c, i64 Kt, const T* th, double W, T& Tstep, T
 // printed; the naive roofline of Sec. II-A (with S_mode) bounds from below.
 template <class T>
 static T model_gemm(const Cfg& c, const T* th, int n_sm) {
+  // A CTA pair (cta_group::2, Sec. III-A.4) runs on two SMs: with fewer than
+  // two there is no pair to run it, so the configuration has no time (NaN,
+  // like any record the model cannot evaluate); the autotuners skip it.
+  if (c.g != 1 && n_sm < 2) return lift<T>(NAN);
   const i64 Kt = ceil_div(c.K, c.BK);
   const i64 tiles = cta_tiles(c.M, c.N, c.BM, c.BN, c.g);
   const i64 n_conc = (c.g == 1) ? n_sm : 2 * (n_sm / 2);
@@ -514,6 +518,7 @@ static double grouped_working_set(int G, const int32_t* Mg, int32_t N, int32_t K
 extern "C" double orc_grouped_predict(int G, const int32_t* Mg, int32_t N, int32_t K,
                                       const int32_t* BMg, const int32_t* BNg, int BK, int s, int g,
                                       int dtype, const double* theta, int n_sm) {
+  if (g != 1 && n_sm < 2) return NAN;   // no SM pair for a cta_group::2 launch
   const i64 n_conc = (g == 1) ? n_sm : 2 * (n_sm / 2);
   std::vector<double> busy(n_conc, 0.0);
   const double W = grouped_working_set(G, Mg, N, K, dtype);

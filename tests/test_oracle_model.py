@@ -399,3 +399,27 @@ def test_pair_tile_count_per_reading(reading):
         assert t3 == pytest.approx(t2, rel=1e-12)
     else:
         assert t3 - th[0] == pytest.approx(2 * step_part, rel=1e-12)
+
+
+def test_pairs_need_two_sms(reading):
+    # a cta_group::2 configuration has no time on one SM (no pair to run it);
+    # a one-SM configuration runs its 64 tiles one after another there, so
+    # T - T_launch is 64 times the one-wave value on 64 SMs (the stage term
+    # stays above the roofline floor in both)
+    th = PRIOR160_MEASURED if reading == 1 else PRIOR160
+    rows = [dict(M=1024, N=1024, K=512, BM=128, BN=128, BK=64, stages=4, cta_group=g, dtype=1) for g in (1, 2)]
+    c = cfgs(rows)
+    t1 = O.model_batch(c, th, 1)
+    assert np.isfinite(t1[0]) and np.isnan(t1[1])
+    assert np.all(np.isfinite(O.model_batch(c, th, 2)))
+    t64 = O.model_batch(c, th, 64)
+    assert t1[0] - th[0] == pytest.approx(64 * (t64[0] - th[0]), rel=1e-12)
+    # the autotuners skip pair configurations on one SM
+    MNK = np.array([[1024, 1024, 512], [4096, 4096, 4096], [16, 16384, 64]], dtype=np.int32)
+    pick, t = O.autotune(MNK, 1, th, 1)
+    assert np.all(pick[:, 4] == 1) and np.all(np.isfinite(t))
+    Mg = np.array([64, 1000, 3000], dtype=np.int32)
+    assert np.isnan(O.grouped_predict(Mg, 1024, 1024, [128] * 3, [128] * 3, 64, 4, 2, 1, th, 1))
+    assert np.isfinite(O.grouped_predict(Mg, 1024, 1024, [128] * 3, [128] * 3, 64, 4, 1, 1, th, 1))
+    tg, _, _, launch = O.grouped_autotune(Mg, 1024, 1024, 1, th, 1)
+    assert launch[2] == 1 and np.isfinite(tg)
