@@ -253,7 +253,9 @@ pm_status pm_grouped_gemm_run(int32_t G, const int32_t* M_host, int32_t N, int32
 /* Stage-model prediction T_hat (FP32 seconds) for n configurations (any
  * kind) on the GPU: Eqs. 2-8 for GEMM tiles with persistent-CTA waves and the
  * naive roofline as a floor; Eq. 16 for copy/triad; the TMA tile model for
- * TMA2D.  cfgs_dev: n pm_cfg; t_out_dev: n floats.  Async. */
+ * TMA2D.  cfgs_dev: n pm_cfg; t_out_dev: n floats.  A record the model cannot
+ * evaluate (a non-positive size, an unknown kind, dtype or cta_group, or a
+ * cta_group 2 pair when n_sm < 2: a pair needs two SMs) gets NaN.  Async. */
 pm_status pm_model_predict(const pm_cfg* cfgs_dev, int64_t n, const pm_params* theta_host, int32_t n_sm,
                            float* t_out_dev, void* stream);
 
@@ -321,7 +323,8 @@ pm_status pm_model_grad_noalloc(const pm_cfg* cfgs_dev, int64_t n, const pm_para
  * guidance): for each of n shapes (MNK_dev: n x {M,N,K} int32) evaluates the
  * model over the 180-point tile space of `dtype` and picks the fastest valid
  * configuration; ties go to the first in lexicographic (BM, BN, BK, stages,
- * cta_group) order.  picks_dev: n pm_cfg; t_pred_dev: n floats.  Async. */
+ * cta_group) order; with n_sm < 2 pairs (cta_group 2) are not candidates.
+ * picks_dev: n pm_cfg; t_pred_dev: n floats.  Async. */
 pm_status pm_autotune_pick(const int32_t* MNK_dev, int64_t n, int32_t dtype, const pm_params* theta_host,
                            int32_t n_sm, pm_cfg* picks_dev, float* t_pred_dev, void* stream);
 
@@ -329,7 +332,7 @@ pm_status pm_autotune_pick(const int32_t* MNK_dev, int64_t n, int32_t dtype, con
  * (the C9 reading of the grouped GEMM: per group tau_g = K_tiles T_step_g +
  * T_store_g, tiles listed group by group, tile t on worker t mod n_conc,
  * T_hat = T_launch + max_w sum tau).  Host arrays of G entries; *t_pred_host
- * in seconds.  Synchronises. */
+ * in seconds, NaN for a cta_group 2 launch when n_sm < 2.  Synchronises. */
 pm_status pm_grouped_predict(int32_t G, const int32_t* M_host, int32_t N, int32_t K, const int16_t* BM_host,
                              const int16_t* BN_host, int32_t BK, int32_t stages, int32_t cta_group, int32_t dtype,
                              const pm_params* theta_host, int32_t n_sm, float* t_pred_host, void* stream);

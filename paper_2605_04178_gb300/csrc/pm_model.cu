@@ -180,7 +180,9 @@ __device__ __forceinline__ void gemm_forward(const pm_cfg& c, const ThetaT<F>& t
   // CTA tiles: ceil(M/BM) ceil(N/BN) (literal); a pair covers 2 BM x BN (measured)
   const int64_t tiles = measured ? (int64_t)g * cdiv(c.M, (int64_t)g * c.BM) * cdiv(c.N, c.BN)
                                  : cdiv(c.M, c.BM) * cdiv(c.N, c.BN);
-  const int64_t n_conc = g == 1 ? n_sm : 2 * (n_sm / 2);
+  // (pairs on fewer than two SMs are rejected by the callers; the guard keeps
+  // the division defined)
+  const int64_t n_conc = g == 1 ? n_sm : (n_sm >= 2 ? 2 * (n_sm / 2) : 1);
   int64_t waves;
   if (th.nc_nsm == n_sm && (uint64_t)tiles < 0x80000000ull) {
     const UDiv u = g == 1 ? th.nc[0] : th.nc[1];
@@ -369,10 +371,13 @@ __device__ __forceinline__ void probe_adjoint(const pm_cfg& c, const ThetaT<F>& 
   }
 }
 
-__device__ __forceinline__ bool cfg_sane(const pm_cfg& c) {
+// A record the model can evaluate on n_sm SMs; a CTA pair (cta_group 2)
+// needs two SMs (Sec. III-A.4), so on one SM a pair record has no time.
+__device__ __forceinline__ bool cfg_sane(const pm_cfg& c, int n_sm) {
   if (c.kind == PM_KIND_GEMM)
     return c.M > 0 && c.N > 0 && c.K > 0 && c.BM > 0 && c.BN > 0 && c.BK > 0 && c.stages > 0 &&
-           (c.cta_group == 1 || c.cta_group == 2) && c.dtype >= 0 && c.dtype <= 2 && (c.tmem_a == 0 || c.tmem_a == 1);
+           (c.cta_group == 1 || (c.cta_group == 2 && n_sm >= 2)) && c.dtype >= 0 && c.dtype <= 2 &&
+           (c.tmem_a == 0 || c.tmem_a == 1);
   if (c.kind == PM_KIND_COPY || c.kind == PM_KIND_TRIAD) return c.M > 0;
   if (c.kind == PM_KIND_TMA2D) return c.M > 0 && c.N > 0 && c.BM > 0 && c.BN > 0;
   return false;
@@ -396,7 +401,7 @@ __global__ void __launch_bounds__(256, 6) model_predict_kernel(const pm_cfg* __r
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     const pm_cfg c = load_cfg(cfgs + i);
     float t;
-    if (!cfg_sane(c)) {
+    if (!cfg_sane(c, n_sm)) {
       t = __int_as_float(0x7fc00000);
     } else if (c.kind == PM_KIND_GEMM) {
       GemmFwd f;
@@ -447,7 +452,7 @@ __global__ void __launch_bounds__(kGradThreads, grad_min_blocks<F>()) model_grad
 #pragma unroll
     for (int j = 0; j < 16; ++j) d[j] = F(0);
     F T;
-    if (!cfg_sane(c)) {
+    if (!cfg_sane(c, n_sm)) {
       T = (F)__int_as_float(0x7fc00000);
     } else if (c.kind == PM_KIND_GEMM) {
       GemmFwdT<F> f;
@@ -535,7 +540,7 @@ __global__ void __launch_bounds__(kTuneThreads) autotune_kernel(const int32_t* _
     int BM = 0, BN = 0, BK = 0, s = 0, g = 0;
     if (t < 180) {
       decode_tile(t, dt, BM, BN, BK, s, g);
-      if (tile_valid(BM, BN, BK, s, g, dt) && c.M > 0 && c.N > 0 && c.K > 0) {
+      if (tile_valid(BM, BN, BK, s, g, dt) && (g == 1 || n_sm >= 2) && c.M > 0 && c.N > 0 && c.K > 0) {
         c.BM = (int16_t)BM; c.BN = (int16_t)BN; c.BK = (int16_t)BK;
         c.stages = (int8_t)s; c.cta_group = (int8_t)g;
         GemmFwd f;
@@ -598,7 +603,7 @@ __global__ void __launch_bounds__(kTuneThreads) autotune_topk_kernel(const int32
     int BM = 0, BN = 0, BK = 0, s = 0, g = 0;
     if (t < 180) {
       decode_tile(t, dt, BM, BN, BK, s, g);
-      if (tile_valid(BM, BN, BK, s, g, dt) && c.M > 0 && c.N > 0 && c.K > 0) {
+      if (tile_valid(BM, BN, BK, s, g, dt) && (g == 1 || n_sm >= 2) && c.M > 0 && c.N > 0 && c.K > 0) {
         c.BM = (int16_t)BM; c.BN = (int16_t)BN; c.BK = (int16_t)BK;
         c.stages = (int8_t)s; c.cta_group = (int8_t)g;
         GemmFwd f;
@@ -740,7 +745,7 @@ __global__ void __launch_bounds__(kGroupThreads) grouped_tune_kernel(const int32
   }
   any_invalid = __syncthreads_or(any_invalid);
   const float t = grouped_makespan(tau, tiles, off, red, G, g == 1 ? n_sm : 2 * (n_sm / 2));
-  if (threadIdx.x == 0) out_t[combo] = any_invalid ? INFINITY : th.v[0] + t;
+  if (threadIdx.x == 0) out_t[combo] = (any_invalid || (g != 1 && n_sm < 2)) ? INFINITY : th.v[0] + t;
 }
 
 // Stage-model makespan of one grouped launch with given per-group tiles
@@ -768,7 +773,7 @@ __global__ void __launch_bounds__(kGroupThreads) grouped_predict_kernel(const in
   }
   __syncthreads();
   const float t = grouped_makespan(tau, tiles, off, red, G, g == 1 ? n_sm : 2 * (n_sm / 2));
-  if (threadIdx.x == 0) out_t[0] = th.v[0] + t;
+  if (threadIdx.x == 0) out_t[0] = (g != 1 && n_sm < 2) ? __int_as_float(0x7fc00000) : th.v[0] + t;
 }
 
 static std::atomic<int> g_reading{PM_READING_LITERAL};

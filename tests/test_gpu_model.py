@@ -221,3 +221,42 @@ def test_grouped_predict_matches_oracle(lib, reading):
         t_g = lib.pm_grouped_predict(Mg, 4096, 4096, bm, bn, *launch, 1, th, N_SM)
         t_o = O.grouped_predict(Mg, 4096, 4096, bm, bn, *launch, 1, th, N_SM)
         assert t_g == pytest.approx(t_o, rel=1e-5)
+
+
+def test_pairs_on_fewer_than_two_sms(lib, reading):
+    # one SM: pair records (cta_group 2) are NaN and never picked, as in the
+    # oracle; one-SM records match it (every tile its own wave).  Three SMs:
+    # one-SM tiles divide by 3, pairs by 2 (the invariant-divisor path)
+    th = theta32()
+    c = random_cfgs(2000, seed=77, strategy_b=True)
+    n = len(c["M"])
+    dev = lib.cfg_tensor(c)
+    out = torch.empty(n, dtype=torch.float32, device="cuda")
+    pair = c["cta_group"] == 2
+    for n_sm in (1, 3):
+        lib.pm_model_predict(dev, n, th, n_sm, out)
+        t_gpu = out.cpu().numpy().astype(np.float64)
+        t_orc = O.model_batch(c, th, n_sm)
+        if n_sm == 1:
+            assert pair.any() and np.all(np.isnan(t_gpu[pair])) and np.all(np.isnan(t_orc[pair]))
+            ok = ~pair
+        else:
+            ok = np.ones(n, dtype=bool)
+        assert np.all(np.abs(t_gpu[ok] - t_orc[ok]) <= 1e-5 * t_orc[ok])
+    MNK = np.array([[512, 512, 512], [4096, 1024, 2048], [16, 16384, 64]], dtype=np.int32)
+    for n_sm in (1, 3):
+        picks = torch.empty(3 * 24, dtype=torch.uint8, device="cuda")
+        t = torch.empty(3, dtype=torch.float32, device="cuda")
+        lib.pm_autotune_pick(torch.from_numpy(MNK.ravel()).cuda(), 3, 1, th, n_sm, picks, t)
+        p = picks.cpu().numpy().view(lib.CFG_DTYPE)
+        _, t_o = O.autotune(MNK, 1, th, n_sm)
+        if n_sm == 1:
+            assert np.all(p["cta_group"] == 1)
+        assert np.all(np.abs(t.cpu().numpy() - t_o) <= 1e-5 * t_o)
+    Mg = S.grouped_m(16, 3)
+    t_g, _, _, launch_g = lib.pm_grouped_autotune(Mg, 1024, 1024, 1, th, 1)
+    t_o, _, _, launch_o = O.grouped_autotune(Mg, 1024, 1024, 1, th, 1)
+    assert launch_g[2] == 1 and launch_o[2] == 1 and t_g == pytest.approx(t_o, rel=1e-5)
+    bm = [128] * len(Mg)
+    assert np.isnan(lib.pm_grouped_predict(Mg, 1024, 1024, bm, bm, 64, 4, 2, 1, th, 1))
+    assert np.isnan(O.grouped_predict(Mg, 1024, 1024, bm, bm, 64, 4, 2, 1, th, 1))
