@@ -123,8 +123,9 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def _cpu_gemm_rate(A, B, rows_per_step: int, steps: int, warmup: int):
-    """Oracle FP64 GEMM on sampled rows; returns (TFLOP/s, seconds, rows)."""
+def _cpu_gemm_rate(A, B, rows_per_step: int, steps: int, warmup: int, keep: bool = True):
+    """Oracle FP64 GEMM on sampled rows; returns (TFLOP/s, seconds, rows, the rows computed or None
+    when keep is False: a long reference run would otherwise hold every step's rows)."""
     import numpy as np
 
     import oracle as O
@@ -136,10 +137,12 @@ def _cpu_gemm_rate(A, B, rows_per_step: int, steps: int, warmup: int):
     out = []
     for i in range(steps):
         r0 = (i * rows_per_step) % (Mr - rows_per_step + 1)
-        out.append(O.gemm_f64(A[r0:r0 + rows_per_step], B))
+        c = O.gemm_f64(A[r0:r0 + rows_per_step], B)
+        if keep:
+            out.append(c)
     dt = time.perf_counter() - t0
     flops = 2.0 * rows_per_step * B.shape[0] * B.shape[1] * steps
-    return flops / dt / 1e12, dt, rows_per_step * steps, np.concatenate(out)
+    return flops / dt / 1e12, dt, rows_per_step * steps, (np.concatenate(out) if keep else None)
 
 
 def run_reference(args):
@@ -160,13 +163,16 @@ def run_reference(args):
     n_rows = rows_per_step * 64
     B = S.matrix(SEED, K, N, "normal", M * K)
     A = S.matrix(SEED, n_rows, K, "normal", 0)          # the first n_rows rows of A
-    tflops, dt, rows, _ = _cpu_gemm_rate(A, B, rows_per_step, args.steps, args.warmup)
+    tflops, dt, rows, _ = _cpu_gemm_rate(A, B, rows_per_step, args.steps, args.warmup, keep=False)
     cores = os.cpu_count()
     line = {
         "impl": "reference", "metric": METRIC, "value": tflops, "unit": "TFLOP/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "gemm_8192^3_rows_sample", "M": M, "N": N, "K": K, "rows_per_step": rows_per_step},
+        # the GPU arm's workload, computed by the oracle on a row sample of the same operands
+        "config": {"workload": "bf16_gemm_8192^3_model_autotuned", "M": M, "N": N, "K": K,
+                   "inputs": "A,B ~ N(0,1) seed 2 (the same FP32 matrices), FP64 arithmetic",
+                   "rows_per_step": rows_per_step, "parallelism": "single"},
         "cpu_baseline": {"value": tflops, "unit": "TFLOP/s", "cores": cores, "kind": "oracle",
                          "sample": "%d rows x 8192 x 8192 FP64 per step (C = A.B definition, OpenMP)" % rows_per_step,
                          "cpu_model": _cpu_model()},
