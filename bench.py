@@ -145,6 +145,21 @@ def _cpu_gemm_rate(A, B, rows_per_step: int, steps: int, warmup: int, keep: bool
     return flops / dt / 1e12, dt, rows_per_step * steps, (np.concatenate(out) if keep else None)
 
 
+def _omp_threads(n=None):
+    """Sets (when n is given) and returns the OpenMP thread count of the
+    oracle's runtime (libgomp); None when libgomp cannot be loaded.  The
+    torch.distributed launcher exports OMP_NUM_THREADS=1 to every rank, which
+    would leave the one working rank of the reference arm on one core."""
+    import ctypes
+    try:
+        gomp = ctypes.CDLL("libgomp.so.1")
+    except OSError:
+        return None
+    if n is not None:
+        gomp.omp_set_num_threads(int(n))
+    return int(gomp.omp_get_max_threads())
+
+
 def run_reference(args):
     rank, world, _ = _dist_env()
     if world > 1:
@@ -163,8 +178,9 @@ def run_reference(args):
     n_rows = rows_per_step * 64
     B = S.matrix(SEED, K, N, "normal", M * K)
     A = S.matrix(SEED, n_rows, K, "normal", 0)          # the first n_rows rows of A
+    threads = _omp_threads(os.cpu_count() or 1)
     tflops, dt, rows, _ = _cpu_gemm_rate(A, B, rows_per_step, args.steps, args.warmup, keep=False)
-    cores = os.cpu_count()
+    cores = threads or os.cpu_count()
     line = {
         "impl": "reference", "metric": METRIC, "value": tflops, "unit": "TFLOP/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True,
