@@ -444,12 +444,14 @@ def run_gpu(args):
             line["model_mae_pct_holdout_measured_reading"] = {k: round(v["mae_pct"], 2)
                                                               for k, v in rep["mae_holdout"].items()}
         line.update(extra)
-        if not args.skip_cpu:
-            # the oracle on the host cores: rows 0..47 of the same product, which
-            # also gives the GPU result's error on those rows
+        if not args.skip_cpu and world == 1:
+            # the oracle on the host cores (one GPU only): rows 0..47 of the same
+            # product, which also gives the GPU result's error on those rows
+            threads = _omp_threads(os.cpu_count() or 1)
             tfl, dt, rows, ref = _cpu_gemm_rate(A_h[:64], B_h, 8, 6, 1)
             err = float(np.linalg.norm(C_h[:48] - ref) / np.linalg.norm(ref))
-            line["cpu_baseline"] = {"value": tfl, "unit": "TFLOP/s", "cores": os.cpu_count(), "kind": "oracle",
+            line["cpu_baseline"] = {"value": tfl, "unit": "TFLOP/s", "cores": threads or os.cpu_count(),
+                                    "kind": "oracle",
                                     "sample": "6 x 8 rows of the 8192^3 GEMM in FP64 (%.1f s)" % dt,
                                     "cpu_model": _cpu_model()}
             line["bf16_rel_frobenius_error_rows0_47"] = err
