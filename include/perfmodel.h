@@ -310,12 +310,15 @@ pm_status pm_gemm_autotune(const pm_cfg* shape, int32_t k, const pm_params* thet
  * fixed 557,056-byte array inside the library, present on every GPU that
  * loads it until the process exits.  At most 1,048,576 configurations per
  * call; larger n returns PM_ENOMEM with a message and launches nothing.
- * The first call on a device looks up that array's device address
- * (cudaGetSymbolAddress, no allocation); make that first call outside any
- * stream capture.  All calls share the array: calls whose kernels overlap on
- * the GPU race and must be serialised by the caller (one stream, or events).
- * Nothing needs clearing between calls: each call writes every partial
- * record it reads.  Async. */
+ * It launches the same grid as pm_model_grad, so its output is bit-identical
+ * to pm_model_grad's for the same inputs.  The first call on a device looks
+ * up that array's device address (cudaGetSymbolAddress, no allocation) and
+ * caches it; make that first call outside any stream capture, and call
+ * pm_shutdown before a device reset (it forgets the cached address).  All
+ * calls share the array: calls whose kernels overlap on the GPU race and must
+ * be serialised by the caller (one stream, or events).  Nothing needs
+ * clearing between calls: each call writes every partial record it reads.
+ * Async. */
 pm_status pm_model_grad_noalloc(const pm_cfg* cfgs_dev, int64_t n, const pm_params* theta_host, int32_t n_sm,
                                 const float* t_meas_dev, double* out_dev, void* stream);
 
@@ -405,11 +408,15 @@ pm_status pm_segment_predict(const pm_segment* segs_dev, int64_t n, const pm_par
 /* Text of the last error on this host thread (valid until the next call). */
 const char* pm_last_error(void);
 
-/* Releases what the library holds beyond the static watchdog word: its pool
+/* Releases what the library holds beyond its static device arrays: its pool
  * of concurrent-probe streams on every device, and the calling thread's
- * host-transfer pipeline (streams, events) and TMA descriptor caches.  Work
- * already queued on those streams completes.  Any later call re-creates what
- * it needs.  Always PM_OK. */
+ * host-transfer pipeline (streams, events) and TMA descriptor caches; it also
+ * forgets the cached device addresses of the static arrays (the watchdog
+ * word, the allocation-free gradient's scratch) and the cached SM counts.
+ * Call it before a device reset (cudaDeviceReset reloads the module, so a
+ * cached address would go stale).  Work already queued on those streams
+ * completes.  Any later call re-creates or looks up what it needs.  Always
+ * PM_OK. */
 pm_status pm_shutdown(void);
 
 /* Reads (and with clear != 0, clears) the device watchdog word of the current

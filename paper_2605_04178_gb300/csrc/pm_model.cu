@@ -1089,8 +1089,11 @@ extern "C" pm_status pm_grouped_gemm_autotune(int32_t G, const int32_t* M_host, 
 // per-block partial sums live in a fixed array compiled into this library,
 // resident on every GPU that loads it for the life of the process.
 //
-// Capacity: kGradStaticRecords block records of 17 doubles (557,056 bytes),
-// one block of kGradThreads threads per record, so at most
+// Capacity: the call launches the same grid as pm_model_grad (grad_blocks(n):
+// at most four blocks per SM, one partial record of 17 doubles each), so its
+// partial sums are added in the same order and its output is bit-identical to
+// pm_model_grad's.  The array holds kGradStaticRecords records (557,056
+// bytes), enough for GPUs of up to 1024 SMs; batches are limited to
 // kGradStaticRecords * kGradThreads = 1,048,576 configurations per call.
 // Every record a call reads is first written by that call, so nothing has to
 // be cleared between calls; two calls whose kernels overlap on a GPU share the
@@ -1106,6 +1109,12 @@ static std::mutex g_grad_scratch_mu;
 // Device address of g_grad_scratch for the current device.  In host code the
 // array's name is only a host-side stand-in, so the address is looked up once
 // per device with that device current.
+// Forgets the cached addresses (pm_shutdown; a device reset reloads the module).
+void clear_grad_scratch_cache() {
+  std::lock_guard<std::mutex> lk(g_grad_scratch_mu);
+  for (auto& p : g_grad_scratch_ptr) p = nullptr;
+}
+
 static pm_status grad_scratch_address(double** out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
@@ -1136,7 +1145,9 @@ extern "C" pm_status pm_model_grad_noalloc(const pm_cfg* cfgs_dev, int64_t n, co
   double* scratch = nullptr;
   pm_status st = grad_scratch_address(&scratch);
   if (st != PM_OK) return st;
-  const int blocks = (int)((n + kGradThreads - 1) / kGradThreads);
+  const int blocks = grad_blocks(n);
+  PM_REQUIRE(blocks <= kGradStaticRecords, PM_ENOMEM, "%d partial records exceed the %d the array holds", blocks,
+             kGradStaticRecords);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   model_grad_kernel<float><<<blocks, kGradThreads, 0, s>>>(cfgs_dev, n, to_theta(theta_host, n_sm), n_sm, t_meas_dev, scratch);
   st = launch_status("model_grad_kernel");

@@ -50,6 +50,20 @@ unsigned int* watchdog_word() {
   return g_wd_ptr[dev];
 }
 
+// The allocation-free gradient's scratch address cache (pm_model.cu).
+void clear_grad_scratch_cache();
+
+// Forget the per-device addresses of the library's static device arrays and
+// the cached SM counts; the next call looks them up again.  A device reset
+// reloads the module, after which a cached address would be stale.
+void clear_device_address_caches() {
+  std::lock_guard<std::mutex> lk(g_mu);
+  for (int d = 0; d < kMaxDevices; ++d) {
+    g_wd_ptr[d] = nullptr;
+    g_sm_count[d] = 0;
+  }
+}
+
 unsigned long long watchdog_limit_ns() {
   static unsigned long long v = [] {
     const char* s = getenv("PM_WATCHDOG_MS");
@@ -179,5 +193,7 @@ extern "C" pm_status pm_shutdown(void) {
   pm::release_stream_pool();
   pm::release_host_pipe_this_thread();
   pm::clear_tmap_caches_this_thread();
+  pm::clear_device_address_caches();
+  pm::clear_grad_scratch_cache();
   return PM_OK;
 }

@@ -15,8 +15,12 @@ FIELDS = C.FIELDS
 
 
 def table(theta):
+    """The calibration table's configurations: config 3 (every valid BF16 and
+    FP8 tile at M = N = K in {1024 .. 16384}, 1,445 rows), config 1 (FP32
+    512^3 over its 55 tiles) and config 2 (copy and triad 2^20 .. 2^30, the
+    five TMA tiles), with the oracle's times under theta as the targets."""
     rows = []
-    for s in (1024, 4096, 16384):
+    for s in (1024, 2048, 4096, 8192, 16384):
         for dt in (1, 2):
             for t in S.tile_space(dt):
                 if O.cfg_valid(*t, dt):
@@ -24,10 +28,6 @@ def table(theta):
     for t in S.tile_space(0):
         if O.cfg_valid(*t, 0):
             rows.append(dict(zip(FIELDS, (512, 512, 512, *t, 0, 0))))
-    for dt in (0, 1, 2):                               # TMEM strategy B rows
-        for t in S.tile_space(dt):
-            if O.cfg_valid(*t, dt, 1):
-                rows.append(dict(zip(FIELDS, (4096, 4096, 4096, *t, dt, 0, 1))))
     for k in range(20, 31):
         rows.append(dict(M=2 ** k, N=0, K=0, BM=0, BN=0, BK=0, stages=0, cta_group=0, dtype=0, kind=1))
         rows.append(dict(M=2 ** k, N=0, K=0, BM=0, BN=0, BK=0, stages=0, cta_group=0, dtype=0, kind=2))
@@ -57,19 +57,59 @@ def test_prior_matches_oracle_prior():
     assert np.allclose(C.prior_theta(N_SM), O.prior_theta(N_SM), rtol=0, atol=0)
 
 
-def test_fit_recovers_generating_parameters():
-    prior = C.prior_theta(N_SM)
-    noise = S.normal(5, 16).astype(np.float64)
-    truth = prior * np.exp(0.3 * noise)
-    truth[15] = 0.4                      # keep alpha's clamp inactive at every depth
+# Parameters the table does not determine one by one at the generating
+# point: TMEM read and write bandwidth enter every strategy-A K-step only as
+# D (1/BW_rd + 1/BW_wr) (Eq. 2), so only that sum is fixed; under the
+# measured reading the ring bound of Eq. 8 sets every K-step of the table at
+# the printed priors, so alpha's c_alpha (Eq. 7) is not seen at all.
+UNIDENTIFIABLE = {0: {10, 11}, 1: {10, 11, 15}}
+
+
+def identifiable(cols, theta):
+    """Parameters j whose direction has no component in the null space of
+    the Jacobian d ln T_hat / d ln theta (singular values below 1e-6 of the
+    largest) at theta."""
+    t, g = O.model_batch(cols, theta, N_SM, grad=True)
+    J = g * theta[None, :] / t[:, None]
+    _, sv, Vt = np.linalg.svd(J, full_matrices=False)
+    null = Vt[sv < 1e-6 * sv[0]]
+    proj = np.sqrt((null ** 2).sum(0)) if len(null) else np.zeros(16)
+    return proj < 1e-6
+
+
+def test_fit_recovers_generating_parameters(reading):
+    # Targets from a known theta* (the printed priors); the fit starts from
+    # theta* exp(N(0, 0.3^2)) (seed 5) and must return ln theta* within 1e-3
+    # on every identifiable parameter (Sec. III-D: parameters fitted to
+    # measured times; here the times are the model's own, so the fit must
+    # find the generating point, not another one that fits as well).
+    truth = C.prior_theta(N_SM, reading=reading)
+    rows, cols = table(truth)
+    assert len(rows) == 1445 + 55 + 27
+    ident = identifiable(cols, truth)
+    assert set(np.where(~ident)[0]) == UNIDENTIFIABLE[reading]
+    t_meas = np.array([r["t"] for r in rows])
+    start = truth * np.exp(0.3 * S.normal(5, 16).astype(np.float64))
+    theta, trace = C.fit(lambda th: OracleLoss.apply(th, cols, t_meas), start, reg=0.0)
+    err = np.abs(np.log(theta) - np.log(truth))
+    assert np.all(err[ident] <= 1e-3), dict(zip(np.where(ident)[0], err[ident]))
+    # the unidentified combination is still fitted: 1/BW_rd + 1/BW_wr
+    assert 1 / theta[10] + 1 / theta[11] == pytest.approx(1 / truth[10] + 1 / truth[11], rel=1e-6)
+    pred = O.model_batch(cols, theta, N_SM)
+    assert C.mae_by_family(rows, pred)["all"]["mae_pct"] < 1e-6
+
+
+def test_fit_leaves_dead_region_of_eq16():
+    # A start with B_sus above B_peak: Eq. 16's blend then never beats the
+    # B_peak floor, so (literal reading) B_sus and w0 have no gradient.  The
+    # fit's ordering penalty moves it out, after which the data fix both.
+    truth = C.prior_theta(N_SM)
     rows, cols = table(truth)
     t_meas = np.array([r["t"] for r in rows])
-    theta, trace = C.fit(lambda th: OracleLoss.apply(th, cols, t_meas), prior, reg=0.0, iters=600)
-    assert trace[-1] < 1e-3 * trace[0]
-    pred = O.model_batch(cols, theta, N_SM)
-    assert np.max(np.abs(pred - t_meas) / t_meas) < 0.02
-    mae = C.mae_by_family(rows, pred)
-    assert mae["all"]["mae_pct"] < 0.5
+    start = truth.copy()
+    start[1], start[2] = 1.4 * truth[2], 0.9 * truth[2]
+    theta, _ = C.fit(lambda th: OracleLoss.apply(th, cols, t_meas), start, reg=0.0)
+    assert abs(np.log(theta[1] / truth[1])) <= 1e-3 and abs(np.log(theta[3] / truth[3])) <= 1e-3
 
 
 def test_split_is_seeded_and_disjoint():

@@ -38,14 +38,42 @@ def test_stage_model_loss_autograd(lib):
     r = np.log(t_true) - np.log(t_meas.astype(np.float64))
     scale = (2.0 / len(r)) * np.sum(np.abs(r[:, None] * gi / t_true[:, None]), axis=0)
     assert np.all(np.abs(theta.grad.numpy() - g_o) <= 1e-4 * scale + 1e-30)
-    # central difference in ln(theta) through the GPU forward only
-    phi = np.log(th)
-    for j in (0, 5, 7, 12, 15):
-        h = 1e-3
+    assert np.all(np.isfinite(theta.grad.numpy()))
+
+
+def test_adjoint_matches_central_differences_all_components(lib, reading):
+    # Central differences of the GPU loss (the all-FP64 objective) in every
+    # ln theta_j against the adjoint kernel's gradient.  Rows that sit within
+    # h of a max() kink in some direction are left out (the oracle finds them
+    # by second differences, as its own gradient test does): across a kink
+    # the two one-sided slopes differ and a central difference averages them.
+    from paper_2605_04178_gb300 import calibrate as C
+    rows, cols = _rows(5000, 63)
+    th = C.prior_theta(N_SM).astype(np.float32).astype(np.float64)
+    phi, h = np.log(th), 1e-4
+    t0 = O.model_batch(cols, th, N_SM)
+    smooth = np.isfinite(t0)
+    for j in range(16):
+        tp = O.model_batch(cols, np.exp(phi + h * np.eye(16)[j]), N_SM)
+        tm = O.model_batch(cols, np.exp(phi - h * np.eye(16)[j]), N_SM)
+        second = np.abs((tp - t0) - (t0 - tm))
+        slope = np.abs(tp - tm) / (2 * h)
+        smooth &= (second <= 1e-9 * t0) | (second <= 10 * h * h * slope)
+    assert smooth.mean() > 0.8
+    keep = [r for r, m in zip(rows, smooth) if m]
+    t_meas = t0[smooth] * np.exp(0.2 * (S.uniform01_f64(64, len(keep)) - 0.5))
+    for r, t in zip(keep, t_meas):
+        r["t"] = float(t)
+    obj = C.GpuObjective(keep, N_SM)
+    theta = torch.tensor(th, dtype=torch.float64, requires_grad=True)
+    obj(theta).backward()
+    an = theta.grad.numpy() * th                      # dL / d ln theta_j
+    gscale = np.max(np.abs(an))
+    for j in range(16):
         Lp = float(obj(torch.tensor(np.exp(phi + h * np.eye(16)[j]))))
         Lm = float(obj(torch.tensor(np.exp(phi - h * np.eye(16)[j]))))
         fd = (Lp - Lm) / (2 * h)
-        assert fd == pytest.approx(theta.grad.numpy()[j] * th[j], rel=5e-2, abs=1e-6)
+        assert abs(fd - an[j]) <= 1e-3 * abs(an[j]) + 1e-9 * gscale, (j, fd, an[j])
 
 
 def test_gpu_fit_lowers_loss(lib):

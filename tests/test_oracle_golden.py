@@ -2,6 +2,7 @@
 paper prints (tests/golden/paper_printed_values.json, each with its
 citation).  The priors are the paper's printed values converted to SI units
 with a 1.9 GHz clock; these tests check the conversion and every range."""
+import importlib.util
 import json
 import os
 
@@ -84,3 +85,33 @@ def test_worked_example_is_only_banded():
     t = float(O.model_batch(cfg, th, w["n_sm_b200"])[0]) * 1e3
     assert w["measured_ms"] / 3 < t < w["measured_ms"] * 3
     assert abs(w["predicted_ms"] / w["measured_ms"] - 1) < 0.02       # the printed 1.8 % error
+
+
+def _hand_script():
+    path = os.path.join(os.path.dirname(__file__), "golden", "hand_eval.py")
+    spec = importlib.util.spec_from_file_location("hand_eval", path)
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    return mod
+
+
+def test_hand_rows_file_is_current():
+    # the stored hand evaluations are exactly what the committed script writes
+    h = _hand_script()
+    stored = json.load(open(h.OUT))
+    assert json.loads(json.dumps(h.compute())) == stored
+
+
+def test_hand_script_reproduces_the_printed_golden_row():
+    # the independent transcription gives the golden values printed with the
+    # model's definition (seven significant digits): FP32 512^3 1.438600e-05 s,
+    # BF16/FP8 8192^3, BF16 16384^3, copy/triad 2^30 and copy 2^20
+    printed = [1.438600e-05, 6.278955e-04, 3.385809e-04, 6.608431e-03, 1.268226e-03, 1.899839e-03, 6.067389e-06]
+    got = _hand_script().compute()["config_times"]["literal"]
+    assert got == pytest.approx(printed, rel=5e-7)
+
+
+@pytest.mark.parametrize("reading", [0, 1])
+def test_oracle_prior_is_the_hand_scripts_printed_prior(reading):
+    h = _hand_script()
+    assert np.array_equal(O.prior_theta(160, F, reading), np.array(h.printed_prior(160, F, reading)))

@@ -7,6 +7,8 @@ Sec. III-A.4), the model's dimensional homogeneity, monotonicity, the
 roofline lower bound, central differences, and brute-force search.
 """
 import itertools
+import json
+import os
 
 import numpy as np
 import pytest
@@ -28,58 +30,52 @@ def one(theta, n_sm=160, **r):
 PRIOR160 = O.prior_theta(160)
 PRIOR160_MEASURED = O.prior_theta(160, reading=O.READING_MEASURED)
 
-CONFIG_ROWS = [
-    dict(M=512, N=512, K=512, BM=128, BN=128, BK=32, stages=2, cta_group=1, dtype=0),
-    dict(M=8192, N=8192, K=8192, BM=128, BN=256, BK=64, stages=4, cta_group=1, dtype=1),
-    dict(M=8192, N=8192, K=8192, BM=128, BN=256, BK=128, stages=4, cta_group=1, dtype=2),
-    dict(M=16384, N=16384, K=16384, BM=128, BN=128, BK=64, stages=2, cta_group=1, dtype=1),
-    dict(M=2 ** 30, kind=1),
-    dict(M=2 ** 30, kind=2),
-    dict(M=2 ** 20, kind=1),
-]
-# Hand evaluations of Eqs. 2-8 with the prior parameters, n_SM = 160 and a
-# 1.9 GHz clock for the cycle counts, done independently of this code.
+# Hand evaluations of Eqs. 2-8 and Eq. 16 with the printed priors, n_SM = 160
+# and a 1.9 GHz clock for the cycle counts, written by an independent scalar
+# restatement of the model (tests/golden/hand_eval.py, which imports neither
+# the oracle nor the library) into tests/golden/hand_rows.json;
+# tests/test_oracle_golden.py checks that file is current.
+HAND = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "hand_rows.json")))
+CONFIG_ROWS = HAND["config_rows"]
 # Literal reading (L_mma once per K-step, alpha = 1 - 0.3/s, T_sync in Eqs. 7
-# and 8): config 1 has T_c = 4.290643e-07 s and T_io = 3.118298e-07 s per step.
+# and 8): the golden values printed with the model's definition (config 1 has
+# T_c = 4.290643e-07 s and T_io = 3.118298e-07 s per step).
 HAND_LITERAL = [1.438600e-05, 6.278955e-04, 3.385809e-04, 6.608431e-03, 1.268226e-03, 1.899839e-03, 6.067389e-06]
 # Measured reading (L_mma per instruction: 12, 4 and 4 per K-step in the first
 # three rows; alpha = 1 - 0.15/(s-1); T_sync once; B_TMA x rho(W); O_misc =
-# the ring bubble, T_step >= (T_tma + T_c + T_sync)/s).  With the prior's
-# per-SM B_TMA the ring binds in all four GEMM rows: config 1 has T_c =
-# 4.98538e-07 s, rho = 1.163209, T_tma = 1.546716e-06 s, Eq. 8 5.459064e-07 s
-# and the ring 1.046311e-06 s per K-step; the 8192^3 BF16 row 3.674625e-07 s
-# (Eq. 8) against 4.362411e-07 s (ring).
-HAND_MEASURED = [2.350406e-05, 7.738715e-04, 4.109904e-04, 1.616707e-02, 1.268226e-03, 1.899839e-03, 6.067389e-06]
+# the ring bubble, T_step >= (T_tma + T_c + T_sync)/s): from the hand script.
+HAND_MEASURED = HAND["config_times"]["measured"]
 
 
 @pytest.mark.parametrize("i", range(len(CONFIG_ROWS)))
 def test_hand_evaluated_rows(reading, i):
     th = PRIOR160 if reading == 0 else PRIOR160_MEASURED
-    expect = (HAND_LITERAL if reading == 0 else HAND_MEASURED)[i]
-    assert one(th, **CONFIG_ROWS[i]) == pytest.approx(expect, rel=2e-6)
+    if reading == 0:
+        # the printed golden row carries seven significant digits
+        assert one(th, **CONFIG_ROWS[i]) == pytest.approx(HAND_LITERAL[i], rel=2e-6)
+    expect = HAND["config_times"]["literal" if reading == 0 else "measured"][i]
+    assert one(th, **CONFIG_ROWS[i]) == pytest.approx(expect, rel=1e-12)
 
 
-# Load-bound rows (T_io > T_c) that pin the overlap law of Eq. 7: hand
-# evaluated as above with c_alpha = 0.9, so 1 - alpha = 0.225 / 0.15 at 4 / 6
-# stages (literal) and 0.3 / 0.18 (measured).  Under the measured reading the
-# TMA bandwidth carries the L2-residency factor rho = B_eff(W)/B_sus of
-# Eq. 16: the working set W = 2 (4096^2 x 2 B) + 4096^2 x 4 B = 2 w0, so
-# rho = 1 + (8/6.8 - 1) e^-2 = 1.023882697, T_tma = 9.7408007e-07 s and
-# T_step = 3.3959244e-07 s (4 stages) / 2.2270283e-07 s (6 stages), above the
-# ring bound (2.863851e-07 / 1.909234e-07 s), so Eq. 7 sets the step; with the
-# blend switched off (w0 <= 0, rho = 1) the same rows take the second values.
-LOAD_BOUND_ROWS = [dict(M=4096, N=4096, K=4096, BM=64, BN=64, BK=128, stages=s, cta_group=1, dtype=1) for s in (4, 6)]
-HAND_LOAD_BOUND = {0: [2.853060e-04, 2.234012e-04], 1: [3.033114e-04, 2.060593e-04]}
-HAND_LOAD_BOUND_NO_BLEND = {0: [2.853060e-04, 2.234012e-04], 1: [3.078003e-04, 2.087526e-04]}
+# Load-bound rows (T_io > T_c) that pin the overlap law of Eq. 7, from the
+# hand script with c_alpha = 0.9, so 1 - alpha = 0.225 / 0.15 at 4 / 6 stages
+# (literal) and 0.3 / 0.18 (measured).  Under the measured reading the TMA
+# bandwidth carries the L2-residency factor rho = B_eff(W)/B_sus of Eq. 16
+# (W = 2 w0 here, rho = 1.0239); with the blend switched off (w0 <= 0,
+# rho = 1) the same rows take the second values.
+LOAD_BOUND_ROWS = HAND["load_bound_rows"]
+HAND_LOAD_BOUND = {0: HAND["load_bound_times"]["literal"], 1: HAND["load_bound_times"]["measured"]}
+HAND_LOAD_BOUND_NO_BLEND = {0: HAND["load_bound_times_no_blend"]["literal"],
+                            1: HAND["load_bound_times_no_blend"]["measured"]}
 
 
 @pytest.mark.parametrize("i", range(2))
 def test_hand_evaluated_load_bound_rows(reading, i):
     th = (PRIOR160 if reading == 0 else PRIOR160_MEASURED).copy()
     th[15] = 0.9
-    assert one(th, **LOAD_BOUND_ROWS[i]) == pytest.approx(HAND_LOAD_BOUND[reading][i], rel=2e-6)
+    assert one(th, **LOAD_BOUND_ROWS[i]) == pytest.approx(HAND_LOAD_BOUND[reading][i], rel=1e-12)
     th[3] = 0.0
-    assert one(th, **LOAD_BOUND_ROWS[i]) == pytest.approx(HAND_LOAD_BOUND_NO_BLEND[reading][i], rel=2e-6)
+    assert one(th, **LOAD_BOUND_ROWS[i]) == pytest.approx(HAND_LOAD_BOUND_NO_BLEND[reading][i], rel=1e-12)
 
 
 def test_l2_residency_of_tma_loads_closed_form(reading):
