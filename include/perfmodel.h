@@ -166,8 +166,29 @@ typedef struct {
   double median_s, p25_s, p75_s, min_s;   /* per-launch device time */
   double bytes;                           /* algorithmic bytes per launch */
   uint32_t final_index;                   /* PCHASE result */
-  uint32_t reserved;
-} pm_probe_result;
+  /* Clock record of the timed region (Sec. V-B protocol: clocks and throttle
+   * state recorded with every measurement): SM clock read through NVML just
+   * before the first timed launch and just after the last one completed, the
+   * maximum SM clock, and the OR of the NVML clock event reasons seen at
+   * both reads (0x4 software power cap, 0x8 hardware slowdown, 0x20
+   * software thermal slowdown, 0x40 hardware thermal slowdown, 0x80 power
+   * brake).  Zero when NVML cannot be read. */
+  uint32_t sm_mhz_begin, sm_mhz_end, sm_max_mhz;
+  uint64_t clock_reasons;
+} pm_probe_result;                        /* 64 bytes */
+
+/* One read-only NVML sample of the current CUDA device (matched by PCI bus
+ * id): SM, maximum SM and memory clocks, board power, clock event reasons
+ * (bitmask as in pm_probe_result), and the host's monotonic time.  Changes
+ * no GPU setting.  PM_EUNSUPPORTED when the driver's NVML library cannot be
+ * loaded or does not know the device. */
+typedef struct {
+  uint32_t sm_mhz, sm_max_mhz, mem_mhz, power_mw;
+  uint64_t reasons;
+  double host_time_s;
+} pm_clock;                               /* 32 bytes */
+
+pm_status pm_clock_sample(pm_clock* out);
 
 /* Concurrent-stream interference probe (Sec. III-A.6: N_c concurrent streams
  * add (N_c - 1) tau_c to the single-stream time).  Launches the probe

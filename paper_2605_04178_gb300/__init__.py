@@ -66,17 +66,40 @@ class pm_probe_args(ctypes.Structure):
 class pm_probe_result(ctypes.Structure):
     _fields_ = [("median_s", ctypes.c_double), ("p25_s", ctypes.c_double), ("p75_s", ctypes.c_double),
                 ("min_s", ctypes.c_double), ("bytes", ctypes.c_double), ("final_index", ctypes.c_uint32),
-                ("reserved", ctypes.c_uint32)]
+                ("sm_mhz_begin", ctypes.c_uint32), ("sm_mhz_end", ctypes.c_uint32), ("sm_max_mhz", ctypes.c_uint32),
+                ("clock_reasons", ctypes.c_uint64)]
 
 
-assert ctypes.sizeof(pm_cfg) == 24 and ctypes.sizeof(pm_probe_args) == 56 and ctypes.sizeof(pm_probe_result) == 48
+class pm_clock(ctypes.Structure):
+    _fields_ = [("sm_mhz", ctypes.c_uint32), ("sm_max_mhz", ctypes.c_uint32), ("mem_mhz", ctypes.c_uint32),
+                ("power_mw", ctypes.c_uint32), ("reasons", ctypes.c_uint64), ("host_time_s", ctypes.c_double)]
+
+
+assert ctypes.sizeof(pm_cfg) == 24 and ctypes.sizeof(pm_probe_args) == 56 and ctypes.sizeof(pm_probe_result) == 64
+assert ctypes.sizeof(pm_clock) == 32
+
+# NVML clock event reasons (bitmask of pm_clock.reasons / pm_probe_result.clock_reasons)
+CLOCK_REASONS = {0x1: "gpu_idle", 0x2: "applications_clocks_setting", 0x4: "sw_power_cap", 0x8: "hw_slowdown",
+                 0x10: "sync_boost", 0x20: "sw_thermal_slowdown", 0x40: "hw_thermal_slowdown",
+                 0x80: "hw_power_brake_slowdown", 0x100: "display_clock_setting"}
+
+
+def clock_reason_names(mask: int) -> list:
+    return [name for bit, name in sorted(CLOCK_REASONS.items()) if mask & bit]
+
+
+def _timing(res) -> dict:
+    """A harness result as a dict: device times, bytes, and the clock record of the timed region."""
+    return dict(median_s=res.median_s, p25_s=res.p25_s, p75_s=res.p75_s, min_s=res.min_s, bytes=res.bytes,
+                final_index=res.final_index, sm_mhz_begin=res.sm_mhz_begin, sm_mhz_end=res.sm_mhz_end,
+                sm_max_mhz=res.sm_max_mhz, clock_reasons=clock_reason_names(res.clock_reasons))
 
 # Every exported symbol of include/perfmodel.h
 EXPORTS = ("pm_probe_launch", "pm_probe_run", "pm_streams_run", "pm_gemm_operand_bytes", "pm_gemm_prepare", "pm_gemm_run",
            "pm_gemm_bench", "pm_gemm_host_workspace", "pm_gemm_host",
            "pm_grouped_gemm_run", "pm_model_predict", "pm_model_set_reading", "pm_model_reading", "pm_model_grad_workspace", "pm_model_grad", "pm_model_grad_f64", "pm_model_grad_noalloc",
            "pm_autotune_pick", "pm_autotune_topk", "pm_gemm_autotune", "pm_grouped_predict", "pm_grouped_autotune", "pm_grouped_gemm_autotune", "pm_segment_predict", "pm_last_error", "pm_device_status", "pm_shutdown",
-           "pm_watchdog_selftest", "pm_version")
+           "pm_watchdog_selftest", "pm_version", "pm_clock_sample")
 
 
 class PMError(RuntimeError):
@@ -126,6 +149,7 @@ def _load():
         "pm_grouped_gemm_autotune": [i32, P, i32, i32, ctypes.POINTER(pm_params), i32, i32, P, P, P, ctypes.c_int,
                                      ctypes.c_int, P, P, P, P, P, ctypes.POINTER(pm_probe_result)],
         "pm_device_status": [ctypes.c_int],
+        "pm_clock_sample": [ctypes.POINTER(pm_clock)],
         "pm_shutdown": [],
         "pm_model_set_reading": [i32],
         "pm_model_reading": [],
@@ -212,8 +236,7 @@ def pm_probe_run(args: pm_probe_args, buf0, buf1=None, buf2=None, warmup=10, rep
     res = pm_probe_result()
     _check(_lib.pm_probe_run(ctypes.byref(args), _ptr(buf0), _ptr(buf1), _ptr(buf2), int(warmup), int(reps),
                              _stream(stream), ctypes.byref(res)), "pm_probe_run")
-    return dict(median_s=res.median_s, p25_s=res.p25_s, p75_s=res.p75_s, min_s=res.min_s, bytes=res.bytes,
-                final_index=res.final_index)
+    return _timing(res)
 
 
 def pm_streams_run(args: pm_probe_args, bufs0, bufs1=None, bufs2=None, warmup=10, reps=100, stream=None) -> dict:
@@ -232,7 +255,7 @@ def pm_streams_run(args: pm_probe_args, bufs0, bufs1=None, bufs2=None, warmup=10
     res = pm_probe_result()
     _check(_lib.pm_streams_run(ctypes.byref(args), int(n), a0[0], a1[0] if a1 else None, a2[0] if a2 else None,
                                int(warmup), int(reps), _stream(stream), ctypes.byref(res)), "pm_streams_run")
-    return dict(median_s=res.median_s, p25_s=res.p25_s, p75_s=res.p75_s, min_s=res.min_s, bytes=res.bytes)
+    return _timing(res)
 
 
 # ----------------------------------------------------------------------- GEMM
@@ -257,7 +280,7 @@ def pm_gemm_bench(c: pm_cfg, A_op, B_op, C, scales=None, warmup=10, reps=100, st
     res = pm_probe_result()
     _check(_lib.pm_gemm_bench(ctypes.byref(c), _ptr(A_op), _ptr(B_op), _ptr(C), _ptr(scales), int(warmup), int(reps),
                               _stream(stream), ctypes.byref(res)), "pm_gemm_bench")
-    return dict(median_s=res.median_s, p25_s=res.p25_s, p75_s=res.p75_s, min_s=res.min_s, bytes=res.bytes)
+    return _timing(res)
 
 
 def pm_gemm_host_workspace(c: pm_cfg, chunks) -> int:
@@ -353,7 +376,7 @@ def pm_gemm_autotune(shape: pm_cfg, k, theta, n_sm, A_op, B_op, C, scales=None, 
     _check(_lib.pm_gemm_autotune(ctypes.byref(shape), int(k), ctypes.byref(params(theta)), int(n_sm), _ptr(A_op),
                                  _ptr(B_op), _ptr(C), _ptr(scales), int(warmup), int(reps), _stream(stream),
                                  ctypes.byref(pick), ctypes.byref(res)), "pm_gemm_autotune")
-    return pick, dict(median_s=res.median_s, p25_s=res.p25_s, p75_s=res.p75_s, min_s=res.min_s)
+    return pick, _timing(res)
 
 
 def pm_grouped_predict(M_list, N, K, BM_list, BN_list, BK, stages, cta_group, dtype, theta, n_sm, stream=None):
@@ -395,8 +418,7 @@ def pm_grouped_gemm_autotune(M_list, N, K, theta, n_sm, k, A_op, B_op, C, warmup
                                          _ptr(A_op), _ptr(B_op), _ptr(C), int(warmup), int(reps), _stream(stream),
                                          bm, bn, launch, ctypes.byref(t), ctypes.byref(res)),
            "pm_grouped_gemm_autotune")
-    return float(t.value), list(bm), list(bn), tuple(launch), dict(median_s=res.median_s, p25_s=res.p25_s,
-                                                                   p75_s=res.p75_s, min_s=res.min_s)
+    return float(t.value), list(bm), list(bn), tuple(launch), _timing(res)
 
 
 # ------------------------------------------------------- generic segment model
@@ -439,6 +461,17 @@ def pm_last_error() -> str:
 def pm_shutdown() -> None:
     """Release the library's streams, host pipeline and descriptor caches (re-created on demand)."""
     _check(_lib.pm_shutdown(), "pm_shutdown")
+
+
+def pm_clock_sample():
+    """One read-only NVML sample of the current device as a dict (SM, maximum
+    SM and memory clocks in MHz, power in W, clock event reasons, host
+    monotonic time in s), or None where NVML cannot be read."""
+    c = pm_clock()
+    if _lib.pm_clock_sample(ctypes.byref(c)) != PM_OK:
+        return None
+    return dict(sm_mhz=c.sm_mhz, sm_max_mhz=c.sm_max_mhz, mem_mhz=c.mem_mhz, power_w=c.power_mw / 1e3,
+                reasons=clock_reason_names(c.reasons), host_time_s=c.host_time_s)
 
 
 def pm_device_status(clear=True) -> int:

@@ -919,12 +919,15 @@ extern "C" pm_status pm_gemm_bench(const pm_cfg* cfg, const void* A_op_dev, cons
   std::vector<cudaEvent_t> ev(2 * (size_t)reps);
   for (auto& e : ev) PM_CUDA(cudaEventCreate(&e));
   pm_status st = PM_OK;
+  pm_clock c0, c1;
+  pm::read_clock(&c0);
   for (int i = 0; i < reps && st == PM_OK; ++i) {
     cudaEventRecord(ev[2 * i], s);
     st = pm::gemm_launch(*cfg, A_op_dev, B_op_dev, C_dev, scales_dev, s);
     cudaEventRecord(ev[2 * i + 1], s);
   }
   cudaError_t e = cudaStreamSynchronize(s);
+  pm::read_clock(&c1);
   std::vector<double> t;
   if (st == PM_OK && e == cudaSuccess)
     for (int i = 0; i < reps; ++i) {
@@ -949,6 +952,7 @@ extern "C" pm_status pm_gemm_bench(const pm_cfg* cfg, const void* A_op_dev, cons
   const double e_b = cfg->dtype == PM_FP32 ? 8.0 : (cfg->dtype == PM_BF16 ? 2.0 : 1.0);
   out->bytes = e_b * ((double)cfg->M * cfg->K + (double)cfg->N * cfg->K) + 4.0 * (double)cfg->M * cfg->N;
   out->final_index = 0;
+  pm::clock_record(out, c0, c1);
   unsigned int* w = pm::watchdog_word();
   unsigned int h[2] = {0, 0};
   PM_CUDA(cudaMemcpy(h, w, sizeof(h), cudaMemcpyDeviceToHost));

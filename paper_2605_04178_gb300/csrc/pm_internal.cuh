@@ -30,6 +30,10 @@ void release_stream_pool();
 void release_host_pipe_this_thread();
 void clear_tmap_caches_this_thread();
 void clear_probe_tmap_cache_this_thread();
+// Read-only NVML sample of the current device (false: NVML unavailable), and
+// the timed region's clock record in a harness result.
+bool read_clock(pm_clock* c);
+void clock_record(pm_probe_result* out, const pm_clock& begin, const pm_clock& end);
 
 // Named NVTX range over a scope (timing harnesses and pipelines); free when
 // no profiler is attached.

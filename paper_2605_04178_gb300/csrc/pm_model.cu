@@ -1031,6 +1031,8 @@ extern "C" pm_status pm_grouped_gemm_autotune(int32_t G, const int32_t* M_host, 
   double best_t = 1e300;
   int best = -1;
   pm_probe_result best_r = {};
+  pm_clock c0, c1;
+  read_clock(&c0);
   for (int j = 0; j < k && st == PM_OK; ++j) {
     const int i = order[j];
     if (!(ht[i] < INFINITY)) break;
@@ -1067,6 +1069,8 @@ extern "C" pm_status pm_grouped_gemm_autotune(int32_t G, const int32_t* M_host, 
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
+  read_clock(&c1);
+  clock_record(&best_r, c0, c1);
   if (st != PM_OK) return st;
   PM_REQUIRE(best >= 0, PM_EUNSUPPORTED, "no valid grouped configuration");
   for (int q = 0; q < G; ++q) {

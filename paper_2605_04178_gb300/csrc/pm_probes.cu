@@ -604,12 +604,15 @@ extern "C" pm_status pm_probe_run(const pm_probe_args* args, void* buf0, void* b
   std::vector<cudaEvent_t> ev(2 * (size_t)reps);
   for (auto& e : ev) PM_CUDA(cudaEventCreate(&e));
   pm_status st = PM_OK;
+  pm_clock c0, c1;
+  read_clock(&c0);
   for (int i = 0; i < reps && st == PM_OK; ++i, ++launches) {
     cudaEventRecord(ev[2 * i], s);
     st = probe_launch(launches == 0 ? args : &cont, buf0, buf1, buf2, s);
     cudaEventRecord(ev[2 * i + 1], s);
   }
   cudaError_t e = cudaStreamSynchronize(s);
+  read_clock(&c1);
   std::vector<double> t;
   if (st == PM_OK && e == cudaSuccess) {
     for (int i = 0; i < reps; ++i) {
@@ -634,6 +637,7 @@ extern "C" pm_status pm_probe_run(const pm_probe_args* args, void* buf0, void* b
   out->min_s = t.front();
   out->bytes = probe_bytes(args);
   out->final_index = 0;
+  clock_record(out, c0, c1);
   if (args->kind == PM_PROBE_PCHASE || args->kind == PM_PROBE_MBAR) {
     uint32_t fi = 0;
     PM_CUDA(cudaMemcpy(&fi, args->kind == PM_PROBE_PCHASE ? buf1 : buf0, 4, cudaMemcpyDeviceToHost));
@@ -718,6 +722,8 @@ extern "C" pm_status pm_streams_run(const pm_probe_args* per_stream, int32_t n_s
   std::vector<cudaEvent_t> ev(2 * (size_t)total), done((size_t)total * n_streams);
   for (auto& e : ev) PM_CUDA(cudaEventCreate(&e));
   for (auto& e : done) PM_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+  pm_clock c0, c1;
+  read_clock(&c0);
   for (int r = 0; r < total && st == PM_OK; ++r) {
     cudaEventRecord(ev[2 * r], s);
     for (int i = 0; i < n_streams && st == PM_OK; ++i) {
@@ -729,6 +735,7 @@ extern "C" pm_status pm_streams_run(const pm_probe_args* per_stream, int32_t n_s
     cudaEventRecord(ev[2 * r + 1], s);
   }
   cudaError_t e = cudaStreamSynchronize(s);
+  read_clock(&c1);
   std::vector<double> t;
   if (st == PM_OK && e == cudaSuccess) {
     for (int r = warmup; r < total; ++r) {
@@ -754,6 +761,7 @@ extern "C" pm_status pm_streams_run(const pm_probe_args* per_stream, int32_t n_s
   out->min_s = t.front();
   out->bytes = (double)n_streams * probe_bytes(per_stream);
   out->final_index = 0;
+  clock_record(out, c0, c1);
   if (k == PM_PROBE_MMA) {
     unsigned int* w = watchdog_word();
     unsigned int h[2] = {0, 0};

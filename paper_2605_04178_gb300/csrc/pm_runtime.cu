@@ -1,10 +1,12 @@
 // Runtime glue of libperfmodel.so: error reporting, the per-device watchdog
 // word, TMA descriptor encoding, device queries and the watchdog self-test.
 #include <cudaTypedefs.h>
+#include <dlfcn.h>
 #include <stdarg.h>
 #include <stdio.h>
 #include <stdlib.h>
 
+#include <chrono>
 #include <mutex>
 
 #include "pm_internal.cuh"
@@ -133,6 +135,83 @@ pm_status make_tmap_2d(CUtensorMap* map, const void* base, int dtype_code, uint6
   return PM_OK;
 }
 
+// Clock and throttle state through NVML, read only.  The driver's NVML
+// library is opened at run time (no link dependency: the library also loads
+// on machines without a driver); the device is matched by PCI bus id, so
+// the CUDA and NVML device orders need not agree.
+namespace {
+struct Nvml {
+  bool ok = false;
+  int (*init)() = nullptr;
+  int (*by_pci)(const char*, void**) = nullptr;
+  int (*clock)(void*, int, unsigned int*) = nullptr;
+  int (*max_clock)(void*, int, unsigned int*) = nullptr;
+  int (*reasons)(void*, unsigned long long*) = nullptr;
+  int (*power)(void*, unsigned int*) = nullptr;
+  void* dev[kMaxDevices] = {};
+};
+Nvml g_nvml;
+std::once_flag g_nvml_once;
+std::mutex g_nvml_mu;
+
+void nvml_open() {
+  void* h = dlopen("libnvidia-ml.so.1", RTLD_NOW | RTLD_LOCAL);
+  if (!h) return;
+  auto sym = [&](const char* name) { return dlsym(h, name); };
+  g_nvml.init = reinterpret_cast<int (*)()>(sym("nvmlInit_v2"));
+  g_nvml.by_pci = reinterpret_cast<int (*)(const char*, void**)>(sym("nvmlDeviceGetHandleByPciBusId_v2"));
+  g_nvml.clock = reinterpret_cast<int (*)(void*, int, unsigned int*)>(sym("nvmlDeviceGetClockInfo"));
+  g_nvml.max_clock = reinterpret_cast<int (*)(void*, int, unsigned int*)>(sym("nvmlDeviceGetMaxClockInfo"));
+  void* r = sym("nvmlDeviceGetCurrentClocksEventReasons");
+  if (!r) r = sym("nvmlDeviceGetCurrentClocksThrottleReasons");
+  g_nvml.reasons = reinterpret_cast<int (*)(void*, unsigned long long*)>(r);
+  g_nvml.power = reinterpret_cast<int (*)(void*, unsigned int*)>(sym("nvmlDeviceGetPowerUsage"));
+  g_nvml.ok = g_nvml.init && g_nvml.by_pci && g_nvml.clock && g_nvml.max_clock && g_nvml.reasons &&
+              g_nvml.power && g_nvml.init() == 0;
+}
+
+void* nvml_device() {
+  std::call_once(g_nvml_once, nvml_open);
+  if (!g_nvml.ok) return nullptr;
+  const int d = current_device();
+  if (d < 0 || d >= kMaxDevices) return nullptr;
+  std::lock_guard<std::mutex> lk(g_nvml_mu);
+  if (!g_nvml.dev[d]) {
+    char bus[32] = {0};
+    if (cudaDeviceGetPCIBusId(bus, sizeof(bus), d) != cudaSuccess) return nullptr;
+    void* h = nullptr;
+    if (g_nvml.by_pci(bus, &h) != 0) return nullptr;
+    g_nvml.dev[d] = h;
+  }
+  return g_nvml.dev[d];
+}
+}  // namespace
+
+bool read_clock(pm_clock* c) {
+  *c = pm_clock{};
+  c->host_time_s = std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+  void* d = nvml_device();
+  if (!d) return false;
+  unsigned int v = 0;
+  unsigned long long r = 0;
+  bool ok = g_nvml.clock(d, 1 /* SM */, &v) == 0;
+  c->sm_mhz = v;
+  ok = ok && g_nvml.max_clock(d, 1, &v) == 0;
+  c->sm_max_mhz = v;
+  if (g_nvml.clock(d, 2 /* memory */, &v) == 0) c->mem_mhz = v;
+  if (g_nvml.power(d, &v) == 0) c->power_mw = v;
+  ok = ok && g_nvml.reasons(d, &r) == 0;
+  c->reasons = r;
+  return ok;
+}
+
+void clock_record(pm_probe_result* out, const pm_clock& begin, const pm_clock& end) {
+  out->sm_mhz_begin = begin.sm_mhz;
+  out->sm_mhz_end = end.sm_mhz;
+  out->sm_max_mhz = end.sm_max_mhz ? end.sm_max_mhz : begin.sm_max_mhz;
+  out->clock_reasons = begin.reasons | end.reasons;
+}
+
 // Waits on an mbarrier that nothing ever completes; the bounded wait gives up
 // after the limit and records PM_ETIMEOUT.
 __global__ void watchdog_selftest_kernel(Watchdog wd) {
@@ -186,6 +265,12 @@ extern "C" pm_status pm_watchdog_selftest(int32_t limit_us, void* stream) {
     set_error("device watchdog expired at site %u", h[1]);
     return (pm_status)(-(int)h[0]);
   }
+  return PM_OK;
+}
+
+extern "C" pm_status pm_clock_sample(pm_clock* out) {
+  PM_REQUIRE(out != nullptr, PM_EINVAL, "out is NULL");
+  PM_REQUIRE(pm::read_clock(out), PM_EUNSUPPORTED, "NVML clock query unavailable for the current device");
   return PM_OK;
 }
 

@@ -106,3 +106,18 @@ def test_stencil_bit_exact(lib, shape):
     r = lib.pm_probe_run(lib.probe_args(lib.PM_PROBE_STENCIL, rows=rows, cols=cols), src, dst, warmup=1, reps=2)
     assert r["bytes"] == 8 * rows * cols
     assert np.array_equal(dst.cpu().numpy().view(np.uint32), O.stencil5_f32(x).view(np.uint32))
+
+
+def test_timing_harness_records_clocks(lib):
+    # Sec. V-B protocol: every measurement carries the clock and throttle
+    # state; the harness reads the SM clock through NVML (read only) right
+    # before its first timed launch and after its last one
+    c = lib.pm_clock_sample()
+    assert c is not None, lib.pm_last_error()
+    assert 0 < c["sm_mhz"] <= c["sm_max_mhz"] and c["mem_mhz"] > 0 and c["power_w"] > 0
+    n = 2 ** 26
+    a = torch.empty(n, dtype=torch.float32, device="cuda").uniform_(-1, 1)
+    b = torch.empty_like(a)
+    r = lib.pm_probe_run(lib.probe_args(lib.PM_PROBE_COPY, n=n), a, b, warmup=2, reps=10)
+    assert 0 < r["sm_mhz_begin"] <= r["sm_max_mhz"] and 0 < r["sm_mhz_end"] <= r["sm_max_mhz"]
+    assert all(name in lib.CLOCK_REASONS.values() for name in r["clock_reasons"])
