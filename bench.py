@@ -360,23 +360,23 @@ def run_gpu(args):
                       "model_only_over_best_time": meas[model_pick] / meas[best],
                       "model_mae_pct": float(np.mean(np.abs(pred - tm) / tm) * 100.0),
                       "protocol": "3 warm-ups, median of 15 CUDA-event timed launches per tile"}
-        # the same under the measured reading with its own calibration
-        calib_m = os.path.join(ROOT, "paper_2605_04178_gb300", "theta_gb300_measured.json")
-        if os.path.exists(calib_m):
-            with open(calib_m) as f:
-                theta_m = np.array(json.load(f)["theta"], dtype=np.float64)
+        # the same under the literal equations with their own calibration
+        calib_l = os.path.join(ROOT, "paper_2605_04178_gb300", "theta_gb300_literal.json")
+        if os.path.exists(calib_l):
+            with open(calib_l) as f:
+                theta_l = np.array(json.load(f)["theta"], dtype=np.float64)
             pred_m = torch.empty(len(tiles), dtype=torch.float32, device="cuda")
-            pm.pm_model_set_reading(pm.PM_READING_MEASURED)
+            pm.pm_model_set_reading(pm.PM_READING_LITERAL)
             try:
-                pm.pm_autotune_pick(MNK, 1, pm.PM_BF16, theta_m, n_sm, picks, t_pred)
-                pm.pm_model_predict(pm.cfg_tensor(cols), len(tiles), theta_m, n_sm, pred_m)
+                pm.pm_autotune_pick(MNK, 1, pm.PM_BF16, theta_l, n_sm, picks, t_pred)
+                pm.pm_model_predict(pm.cfg_tensor(cols), len(tiles), theta_l, n_sm, pred_m)
                 torch.cuda.synchronize()
             finally:
-                pm.pm_model_set_reading(pm.PM_READING_LITERAL)
+                pm.pm_model_set_reading(pm.PM_READING_MEASURED)
             pq = picks.cpu().numpy().view(pm.CFG_DTYPE)[0]
             mp = tuple(int(pq[k]) for k in ("BM", "BN", "BK", "stages", "cta_group"))
             pm_np = pred_m.cpu().numpy().astype(np.float64)
-            exhaustive["measured_reading"] = {
+            exhaustive["literal_reading"] = {
                 "model_only_tile": dict(zip(("BM", "BN", "BK", "stages", "cta_group"), mp)),
                 "model_only_over_best_time": meas[mp] / meas[best] if mp in meas else None,
                 "model_mae_pct": float(np.mean(np.abs(pm_np - tm) / tm) * 100.0)}
@@ -456,12 +456,12 @@ def run_gpu(args):
             with open(calib_rep) as f:
                 rep = json.load(f)
             line["model_mae_pct_holdout"] = {k: round(v["mae_pct"], 2) for k, v in rep["mae_holdout"].items()}
-        calib_meas = os.path.join(ROOT, "paper_2605_04178_gb300", "data", "calib_report_gb300_measured.json")
-        if os.path.exists(calib_meas):
-            with open(calib_meas) as f:
+        calib_lit = os.path.join(ROOT, "paper_2605_04178_gb300", "data", "calib_report_gb300_literal.json")
+        if os.path.exists(calib_lit):
+            with open(calib_lit) as f:
                 rep = json.load(f)
-            line["model_mae_pct_holdout_measured_reading"] = {k: round(v["mae_pct"], 2)
-                                                              for k, v in rep["mae_holdout"].items()}
+            line["model_mae_pct_holdout_literal_reading"] = {k: round(v["mae_pct"], 2)
+                                                             for k, v in rep["mae_holdout"].items()}
         line.update(extra)
         if not args.skip_cpu and world == 1:
             # the oracle on the host cores (one GPU only): rows 0..47 of the same
@@ -626,7 +626,7 @@ def secondary(pm, S, theta, n_sm, peaks):
     out["probes"]["pchase_256MB_ns_per_hop"] = 1e9 * r_pc["median_s"] / hops
     del buf
     # config 1: FP32 (three-pass TF32) GEMM 512^3 in its fixed tile, and the
-    # stage model's prediction for that launch (calibrated literal theta)
+    # stage model's prediction for that launch (calibrated theta, measured reading)
     A1 = torch.from_numpy(S.matrix(0, 512, 512, "uniform", 0)).cuda()
     B1 = torch.from_numpy(S.matrix(0, 512, 512, "uniform", 512 * 512)).cuda()
     ops1 = pm.GemmOperands(pm.PM_FP32, 512, 512, 512)
@@ -641,21 +641,21 @@ def secondary(pm, S, theta, n_sm, peaks):
     out["config1"] = {"workload": "fp32_gemm_512^3_128x128x32_s2_g1", "gpu_us": r1["median_s"] * 1e6,
                       "TFLOPps": 2 * 512 ** 3 / r1["median_s"] / 1e12, "model_pred_us": float(p1.item()) * 1e6,
                       "model_ape_pct": abs(float(p1.item()) - r1["median_s"]) / r1["median_s"] * 100}
-    # the same launch under the measured reading with its own calibration
-    calib_m = os.path.join(ROOT, "paper_2605_04178_gb300", "theta_gb300_measured.json")
-    if os.path.exists(calib_m):
-        with open(calib_m) as f:
-            theta_m = np.array(json.load(f)["theta"], dtype=np.float64)
-        pm.pm_model_set_reading(pm.PM_READING_MEASURED)
+    # the same launch under the literal equations with their own calibration
+    calib_l = os.path.join(ROOT, "paper_2605_04178_gb300", "theta_gb300_literal.json")
+    if os.path.exists(calib_l):
+        with open(calib_l) as f:
+            theta_l = np.array(json.load(f)["theta"], dtype=np.float64)
+        pm.pm_model_set_reading(pm.PM_READING_LITERAL)
         try:
             pm.pm_model_predict(pm.cfg_tensor({k: np.array([v]) for k, v in dict(
                 M=512, N=512, K=512, BM=128, BN=128, BK=32, stages=2, cta_group=1, dtype=0, kind=0).items()}),
-                1, theta_m, n_sm, p1)
+                1, theta_l, n_sm, p1)
             torch.cuda.synchronize()
         finally:
-            pm.pm_model_set_reading(pm.PM_READING_LITERAL)
-        out["config1"]["model_pred_us_measured_reading"] = float(p1.item()) * 1e6
-        out["config1"]["model_ape_pct_measured_reading"] = abs(float(p1.item()) - r1["median_s"]) / r1["median_s"] * 100
+            pm.pm_model_set_reading(pm.PM_READING_MEASURED)
+        out["config1"]["model_pred_us_literal_reading"] = float(p1.item()) * 1e6
+        out["config1"]["model_ape_pct_literal_reading"] = abs(float(p1.item()) - r1["median_s"]) / r1["median_s"] * 100
     del A1, B1, C1, ops1
     # batched model over 1e6 configurations: forward and adjoint
     nc = 10 ** 6
@@ -665,7 +665,7 @@ def secondary(pm, S, theta, n_sm, peaks):
     t_out = torch.empty(nc, dtype=torch.float32, device="cuda")
     tm = torch.ones(nc, dtype=torch.float32, device="cuda") * 1e-3
     ws = torch.empty(pm.pm_model_grad_workspace(nc) // 8, dtype=torch.float64, device="cuda")
-    go = torch.empty(17, dtype=torch.float64, device="cuda")
+    go = torch.empty(pm.N_GRAD_OUT, dtype=torch.float64, device="cuda")
     MNK = torch.from_numpy(np.stack([cf["M"], cf["N"], cf["K"]], 1)[: nc // 180].astype(np.int32).ravel()).cuda()
     picks = torch.empty((nc // 180) * 24, dtype=torch.uint8, device="cuda")
     tp = torch.empty(nc // 180, dtype=torch.float32, device="cuda")

@@ -77,22 +77,30 @@ typedef struct {
  *  0 T_launch   1 B_sus      2 B_peak     3 w0          4 L_TMA      5 B_TMA/SM
  *  6 R_TC tf32  7 R_TC bf16  8 R_TC fp8   9 L_mma      10 BW_TMEM_rd 11 BW_TMEM_wr
  * 12 L_mbar    13 L_alloc+L_dealloc      14 S_2SM      15 c_alpha
+ * 16 rho_L2 (measured reading only: TMA load speed-up of an L2-resident
+ *    working set, Sec. III-A.2)
  * with the overlap law alpha(stages) = clamp(1 - c_alpha/stages, 0, 1) (the
  * measured reading: clamp(1 - c_alpha/(stages - 1), 0, 1)). */
-typedef struct { float v[16]; } pm_params;
+#define PM_NPARAMS 17
+typedef struct { float v[PM_NPARAMS]; } pm_params;
 
 /* Readings of the points the paper leaves open in the stage model:
- *  PM_READING_LITERAL (default): the equations as printed -- L_mma once per
- *    K-step (Eq. 2), alpha = 1 - c_alpha/stages, T_sync in both Eq. 7 and
- *    Eq. 8;
- *  PM_READING_MEASURED: readings measured on this library's kernels -- L_mma
- *    once per tensor-pipe instruction of the K-step (BK/k_instr per 128-row
- *    block per pass, plus strategy B's copies), alpha = 1 - c_alpha/(stages-1),
- *    T_sync once per K-step (Eq. 8), O_misc of Eq. 8 = the bubble of the
- *    s-deep ring (T_step >= (T_tma + T_c + T_sync)/s), and the TMA bandwidth
- *    scaled by the L2-residency factor B_eff(W)/B_sus of Eq. 16 over the
- *    launch's working set W (operands and C; Sec. III-A.2 notes that L2 hits
- *    change B_TMA).
+ *  PM_READING_LITERAL: the equations as printed -- L_mma once per K-step
+ *    (Eq. 2), alpha = 1 - c_alpha/stages, T_sync in both Eq. 7 and Eq. 8,
+ *    TMEM management amortised over the K-steps (Sec. III-A.5);
+ *  PM_READING_MEASURED (default): readings measured on this library's
+ *    kernels -- L_mma once per tensor-pipe instruction of the K-step
+ *    (BK/k_instr per 128-row block per pass, plus strategy B's copies),
+ *    alpha = 1 - c_alpha/(stages-1), T_sync once per K-step (Eq. 8), O_misc
+ *    of Eq. 8 = the bubble of the s-deep ring (T_step >= (T_tma + T_c +
+ *    T_sync)/s), the TMA bandwidth scaled by an L2-residency factor
+ *    rho(W) = 1 + (rho_L2 - 1) exp(-W/w0) over the launch's working set W
+ *    (operands and C; Sec. III-A.2 notes that L2 hits change B_TMA; the
+ *    shape of Eq. 16's blend), the TMEM management paid once per launch (a
+ *    persistent CTA allocates tensor memory once: T_launch + L_alloc+L_dealloc
+ *    starts every GEMM launch), and a one-SM tile of 64 rows at the tensor
+ *    time of 128 rows (an M = 64 tcgen05.mma on one SM takes as long as an
+ *    M = 128 one).
  * The setting is process-wide and read by every model entry point at launch;
  * fit theta under the reading it will be used with. */
 typedef enum { PM_READING_LITERAL = 0, PM_READING_MEASURED = 1 } pm_reading;
@@ -280,15 +288,16 @@ pm_status pm_grouped_gemm_run(int32_t G, const int32_t* M_host, int32_t N, int32
 pm_status pm_model_predict(const pm_cfg* cfgs_dev, int64_t n, const pm_params* theta_host, int32_t n_sm,
                            float* t_out_dev, void* stream);
 
-/* Scratch the gradient needs: partial sums of 17 doubles per block. */
+/* Scratch the gradient needs: partial sums of 1 + PM_NPARAMS doubles per block. */
 pm_status pm_model_grad_workspace(int64_t n, size_t* bytes);
 
 /* Calibration objective of Sec. III-D (parameters fitted to measured times):
- *   L = (1/n) sum_i (ln T_hat_i - ln T_i)^2 and dL/dtheta (16 values),
+ *   L = (1/n) sum_i (ln T_hat_i - ln T_i)^2 and dL/dtheta (PM_NPARAMS values),
  * from a hand-written adjoint of the model (ties of max() go to the first
  * argument, the alpha clamp has zero slope outside (0,1)).  Per-block partial
  * sums go to workspace_dev (pm_model_grad_workspace bytes) and are reduced in
- * FP64 in a fixed order; out_dev receives 17 doubles {L, dL/dtheta_0..15}.
+ * FP64 in a fixed order; out_dev receives 1 + PM_NPARAMS doubles
+ * {L, dL/dtheta_0 .. dL/dtheta_16}.
  * Async. */
 pm_status pm_model_grad(const pm_cfg* cfgs_dev, int64_t n, const pm_params* theta_host, int32_t n_sm,
                         const float* t_meas_dev, void* workspace_dev, size_t workspace_bytes, double* out_dev,
@@ -297,7 +306,7 @@ pm_status pm_model_grad(const pm_cfg* cfgs_dev, int64_t n, const pm_params* thet
 /* pm_model_grad evaluated entirely in FP64 (parameters, per-configuration
  * model and adjoint, log residuals), for the calibration fit: the FP32
  * objective is piecewise flat at the 1e-7 level, which stalls the line
- * searches of a quasi-Newton fit near its optimum.  theta_host: 16 doubles
+ * searches of a quasi-Newton fit near its optimum.  theta_host: PM_NPARAMS doubles
  * in the pm_params order; t_meas_dev: n doubles (8-byte aligned); workspace
  * and output as for pm_model_grad.  Async. */
 pm_status pm_model_grad_f64(const pm_cfg* cfgs_dev, int64_t n, const double* theta_host, int32_t n_sm,
@@ -328,7 +337,7 @@ pm_status pm_gemm_autotune(const pm_cfg* shape, int32_t k, const pm_params* thet
  * fixed device-memory budget).  The paper has no counterpart: this is an
  * interface convenience of this library.  Same inputs and output as
  * pm_model_grad, minus the workspace: the per-block partial sums go to a
- * fixed 557,056-byte array inside the library, present on every GPU that
+ * fixed 589,824-byte array inside the library, present on every GPU that
  * loads it until the process exits.  At most 1,048,576 configurations per
  * call; larger n returns PM_ENOMEM with a message and launches nothing.
  * It launches the same grid as pm_model_grad, so its output is bit-identical

@@ -38,12 +38,12 @@ _lib = None
 
 KIND_GEMM, KIND_COPY, KIND_TRIAD, KIND_TMA2D = 0, 1, 2, 3
 DT_FP32, DT_BF16, DT_FP8 = 0, 1, 2
-N_PARAMS = 16
+N_PARAMS = 17
 
 PARAM_NAMES = ("T_launch", "B_sus", "B_peak", "w0", "L_TMA", "B_TMA", "R_tf32", "R_bf16", "R_fp8",
-               "L_mma", "BW_tmem_rd", "BW_tmem_wr", "L_mbar", "L_tmem_mgmt", "S_2SM", "c_alpha")
+               "L_mma", "BW_tmem_rd", "BW_tmem_wr", "L_mbar", "L_tmem_mgmt", "S_2SM", "c_alpha", "rho_L2")
 # Time-like parameters (seconds) and rate-like parameters (per second); the
-# rest (w0, S_2SM, c_alpha) are dimensionless or sizes.
+# rest (w0, S_2SM, c_alpha, rho_L2) are dimensionless or sizes.
 LATENCY_IDX = (0, 4, 9, 12, 13)
 RATE_IDX = (1, 2, 5, 6, 7, 8, 10, 11)
 
@@ -202,7 +202,7 @@ def _soa(cfgs: dict):
 
 
 def model_batch(cfgs: dict, theta, n_sm: int, grad: bool = False):
-    """Stage-model prediction (FP64) per configuration; with grad, also dT/dtheta [n, 16]."""
+    """Stage-model prediction (FP64) per configuration; with grad, also dT/dtheta [n, N_PARAMS]."""
     n, cols = _soa(cfgs)
     th = _c(theta, np.float64)
     assert th.size == N_PARAMS
@@ -291,11 +291,13 @@ READING_LITERAL, READING_MEASURED = 0, 1
 
 def set_reading(reading: int) -> None:
     """Select the readings of the stage model's open points (process-wide):
-    0 the literal equations (L_mma per K-step, alpha = 1 - c/s, T_sync in Eqs. 7 and 8),
+    0 the literal equations (L_mma per K-step, alpha = 1 - c/s, T_sync in Eqs. 7 and 8,
+    TMEM management amortised per K-step),
     1 the readings measured on the GPU's kernels (L_mma per tensor-pipe instruction,
     alpha = 1 - c/(s-1), T_sync once, the ring bubble (T_tma + T_c + T_sync)/s as a
     lower bound of T_step, B_TMA scaled by the L2-residency factor
-    B_eff(W)/B_sus of Eq. 16 over the launch's working set W)."""
+    rho(W) = 1 + (rho_L2 - 1) exp(-W/w0) over the launch's working set W, TMEM
+    management once per launch, 64-row one-SM tiles at the tensor time of 128 rows)."""
     _load().orc_set_reading(int(reading))
 
 
@@ -303,7 +305,7 @@ def reading() -> int:
     return int(_load().orc_reading())
 
 
-def prior_theta(n_sm: int, f_hz: float = 1.9e9, reading: int = READING_LITERAL) -> np.ndarray:
+def prior_theta(n_sm: int, f_hz: float = 1.9e9, reading: int = READING_MEASURED) -> np.ndarray:
     """Prior parameter vector built from the paper's printed values (Table "parameters",
     Sec. II-A sustained figures); cycles are converted with the clock f_hz.  c_alpha puts
     alpha in the printed 0.85-0.95 range under either overlap law."""
@@ -325,6 +327,7 @@ def prior_theta(n_sm: int, f_hz: float = 1.9e9, reading: int = READING_LITERAL) 
     th[14] = 1.0                      # S_2SM
     # alpha(2) = 0.85, alpha(6) = 0.95 (reading 0); alpha(2) = 0.85, alpha(3) = 0.925 (reading 1)
     th[15] = 0.3 if reading == READING_LITERAL else 0.15
+    th[16] = th[2] / th[1]            # rho_L2: an L2-resident launch loads at the HBM peak/sustained ratio
     return th
 
 

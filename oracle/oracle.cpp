@@ -173,7 +173,7 @@ extern "C" uint32_t orc_pchase(const uint32_t* buf, i64 stride_words, uint32_t s
 // Dual numbers: value plus the 16 partial derivatives with respect to the
 // model parameters theta.  Arithmetic follows the usual differentiation rules.
 // ---------------------------------------------------------------------------
-enum { NP = 16 };
+enum { NP = 17 };
 struct Dual {
   double v;
   double d[NP];
@@ -226,6 +226,9 @@ template <> inline Dual lift<Dual>(double v) { return dconst(v); }
 // 13 L_alloc+L_dealloc  TMEM management                      (T_TMEM_mgmt)
 // 14 S_2SM         2-SM cooperative speedup                  (Eq. 6)
 // 15 c_alpha       overlap law alpha(s) = clamp(1 - c_alpha/s, 0, 1) (reading 1: s - 1)
+// 16 rho_L2        TMA load speed-up of an L2-resident working set over a
+//                  streaming one (reading 1; Sec. III-A.2: L2 hit rates
+//                  strongly affect B_TMA); unused by reading 0
 // ---------------------------------------------------------------------------
 
 enum { K_GEMM = 0, K_COPY = 1, K_TRIAD = 2, K_TMA2D = 3 };
@@ -282,18 +285,23 @@ static T b_eff(const T* th, double W) {
 }
 
 // Two sets of readings of the points the paper leaves open:
-//   0 (default) the literal equations: L_mma once per K-step (Eq. 2),
-//     alpha(s) = clamp(1 - c_alpha/s, 0, 1), T_sync in both Eq. 7 and Eq. 8;
-//   1 readings measured on this GPU's kernels: L_mma once per tensor-pipe
+//   0 the literal equations: L_mma once per K-step (Eq. 2),
+//     alpha(s) = clamp(1 - c_alpha/s, 0, 1), T_sync in both Eq. 7 and Eq. 8,
+//     TMEM management amortised per K-step;
+//   1 (default) readings measured on this GPU's kernels: L_mma once per tensor-pipe
 //     instruction the K-step issues (BK/k_instr per 128-row block per pass,
 //     plus strategy B's copies), alpha(s) = clamp(1 - c_alpha/(s-1), 0, 1)
 //     (an s-stage ring keeps s-1 loads in flight), T_sync once per K-step
 //     (Eq. 8; the barrier of Eq. 7 is the same one), O_misc of Eq. 8 = the
-//     bubble of the s-deep ring (T_step >= (T_tma + T_c + T_sync)/s), and
-//     B_TMA scaled by the working-set ratio B_eff(W)/B_sus of Eq. 16 (L2
-//     residency of the loads).
-static int g_reading = 0;
-extern "C" void orc_set_reading(int r) { g_reading = r == 1 ? 1 : 0; }
+//     bubble of the s-deep ring (T_step >= (T_tma + T_c + T_sync)/s), B_TMA
+//     scaled by an L2-residency factor rho(W) = 1 + (rho_L2 - 1) exp(-W/w0)
+//     over the launch's working set W (Eq. 16's blend shape), the TMEM
+//     management of Sec. III-A.5 paid once per launch (a persistent CTA
+//     allocates its tensor memory once, not once per tile), and a single-SM
+//     tile of 64 rows taking the tensor time of 128 rows (an M = 64
+//     tcgen05.mma on one SM runs at half the per-SM rate).
+static int g_reading = 1;   // the measured readings by default
+extern "C" void orc_set_reading(int r) { g_reading = r == 0 ? 0 : 1; }
 extern "C" int orc_reading() { return g_reading; }
 
 // Output tiles a launch runs on its CTAs: ceil(M/BM) ceil(N/BN) in the literal
@@ -327,20 +335,27 @@ static void stage_terms(const Cfg& c, i64 Kt, const T* th, double W, T& Tstep, T
   const double DA_r = c.tmem_a ? np * e * c.BM * c.BK : 0.0;
   if (c.tmem_a && measured) n_instr += l * (c.BK * e / 32.0) * (double)ceil_div(c.BM, 128);
   const T T_tmem = (D + DA_r) / th[10] + n_instr * th[9] + (D + DA_w) / th[11];
-  // T_TMEM_mgmt amortised over the K-steps (Sec. III-A.5).
-  const T T_mgmt = th[13] / lift<T>((double)Kt);
-  // Eqs. 3 and 6: S_mode = 1 for one SM, S_2SM for a CTA pair.
+  // T_TMEM_mgmt amortised over the K-steps (Sec. III-A.5); the measured
+  // reading charges it once per launch instead (model_gemm).
+  const T T_mgmt = measured ? lift<T>(0.0) : th[13] / lift<T>((double)Kt);
+  // Eqs. 3 and 6: S_mode = 1 for one SM, S_2SM for a CTA pair.  Measured
+  // reading: a one-SM tile of 64 rows issues M = 64 instructions, which take
+  // as long as M = 128 ones, so its tensor time is that of 128 rows.
   const T S = (c.g == 1) ? lift<T>(1.0) : th[14];
-  const T T_c = lift<T>(np * 2.0 * c.BM * c.BN * c.BK) / (R * S) + T_tmem + T_mgmt;
+  const double rows = (measured && c.g == 1 && c.BM < 128) ? 128.0 : (double)c.BM;
+  const T T_c = lift<T>(np * 2.0 * rows * c.BN * c.BK) / (R * S) + T_tmem + T_mgmt;
   // Eq. 4 with P = 1 (no multicast); the CTA pair loads 2 M_A + M_B per
   // K-step, i.e. each CTA its own A rows and half of B (Sec. III-A.4).
   const double b_step = l * e * c.BK * (c.BM + (double)c.BN / c.g);
   // B_TMA depends on how many of the loads hit in L2 (Sec. III-A.2).  The
-  // measured reading takes the working-set law of Eq. 16 for it: B_TMA is
-  // scaled by B_eff(W) / B_sus, which falls from B_peak / B_sus for a launch
-  // whose operands stay in L2 to 1 for one streaming from HBM.  The literal
-  // reading keeps B_TMA constant.
-  const T B_tma = measured ? th[5] * (b_eff<T>(th, W) / th[1]) : th[5];
+  // measured reading gives it the working-set shape of Eq. 16: B_TMA is
+  // scaled by rho(W) = 1 + (rho_L2 - 1) exp(-W / w0), which falls from
+  // rho_L2 for a launch whose operands stay in L2 to 1 for one streaming
+  // from HBM (w0 <= 0 switches it off).  The literal reading keeps B_TMA
+  // constant.
+  T rho = lift<T>(1.0);
+  if (measured && !(th[3] <= lift<T>(0.0))) rho = 1.0 + (th[16] - lift<T>(1.0)) * dexp(lift<T>(-W) / th[3]);
+  const T B_tma = th[5] * rho;
   const T T_tma = th[4] + b_step / B_tma;
   // T_sync = N_bar * L_mbar with N_bar = 2 (full and empty barrier per stage).
   const T T_sync = 2.0 * th[12];
@@ -384,11 +399,14 @@ static T model_gemm(const Cfg& c, const T* th, int n_sm) {
   const double bytes_min = l * e * ((double)c.M * c.K + (double)c.N * c.K) + 4.0 * (double)c.M * c.N;
   T Tstep, Tstore;
   stage_terms<T>(c, Kt, th, bytes_min, Tstep, Tstore);
-  const T T_stage = th[0] + lift<T>((double)waves) * (lift<T>((double)Kt) * Tstep + Tstore);
+  // the launch: T_launch, plus under the measured reading the TMEM
+  // management the persistent kernel pays once
+  const T launch = g_reading == 1 ? th[0] + th[13] : th[0];
+  const T T_stage = launch + lift<T>((double)waves) * (lift<T>((double)Kt) * Tstep + Tstore);
   const T& R = th[rate_index(c.dtype)];
   const T S = (c.g == 1) ? lift<T>(1.0) : th[14];
   const double flops = np * 2.0 * (double)c.M * (double)c.N * (double)c.K;
-  const T T_rl = th[0] + dmax(lift<T>(flops) / (lift<T>((double)n_sm) * R * S), lift<T>(bytes_min) / th[2]);
+  const T T_rl = launch + dmax(lift<T>(flops) / (lift<T>((double)n_sm) * R * S), lift<T>(bytes_min) / th[2]);
   return dmax(T_stage, T_rl);
 }
 
@@ -538,7 +556,7 @@ extern "C" double orc_grouped_predict(int G, const int32_t* Mg, int32_t N, int32
   }
   double mx = 0.0;
   for (double b : busy) mx = std::max(mx, b);
-  return theta[0] + mx;
+  return theta[0] + (g_reading == 1 ? theta[13] : 0.0) + mx;
 }
 
 // Grouped autotune: for each launch-level (BK, stages, cta_group) in

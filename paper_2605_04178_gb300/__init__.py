@@ -22,6 +22,8 @@ PM_OK, PM_EINVAL, PM_EUNSUPPORTED, PM_ECUDA, PM_ETIMEOUT, PM_ENOMEM = 0, -1, -2,
 PM_FP32, PM_BF16, PM_FP8E4M3 = 0, 1, 2
 PM_KIND_GEMM, PM_KIND_COPY, PM_KIND_TRIAD, PM_KIND_TMA2D = 0, 1, 2, 3
 PM_READING_LITERAL, PM_READING_MEASURED = 0, 1
+N_PARAMS = 17                     # PM_NPARAMS: entries of theta (pm_params)
+N_GRAD_OUT = N_PARAMS + 1         # pm_model_grad output: loss, then the gradient
 PM_PROBE_COPY, PM_PROBE_TRIAD, PM_PROBE_TMA2D, PM_PROBE_PCHASE = 1, 2, 3, 4
 PM_PROBE_H2D, PM_PROBE_D2H, PM_PROBE_MMA, PM_PROBE_MBAR, PM_PROBE_TMEM_LD, PM_PROBE_TMEM_ST = 5, 6, 7, 8, 9, 10
 PM_PROBE_HOST_READ, PM_PROBE_HOST_WRITE, PM_PROBE_STENCIL = 11, 12, 13
@@ -41,7 +43,7 @@ class pm_cfg(ctypes.Structure):
 
 
 class pm_params(ctypes.Structure):
-    _fields_ = [("v", ctypes.c_float * 16)]
+    _fields_ = [("v", ctypes.c_float * N_PARAMS)]
 
 
 # numpy view of pm_segment (64 bytes)
@@ -192,8 +194,8 @@ def _stream(stream):
 def params(theta) -> pm_params:
     p = pm_params()
     th = np.asarray(theta, dtype=np.float32)
-    assert th.size == 16
-    for j in range(16):
+    assert th.size == N_PARAMS, "theta has %d entries, not %d" % (th.size, N_PARAMS)
+    for j in range(N_PARAMS):
         p.v[j] = float(th[j])
     return p
 
@@ -345,8 +347,9 @@ def pm_model_grad(cfgs_dev, n, theta, n_sm, t_meas, workspace, out, stream=None)
 
 
 def pm_model_grad_f64(cfgs_dev, n, theta, n_sm, t_meas, workspace, out, stream=None):
-    """pm_model_grad in FP64 throughout: theta as 16 doubles, t_meas a float64 device tensor."""
-    th = (ctypes.c_double * 16)(*[float(v) for v in theta])
+    """pm_model_grad in FP64 throughout: theta as N_PARAMS doubles, t_meas a float64 device tensor."""
+    assert len(theta) == N_PARAMS
+    th = (ctypes.c_double * N_PARAMS)(*[float(v) for v in theta])
     _check(_lib.pm_model_grad_f64(_ptr(cfgs_dev), int(n), ctypes.cast(th, ctypes.c_void_p), int(n_sm), _ptr(t_meas),
                                   _ptr(workspace), int(workspace.numel() * workspace.element_size()), _ptr(out),
                                   _stream(stream)), "pm_model_grad_f64")

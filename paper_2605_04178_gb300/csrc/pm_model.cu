@@ -53,10 +53,13 @@ __device__ __forceinline__ uint32_t udiv(uint32_t x, const UDiv& u) {
 // multiplies where the equations divide by a parameter.  nc[0] / nc[1]
 // divide by the concurrent CTAs of one-SM / paired tiles on nc_nsm SMs
 // (nc_nsm = 0: not prepared, the generic division is used).
+constexpr int NP = PM_NPARAMS;     // model parameters
+constexpr int NREC = NP + 1;        // loss + gradient per partial record
+
 template <class F>
 struct ThetaT {
-  F v[16];
-  F inv[16];
+  F v[NP];
+  F inv[NP];
   int reading;       // PM_READING_LITERAL or PM_READING_MEASURED (see pm_model_set_reading)
   int nc_nsm;
   UDiv nc[2];
@@ -139,6 +142,7 @@ struct GemmFwdT {
   F D, DA_r, DA_w, bstep, store_bytes, n_instr;
   F waves, Kt;
   F W, E, rho;          // L2 residency of the TMA loads (measured reading)
+  F launch;             // T_launch (+ L_alloc + L_dealloc once per launch, measured reading)
   F T_eq8, T_ring;       // Eq. 8 and the ring bound (measured reading)
   int ri;
   bool oma_free, blend, ring;
@@ -152,18 +156,23 @@ using GemmFwd = GemmFwdT<float>;
 //            (D_A,r = n_p e BM BK); n_instr = 1 (literal reading) or the
 //            tensor-pipe instructions of the K-step incl. strategy B's
 //            tcgen05.cp copies (measured reading)
-//   T_c    = n_p 2 BM BN BK / (R S) + T_TMEM + T_mgmt/K_tiles     (Eqs. 3, 6)
+//   T_c    = n_p 2 BM' BN BK / (R S) + T_TMEM + T_mgmt/K_tiles    (Eqs. 3, 6)
+//            BM' = BM, except 128 for a one-SM 64-row tile (measured
+//            reading: M = 64 instructions take the M = 128 time); the
+//            measured reading has no T_mgmt/K_tiles (paid once per launch)
 //   T_tma  = L_TMA + b_step / (B_TMA rho), b_step = l e BK (BM + BN/g) (Eq. 4,
 //            P = 1); rho = 1 (literal reading) or the L2-residency factor
-//            B_eff(W)/B_sus of Eq. 16 over the launch's working set W
+//            1 + (rho_L2 - 1) exp(-W/w0) over the launch's working set W
 //            (measured reading)
 //   T_io   = (1 - alpha) T_tma + T_sync, T_sync = 2 L_mbar       (Eq. 7; the
 //            measured reading drops this T_sync: one barrier per K-step)
 //   T_step = max(T_c, T_io) + T_sync                             (Eq. 8; the
 //            measured reading adds the bubble of the s-deep ring as O_misc:
 //            T_step = max(Eq. 8, (T_tma + T_c + T_sync) / s))
-//   T_stage = T_launch + waves (K_tiles T_step + T_store)
-//   T_hat = max(T_stage, T_launch + max(FLOPs/(n_SM R S), bytes_min/B_peak))
+//   T_stage = launch + waves (K_tiles T_step + T_store)
+//   T_hat = max(T_stage, launch + max(FLOPs/(n_SM R S), bytes_min/B_peak))
+//            launch = T_launch (literal) or T_launch + L_alloc + L_dealloc
+//            (measured: the persistent CTAs allocate TMEM once per launch)
 // W_launch > 0 overrides the working set (a grouped launch passes its own);
 // otherwise W = bytes_min of this GEMM (operands once, C once).
 template <class F>
@@ -202,20 +211,22 @@ __device__ __forceinline__ void gemm_forward(const pm_cfg& c, const ThetaT<F>& t
   // measured: strategy B's tcgen05.cp per 128-row x 32-byte A slice, each charged L_mma
   if (c.tmem_a && measured) f.n_instr += l * (F)(c.BK * (int)e / 32) * (F)((c.BM + 127) / 128);
   const F T_tmem = (f.D + f.DA_r) * th.inv[10] + f.n_instr * th.v[9] + (f.D + f.DA_w) * th.inv[11];
-  const F T_mgmt = th.v[13] / f.Kt;
+  const F T_mgmt = measured ? F(0) : th.v[13] / f.Kt;
   f.S = g == 1 ? F(1) : th.v[14];
   f.invS = g == 1 ? F(1) : th.inv[14];
-  f.X = (np * F(2) * c.BM * c.BN * c.BK) * (f.invR * f.invS);
+  const int rows = (measured && g == 1 && c.BM < 128) ? 128 : (int)c.BM;
+  f.X = (np * F(2) * rows * c.BN * c.BK) * (f.invR * f.invS);
   f.T_c = f.X + T_tmem + T_mgmt;
   // BN / g: halving is exact, so pairs need no division
   const F bn_g = g == 1 ? (F)c.BN : (g == 2 ? F(0.5) * (F)c.BN : (F)c.BN / (F)g);
   f.bstep = l * e * c.BK * ((F)c.BM + bn_g);
-  // measured: B_TMA x B_eff(W)/B_sus (Eq. 16; loads that hit in L2 arrive
-  // faster, Sec. III-A.2); w0 <= 0 switches the blend off
+  // measured: B_TMA x rho(W), rho = 1 + (rho_L2 - 1) exp(-W/w0) (loads that
+  // hit in L2 arrive faster, Sec. III-A.2; Eq. 16's blend shape); w0 <= 0
+  // switches the blend off
   f.W = W_launch > F(0) ? W_launch : bytes_min;
   f.blend = measured && th.v[3] > F(0);
   f.E = f.blend ? pm_exp(-f.W / th.v[3]) : F(0);
-  f.rho = f.blend ? F(1) + (th.v[2] * th.inv[1] - F(1)) * f.E : F(1);
+  f.rho = f.blend ? F(1) + (th.v[16] - F(1)) * f.E : F(1);
   f.T_tma = th.v[4] + (f.blend ? f.bstep * th.inv[5] / f.rho : f.bstep * th.inv[5]);   // rho = 1 unblended
   const F T_sync = F(2) * th.v[12];
   // 1 - alpha = clamp(c_alpha / s, 0, 1) (literal) or clamp(c_alpha / (s - 1),
@@ -233,11 +244,12 @@ __device__ __forceinline__ void gemm_forward(const pm_cfg& c, const ThetaT<F>& t
   f.T_step = f.ring ? f.T_ring : f.T_eq8;
   f.store_bytes = F(4) * c.BM * c.BN;
   f.T_store = th.v[4] + f.store_bytes * th.inv[5];
-  f.T_stage = th.v[0] + f.waves * (f.Kt * f.T_step + f.T_store);
+  f.launch = measured ? th.v[0] + th.v[13] : th.v[0];
+  f.T_stage = f.launch + f.waves * (f.Kt * f.T_step + f.T_store);
   const F flops = np * F(2) * (F)c.M * (F)c.N * (F)c.K;
   f.A_rl = flops * (f.invR * f.invS) / (F)n_sm;
   f.B_rl = bytes_min * th.inv[2];
-  f.T_rl = th.v[0] + (f.A_rl >= f.B_rl ? f.A_rl : f.B_rl);
+  f.T_rl = f.launch + (f.A_rl >= f.B_rl ? f.A_rl : f.B_rl);
   f.T = f.T_stage >= f.T_rl ? f.T_stage : f.T_rl;
 }
 
@@ -245,10 +257,13 @@ __device__ __forceinline__ void gemm_forward(const pm_cfg& c, const ThetaT<F>& t
 // gradient to its first argument on ties; the clamp stops it outside (0,1).
 template <class F>
 __device__ __forceinline__ void gemm_adjoint(const pm_cfg& c, const ThetaT<F>& th, const GemmFwdT<F>& f, F w,
-                                             F (&d)[16]) {
+                                             F (&d)[NP]) {
+  const bool measured = th.reading == PM_READING_MEASURED;
   F g_stage = F(0), g_rl = F(0);
   if (f.T_stage >= f.T_rl) g_stage = w; else g_rl = w;
   F gR = F(0), gS = F(0);
+  // the launch term of both branches
+  if (measured) d[13] += g_rl + g_stage;
   // roofline branch
   d[0] += g_rl;
   if (g_rl != F(0)) {
@@ -280,12 +295,10 @@ __device__ __forceinline__ void gemm_adjoint(const pm_cfg& c, const ThetaT<F>& t
   const F t_bw = f.blend ? f.bstep * th.inv[5] / f.rho : f.bstep * th.inv[5];   // b_step / (B_TMA rho)
   d[5] -= g_tma * t_bw * th.inv[5];
   if (f.blend) {
-    // rho = 1 + (B_peak/B_sus - 1) E, E = exp(-W/w0)
+    // rho = 1 + (rho_L2 - 1) E, E = exp(-W/w0)
     const F g_rho = -g_tma * t_bw / f.rho;
-    const F q = th.v[2] * th.inv[1];
-    d[1] -= g_rho * q * f.E * th.inv[1];
-    d[2] += g_rho * f.E * th.inv[1];
-    d[3] += g_rho * (q - F(1)) * f.E * (f.W * th.inv[3]) * th.inv[3];
+    d[16] += g_rho * f.E;
+    d[3] += g_rho * (th.v[16] - F(1)) * f.E * (f.W * th.inv[3]) * th.inv[3];
   }
   d[12] += F(2) * g_sync;
   // T_c = X + (D + D_A,r)/BW_rd + n_instr L_mma + (D + D_A,w)/BW_wr + L_mgmt/K_tiles
@@ -294,7 +307,7 @@ __device__ __forceinline__ void gemm_adjoint(const pm_cfg& c, const ThetaT<F>& t
   d[10] -= g_c * ((f.D + f.DA_r) * th.inv[10]) * th.inv[10];
   d[9] += g_c * f.n_instr;
   d[11] -= g_c * ((f.D + f.DA_w) * th.inv[11]) * th.inv[11];
-  d[13] += g_c / f.Kt;
+  if (!measured) d[13] += g_c / f.Kt;
   // static indices keep d[] in registers
   d[6] += f.ri == 6 ? gR : F(0);
   d[7] += f.ri == 7 ? gR : F(0);
@@ -342,7 +355,7 @@ __device__ __forceinline__ void probe_forward(const pm_cfg& c, const ThetaT<F>& 
 }
 
 template <class F>
-__device__ __forceinline__ void bw_adjoint(const ThetaT<F>& th, const ProbeFwdT<F>& f, F gB, F (&d)[16]) {
+__device__ __forceinline__ void bw_adjoint(const ThetaT<F>& th, const ProbeFwdT<F>& f, F gB, F (&d)[NP]) {
   if (f.blend) {
     d[1] += gB * (F(1) - f.E);
     d[2] += gB * f.E;
@@ -355,7 +368,7 @@ __device__ __forceinline__ void bw_adjoint(const ThetaT<F>& th, const ProbeFwdT<
 
 template <class F>
 __device__ __forceinline__ void probe_adjoint(const pm_cfg& c, const ThetaT<F>& th, const ProbeFwdT<F>& f, F w,
-                                              F (&d)[16]) {
+                                              F (&d)[NP]) {
   d[0] += w;
   const bool first = f.T1 >= f.T2;
   if (c.kind == PM_KIND_COPY || c.kind == PM_KIND_TRIAD) {
@@ -417,8 +430,8 @@ __global__ void __launch_bounds__(256, 6) model_predict_kernel(const pm_cfg* __r
 }
 
 // Loss and gradient: per-thread terms and warp sums in F, warp totals
-// combined in FP64 into one partial record of 17 values per block; a second
-// kernel adds the records in block order (deterministic).
+// combined in FP64 into one partial record of NREC values per block; a
+// second kernel adds the records in block order (deterministic).
 constexpr int kGradThreads = 256;
 
 template <class T>
@@ -442,15 +455,15 @@ __global__ void __launch_bounds__(kGradThreads, grad_min_blocks<F>()) model_grad
                                                                   ThetaT<F> th, int n_sm,
                                                                   const F* __restrict__ t_meas,
                                                                   double* __restrict__ partials) {
-  F acc[16];
+  F acc[NP];
 #pragma unroll
-  for (int j = 0; j < 16; ++j) acc[j] = F(0);
+  for (int j = 0; j < NP; ++j) acc[j] = F(0);
   F loss = F(0);
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     const pm_cfg c = load_cfg(cfgs + i);
-    F d[16];
+    F d[NP];
 #pragma unroll
-    for (int j = 0; j < 16; ++j) d[j] = F(0);
+    for (int j = 0; j < NP; ++j) d[j] = F(0);
     F T;
     if (!cfg_sane(c, n_sm)) {
       T = (F)__int_as_float(0x7fc00000);
@@ -469,37 +482,37 @@ __global__ void __launch_bounds__(kGradThreads, grad_min_blocks<F>()) model_grad
     loss = fma(r, r, loss);
     const F w = F(2) * r / T;
 #pragma unroll
-    for (int j = 0; j < 16; ++j) acc[j] = fma(w, d[j], acc[j]);
+    for (int j = 0; j < NP; ++j) acc[j] = fma(w, d[j], acc[j]);
   }
   // warp sums in F (FP64 arithmetic is scarce on this GPU), warp totals
   // combined in FP64
-  __shared__ double red[kGradThreads / 32][17];
+  __shared__ double red[kGradThreads / 32][NREC];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   F v = warp_sum<F>(loss);
   if (lane == 0) red[warp][0] = (double)v;
 #pragma unroll
-  for (int j = 0; j < 16; ++j) {
+  for (int j = 0; j < NP; ++j) {
     v = warp_sum<F>(acc[j]);
     if (lane == 0) red[warp][j + 1] = (double)v;
   }
   __syncthreads();
-  if (threadIdx.x < 17) {
+  if (threadIdx.x < NREC) {
     double s = 0.0;
     for (int w = 0; w < kGradThreads / 32; ++w) s += red[w][threadIdx.x];
-    partials[(int64_t)blockIdx.x * 17 + threadIdx.x] = s;
+    partials[(int64_t)blockIdx.x * NREC + threadIdx.x] = s;
   }
 }
 
 // Warp j sums component j of the block records: lane l adds records l,
 // l+32, ... in order, then a fixed butterfly combines the lanes, so the
 // result depends only on the number of records (deterministic).
-__global__ void __launch_bounds__(17 * 32) model_grad_finish_kernel(const double* __restrict__ partials,
+__global__ void __launch_bounds__(NREC * 32) model_grad_finish_kernel(const double* __restrict__ partials,
                                                                     int blocks, int64_t n,
                                                                     double* __restrict__ out) {
   const int j = threadIdx.x >> 5, lane = threadIdx.x & 31;
   double s = 0.0;
 #pragma unroll 4
-  for (int b = lane; b < blocks; b += 32) s += partials[(int64_t)b * 17 + j];
+  for (int b = lane; b < blocks; b += 32) s += partials[(int64_t)b * NREC + j];
   s = warp_sum_d(s);
   if (lane == 0) out[j] = s / (double)n;
 }
@@ -745,7 +758,8 @@ __global__ void __launch_bounds__(kGroupThreads) grouped_tune_kernel(const int32
   }
   any_invalid = __syncthreads_or(any_invalid);
   const float t = grouped_makespan(tau, tiles, off, red, G, g == 1 ? n_sm : 2 * (n_sm / 2));
-  if (threadIdx.x == 0) out_t[combo] = (any_invalid || (g != 1 && n_sm < 2)) ? INFINITY : th.v[0] + t;
+  const float launch = th.reading == PM_READING_MEASURED ? th.v[0] + th.v[13] : th.v[0];
+  if (threadIdx.x == 0) out_t[combo] = (any_invalid || (g != 1 && n_sm < 2)) ? INFINITY : launch + t;
 }
 
 // Stage-model makespan of one grouped launch with given per-group tiles
@@ -773,14 +787,15 @@ __global__ void __launch_bounds__(kGroupThreads) grouped_predict_kernel(const in
   }
   __syncthreads();
   const float t = grouped_makespan(tau, tiles, off, red, G, g == 1 ? n_sm : 2 * (n_sm / 2));
-  if (threadIdx.x == 0) out_t[0] = (g != 1 && n_sm < 2) ? __int_as_float(0x7fc00000) : th.v[0] + t;
+  const float launch = th.reading == PM_READING_MEASURED ? th.v[0] + th.v[13] : th.v[0];
+  if (threadIdx.x == 0) out_t[0] = (g != 1 && n_sm < 2) ? __int_as_float(0x7fc00000) : launch + t;
 }
 
-static std::atomic<int> g_reading{PM_READING_LITERAL};
+static std::atomic<int> g_reading{PM_READING_MEASURED};
 
 static Theta to_theta(const pm_params* p, int n_sm) {
   Theta t;
-  for (int j = 0; j < 16; ++j) {
+  for (int j = 0; j < NP; ++j) {
     t.v[j] = p->v[j];
     t.inv[j] = (float)(1.0 / (double)p->v[j]);
   }
@@ -808,7 +823,7 @@ extern "C" pm_status pm_model_predict(const pm_cfg* cfgs_dev, int64_t n, const p
 
 extern "C" pm_status pm_model_grad_workspace(int64_t n, size_t* bytes) {
   PM_REQUIRE(bytes != nullptr && n >= 0, PM_EINVAL, "bad arguments");
-  *bytes = (size_t)grad_blocks(std::max<int64_t>(n, 1)) * 17 * sizeof(double);
+  *bytes = (size_t)grad_blocks(std::max<int64_t>(n, 1)) * NREC * sizeof(double);
   return PM_OK;
 }
 
@@ -821,15 +836,15 @@ extern "C" pm_status pm_model_grad(const pm_cfg* cfgs_dev, int64_t n, const pm_p
   PM_REQUIRE(((uintptr_t)cfgs_dev & 7) == 0 && ((uintptr_t)workspace_dev & 7) == 0, PM_EINVAL,
              "cfgs_dev and workspace_dev must be 8-byte aligned");
   const int blocks = grad_blocks(n);
-  PM_REQUIRE(workspace_bytes >= (size_t)blocks * 17 * sizeof(double), PM_ENOMEM,
+  PM_REQUIRE(workspace_bytes >= (size_t)blocks * NREC * sizeof(double), PM_ENOMEM,
              "workspace of %zu bytes is smaller than the %zu needed", workspace_bytes,
-             (size_t)blocks * 17 * sizeof(double));
+             (size_t)blocks * NREC * sizeof(double));
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   model_grad_kernel<float><<<blocks, kGradThreads, 0, s>>>(cfgs_dev, n, to_theta(theta_host, n_sm), n_sm, t_meas_dev,
                                                            static_cast<double*>(workspace_dev));
   pm_status st = launch_status("model_grad_kernel");
   if (st != PM_OK) return st;
-  model_grad_finish_kernel<<<1, 17 * 32, 0, s>>>(static_cast<const double*>(workspace_dev), blocks, n, out_dev);
+  model_grad_finish_kernel<<<1, NREC * 32, 0, s>>>(static_cast<const double*>(workspace_dev), blocks, n, out_dev);
   return launch_status("model_grad_finish_kernel");
 }
 
@@ -842,11 +857,11 @@ extern "C" pm_status pm_model_grad_f64(const pm_cfg* cfgs_dev, int64_t n, const 
   PM_REQUIRE(((uintptr_t)cfgs_dev & 7) == 0 && ((uintptr_t)workspace_dev & 7) == 0 && ((uintptr_t)t_meas_dev & 7) == 0,
              PM_EINVAL, "cfgs_dev, t_meas_dev and workspace_dev must be 8-byte aligned");
   const int blocks = grad_blocks(n);
-  PM_REQUIRE(workspace_bytes >= (size_t)blocks * 17 * sizeof(double), PM_ENOMEM,
+  PM_REQUIRE(workspace_bytes >= (size_t)blocks * NREC * sizeof(double), PM_ENOMEM,
              "workspace of %zu bytes is smaller than the %zu needed", workspace_bytes,
-             (size_t)blocks * 17 * sizeof(double));
+             (size_t)blocks * NREC * sizeof(double));
   ThetaT<double> th;
-  for (int j = 0; j < 16; ++j) {
+  for (int j = 0; j < NP; ++j) {
     th.v[j] = theta_host[j];
     th.inv[j] = 1.0 / theta_host[j];
   }
@@ -857,7 +872,7 @@ extern "C" pm_status pm_model_grad_f64(const pm_cfg* cfgs_dev, int64_t n, const 
                                                             static_cast<double*>(workspace_dev));
   pm_status st = launch_status("model_grad_kernel");
   if (st != PM_OK) return st;
-  model_grad_finish_kernel<<<1, 17 * 32, 0, s>>>(static_cast<const double*>(workspace_dev), blocks, n, out_dev);
+  model_grad_finish_kernel<<<1, NREC * 32, 0, s>>>(static_cast<const double*>(workspace_dev), blocks, n, out_dev);
   return launch_status("model_grad_finish_kernel");
 }
 
@@ -1094,9 +1109,9 @@ extern "C" pm_status pm_grouped_gemm_autotune(int32_t G, const int32_t* M_host, 
 // resident on every GPU that loads it for the life of the process.
 //
 // Capacity: the call launches the same grid as pm_model_grad (grad_blocks(n):
-// at most four blocks per SM, one partial record of 17 doubles each), so its
+// at most four blocks per SM, one partial record of NREC doubles each), so its
 // partial sums are added in the same order and its output is bit-identical to
-// pm_model_grad's.  The array holds kGradStaticRecords records (557,056
+// pm_model_grad's.  The array holds kGradStaticRecords records (589,824
 // bytes), enough for GPUs of up to 1024 SMs; batches are limited to
 // kGradStaticRecords * kGradThreads = 1,048,576 configurations per call.
 // Every record a call reads is first written by that call, so nothing has to
@@ -1105,7 +1120,7 @@ extern "C" pm_status pm_grouped_gemm_autotune(int32_t G, const int32_t* M_host, 
 namespace pm {
 
 constexpr int kGradStaticRecords = 4096;
-static __device__ __align__(256) double g_grad_scratch[kGradStaticRecords * 17];
+static __device__ __align__(256) double g_grad_scratch[kGradStaticRecords * NREC];
 
 static double* g_grad_scratch_ptr[64];
 static std::mutex g_grad_scratch_mu;
@@ -1156,6 +1171,6 @@ extern "C" pm_status pm_model_grad_noalloc(const pm_cfg* cfgs_dev, int64_t n, co
   model_grad_kernel<float><<<blocks, kGradThreads, 0, s>>>(cfgs_dev, n, to_theta(theta_host, n_sm), n_sm, t_meas_dev, scratch);
   st = launch_status("model_grad_kernel");
   if (st != PM_OK) return st;
-  model_grad_finish_kernel<<<1, 17 * 32, 0, s>>>(scratch, blocks, n, out_dev);
+  model_grad_finish_kernel<<<1, NREC * 32, 0, s>>>(scratch, blocks, n, out_dev);
   return launch_status("model_grad_finish_kernel");
 }

@@ -10,7 +10,7 @@
 namespace pm {
 
 struct SegParams {
-  double th[16];     // stage-model theta (T_launch, B_sus, B_peak, w0, R_TC ...)
+  double th[PM_NPARAMS];   // stage-model theta (T_launch, B_sus, B_peak, w0, R_TC ...)
   double psi[12];    // class scales, precision efficiencies, host link, sync
 };
 
@@ -52,7 +52,7 @@ extern "C" pm_status pm_segment_predict(const pm_segment* segs_dev, int64_t n, c
   PM_REQUIRE(((uintptr_t)segs_dev & 7) == 0 && ((uintptr_t)t_out_dev & 7) == 0, PM_EINVAL,
              "segs_dev and t_out_dev must be 8-byte aligned");
   SegParams p;
-  for (int j = 0; j < 16; ++j) p.th[j] = theta_host->v[j];
+  for (int j = 0; j < PM_NPARAMS; ++j) p.th[j] = theta_host->v[j];
   for (int j = 0; j < 12; ++j) p.psi[j] = psi_host->v[j];
   const int grid = (int)std::min<int64_t>((n + 255) / 256, (int64_t)std::max(1, sm_count()) * 8);
   segment_predict_kernel<<<grid, 256, 0, static_cast<cudaStream_t>(stream)>>>(segs_dev, n, p, n_sm, t_out_dev);

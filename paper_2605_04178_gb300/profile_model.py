@@ -20,7 +20,7 @@ import statistics
 def main():
     ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
     ap.add_argument("--configs", type=int, default=10 ** 6)
-    ap.add_argument("--reading", type=int, default=0, help="0 literal, 1 measured (with its own calibration)")
+    ap.add_argument("--reading", type=int, default=1, help="0 literal, 1 measured (default); each with its own calibration")
     ap.add_argument("--warmup", type=int, default=1)
     ap.add_argument("--reps", type=int, default=5)
     args = ap.parse_args()
@@ -31,7 +31,7 @@ def main():
     import paper_2605_04178_gb300 as pm
     import synthetic as S
     here = os.path.dirname(os.path.abspath(pm.__file__))
-    name = "theta_gb300_measured.json" if args.reading == pm.PM_READING_MEASURED else "theta_gb300.json"
+    name = "theta_gb300.json" if args.reading == pm.PM_READING_MEASURED else "theta_gb300_literal.json"
     with open(os.path.join(here, name)) as f:
         theta = json.load(f)["theta"]
     n_sm = pm.sm_count()
@@ -42,7 +42,7 @@ def main():
     t_out = torch.empty(nc, dtype=torch.float32, device="cuda")
     tm = torch.full((nc,), 1e-3, dtype=torch.float32, device="cuda")
     ws = torch.empty(pm.pm_model_grad_workspace(nc) // 8, dtype=torch.float64, device="cuda")
-    go = torch.empty(17, dtype=torch.float64, device="cuda")
+    go = torch.empty(pm.N_GRAD_OUT, dtype=torch.float64, device="cuda")
     ns = max(1, nc // 180)
     MNK = torch.from_numpy(np.stack([cf["M"], cf["N"], cf["K"]], 1)[:ns].astype(np.int32).ravel()).cuda()
     picks = torch.empty(ns * 24, dtype=torch.uint8, device="cuda")
@@ -65,7 +65,7 @@ def main():
                 times[k].append((s, e))
         torch.cuda.synchronize()
     finally:
-        pm.pm_model_set_reading(pm.PM_READING_LITERAL)
+        pm.pm_model_set_reading(pm.PM_READING_MEASURED)
     for k, _, units in steps:
         ms = statistics.median(s.elapsed_time(e) for s, e in times[k])
         print("%s: %.2f us, %.1f G configurations/s" % (k, ms * 1e3, units / ms / 1e6))

@@ -32,6 +32,6 @@ def reading(request):
     if pm is not None:
         pm.pm_model_set_reading(request.param)
     yield request.param
-    O.set_reading(0)
+    O.set_reading(1)
     if pm is not None:
-        pm.pm_model_set_reading(0)
+        pm.pm_model_set_reading(1)

@@ -17,7 +17,8 @@ reads its values.
 Units: seconds, bytes, bytes/s, FLOP/s.  Parameters theta, by index:
   0 T_launch, 1 B_sus, 2 B_peak, 3 w0, 4 L_TMA, 5 B_TMA per SM,
   6/7/8 R_TC per SM (TF32/BF16/FP8), 9 L_mma, 10/11 TMEM read/write bandwidth
-  per SM, 12 L_mbar, 13 L_alloc + L_dealloc, 14 S_2SM, 15 c_alpha.
+  per SM, 12 L_mbar, 13 L_alloc + L_dealloc, 14 S_2SM, 15 c_alpha,
+  16 rho_L2 (the measured reading's L2-resident TMA speed-up).
 """
 import json
 import math
@@ -36,7 +37,8 @@ def printed_prior(n_sm, f_hz=1.9e9, reading=LITERAL):
     (Table "parameters"), TMEM 16/8 TB/s read/write (Table "parameters"),
     BF16 8192 FLOP per cycle per SM (the dense datasheet rate), TF32 half and
     FP8 twice that, TMEM management 100 ns, S_2SM 1, c_alpha for alpha(2) =
-    0.85.  Cycles are converted at f_hz."""
+    0.85, rho_L2 the peak-to-sustained HBM ratio.  Cycles are converted at
+    f_hz."""
     bf16 = 8192.0 * f_hz
     return [
         5e-6,                      # 0 T_launch
@@ -55,6 +57,7 @@ def printed_prior(n_sm, f_hz=1.9e9, reading=LITERAL):
         100e-9,                    # 13 TMEM alloc + dealloc
         1.0,                       # 14 S_2SM
         0.3 if reading == LITERAL else 0.15,   # 15 c_alpha
+        8.0e12 / 6.8e12,           # 16 rho_L2
     ]
 
 
@@ -86,18 +89,24 @@ def gemm_time(th, n_sm, reading, M, N, K, BM, BN, BK, stages, cta_group, dtype):
     else:
         mmas = n_pass * (BK // k_instr) * up(BM, 128)
     T_TMEM = D / th[10] + mmas * th[9] + D / th[11]
-    # Eq. 3 (and Eq. 6's S_2SM for a pair), TMEM management amortised per K-step
+    # Eq. 3 (and Eq. 6's S_2SM for a pair).  Literal: TMEM management
+    # amortised per K-step.  Measured: it is paid once per launch (below), and
+    # a 64-row tile on one SM takes the tensor time of 128 rows.
     S = 1.0 if g == 1 else th[14]
-    T_c = n_pass * 2.0 * BM * BN * BK / (R * S) + T_TMEM + th[13] / K_tiles
+    if reading == LITERAL:
+        T_c = n_pass * 2.0 * BM * BN * BK / (R * S) + T_TMEM + th[13] / K_tiles
+    else:
+        rows = 128 if (g == 1 and BM < 128) else BM
+        T_c = n_pass * 2.0 * rows * BN * BK / (R * S) + T_TMEM
 
     # Eq. 4 with P = 1: each CTA loads its A rows and 1/g of the B tile
     b_step = l * e * BK * (BM + BN / g)
     working_set = l * e * (M * K + N * K) + 4.0 * M * N
     B_TMA = th[5]
     if reading == MEASURED and th[3] > 0:
-        # loads that hit in L2 arrive faster: scale by B_eff(W)/B_sus (Eq. 16)
-        B_eff = th[1] + (th[2] - th[1]) * math.exp(-working_set / th[3])
-        B_TMA = th[5] * B_eff / th[1]
+        # loads that hit in L2 arrive faster: rho_L2 for a resident working
+        # set, falling to 1 with Eq. 16's exponential shape
+        B_TMA = th[5] * (1.0 + (th[16] - 1.0) * math.exp(-working_set / th[3]))
     T_tma = th[4] + b_step / B_TMA
 
     # Eq. 7: overlap from the ring depth
@@ -115,13 +124,15 @@ def gemm_time(th, n_sm, reading, M, N, K, BM, BN, BK, stages, cta_group, dtype):
         # O_misc: s stages cycle through load, MMAs and barriers
         T_step = max(T_step, (T_tma + T_c + T_sync) / stages)
 
-    # writeback of the FP32 tile, then the kernel total
+    # writeback of the FP32 tile, then the kernel total; the measured reading's
+    # launch includes the TMEM allocation and release of the persistent CTAs
     T_store = th[4] + 4.0 * BM * BN / th[5]
-    T_stage = th[0] + waves * (K_tiles * T_step + T_store)
+    launch = th[0] if reading == LITERAL else th[0] + th[13]
+    T_stage = launch + waves * (K_tiles * T_step + T_store)
 
     # naive roofline floor (Sec. II-A)
     flops = n_pass * 2.0 * M * N * K
-    T_roof = th[0] + max(flops / (n_sm * R * S), working_set / th[2])
+    T_roof = launch + max(flops / (n_sm * R * S), working_set / th[2])
     return max(T_stage, T_roof)
 
 
@@ -145,7 +156,7 @@ CONFIG_ROWS = [
     dict(M=2 ** 20, kind=1),
 ]
 # Load-bound rows (T_io > T_c) that pin the overlap law of Eq. 7: c_alpha = 0.9.
-LOAD_BOUND_ROWS = [dict(M=4096, N=4096, K=4096, BM=64, BN=64, BK=128, stages=s, cta_group=1, dtype=1)
+LOAD_BOUND_ROWS = [dict(M=4096, N=4096, K=4096, BM=128, BN=64, BK=128, stages=s, cta_group=1, dtype=1)
                    for s in (4, 6)]
 
 

@@ -42,16 +42,16 @@ def test_library_exports_every_declared_symbol(pm):
 
 def test_struct_layouts(pm):
     assert ctypes.sizeof(pm.pm_cfg) == 24 == pm.CFG_DTYPE.itemsize
-    assert ctypes.sizeof(pm.pm_params) == 64
+    assert ctypes.sizeof(pm.pm_params) == 4 * pm.N_PARAMS == 68
     assert pm.SEGMENT_DTYPE.itemsize == 64 and ctypes.sizeof(pm.pm_segment_params) == 96
     assert pm.pm_version() == 10000
     assert pm._lib.pm_shutdown() == pm.PM_OK                 # nothing created yet: nothing to release
-    # reading switch: default literal, round trip, bad value refused
-    assert pm.pm_model_reading() == pm.PM_READING_LITERAL
-    pm.pm_model_set_reading(pm.PM_READING_MEASURED)
+    # reading switch: default measured, round trip, bad value refused
     assert pm.pm_model_reading() == pm.PM_READING_MEASURED
     pm.pm_model_set_reading(pm.PM_READING_LITERAL)
-    assert pm._lib.pm_model_set_reading(2) == pm.PM_EINVAL and pm.pm_model_reading() == pm.PM_READING_LITERAL
+    assert pm.pm_model_reading() == pm.PM_READING_LITERAL
+    pm.pm_model_set_reading(pm.PM_READING_MEASURED)
+    assert pm._lib.pm_model_set_reading(2) == pm.PM_EINVAL and pm.pm_model_reading() == pm.PM_READING_MEASURED
 
 
 def test_invalid_tile_rejected_before_launch(pm):
@@ -86,7 +86,7 @@ def test_bad_arguments_rejected(pm):
     assert L.pm_probe_launch(ctypes.byref(a), ctypes.c_void_p(16), ctypes.c_void_p(32), None, None) == pm.PM_EINVAL
     a = pm.probe_args(pm.PM_PROBE_TMA2D, rows=64, cols=64, tile_r=4, tile_c=64)
     assert L.pm_probe_launch(ctypes.byref(a), ctypes.c_void_p(16), ctypes.c_void_p(32), None, None) == pm.PM_EINVAL
-    th = pm.params(np.ones(16))
+    th = pm.params(np.ones(pm.N_PARAMS))
     assert L.pm_model_predict(None, 10, ctypes.byref(th), 152, None, None) == pm.PM_EINVAL
     assert L.pm_model_predict(ctypes.c_void_p(8), 10, ctypes.byref(th), 0, ctypes.c_void_p(8), None) == pm.PM_EINVAL
     assert L.pm_model_predict(None, 0, ctypes.byref(th), 152, None, None) == pm.PM_OK   # empty batch: nothing to do

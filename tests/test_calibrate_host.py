@@ -53,16 +53,18 @@ class OracleLoss(torch.autograd.Function):
         return go * g, None, None
 
 
-def test_prior_matches_oracle_prior():
-    assert np.allclose(C.prior_theta(N_SM), O.prior_theta(N_SM), rtol=0, atol=0)
+@pytest.mark.parametrize("r", [0, 1])
+def test_prior_matches_oracle_prior(r):
+    assert np.array_equal(C.prior_theta(N_SM, reading=r), O.prior_theta(N_SM, reading=r))
 
 
 # Parameters the table does not determine one by one at the generating
 # point: TMEM read and write bandwidth enter every strategy-A K-step only as
-# D (1/BW_rd + 1/BW_wr) (Eq. 2), so only that sum is fixed; under the
-# measured reading the ring bound of Eq. 8 sets every K-step of the table at
-# the printed priors, so alpha's c_alpha (Eq. 7) is not seen at all.
-UNIDENTIFIABLE = {0: {10, 11}, 1: {10, 11, 15}}
+# D (1/BW_rd + 1/BW_wr) (Eq. 2), so only that sum is fixed; the literal
+# reading does not use rho_L2; under the measured reading the ring bound of
+# Eq. 8 sets every K-step of the table at the printed priors, so alpha's
+# c_alpha (Eq. 7) is not seen at all.
+UNIDENTIFIABLE = {0: {10, 11, 16}, 1: {10, 11, 15}}
 
 
 def identifiable(cols, theta):
@@ -73,7 +75,7 @@ def identifiable(cols, theta):
     J = g * theta[None, :] / t[:, None]
     _, sv, Vt = np.linalg.svd(J, full_matrices=False)
     null = Vt[sv < 1e-6 * sv[0]]
-    proj = np.sqrt((null ** 2).sum(0)) if len(null) else np.zeros(16)
+    proj = np.sqrt((null ** 2).sum(0)) if len(null) else np.zeros(O.N_PARAMS)
     return proj < 1e-6
 
 
@@ -89,7 +91,7 @@ def test_fit_recovers_generating_parameters(reading):
     ident = identifiable(cols, truth)
     assert set(np.where(~ident)[0]) == UNIDENTIFIABLE[reading]
     t_meas = np.array([r["t"] for r in rows])
-    start = truth * np.exp(0.3 * S.normal(5, 16).astype(np.float64))
+    start = truth * np.exp(0.3 * S.normal(5, O.N_PARAMS).astype(np.float64))
     theta, trace = C.fit(lambda th: OracleLoss.apply(th, cols, t_meas), start, reg=0.0)
     err = np.abs(np.log(theta) - np.log(truth))
     assert np.all(err[ident] <= 1e-3), dict(zip(np.where(ident)[0], err[ident]))

@@ -53,9 +53,9 @@ def test_adjoint_matches_central_differences_all_components(lib, reading):
     phi, h = np.log(th), 1e-4
     t0 = O.model_batch(cols, th, N_SM)
     smooth = np.isfinite(t0)
-    for j in range(16):
-        tp = O.model_batch(cols, np.exp(phi + h * np.eye(16)[j]), N_SM)
-        tm = O.model_batch(cols, np.exp(phi - h * np.eye(16)[j]), N_SM)
+    for j in range(O.N_PARAMS):
+        tp = O.model_batch(cols, np.exp(phi + h * np.eye(O.N_PARAMS)[j]), N_SM)
+        tm = O.model_batch(cols, np.exp(phi - h * np.eye(O.N_PARAMS)[j]), N_SM)
         second = np.abs((tp - t0) - (t0 - tm))
         slope = np.abs(tp - tm) / (2 * h)
         smooth &= (second <= 1e-9 * t0) | (second <= 10 * h * h * slope)
@@ -69,9 +69,9 @@ def test_adjoint_matches_central_differences_all_components(lib, reading):
     obj(theta).backward()
     an = theta.grad.numpy() * th                      # dL / d ln theta_j
     gscale = np.max(np.abs(an))
-    for j in range(16):
-        Lp = float(obj(torch.tensor(np.exp(phi + h * np.eye(16)[j]))))
-        Lm = float(obj(torch.tensor(np.exp(phi - h * np.eye(16)[j]))))
+    for j in range(O.N_PARAMS):
+        Lp = float(obj(torch.tensor(np.exp(phi + h * np.eye(O.N_PARAMS)[j]))))
+        Lm = float(obj(torch.tensor(np.exp(phi - h * np.eye(O.N_PARAMS)[j]))))
         fd = (Lp - Lm) / (2 * h)
         assert abs(fd - an[j]) <= 1e-3 * abs(an[j]) + 1e-9 * gscale, (j, fd, an[j])
 
@@ -79,7 +79,7 @@ def test_adjoint_matches_central_differences_all_components(lib, reading):
 def test_gpu_fit_lowers_loss(lib):
     from paper_2605_04178_gb300 import calibrate as C
     rows, cols = _rows(3000, 71)
-    truth = C.prior_theta(N_SM) * np.exp(0.2 * S.normal(72, 16).astype(np.float64))
+    truth = C.prior_theta(N_SM) * np.exp(0.2 * S.normal(72, O.N_PARAMS).astype(np.float64))
     truth[15] = 0.4
     t = O.model_batch(cols, truth.astype(np.float32).astype(np.float64), N_SM)
     for r, v in zip(rows, t):

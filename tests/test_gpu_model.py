@@ -87,7 +87,7 @@ def grad_gpu(lib, c, theta, t_meas):
     dev = lib.cfg_tensor(c)
     tm = torch.from_numpy(t_meas.astype(np.float32)).cuda()
     ws = torch.empty(lib.pm_model_grad_workspace(n) // 8, dtype=torch.float64, device="cuda")
-    out = torch.empty(17, dtype=torch.float64, device="cuda")
+    out = torch.empty(lib.N_GRAD_OUT, dtype=torch.float64, device="cuda")
     lib.pm_model_grad(dev, n, theta, N_SM, tm, ws, out)
     o = out.cpu().numpy()
     return o[0], o[1:]
@@ -200,7 +200,7 @@ def test_grad_f64_matches_oracle_tightly(lib, reading, n):
     dev = lib.cfg_tensor(c)
     m = len(t_meas)
     ws = torch.empty(lib.pm_model_grad_workspace(m) // 8, dtype=torch.float64, device="cuda")
-    out = torch.empty(17, dtype=torch.float64, device="cuda")
+    out = torch.empty(lib.N_GRAD_OUT, dtype=torch.float64, device="cuda")
     lib.pm_model_grad_f64(dev, m, th, N_SM, torch.from_numpy(t_meas).cuda(), ws, out)
     o = out.cpu().numpy()
     L_orc, g_orc = O.model_loss_grad(c, th, N_SM, t_meas)

@@ -58,7 +58,7 @@ def test_prior_overlap_in_the_printed_alpha_range(reading):
 def test_cta_pair_traffic_reduction_matches_the_printed_factor():
     # per-K-step bytes of one CTA, b_step = l e BK (BM + BN/g): a square tile in
     # a pair loads 3/4 of what it loads alone, the printed ~1.33x reduction
-    th = O.prior_theta(160, F)
+    th = O.prior_theta(160, F, O.READING_LITERAL)
     th[15] = 10.0                      # loads fully exposed
     th[4] = th[12] = th[9] = th[13] = 0.0
     th[6] = th[7] = th[8] = th[10] = th[11] = th[2] = 1e30
@@ -79,10 +79,14 @@ def test_worked_example_is_only_banded():
     # B200's 148 SMs gives 10.5 ms, within a factor-of-three band of the
     # printed measurement
     w = GOLDEN["worked_example_b200"]
-    th = O.prior_theta(w["n_sm_b200"], F)
+    th = O.prior_theta(w["n_sm_b200"], F, O.READING_LITERAL)
     cfg = {k: np.array([v]) for k, v in dict(M=w["M"], N=w["N"], K=w["K"], BM=w["BM"], BN=w["BN"], BK=w["BK"],
                                                 stages=2, cta_group=1, dtype=1, kind=0).items()}
-    t = float(O.model_batch(cfg, th, w["n_sm_b200"])[0]) * 1e3
+    O.set_reading(O.READING_LITERAL)          # the printed equations
+    try:
+        t = float(O.model_batch(cfg, th, w["n_sm_b200"])[0]) * 1e3
+    finally:
+        O.set_reading(O.READING_MEASURED)
     assert w["measured_ms"] / 3 < t < w["measured_ms"] * 3
     assert abs(w["predicted_ms"] / w["measured_ms"] - 1) < 0.02       # the printed 1.8 % error
 

@@ -49,11 +49,11 @@ def test_noalloc_matches_oracle_on_consecutive_calls(lib):
         scale = (2.0 / n) * np.sum(np.abs(r[:, None] * gi / tt[:, None]), axis=0)
         # the workspace entry point on the same inputs
         ws = torch.empty(lib.pm_model_grad_workspace(n) // 8, dtype=torch.float64, device="cuda")
-        ref = torch.empty(17, dtype=torch.float64, device="cuda")
+        ref = torch.empty(lib.N_GRAD_OUT, dtype=torch.float64, device="cuda")
         lib.pm_model_grad(dev, n, th, N_SM, tm, ws, ref)
         rr = ref.cpu().numpy()
         for _ in range(2):
-            out = torch.full((17,), float("nan"), dtype=torch.float64, device="cuda")
+            out = torch.full((lib.N_GRAD_OUT,), float("nan"), dtype=torch.float64, device="cuda")
             lib.pm_model_grad_noalloc(dev, n, th, N_SM, tm, out)
             torch.cuda.synchronize()
             o = out.cpu().numpy()
@@ -65,8 +65,8 @@ def test_noalloc_matches_oracle_on_consecutive_calls(lib):
 def test_noalloc_rejects_batches_beyond_capacity(lib):
     n = 1048576 + 1
     dev = torch.zeros(24, dtype=torch.uint8, device="cuda")
-    out = torch.zeros(17, dtype=torch.float64, device="cuda")
+    out = torch.zeros(lib.N_GRAD_OUT, dtype=torch.float64, device="cuda")
     tm = torch.ones(1, dtype=torch.float32, device="cuda")
     with pytest.raises(lib.PMError) as e:
-        lib.pm_model_grad_noalloc(dev, n, np.ones(16), N_SM, tm, out)
+        lib.pm_model_grad_noalloc(dev, n, np.ones(lib.N_PARAMS), N_SM, tm, out)
     assert e.value.status == lib.PM_ENOMEM and "at most 1048576" in str(e.value)
