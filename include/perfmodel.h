@@ -362,23 +362,47 @@ pm_status pm_autotune_pick(const int32_t* MNK_dev, int64_t n, int32_t dtype, con
                            int32_t n_sm, pm_cfg* picks_dev, float* t_pred_dev, void* stream);
 
 /* Stage-model makespan of one grouped launch with given per-group tiles
- * (the C9 reading of the grouped GEMM: per group tau_g = K_tiles T_step_g +
- * T_store_g, tiles listed group by group, tile t on worker t mod n_conc,
- * T_hat = T_launch + max_w sum tau).  Host arrays of G entries; *t_pred_host
- * in seconds, NaN for a cta_group 2 launch when n_sm < 2.  Synchronises. */
+ * (the grouped reading of Eq. 8, exact for pm_grouped_gemm_run's static
+ * schedule: per group tau_g = K_tiles T_step_g + T_store_g; the launch lists
+ * the groups largest tile (BM x BN) first, ties in the caller's order, and
+ * deals the listed tiles to the n_conc workers round by round, the worker
+ * order reversed on odd rounds when G > 1; T_hat = launch + max_w sum of the
+ * worker's tau, launch = T_launch, plus L_alloc + L_dealloc under the
+ * measured reading).  Host arrays of G entries (G <= 1024); *t_pred_host in
+ * seconds, NaN for a cta_group 2 launch when n_sm < 2.  Allocates a few KB
+ * of stream-ordered device scratch.  Synchronises. */
 pm_status pm_grouped_predict(int32_t G, const int32_t* M_host, int32_t N, int32_t K, const int16_t* BM_host,
                              const int16_t* BN_host, int32_t BK, int32_t stages, int32_t cta_group, int32_t dtype,
                              const pm_params* theta_host, int32_t n_sm, float* t_pred_host, void* stream);
 
+/* pm_grouped_predict in FP64 with the makespan's gradient, for the
+ * calibration fit's grouped rows (Sec. III-D): the busiest worker's tiles
+ * (the first such worker on ties) carry the gradient, each through the
+ * adjoint of its K-steps and writeback.  theta_host: PM_NPARAMS doubles;
+ * out_host: 1 + PM_NPARAMS doubles {T_hat, dT_hat/dtheta_0 ..}.  Errors as
+ * pm_grouped_predict.  Synchronises. */
+pm_status pm_grouped_grad(int32_t G, const int32_t* M_host, int32_t N, int32_t K, const int16_t* BM_host,
+                          const int16_t* BN_host, int32_t BK, int32_t stages, int32_t cta_group, int32_t dtype,
+                          const double* theta_host, int32_t n_sm, double* out_host, void* stream);
+
 /* Grouped autotuner: for each launch-level (BK, stages, cta_group), each
  * group takes the (BM, BN) minimising tiles_g * (K_tiles T_step_g + T_store_g);
- * the launch whose static schedule has the smallest makespan
- *   T_launch + max_w sum_{t = w mod n_conc} tau(t)
- * wins.  Results to host: BM_out_host/BN_out_host (G each), launch_out_host
+ * the launch whose static schedule (pm_grouped_predict) has the smallest
+ * makespan wins.  Results to host: BM_out_host/BN_out_host (G each), launch_out_host
  * {BK, stages, cta_group}, *t_pred_host.  Synchronises. */
 pm_status pm_grouped_autotune(int32_t G, const int32_t* M_host, int32_t N, int32_t K, int32_t dtype,
                               const pm_params* theta_host, int32_t n_sm, int16_t* BM_out_host,
                               int16_t* BN_out_host, int32_t* launch_out_host, float* t_pred_host, void* stream);
+
+/* Every launch-level candidate the grouped autotuner weighs, in its order
+ * (BK, stages, cta_group lexicographic; 20 candidates): t_pred_host[20]
+ * their predicted makespans (+inf where some group has no valid tile),
+ * BM_host/BN_host [20 x G] the per-group tiles each picks, launch_host
+ * [20 x 3] {BK, stages, cta_group}.  For measuring the grouped family over
+ * the launch space.  Synchronises. */
+pm_status pm_grouped_candidates(int32_t G, const int32_t* M_host, int32_t N, int32_t K, int32_t dtype,
+                                const pm_params* theta_host, int32_t n_sm, float* t_pred_host, int16_t* BM_host,
+                                int16_t* BN_host, int32_t* launch_host, void* stream);
 
 /* Model-pruned measured grouped autotuning (BF16): the grouped autotuner's
  * k best launch-level candidates (k in 1..20, each with its per-group tiles)
@@ -404,9 +428,14 @@ pm_status pm_grouped_gemm_autotune(int32_t G, const int32_t* M_host, int32_t N, 
  *     + [h2d_bytes > 0] (h2d_bytes / B_h2d + tau_h2d)           (Eq. 15)
  *     + [d2h_bytes > 0] (d2h_bytes / B_d2h + tau_d2h)
  *     + syncs * tau_sync
- * (the roofline term only when kernels >= 1; copies and kernels are summed,
- * not overlapped, as the paper states).  T_launch, B_sus, B_peak, w0 and the
- * per-SM rates R_TC come from the stage model's theta. */
+ *     + (N_c - 1) tau_c,  tau_c = kappa_launch * kernels * T_launch
+ *                                + kappa[class] * (the s_class roofline term)
+ * (the roofline and tau_c terms only when kernels >= 1; copies and kernels
+ * are summed, not overlapped, as the paper states; the last line is Sec.
+ * III-A.6's (N_c - 1) tau_c for a segment run as N_c concurrent copies on N_c
+ * streams, with tau_c the part of one copy that cannot overlap the others).
+ * T_launch, B_sus, B_peak, w0 and the per-SM rates R_TC come from the stage
+ * model's theta. */
 typedef enum { PM_SEG_MEMORY = 0, PM_SEG_COMPUTE = 1, PM_SEG_BALANCED = 2, PM_SEG_STENCIL = 3 } pm_segment_class;
 
 typedef struct {
@@ -420,16 +449,18 @@ typedef struct {
   int32_t kernels;       /* kernel launches per execution (>= 0) */
   int32_t syncs;         /* host synchronisation points per execution */
   int32_t execs;         /* executions of the segment (>= 1) */
-  int32_t reserved;      /* must be 0 */
+  int32_t streams;       /* concurrent copies N_c on as many streams (0 or 1: one) */
 } pm_segment;            /* 64 bytes */
 
 /* Segment parameters psi (SI units): 0-3 class scales s_class (memory,
  * compute, balanced, stencil), 4-6 precision efficiencies eta (FP32, BF16,
- * FP8), 7 B_h2d, 8 tau_h2d, 9 B_d2h, 10 tau_d2h, 11 tau_sync. */
-typedef struct { double v[12]; } pm_segment_params;
+ * FP8), 7 B_h2d, 8 tau_h2d, 9 B_d2h, 10 tau_d2h, 11 tau_sync, 12-15 kappa per
+ * class, 16 kappa_launch (concurrent-stream interference). */
+#define PM_NPSI 17
+typedef struct { double v[PM_NPSI]; } pm_segment_params;
 
 /* T (seconds, FP64) of n segments on the GPU.  segs_dev: n pm_segment;
- * t_out_dev: n doubles.  A record with an unknown class or precision, a
+ * t_out_dev: n doubles.  A record with a negative stream count, an unknown class or precision, a
  * negative size or count, or execs < 1 yields NaN.  Async. */
 pm_status pm_segment_predict(const pm_segment* segs_dev, int64_t n, const pm_params* theta_host,
                              const pm_segment_params* psi_host, int32_t n_sm, double* t_out_dev, void* stream);

@@ -15,9 +15,11 @@ Parity status of each part (pins are in tests/test_oracle_*.py):
   model_batch         pinned: hand-evaluated rows, closed forms, homogeneity, monotonicity
   model gradient      pinned: central differences and Euler's homogeneity identity
   autotune            pinned: brute force in plain Python on small spaces
-  grouped model       pinned: reduces to the single-GEMM stage time for one group
+  grouped model       pinned: reduces to the single-GEMM stage time for one group; brute-force
+                      worker loop of the launch's schedule; central differences and Euler's
+                      identity for its gradient
   segment_predict     pinned: closed forms of each term (Eq. 16 off, pure transfers, extra launches,
-                      executions), hand-evaluated rows, homogeneity
+                      executions, concurrent streams), hand-evaluated rows, homogeneity
   mma/tmem probe sums closed forms (exact integer arithmetic)
 """
 from __future__ import annotations
@@ -86,12 +88,14 @@ def _load():
                                                 ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                                 P, ctypes.c_int]
             lib.orc_grouped_predict.restype = ctypes.c_double
+            lib.orc_grouped_predict_grad.argtypes = lib.orc_grouped_predict.argtypes + [P]
+            lib.orc_grouped_predict_grad.restype = ctypes.c_double
             lib.orc_grouped_autotune.argtypes = [ctypes.c_int, P, ctypes.c_int32, ctypes.c_int32,
                                                  ctypes.c_int, P, ctypes.c_int, P, P, P]
             lib.orc_grouped_autotune.restype = ctypes.c_double
             lib.orc_set_reading.argtypes = [ctypes.c_int]
             lib.orc_reading.restype = ctypes.c_int
-            lib.orc_segment_predict.argtypes = [i64] + [P] * 10 + [P, P, ctypes.c_int, P]
+            lib.orc_segment_predict.argtypes = [i64] + [P] * 11 + [P, P, ctypes.c_int, P]
             lib.orc_stencil5_f32.argtypes = [P, i64, i64, P]
             _lib = lib
     return _lib
@@ -245,6 +249,18 @@ def grouped_predict(Mg, N, K, BMg, BNg, BK, s, g, dtype, theta, n_sm) -> float:
                                              int(BK), int(s), int(g), int(dtype), _ptr(th), int(n_sm)))
 
 
+def grouped_predict_grad(Mg, N, K, BMg, BNg, BK, s, g, dtype, theta, n_sm):
+    """(T_hat, dT_hat/dtheta [N_PARAMS]) of one grouped launch (dual numbers)."""
+    Mg = _c(Mg, np.int32)
+    BMg = _c(BMg, np.int32)
+    BNg = _c(BNg, np.int32)
+    th = _c(theta, np.float64)
+    grad = np.zeros(N_PARAMS, dtype=np.float64)
+    t = _load().orc_grouped_predict_grad(len(Mg), _ptr(Mg), int(N), int(K), _ptr(BMg), _ptr(BNg), int(BK), int(s),
+                                         int(g), int(dtype), _ptr(th), int(n_sm), _ptr(grad))
+    return float(t), grad
+
+
 def grouped_autotune(Mg, N, K, dtype, theta, n_sm):
     """(T_hat, BM per group, BN per group, (BK, stages, cta_group)) of the best grouped launch."""
     Mg = _c(Mg, np.int32)
@@ -269,7 +285,8 @@ def stencil5_f32(x: np.ndarray) -> np.ndarray:
 
 
 _SEG_F64 = ("flops", "bytes", "working_set", "h2d_bytes", "d2h_bytes")
-_SEG_I32 = ("cls", "precision", "kernels", "syncs", "execs")
+_SEG_I32 = ("cls", "precision", "kernels", "syncs", "execs", "streams")
+N_PSI = 17
 
 
 def segment_predict(segs: dict, theta, psi, n_sm: int) -> np.ndarray:
@@ -280,7 +297,7 @@ def segment_predict(segs: dict, theta, psi, n_sm: int) -> np.ndarray:
     cols += [_c(segs.get(f, np.ones(n) if f == "execs" else np.zeros(n)), np.int32) for f in _SEG_I32]
     th = _c(theta, np.float64)
     ps = _c(psi, np.float64)
-    assert th.size == N_PARAMS and ps.size == 12
+    assert th.size == N_PARAMS and ps.size == N_PSI
     t = np.empty(n, dtype=np.float64)
     _load().orc_segment_predict(n, *[_ptr(c) for c in cols], _ptr(th), _ptr(ps), int(n_sm), _ptr(t))
     return t

@@ -207,6 +207,9 @@ static inline double dmax(double a, double b) { return (a >= b) ? a : b; }
 static inline double dclamp01(double a) { return a <= 0.0 ? 0.0 : (a >= 1.0 ? 1.0 : a); }
 template <class T> static inline T lift(double v) { return T(v); }
 template <> inline Dual lift<Dual>(double v) { return dconst(v); }
+// The value of either type, for comparisons that choose a branch.
+static inline double value_of(double a) { return a; }
+static inline double value_of(const Dual& a) { return a.v; }
 
 // ---------------------------------------------------------------------------
 // Model parameters theta (SI units: seconds, bytes/s, FLOP/s, bytes):
@@ -520,10 +523,14 @@ extern "C" void orc_autotune(i64 n, const int32_t* MNK, int dtype, const double*
 // ---------------------------------------------------------------------------
 // Grouped launch (one persistent kernel over G problems with shared N, K).
 // The paper has no grouped model; this extends Eq. 8 to the kernel's static
-// schedule: tiles are listed group by group, tile t runs on worker
-// t mod n_conc, a group-g tile costs tau_g = K_tiles * T_step_g + T_store_g,
-// and the launch ends with its busiest worker:
-//   T_hat = T_launch + max_w sum_{t = w mod n_conc} tau(t).
+// schedule.  With several groups the launch lists them largest tile first
+// (BM x BN; ties keep the caller's order) and its tiles are dealt to the
+// n_conc workers (CTAs) round by round, reversing the worker order on odd
+// rounds; one group is dealt plainly round by round.  A group-g tile costs
+// tau_g = K_tiles * T_step_g + T_store_g, and the launch ends with its
+// busiest worker:
+//   T_hat = launch + max_w sum_g n_{w,g} tau_g,
+// n_{w,g} = the number of group-g tiles worker w is dealt.
 // ---------------------------------------------------------------------------
 // Working set of a grouped launch: every group's A rows, its own B and its C.
 static double grouped_working_set(int G, const int32_t* Mg, int32_t N, int32_t K, int dtype) {
@@ -533,30 +540,70 @@ static double grouped_working_set(int G, const int32_t* Mg, int32_t N, int32_t K
   return W;
 }
 
-extern "C" double orc_grouped_predict(int G, const int32_t* Mg, int32_t N, int32_t K,
-                                      const int32_t* BMg, const int32_t* BNg, int BK, int s, int g,
-                                      int dtype, const double* theta, int n_sm) {
-  if (g != 1 && n_sm < 2) return NAN;   // no SM pair for a cta_group::2 launch
+// The order in which a launch lists its groups.
+static std::vector<int> group_order(int G, const int32_t* BMg, const int32_t* BNg) {
+  std::vector<int> order(G);
+  for (int q = 0; q < G; ++q) order[q] = q;
+  if (G > 1)
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int a, int b) { return (i64)BMg[a] * BNg[a] > (i64)BMg[b] * BNg[b]; });
+  return order;
+}
+
+// The worker that runs the tile at position i of the launch's list.
+static i64 worker_of(i64 i, i64 n_conc, bool reverse_odd_rounds) {
+  const i64 round = i / n_conc, j = i % n_conc;
+  return (reverse_odd_rounds && round % 2 == 1) ? n_conc - 1 - j : j;
+}
+
+template <class T>
+static T grouped_time(int G, const int32_t* Mg, int32_t N, int32_t K, const int32_t* BMg, const int32_t* BNg,
+                      int BK, int s, int g, int dtype, const T* th, int n_sm) {
+  if (g != 1 && n_sm < 2) return lift<T>(NAN);   // no SM pair for a cta_group::2 launch
   const i64 n_conc = (g == 1) ? n_sm : 2 * (n_sm / 2);
-  std::vector<double> busy(n_conc, 0.0);
   const double W = grouped_working_set(G, Mg, N, K, dtype);
+  const std::vector<int> order = group_order(G, BMg, BNg);
+  std::vector<T> busy(n_conc, lift<T>(0.0));
+  std::vector<i64> count(n_conc);
   i64 t = 0;
-  for (int q = 0; q < G; ++q) {
+  for (int q : order) {
     Cfg c;
     c.M = Mg[q]; c.N = N; c.K = K; c.BM = BMg[q]; c.BN = BNg[q]; c.BK = BK; c.s = s; c.g = g;
     c.dtype = dtype; c.kind = K_GEMM;
     const i64 Kt = ceil_div(K, BK);
-    double Tstep, Tstore;
-    stage_terms<double>(c, Kt, theta, W, Tstep, Tstore);
-    const double tau = (double)Kt * Tstep + Tstore;
-    const i64 tiles = cta_tiles(c.M, N, c.BM, c.BN, g);
+    T Tstep, Tstore;
+    stage_terms<T>(c, Kt, th, W, Tstep, Tstore);
+    const T tau = lift<T>((double)Kt) * Tstep + Tstore;
     // With cta_group 2 a pair of consecutive tiles runs on a worker pair;
     // each CTA of the pair is one worker.
-    for (i64 j = 0; j < tiles; ++j, ++t) busy[t % n_conc] += tau;
+    const i64 tiles = cta_tiles(c.M, N, c.BM, c.BN, g);
+    std::fill(count.begin(), count.end(), (i64)0);
+    for (i64 j = 0; j < tiles; ++j, ++t) ++count[worker_of(t, n_conc, G > 1)];
+    for (i64 w = 0; w < n_conc; ++w)
+      if (count[w]) busy[w] = busy[w] + lift<T>((double)count[w]) * tau;
   }
-  double mx = 0.0;
-  for (double b : busy) mx = std::max(mx, b);
-  return theta[0] + (g_reading == 1 ? theta[13] : 0.0) + mx;
+  T mx = busy[0];                                  // the first busiest worker
+  for (i64 w = 1; w < n_conc; ++w)
+    if (value_of(busy[w]) > value_of(mx)) mx = busy[w];
+  const T launch = g_reading == 1 ? th[0] + th[13] : th[0];
+  return launch + mx;
+}
+
+extern "C" double orc_grouped_predict(int G, const int32_t* Mg, int32_t N, int32_t K,
+                                      const int32_t* BMg, const int32_t* BNg, int BK, int s, int g,
+                                      int dtype, const double* theta, int n_sm) {
+  return grouped_time<double>(G, Mg, N, K, BMg, BNg, BK, s, g, dtype, theta, n_sm);
+}
+
+// The same makespan with its gradient in theta (grad: NP doubles).
+extern "C" double orc_grouped_predict_grad(int G, const int32_t* Mg, int32_t N, int32_t K,
+                                           const int32_t* BMg, const int32_t* BNg, int BK, int s, int g,
+                                           int dtype, const double* theta, int n_sm, double* grad) {
+  Dual th[NP];
+  for (int j = 0; j < NP; ++j) th[j] = dvar(theta[j], j);
+  const Dual t = grouped_time<Dual>(G, Mg, N, K, BMg, BNg, BK, s, g, dtype, th, n_sm);
+  for (int j = 0; j < NP; ++j) grad[j] = t.d[j];
+  return t.v;
 }
 
 // Grouped autotune: for each launch-level (BK, stages, cta_group) in
@@ -608,19 +655,25 @@ extern "C" double orc_grouped_autotune(int G, const int32_t* Mg, int32_t N, int3
 // launches, a class-scaled roofline whose bandwidth follows Eq. 16, the host
 // transfers of Eq. 15 and its synchronisation points; the total multiplies by
 // the number of executions.  Copies and kernels are summed (no overlap).
+// Concurrent streams (Sec. III-A.6): a segment run as N_c copies on N_c
+// streams adds (N_c - 1) tau_c to its single-stream time, with tau_c the part
+// of one copy that cannot overlap the others: a fraction kappa_launch of its
+// launches and a fraction kappa_class of its class-scaled roofline time.
 //   psi: 0-3 class scales (memory, compute, balanced, stencil),
 //        4-6 precision efficiencies (FP32, BF16, FP8),
-//        7 B_h2d, 8 tau_h2d, 9 B_d2h, 10 tau_d2h, 11 tau_sync.
+//        7 B_h2d, 8 tau_h2d, 9 B_d2h, 10 tau_d2h, 11 tau_sync,
+//        12-15 kappa per class, 16 kappa_launch.
 // ---------------------------------------------------------------------------
+enum { NPSI = 17 };
 extern "C" void orc_segment_predict(i64 n, const double* flops, const double* bytes, const double* wset,
                                     const double* h2d, const double* d2h, const int32_t* cls,
                                     const int32_t* prec, const int32_t* kernels, const int32_t* syncs,
-                                    const int32_t* execs, const double* theta, const double* psi, int n_sm,
-                                    double* t_out) {
+                                    const int32_t* execs, const int32_t* streams, const double* theta,
+                                    const double* psi, int n_sm, double* t_out) {
   for (i64 i = 0; i < n; ++i) {
     const bool ok = cls[i] >= 0 && cls[i] <= 3 && prec[i] >= 0 && prec[i] <= 2 && kernels[i] >= 0 &&
-                    syncs[i] >= 0 && execs[i] >= 1 && flops[i] >= 0 && bytes[i] >= 0 && wset[i] >= 0 &&
-                    h2d[i] >= 0 && d2h[i] >= 0;
+                    syncs[i] >= 0 && execs[i] >= 1 && streams[i] >= 0 && flops[i] >= 0 && bytes[i] >= 0 &&
+                    wset[i] >= 0 && h2d[i] >= 0 && d2h[i] >= 0;
     if (!ok) {
       t_out[i] = NAN;
       continue;
@@ -633,7 +686,10 @@ extern "C" void orc_segment_predict(i64 n, const double* flops, const double* by
       const double peak = n_sm * theta[rate_index(prec[i])] * psi[4 + prec[i]];
       const double memory_time = bytes[i] / bandwidth;
       const double compute_time = flops[i] / peak;
-      t += launches + psi[cls[i]] * (compute_time > memory_time ? compute_time : memory_time);
+      const double roof = psi[cls[i]] * (compute_time > memory_time ? compute_time : memory_time);
+      t += launches + roof;
+      // N_c concurrent copies: (N_c - 1) tau_c more (0 or 1 stream: none)
+      if (streams[i] > 1) t += (streams[i] - 1) * (psi[16] * launches + psi[12 + cls[i]] * roof);
     }
     if (h2d[i] > 0) t += h2d[i] / psi[7] + psi[8];                          // Eq. 15
     if (d2h[i] > 0) t += d2h[i] / psi[9] + psi[10];

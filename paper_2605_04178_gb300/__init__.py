@@ -24,6 +24,7 @@ PM_KIND_GEMM, PM_KIND_COPY, PM_KIND_TRIAD, PM_KIND_TMA2D = 0, 1, 2, 3
 PM_READING_LITERAL, PM_READING_MEASURED = 0, 1
 N_PARAMS = 17                     # PM_NPARAMS: entries of theta (pm_params)
 N_GRAD_OUT = N_PARAMS + 1         # pm_model_grad output: loss, then the gradient
+N_PSI = 17                        # PM_NPSI: entries of the segment parameters (pm_segment_params)
 PM_PROBE_COPY, PM_PROBE_TRIAD, PM_PROBE_TMA2D, PM_PROBE_PCHASE = 1, 2, 3, 4
 PM_PROBE_H2D, PM_PROBE_D2H, PM_PROBE_MMA, PM_PROBE_MBAR, PM_PROBE_TMEM_LD, PM_PROBE_TMEM_ST = 5, 6, 7, 8, 9, 10
 PM_PROBE_HOST_READ, PM_PROBE_HOST_WRITE, PM_PROBE_STENCIL = 11, 12, 13
@@ -49,13 +50,13 @@ class pm_params(ctypes.Structure):
 # numpy view of pm_segment (64 bytes)
 SEGMENT_DTYPE = np.dtype([("flops", "<f8"), ("bytes", "<f8"), ("working_set", "<f8"), ("h2d_bytes", "<f8"),
                           ("d2h_bytes", "<f8"), ("cls", "<i4"), ("precision", "<i4"), ("kernels", "<i4"),
-                          ("syncs", "<i4"), ("execs", "<i4"), ("reserved", "<i4")], align=True)
+                          ("syncs", "<i4"), ("execs", "<i4"), ("streams", "<i4")], align=True)
 assert SEGMENT_DTYPE.itemsize == 64
 PM_SEG_MEMORY, PM_SEG_COMPUTE, PM_SEG_BALANCED, PM_SEG_STENCIL = 0, 1, 2, 3
 
 
 class pm_segment_params(ctypes.Structure):
-    _fields_ = [("v", ctypes.c_double * 12)]
+    _fields_ = [("v", ctypes.c_double * N_PSI)]
 
 
 class pm_probe_args(ctypes.Structure):
@@ -100,7 +101,7 @@ def _timing(res) -> dict:
 EXPORTS = ("pm_probe_launch", "pm_probe_run", "pm_streams_run", "pm_gemm_operand_bytes", "pm_gemm_prepare", "pm_gemm_run",
            "pm_gemm_bench", "pm_gemm_host_workspace", "pm_gemm_host",
            "pm_grouped_gemm_run", "pm_model_predict", "pm_model_set_reading", "pm_model_reading", "pm_model_grad_workspace", "pm_model_grad", "pm_model_grad_f64", "pm_model_grad_noalloc",
-           "pm_autotune_pick", "pm_autotune_topk", "pm_gemm_autotune", "pm_grouped_predict", "pm_grouped_autotune", "pm_grouped_gemm_autotune", "pm_segment_predict", "pm_last_error", "pm_device_status", "pm_shutdown",
+           "pm_autotune_pick", "pm_autotune_topk", "pm_gemm_autotune", "pm_grouped_predict", "pm_grouped_grad", "pm_grouped_candidates", "pm_grouped_autotune", "pm_grouped_gemm_autotune", "pm_segment_predict", "pm_last_error", "pm_device_status", "pm_shutdown",
            "pm_watchdog_selftest", "pm_version", "pm_clock_sample")
 
 
@@ -147,6 +148,8 @@ def _load():
                              ctypes.c_int, P, ctypes.POINTER(pm_cfg), ctypes.POINTER(pm_probe_result)],
         "pm_grouped_autotune": [i32, P, i32, i32, i32, ctypes.POINTER(pm_params), i32, P, P, P, P, P],
         "pm_grouped_predict": [i32, P, i32, i32, P, P, i32, i32, i32, i32, ctypes.POINTER(pm_params), i32, P, P],
+        "pm_grouped_grad": [i32, P, i32, i32, P, P, i32, i32, i32, i32, P, i32, P, P],
+        "pm_grouped_candidates": [i32, P, i32, i32, i32, ctypes.POINTER(pm_params), i32, P, P, P, P, P],
         "pm_segment_predict": [P, i64, ctypes.POINTER(pm_params), ctypes.POINTER(pm_segment_params), i32, P, P],
         "pm_grouped_gemm_autotune": [i32, P, i32, i32, ctypes.POINTER(pm_params), i32, i32, P, P, P, ctypes.c_int,
                                      ctypes.c_int, P, P, P, P, P, ctypes.POINTER(pm_probe_result)],
@@ -395,6 +398,36 @@ def pm_grouped_predict(M_list, N, K, BM_list, BN_list, BK, stages, cta_group, dt
     return float(t.value)
 
 
+def pm_grouped_grad(M_list, N, K, BM_list, BN_list, BK, stages, cta_group, dtype, theta, n_sm, stream=None):
+    """(T_hat, dT_hat/dtheta) of one grouped launch, FP64 on the GPU."""
+    G = len(M_list)
+    Mh = (ctypes.c_int32 * G)(*[int(m) for m in M_list])
+    bm = (ctypes.c_int16 * G)(*[int(v) for v in BM_list])
+    bn = (ctypes.c_int16 * G)(*[int(v) for v in BN_list])
+    assert len(theta) == N_PARAMS
+    th = (ctypes.c_double * N_PARAMS)(*[float(v) for v in theta])
+    out = (ctypes.c_double * N_GRAD_OUT)()
+    _check(_lib.pm_grouped_grad(G, Mh, int(N), int(K), bm, bn, int(BK), int(stages), int(cta_group), int(dtype),
+                                ctypes.cast(th, ctypes.c_void_p), int(n_sm), ctypes.cast(out, ctypes.c_void_p),
+                                _stream(stream)), "pm_grouped_grad")
+    return float(out[0]), np.array(out[1:], dtype=np.float64)
+
+
+def pm_grouped_candidates(M_list, N, K, dtype, theta, n_sm, stream=None):
+    """The grouped autotuner's 20 launch-level candidates: list of
+    (t_pred, BM list, BN list, (BK, stages, cta_group))."""
+    G = len(M_list)
+    Mh = (ctypes.c_int32 * G)(*[int(m) for m in M_list])
+    t = (ctypes.c_float * 20)()
+    bm = (ctypes.c_int16 * (20 * G))()
+    bn = (ctypes.c_int16 * (20 * G))()
+    launch = (ctypes.c_int32 * 60)()
+    _check(_lib.pm_grouped_candidates(G, Mh, int(N), int(K), int(dtype), ctypes.byref(params(theta)), int(n_sm),
+                                      t, bm, bn, launch, _stream(stream)), "pm_grouped_candidates")
+    return [(float(t[i]), list(bm[i * G:(i + 1) * G]), list(bn[i * G:(i + 1) * G]), tuple(launch[3 * i:3 * i + 3]))
+            for i in range(20)]
+
+
 def pm_grouped_autotune(M_list, N, K, dtype, theta, n_sm, stream=None):
     G = len(M_list)
     Mh = (ctypes.c_int32 * G)(*[int(m) for m in M_list])
@@ -441,7 +474,8 @@ def pm_segment_predict(segs: np.ndarray, theta, psi, n_sm, stream=None) -> np.nd
     n = len(segs)
     dev = torch.from_numpy(np.ascontiguousarray(segs).view(np.uint8).copy()).cuda()
     out = torch.empty(max(n, 1), dtype=torch.float64, device="cuda")
-    ps = pm_segment_params((ctypes.c_double * 12)(*[float(v) for v in psi]))
+    assert len(psi) == N_PSI, "psi has %d entries, not %d" % (len(psi), N_PSI)
+    ps = pm_segment_params((ctypes.c_double * N_PSI)(*[float(v) for v in psi]))
     _check(_lib.pm_segment_predict(_ptr(dev), int(n), ctypes.byref(params(theta)), ctypes.byref(ps), int(n_sm),
                                    _ptr(out), _stream(stream)), "pm_segment_predict")
     return out[:n].cpu().numpy()

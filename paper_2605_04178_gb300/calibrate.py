@@ -88,7 +88,16 @@ def prior_theta(n_sm: int, f_hz: float = 1.9e9, reading: int = pm.PM_READING_MEA
     return th
 
 
+def clock_of(r: dict) -> dict:
+    """The harness's clock record of one measurement (SM MHz before the first
+    and after the last timed launch, the clock event reasons seen)."""
+    return dict(sm_mhz_begin=r.get("sm_mhz_begin", 0), sm_mhz_end=r.get("sm_mhz_end", 0),
+                clock_reasons=r.get("clock_reasons", []))
+
+
 def family_of(r: dict) -> str:
+    if "family" in r:
+        return r["family"]
     if r["kind"] == pm.PM_KIND_COPY or r["kind"] == pm.PM_KIND_TRIAD:
         return "2a_stream"
     if r["kind"] == pm.PM_KIND_TMA2D:
@@ -134,7 +143,7 @@ def measure_sweep(shapes=(1024, 2048, 4096, 8192, 16384), dtypes=(1, 2), log=pri
             continue
         r = ops.bench(pm.cfg(512, 512, 512, *t, dtype=0), C, warmup=10, reps=100)
         rows.append(dict(zip(FIELDS, (512, 512, 512, *t, 0, 0, 0)), t=r["median_s"], p25=r["p25_s"],
-                         p75=r["p75_s"]))
+                         p75=r["p75_s"], **clock_of(r)))
     log("config 1 done (%d rows, %.0f s)" % (len(rows), time.time() - t0))
     # config 2: copy / triad over 2^20 .. 2^30 FP32 elements
     nmax = 2 ** 30
@@ -148,7 +157,7 @@ def measure_sweep(shapes=(1024, 2048, 4096, 8192, 16384), dtypes=(1, 2), log=pri
             r = pm.pm_probe_run(args, a, b, c, warmup=10, reps=100) if pk == pm.PM_PROBE_TRIAD else \
                 pm.pm_probe_run(args, a, b, warmup=10, reps=100)
             rows.append(dict(M=n, N=0, K=0, BM=0, BN=0, BK=0, stages=0, cta_group=0, dtype=0, kind=kind,
-                             t=r["median_s"], p25=r["p25_s"], p75=r["p75_s"]))
+                             t=r["median_s"], p25=r["p25_s"], p75=r["p75_s"], **clock_of(r)))
     del b, c
     # TMA 2D tiles over a 1 GiB FP32 matrix (16384 x 16384)
     src = a[: 16384 * 16384].view(16384, 16384)
@@ -157,7 +166,7 @@ def measure_sweep(shapes=(1024, 2048, 4096, 8192, 16384), dtypes=(1, 2), log=pri
         r = pm.pm_probe_run(pm.probe_args(pm.PM_PROBE_TMA2D, rows=16384, cols=16384, tile_r=tr, tile_c=tc),
                             src, dst, warmup=3, reps=20)
         rows.append(dict(M=16384, N=16384, K=0, BM=tr, BN=tc, BK=0, stages=0, cta_group=0, dtype=0,
-                         kind=pm.PM_KIND_TMA2D, t=r["median_s"], p25=r["p25_s"], p75=r["p75_s"]))
+                         kind=pm.PM_KIND_TMA2D, t=r["median_s"], p25=r["p25_s"], p75=r["p75_s"], **clock_of(r)))
     del a, src, dst
     torch.cuda.empty_cache()
     log("config 2 probes done (%.0f s)" % (time.time() - t0))
@@ -199,7 +208,7 @@ def measure_sweep(shapes=(1024, 2048, 4096, 8192, 16384), dtypes=(1, 2), log=pri
                     continue
                 r = ops.bench(pm.cfg(s, s, s, *t, dtype=dt), C, warmup=10, reps=reps)
                 rows.append(dict(zip(FIELDS, (s, s, s, *t, dt, 0, 0)), t=r["median_s"], p25=r["p25_s"],
-                                 p75=r["p75_s"]))
+                                 p75=r["p75_s"], **clock_of(r)))
             del ops
         del Ad, Bd, C
         torch.cuda.empty_cache()
@@ -209,9 +218,14 @@ def measure_sweep(shapes=(1024, 2048, 4096, 8192, 16384), dtypes=(1, 2), log=pri
     settle()
     props = torch.cuda.get_device_properties(0)
     segments = measure_segments(dict(rows=rows), log)
+    settle()
+    grouped = measure_grouped(grouped_theta(props.multi_processor_count, dict(instr=instr)),
+                              props.multi_processor_count, log=log)
     torch.cuda.nvtx.range_pop()
     return dict(environment=environment(), device=props.name, n_sm=props.multi_processor_count, rows=rows, pchase=pchase, instr=instr,
-                streams=streams, segments=segments, protocol="10 warm-ups; 100 timed runs (20-40 at 8192-16384, 20 for TMA), median of CUDA-event times")
+                streams=streams, segments=segments, grouped=grouped,
+                protocol="10 warm-ups; 100 timed runs (20-40 at 8192-16384, 20 for TMA), median of CUDA-event times; "
+                         "grouped launches 3 warm-ups, median of 15")
 
 
 def measure_tmem_b(shapes=(1024, 2048, 4096, 8192, 16384), dtypes=(1, 2), log=print) -> list:
@@ -234,7 +248,7 @@ def measure_tmem_b(shapes=(1024, 2048, 4096, 8192, 16384), dtypes=(1, 2), log=pr
                     continue
                 r = ops.bench(pm.cfg(s, s, s, *t, dtype=dt, tmem_a=1), C, warmup=10, reps=reps)
                 rows.append(dict(zip(FIELDS, (s, s, s, *t, dt, 0, 1)), t=r["median_s"], p25=r["p25_s"],
-                                 p75=r["p75_s"]))
+                                 p75=r["p75_s"], **clock_of(r)))
             del ops
         del Ad, Bd, C
         torch.cuda.empty_cache()
@@ -397,24 +411,65 @@ class StageModelLoss(torch.autograd.Function):
         return g * grad, None, None, None, None, None
 
 
-class GpuObjective:
-    """Binds a calibration table to the GPU loss: call with theta (float64 tensor)."""
+class GroupedLoss(torch.autograd.Function):
+    """Sum over grouped launches of (ln T_hat - ln T)^2, T_hat the stage
+    model's makespan of the launch's schedule (pm_grouped_grad, FP64 on the
+    GPU); the backward pass returns the sum of the makespans' gradients."""
 
-    def __init__(self, rows, n_sm):
+    @staticmethod
+    def forward(ctx, theta, grouped, n_sm):
+        th = theta.detach().cpu().numpy()
+        total, grad = 0.0, np.zeros(pm.N_PARAMS)
+        for r in grouped:
+            t_hat, g = pm.pm_grouped_grad(r["M"], r["N"], r["K"], r["bm"], r["bn"], *r["launch"], pm.PM_BF16, th,
+                                          n_sm)
+            res = math.log(t_hat) - math.log(r["t"])
+            total += res * res
+            grad += 2.0 * res * g / t_hat
+        ctx.save_for_backward(torch.tensor(grad, dtype=theta.dtype))
+        return torch.tensor(total, dtype=theta.dtype)
+
+    @staticmethod
+    def backward(ctx, g):
+        (grad,) = ctx.saved_tensors
+        return g * grad, None, None
+
+
+class GpuObjective:
+    """Binds a calibration table to the GPU loss: call with theta (float64
+    tensor).  rows: configuration records (pm_cfg fields and the measured t);
+    grouped: measured grouped launches (family 4), each one term of the mean
+    like a configuration."""
+
+    def __init__(self, rows, n_sm, grouped=()):
         self.n = len(rows)
         cols = {f: np.array([r.get(f, 0) for r in rows], dtype=np.int64) for f in FIELDS}
         self.cfg = pm.cfg_tensor(cols)
         self.t = torch.tensor([r["t"] for r in rows], dtype=torch.float64, device="cuda")
         self.ws = torch.empty(pm.pm_model_grad_workspace(self.n) // 8 + 1, dtype=torch.float64, device="cuda")
         self.n_sm = n_sm
+        self.grouped = list(grouped)
 
     def __call__(self, theta):
-        return StageModelLoss.apply(theta, self.cfg, self.n, self.t, self.n_sm, self.ws)
+        loss = StageModelLoss.apply(theta, self.cfg, self.n, self.t, self.n_sm, self.ws)
+        if not self.grouped:
+            return loss
+        n_g = len(self.grouped)
+        return (self.n * loss + GroupedLoss.apply(theta, self.grouped, self.n_sm)) / (self.n + n_g)
 
     def predict(self, theta) -> np.ndarray:
         out = torch.empty(self.n, dtype=torch.float32, device="cuda")
         pm.pm_model_predict(self.cfg, self.n, np.asarray(theta, dtype=np.float64), self.n_sm, out)
         return out.cpu().numpy().astype(np.float64)
+
+    def predict_grouped(self, theta) -> np.ndarray:
+        return predict_grouped(self.grouped, theta, self.n_sm)
+
+
+def predict_grouped(grouped, theta, n_sm) -> np.ndarray:
+    """The stage model's makespan (pm_grouped_predict) of each grouped launch."""
+    return np.array([pm.pm_grouped_predict(r["M"], r["N"], r["K"], r["bm"], r["bn"], *r["launch"], pm.PM_BF16,
+                                           np.asarray(theta, dtype=np.float64), n_sm) for r in grouped])
 
 
 # Parameter pairs (lo, hi) the fit keeps ordered, theta[lo] <= theta[hi]:
@@ -649,7 +704,7 @@ def load_theta(path=THETA_PATH):
 
 # ---------------------------------------------------------- generic segments
 SEG_FIELDS = ("flops", "bytes", "working_set", "h2d_bytes", "d2h_bytes", "cls", "precision", "kernels", "syncs",
-              "execs")
+              "execs", "streams")
 SEG_CLASS_NAMES = ("memory", "compute", "balanced", "stencil")
 
 
@@ -778,6 +833,78 @@ def measure_segments(table, log=print) -> dict:
     return dict(rows=rows, tau_sync_s=float(np.median(ts)))
 
 
+# Grouped problems of family 4 (config 4's recipe at several sizes): number of
+# groups, seed of M_g = round(exp(U[ln 16, ln 4096])), N = K.
+GROUPED_PROBLEMS = ((64, 3, 1024), (64, 3, 2048), (64, 3, 4096), (16, 5, 2048), (16, 5, 4096), (32, 9, 1024))
+
+
+def measure_grouped(theta, n_sm, problems=GROUPED_PROBLEMS, warmup=3, reps=15, log=print) -> list:
+    """Family 4: every launch-level candidate of the grouped autotuner (its
+    per-group tiles under theta) of each grouped BF16 problem, timed as one
+    persistent launch (CUDA events, median of `reps`), operands drawn on the
+    device from a seeded generator."""
+    rows = []
+    for G, seed, NK in problems:
+        Mg = [int(m) for m in S.grouped_m(G, seed)]
+        sum_m = sum(Mg)
+        gen = torch.Generator(device="cuda")
+        gen.manual_seed(seed)
+        A = torch.randn(sum_m, NK, device="cuda", generator=gen).to(torch.bfloat16)
+        B = torch.randn(G * NK, NK, device="cuda", generator=gen).to(torch.bfloat16)
+        C = torch.empty(sum_m, NK, dtype=torch.float32, device="cuda")
+        for t_pred, bm, bn, launch in pm.pm_grouped_candidates(Mg, NK, NK, pm.PM_BF16, theta, n_sm):
+            if not math.isfinite(t_pred):
+                continue
+            run = lambda: pm.pm_grouped_gemm_run(Mg, NK, NK, bm, bn, *launch, A, B, C)
+            ts = _events_times(run, warmup, reps)
+            rows.append(dict(family="4_grouped", G=G, seed=seed, M=Mg, N=NK, K=NK, bm=bm, bn=bn,
+                             launch=list(launch), t=float(np.median(ts)), p25=float(np.percentile(ts, 25)),
+                             p75=float(np.percentile(ts, 75))))
+        del A, B, C
+        torch.cuda.empty_cache()
+        log("grouped G=%d N=K=%d: %d launches" % (G, NK, sum(1 for r in rows if r["G"] == G and r["N"] == NK)))
+    return rows
+
+
+def _events_times(fn, warmup, reps) -> list:
+    for _ in range(warmup):
+        fn()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+    for a, b in ev:
+        a.record()
+        fn()
+        b.record()
+    torch.cuda.synchronize()
+    return [a.elapsed_time(b) * 1e-3 for a, b in ev]
+
+
+def grouped_theta(n_sm, table) -> np.ndarray:
+    """The theta whose grouped-autotuner candidates are measured: the
+    calibrated file of the measured reading if there is one, else the probe
+    priors."""
+    if os.path.exists(THETA_PATH):
+        th = load_theta(THETA_PATH)
+        if th.size == pm.N_PARAMS:
+            return th
+    return probe_priors(table["instr"], n_sm) if table.get("instr") else prior_theta(n_sm)
+
+
+def grouped_autotune_report(grouped, theta, n_sm) -> list:
+    """Per grouped problem: the stage model's own pick (pm_grouped_autotune)
+    against the fastest measured launch candidate."""
+    out = []
+    for key in sorted(set((r["G"], r["seed"], r["N"]) for r in grouped)):
+        cand = [r for r in grouped if (r["G"], r["seed"], r["N"]) == key]
+        best = min(cand, key=lambda r: r["t"])
+        _, bm, bn, launch = pm.pm_grouped_autotune(cand[0]["M"], key[2], key[2], pm.PM_BF16, theta, n_sm)
+        pick = [r for r in cand if tuple(r["launch"]) == tuple(launch) and list(r["bm"]) == list(bm)
+                and list(r["bn"]) == list(bn)]
+        out.append(dict(G=key[0], seed=key[1], N=key[2], K=key[2], pick_launch=list(launch),
+                        best_launch=best["launch"], t_best=best["t"], t_pick=pick[0]["t"] if pick else None,
+                        pick_over_best=pick[0]["t"] / best["t"] if pick else None))
+    return out
+
+
 def grouped_family(seg_table, theta, n_sm) -> dict:
     """Family 4 (grouped GEMM): the stage model's makespan (pm_grouped_predict)
     of each measured grouped launch against its time."""
@@ -795,8 +922,8 @@ def grouped_family(seg_table, theta, n_sm) -> dict:
 
 
 def _seg_predict(rows, theta, psi, n_sm):
-    return pm.pm_segment_predict(pm.segment_array({f: np.array([r[f] for r in rows]) for f in SEG_FIELDS}),
-                                 theta, psi, n_sm)
+    return pm.pm_segment_predict(pm.segment_array({f: np.array([r.get(f, 1 if f == "execs" else 0) for r in rows])
+                                                   for f in SEG_FIELDS}), theta, psi, n_sm)
 
 
 def _fit_1d(rows, theta, psi, n_sm, idx, lo=1e-3, hi=1e3):
@@ -824,12 +951,91 @@ def _fit_1d(rows, theta, psi, n_sm, idx, lo=1e-3, hi=1e3):
     return math.exp(0.5 * (a + b))
 
 
-def fit_segments(seg_table, theta, n_sm, eq15=None) -> dict:
+def stream_segments(name: str, n_sm: int):
+    """The concurrent-stream probe classes of measure_streams as generic-path
+    segments (one launch per stream), or None for a class the generic path
+    cannot describe: the MMA probe on an eighth of the SMs runs at a fraction
+    of the chip's rate, which a full-chip roofline has no term for."""
+    if name.startswith("triad_2^"):
+        n = 1 << int(name.split("^")[1].split("_")[0])
+        return dict(flops=2.0 * n, bytes=12.0 * n, working_set=12.0 * n, cls=pm.PM_SEG_MEMORY,
+                    precision=pm.PM_FP32, kernels=1)
+    if name.startswith("copy_2^"):
+        n = 1 << int(name.split("^")[1].split("_")[0])
+        return dict(flops=0.0, bytes=8.0 * n, working_set=8.0 * n, cls=pm.PM_SEG_MEMORY, precision=pm.PM_FP32,
+                    kernels=1)
+    if name == "mma_bf16_%d_ctas_per_stream" % n_sm:
+        # the probe: n_sm CTAs x 2^13 tcgen05.mma of 128 x 256 x 16 (BF16)
+        return dict(flops=float(n_sm) * (1 << 13) * 2.0 * 128 * 256 * 16, bytes=0.0, working_set=0.0,
+                    cls=pm.PM_SEG_COMPUTE, precision=pm.PM_BF16, kernels=1)
+    return None
+
+
+def fit_stream_interference(streams: dict, theta, psi, n_sm) -> dict:
+    """kappa_launch and kappa per class of the generic path's concurrent-stream
+    term (Sec. III-A.6: N_c concurrent copies add (N_c - 1) tau_c), with
+    tau_c = kappa_launch * launches + kappa_class * roofline term, by least
+    squares on the measured makespan increments T(N_c) - T(1) of the probe
+    classes (kappa >= 0).  The balanced class takes the compute kappa and the
+    stencil class the memory one (no probe of their own).  Returns psi with
+    entries 12-16 filled, and per class the makespans the generic path then
+    predicts (its own single-stream time plus the term) with their MAE."""
+    psi = np.array(psi, dtype=np.float64)
+    cases = []
+    for name, v in streams.items():
+        seg = stream_segments(name, n_sm)
+        if seg is None:
+            continue
+        base = dict(seg, streams=1)
+        one = _seg_predict([base], theta, np.concatenate([psi[:12], np.zeros(5)]), n_sm)[0]
+        launches = seg["kernels"] * float(theta[0])
+        roof = one - launches
+        cases.append((name, seg, np.array(v["counts"], dtype=np.float64), np.array(v["t_s"]), launches, roof))
+    if not cases:
+        psi[12:17] = 1.0
+        return dict(psi=psi.tolist(), classes={})
+    # unknowns x = (kappa_launch, kappa_memory, kappa_compute)
+    rows_a, rows_b = [], []
+    for _, seg, counts, t, launches, roof in cases:
+        t1 = t[counts == 1][0]
+        for c, tc in zip(counts, t):
+            if c > 1:
+                k = c - 1.0
+                a = [k * launches, k * roof if seg["cls"] == pm.PM_SEG_MEMORY else 0.0,
+                     k * roof if seg["cls"] == pm.PM_SEG_COMPUTE else 0.0]
+                w = 1.0 / tc                                   # relative errors
+                rows_a.append([x * w for x in a])
+                rows_b.append((tc - t1) * w)
+    A, b = np.array(rows_a), np.array(rows_b)
+    active = [j for j in range(3) if np.any(A[:, j] != 0.0)]
+    x = np.zeros(3)
+    while active:
+        sol = np.linalg.lstsq(A[:, active], b, rcond=None)[0]
+        if np.all(sol >= 0.0):
+            x[active] = sol
+            break
+        active.remove(active[int(np.argmin(sol))])            # drop the most negative, refit (kappa >= 0)
+    psi[16] = x[0]
+    psi[12] = psi[15] = x[1]                                   # memory, stencil
+    psi[13] = psi[14] = x[2]                                   # compute, balanced
+    out = {}
+    for name, seg, counts, t, _, _ in cases:
+        pred = _seg_predict([dict(seg, streams=int(c)) for c in counts], theta, psi, n_sm)
+        m = counts > 1
+        out[name] = dict(counts=counts.tolist(), t_s=t.tolist(), pred_s=pred.tolist(),
+                         mae_pct=float(np.mean(np.abs(pred[m] - t[m]) / t[m]) * 100.0),
+                         single_stream_ape_pct=float(abs(pred[0] - t[0]) / t[0] * 100.0))
+    return dict(psi=psi.tolist(), kappa_launch=float(x[0]), kappa_memory=float(x[1]), kappa_compute=float(x[2]),
+                classes=out)
+
+
+def fit_segments(seg_table, theta, n_sm, eq15=None, streams=None) -> dict:
     """psi of the generic path: host link from the Eq. 15 fit, tau_sync measured,
     one scale per class and an efficiency per precision (BF16's fixed at 1)
-    fitted to the measured segments; MAE per class in-sample and leave-one-out."""
+    fitted to the measured segments; MAE per class in-sample and leave-one-out;
+    the concurrent-stream entries from the stream probes (fit_stream_interference)."""
     rows = seg_table["rows"]
-    psi = np.ones(12)
+    psi = np.ones(pm.N_PSI)
     if eq15:
         psi[7], psi[8] = eq15["h2d"]["B_eff"], eq15["h2d"]["tau_s"]
         psi[9], psi[10] = eq15["d2h"]["B_eff"], eq15["d2h"]["tau_s"]
@@ -871,9 +1077,12 @@ def fit_segments(seg_table, theta, n_sm, eq15=None) -> dict:
         m = np.array([sel(r) for r in rows])
         if m.any():
             extra[name] = dict(n=int(m.sum()), mae_pct=float(ape[m].mean()), loo_mae_pct=float(loo[m].mean()))
+    interference = fit_stream_interference(streams or {}, theta, psi, n_sm)
+    psi = np.array(interference["psi"])
     return dict(psi=psi.tolist(), by_class=by_class, by_feature=extra, all=dict(
         n=len(rows), mae_pct=float(ape.mean()), loo_mae_pct=float(loo.mean())),
-        rows=[dict(name=r["name"], t=r["t"], pred=float(pp)) for r, pp in zip(rows, pred)])
+        rows=[dict(name=r["name"], t=r["t"], pred=float(pp)) for r, pp in zip(rows, pred)],
+        streams=interference)
 
 
 def main():
@@ -884,6 +1093,7 @@ def main():
     ap.add_argument("--measure-tmem-b", action="store_true", help="re-measure only the strategy-B GEMM rows")
     ap.add_argument("--measure-streams", action="store_true", help="re-measure only the concurrent-stream probes")
     ap.add_argument("--measure-segments", action="store_true", help="re-measure only the generic-path segments")
+    ap.add_argument("--measure-grouped", action="store_true", help="re-measure only the grouped launches (family 4)")
     ap.add_argument("--reading", type=int, default=pm.PM_READING_MEASURED,
                     help="0: literal equations; 1: readings measured on the kernels (default)")
     ap.add_argument("--sweep", default=SWEEP_PATH)
@@ -913,25 +1123,44 @@ def main():
     if args.measure_segments:
         settle()
         table["segments"] = measure_segments(table)
-    if args.measure_instr or args.measure_tmem_b or args.measure_streams or args.measure_segments:
+    if args.measure_grouped:
+        settle()
+        table["grouped"] = measure_grouped(grouped_theta(n_sm, table), n_sm)
+    if (args.measure_instr or args.measure_tmem_b or args.measure_streams or args.measure_segments or
+            args.measure_grouped):
         with open(args.sweep, "w") as f:
             json.dump(table, f)
     rows = table["rows"]
+    grouped = table.get("grouped", [])
     train, hold = split(len(rows))
+    gtrain, ghold = split(len(grouped)) if grouped else (np.zeros(0, bool), np.zeros(0, bool))
     th_paper = prior_theta(n_sm, reading=args.reading)
     th0 = probe_priors(table["instr"], n_sm, reading=args.reading) if "instr" in table else th_paper
-    obj = GpuObjective([r for r, m in zip(rows, train) if m], n_sm)
+    obj = GpuObjective([r for r, m in zip(rows, train) if m], n_sm, [r for r, m in zip(grouped, gtrain) if m])
     theta, trace = fit(obj, th0, reg=FIT_REG, log=print)
-    allobj = GpuObjective(rows, n_sm)
-    pred0, pred = allobj.predict(th0), allobj.predict(theta)
-    rep = dict(reading=args.reading, n_rows=len(rows), n_train=int(train.sum()), n_holdout=int(hold.sum()),
+    allobj = GpuObjective(rows, n_sm, grouped)
+    # every measured row (configurations, then grouped launches) with its prediction
+    all_rows = rows + grouped
+    hold_all = np.concatenate([hold, ghold])
+    train_all = np.concatenate([train, gtrain])
+
+    def predict_all(th):
+        return np.concatenate([allobj.predict(th), allobj.predict_grouped(th) if grouped else np.zeros(0)])
+
+    pred0, pred_all = predict_all(th0), predict_all(theta)
+    pred = pred_all[:len(rows)]
+    rep = dict(reading=args.reading, n_rows=len(all_rows), n_train=int(train_all.sum()),
+               n_holdout=int(hold_all.sum()),
                loss_trace=[float(x) for x in trace], theta=theta.tolist(), prior=th0.tolist(),
                environment=environment(), two_sm=two_sm_report(rows),
                per_config=[dict(family=family_of(r), cfg=[r.get(f, 0) for f in FIELDS], t=r["t"], pred=float(p),
                                 holdout=bool(h)) for r, p, h in zip(rows, pred, hold)],
-               mae_paper_prior=mae_by_family(rows, allobj.predict(th_paper)),
-               mae_prior=mae_by_family(rows, pred0), mae_train=mae_by_family(rows, pred, train),
-               mae_holdout=mae_by_family(rows, pred, hold), mae_all=mae_by_family(rows, pred),
+               per_grouped=[dict(G=r["G"], seed=r["seed"], N=r["N"], launch=r["launch"], t=r["t"], pred=float(p),
+                                 holdout=bool(h)) for r, p, h in zip(grouped, pred_all[len(rows):], ghold)],
+               mae_paper_prior=mae_by_family(all_rows, predict_all(th_paper)),
+               mae_prior=mae_by_family(all_rows, pred0), mae_train=mae_by_family(all_rows, pred_all, train_all),
+               mae_holdout=mae_by_family(all_rows, pred_all, hold_all), mae_all=mae_by_family(all_rows, pred_all),
+               grouped_autotune=grouped_autotune_report(grouped, theta, n_sm) if grouped else [],
                roofline_mae=roofline_mae(rows, dict(hbm=8.0e12, bf16=2.25e15, fp8=4.5e15, tf32=1.1e15)),
                autotune=autotune_vs_best(rows, theta, n_sm), pchase=table.get("pchase"),
                instr=table.get("instr"), tmem_strategy=tmem_strategy_report(rows, pred),
@@ -946,9 +1175,10 @@ def main():
         # probe), not the stage model's fitted per-step rates
         theta_generic = theta.copy()
         theta_generic[6:9] = th0[6:9]
-        rep["segments"] = fit_segments(table["segments"], theta_generic, n_sm, (table.get("instr") or {}).get("eq15"))
+        rep["segments"] = fit_segments(table["segments"], theta_generic, n_sm, (table.get("instr") or {}).get("eq15"),
+                                       table.get("streams"))
         rep["segments"]["theta"] = theta_generic.tolist()
-        rep["grouped_family"] = grouped_family(table["segments"], theta, n_sm)
+        rep["grouped_segments"] = grouped_family(table["segments"], theta, n_sm)
     meta = dict(device=table.get("device"), n_sm=n_sm, fitted_on=os.path.basename(args.sweep),
                 reading=args.reading, mae_holdout=rep["mae_holdout"])
     if rep.get("segments"):
@@ -969,10 +1199,9 @@ def main():
         pl = rep["pchase_levels"]
         print("pointer chase levels: L1 %s ns, L2 %s ns, DRAM %s ns (capacities %.0f KB, %.0f MB)" % (
             pl["l1_ns"], pl["l2_ns"], pl["dram_ns"], pl["l1_bytes"] / 1024, pl["l2_bytes"] / 2 ** 20))
-    if rep.get("grouped_family"):
-        gf = rep["grouped_family"]
-        print("family 4 grouped GEMM: n=%d MAE %.1f %% (%s)" % (gf["n"], gf["mae_pct"], ", ".join(
-            "%s %.1f%%" % (x["name"], x["ape_pct"]) for x in gf["rows"])))
+    for a in rep["grouped_autotune"]:
+        print("grouped autotune G=%(G)d N=K=%(N)d pick=%(pick_launch)s best=%(best_launch)s pick/best=%(pick_over_best)s"
+              % a)
     if rep.get("segments"):
         sg = rep["segments"]
         print("generic path psi %s" % ["%.3g" % v for v in sg["psi"]])
@@ -982,6 +1211,13 @@ def main():
     for name, v in (rep.get("streams") or {}).items():
         print("streams %s: T(N_c) %s s, tau_c %.3g s (%.2f T1), additive-law MAE %.1f %%" % (
             name, ["%.3g" % x for x in v["t_s"]], v["fit"]["tau_c_s"], v["fit"]["tau_over_T1"], v["fit"]["mae_pct"]))
+    si = (rep.get("segments") or {}).get("streams") or {}
+    if si.get("classes"):
+        print("generic path, concurrent streams: kappa_launch %.3g, kappa_memory %.3g, kappa_compute %.3g" % (
+            si["kappa_launch"], si["kappa_memory"], si["kappa_compute"]))
+        for name, v in si["classes"].items():
+            print("  %s: predicted T(N_c) %s s, MAE %.1f %% (single stream %.1f %%)" % (
+                name, ["%.3g" % x for x in v["pred_s"]], v["mae_pct"], v["single_stream_ape_pct"]))
     for r in rep["tmem_strategy"]:
         print("TMEM strategy %d dt=%d: best A %s %.3g s, best B %s %.3g s, measured B/A %.3f, predicted %.3f" % (
             r["M"], r["dtype"], r["A"]["tile"], r["A"]["t"], r["B"]["tile"], r["B"]["t"], r["measured_B_over_A"],

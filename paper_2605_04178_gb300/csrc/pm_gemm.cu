@@ -7,9 +7,10 @@
 // Kernel shape (sm_103a): one persistent CTA per SM (CTA pair per two SMs for
 // cta_group 2), 6 warps:
 //   warp 0      TMA producer (one thread): waits empty[s], loads stage s;
-//   warp 1      TMEM allocator and MMA issuer (one thread): waits full[s],
-//               issues BK/k_instr MMAs per row block, commits to empty[s];
-//               after the last K-step commits to acc_full[buffer];
+//   warp 1      TMEM allocator and MMA issuer: the whole warp runs the
+//               K-loop (waits full[s], forms the descriptors) and one lane
+//               issues BK/k_instr MMAs per row block and commits to
+//               empty[s]; after the last K-step it commits to acc_full[buffer];
 //   warps 2..5  epilogue: wait acc_full, tcgen05.ld 32-column chunks, scale,
 //               store FP32 C (masked at the M/N edges), release the buffer.
 // TMEM strategy A keeps only the accumulators in tensor memory and feeds both
@@ -42,7 +43,9 @@ constexpr int kMaxGroups = 128;
 
 // Problems of one launch.  A single GEMM is one group.  Tiles are listed
 // group by group (tile_off is the prefix sum); inside a group they are
-// visited in bands of kRasterGroup (pair-)rows for L2 reuse.
+// visited in bands of kRasterGroup (pair-)rows for L2 reuse.  A launch of
+// several groups lists them largest tile (BM x BN) first and its CTAs (CTA
+// pairs) take the tiles in alternating round-robin order (round_tile).
 struct GroupTable {
   int n_groups;
   int tile_off[kMaxGroups + 1];
@@ -79,6 +82,18 @@ struct GemmParams {
   Watchdog wd;
 };
 
+// Position of the tile CTA (pair) `cta` of `n_ctas` runs in round r, or -1
+// past the last tile.  One group: plain round-robin (round r holds tiles
+// r*n_ctas .. r*n_ctas + n_ctas - 1, CTA c the c-th).  Several groups: the
+// order is reversed on odd rounds, so the CTA that took the largest tile of
+// a round takes the smallest of the next; with the groups listed largest
+// tile first this evens out the CTAs' busy time like a longest-first
+// schedule, and the stage model's grouped makespan follows the same rule.
+__device__ __forceinline__ int round_tile(int r, int cta, int n_ctas, int n_tiles, bool snake) {
+  const int t = r * n_ctas + ((snake && (r & 1)) ? n_ctas - 1 - cta : cta);
+  return t < n_tiles ? t : -1;
+}
+
 // Everything the three roles need about one tile.
 struct Tile {
   int arow, brow;                  // first operand rows this CTA loads
@@ -87,11 +102,15 @@ struct Tile {
   uint32_t a_part, b_part, tx, idesc;
 };
 
+// q_hint: the group of this role's previous tile (0 at the start).  A
+// role's tile positions only increase, so the search for the tile's group
+// resumes there instead of scanning the table from its first group.
 template <int CG, int L>
 __device__ __forceinline__ void decode_tile(int t, const GemmParams& p, const GroupTable& g, uint32_t rank,
-                                            Tile& T) {
-  int q = 0;
+                                            Tile& T, int& q_hint) {
+  int q = q_hint;
   while (q + 1 < g.n_groups && t >= g.tile_off[q + 1]) ++q;
+  q_hint = q;
   const int lt = t - g.tile_off[q];
   const int tiles_n = g.tiles_n[q], tiles_m = g.tiles_m[q];
   const int per_band = kRasterGroup * tiles_n;
@@ -138,7 +157,7 @@ __device__ __forceinline__ constexpr uint32_t ta_col(int h, int a, int kk, int m
 template <int CG, int KIND, int NATOMS, int NK, int NMBLK, int TA>
 __device__ __forceinline__ void issue_stage(uint32_t d0, uint64_t a0, uint64_t b0, uint32_t a_part16,
                                             uint32_t b_part16, uint32_t mblk16, uint32_t idesc, uint32_t bn,
-                                            bool first, uint32_t a_tm) {
+                                            bool first, uint32_t a_tm, uint32_t issue) {
   constexpr int PASSES = (KIND == 1) ? 3 : 1;
   if constexpr (TA) {
     constexpr int L = (KIND == 1) ? 2 : 1;
@@ -151,7 +170,7 @@ __device__ __forceinline__ void issue_stage(uint32_t d0, uint64_t a0, uint64_t b
 #pragma unroll
           for (int m = 0; m < NMBLK; ++m)
             tmem_cp_128x256b(a_tm + ta_col<NATOMS, NK, NMBLK>(h, a, kk, m),
-                             a0 + (uint64_t)((h * NATOMS + a) * a_part16 + m * mblk16 + 2u * kk));
+                             a0 + (uint64_t)((h * NATOMS + a) * a_part16 + m * mblk16 + 2u * kk), issue);
   }
 #pragma unroll
   for (int pass = 0; pass < PASSES; ++pass) {
@@ -165,10 +184,11 @@ __device__ __forceinline__ void issue_stage(uint32_t d0, uint64_t a0, uint64_t b
 #pragma unroll
         for (int m = 0; m < NMBLK; ++m) {
           if constexpr (TA) {
-            umma_ta<KIND>(d0 + (uint32_t)m * bn, a_tm + ta_col<NATOMS, NK, NMBLK>(ha, a, kk, m), bd, idesc, acc);
+            umma_ta<KIND>(d0 + (uint32_t)m * bn, a_tm + ta_col<NATOMS, NK, NMBLK>(ha, a, kk, m), bd, idesc, acc,
+                          issue);
           } else {
             const uint64_t ad = a0 + (uint64_t)((ha * NATOMS + a) * a_part16 + m * mblk16 + 2u * kk);
-            umma<CG, KIND>(d0 + (uint32_t)m * bn, ad, bd, idesc, acc);
+            umma<CG, KIND>(d0 + (uint32_t)m * bn, ad, bd, idesc, acc, issue);
           }
         }
       }
@@ -183,16 +203,24 @@ struct MmaRing {
   uint64_t* acce;
   int stage;
   uint32_t phase;
+  uint32_t issue;                  // this lane issues the warp's tensor instructions
 };
+
+// A wait of the whole MMA warp: every lane waits, and the outcome is made
+// warp-uniform so the warp leaves together if the watchdog gave up.
+__device__ __forceinline__ bool warp_wait(uint32_t bar, uint32_t parity, const Watchdog& wd, volatile int* abort_p,
+                                          unsigned site) {
+  return __all_sync(0xffffffffu, mbar_wait(bar, parity, wd, abort_p, site)) != 0;
+}
 
 // One K-step's MMAs and the commit that frees its ring stage.
 template <int CG, int KIND, int NA, int NK, int NM, int TA>
 __device__ __forceinline__ void mma_step(MmaRing& r, const GemmParams& p, uint32_t d0, uint64_t a0, uint64_t b0,
                                          uint32_t a16, uint32_t b16, uint32_t m16, uint32_t idesc, uint32_t bn,
                                          bool first, uint32_t a_tm) {
-  issue_stage<CG, KIND, NA, NK, NM, TA>(d0, a0, b0, a16, b16, m16, idesc, bn, first, a_tm);
-  if constexpr (CG == 1) umma_commit(smem_u32(&r.empty[r.stage]));
-  else umma_commit_pair(smem_u32(&r.empty[r.stage]), (uint16_t)3);
+  issue_stage<CG, KIND, NA, NK, NM, TA>(d0, a0, b0, a16, b16, m16, idesc, bn, first, a_tm, r.issue);
+  if constexpr (CG == 1) umma_commit(smem_u32(&r.empty[r.stage]), r.issue);
+  else umma_commit_pair(smem_u32(&r.empty[r.stage]), (uint16_t)3, r.issue);
   if (++r.stage == p.stages) { r.stage = 0; r.phase ^= 1u; }
 }
 
@@ -219,19 +247,19 @@ __device__ __forceinline__ bool mma_tile(MmaRing& r, const GemmParams& p, const 
     if (p.split) {
       // row block 0 now, row block 1 once the epilogue has drained it from
       // the previous tile
-      if (!mbar_wait(smem_u32(&r.full[r.stage]), r.phase, p.wd, abort_p, SITE_GEMM_MMA)) return false;
+      if (!warp_wait(smem_u32(&r.full[r.stage]), r.phase, p.wd, abort_p, SITE_GEMM_MMA)) return false;
       tc_fence_after();
       const uint64_t a0 = desc0 + (uint64_t)((uint32_t)r.stage * stage16);
       const uint64_t b0 = a0 + (uint64_t)boff16;
-      issue_stage<CG, KIND, NA, NK, 1, TA>(d0, a0, b0, a16, b16, m16, T.idesc, bn, true, 0u);
-      if (!mbar_wait(smem_u32(&r.acce[1]), (use & 1u) ^ 1u, p.wd, abort_p, SITE_GEMM_MMA)) return false;
+      issue_stage<CG, KIND, NA, NK, 1, TA>(d0, a0, b0, a16, b16, m16, T.idesc, bn, true, 0u, r.issue);
+      if (!warp_wait(smem_u32(&r.acce[1]), (use & 1u) ^ 1u, p.wd, abort_p, SITE_GEMM_MMA)) return false;
       tc_fence_after();
       mma_step<CG, KIND, NA, NK, 1, TA>(r, p, d0 + bn, a0 + (uint64_t)m16, b0, a16, b16, m16, T.idesc, bn, true, 0u);
       kt0 = 1;
     }
   }
   for (int kt = kt0; kt < p.Kt; ++kt) {
-    if (!mbar_wait(smem_u32(&r.full[r.stage]), r.phase, p.wd, abort_p, SITE_GEMM_MMA)) return false;
+    if (!warp_wait(smem_u32(&r.full[r.stage]), r.phase, p.wd, abort_p, SITE_GEMM_MMA)) return false;
     tc_fence_after();
     const uint64_t a0 = desc0 + (uint64_t)((uint32_t)r.stage * stage16);
     const uint32_t a_tm = TA ? tmem_base + (uint32_t)(p.a_col0 + r.stage * p.a_cols) : 0u;
@@ -261,6 +289,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
   const int cta = (CG == 2) ? (int)(blockIdx.x >> 1) : (int)blockIdx.x;
   const int n_ctas = (CG == 2) ? (int)(gridDim.x >> 1) : (int)gridDim.x;
   const int n_tiles = g.tile_off[g.n_groups];
+  const bool snake = g.n_groups > 1;
   const uint32_t base = (smem_u32(dsmem) + 1023u) & ~1023u;
   volatile int* abort_p = &abort_flag;
 
@@ -298,9 +327,12 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
       int stage = 0;
       uint32_t phase = 0;
       bool ok = true;
-      for (int t = cta; t < n_tiles && ok; t += n_ctas) {
+      int qh = 0;
+      for (int rd = 0; rd * n_ctas < n_tiles && ok; ++rd) {
+        const int t = round_tile(rd, cta, n_ctas, n_tiles, snake);
+        if (t < 0) continue;
         Tile T;
-        decode_tile<CG, L>(t, p, g, rank, T);
+        decode_tile<CG, L>(t, p, g, rank, T, qh);
         const CUtensorMap* ma = &maps.a[T.ma];
         const CUtensorMap* mb = &maps.b[T.mb];
         for (int kt = 0; kt < p.Kt; ++kt) {
@@ -343,17 +375,21 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
     }
   } else if (warp == 1) {
     // ------------------------------------------------------------- MMA issuer
-    if (lane == 0 && rank == 0) {
-      MmaRing r{full_bar, empty_bar, acce_bar, 0, 0u};
+    // the whole warp runs the loop in step; lane 0 issues
+    if (rank == 0) {
+      MmaRing r{full_bar, empty_bar, acce_bar, 0, 0u, lane == 0 ? 1u : 0u};
       bool ok = true;
       int it = 0;
-      for (int t = cta; t < n_tiles && ok; t += n_ctas, ++it) {
+      int qh = 0;
+      for (int rd = 0; rd * n_ctas < n_tiles && ok; ++rd) {
+        const int t = round_tile(rd, cta, n_ctas, n_tiles, snake);
+        if (t < 0) continue;
         Tile T;
-        decode_tile<CG, L>(t, p, g, 0, T);
+        decode_tile<CG, L>(t, p, g, 0, T, qh);
         const int buf = it % p.nbuf;
         const uint32_t use = (uint32_t)(it / p.nbuf);
         // split release: acce_bar[0] / [1] guard row blocks 0 / 1 of the single buffer
-        if (!mbar_wait(smem_u32(&acce_bar[buf]), (use & 1u) ^ 1u, p.wd, abort_p, SITE_GEMM_MMA)) {
+        if (!warp_wait(smem_u32(&acce_bar[buf]), (use & 1u) ^ 1u, p.wd, abort_p, SITE_GEMM_MMA)) {
           ok = false;
           break;
         }
@@ -372,13 +408,15 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
                              : mma_tile<CG, KIND, TA, 1, 2, 2>(r, p, T, d0, base, tmem_base, use, abort_p);
         }
         if (!ok) break;
-        if constexpr (CG == 1) umma_commit(smem_u32(&accf_bar[buf]));
-        else umma_commit_pair(smem_u32(&accf_bar[buf]), (uint16_t)3);
+        if constexpr (CG == 1) umma_commit(smem_u32(&accf_bar[buf]), r.issue);
+        else umma_commit_pair(smem_u32(&accf_bar[buf]), (uint16_t)3, r.issue);
+        ++it;
       }
-      // all MMAs of this thread complete before the teardown frees TMEM
-      if constexpr (CG == 1) umma_commit(smem_u32(&done_bar));
-      else umma_commit_pair(smem_u32(&done_bar), (uint16_t)1);
+      // all MMAs of the issuing lane complete before the teardown frees TMEM
+      if constexpr (CG == 1) umma_commit(smem_u32(&done_bar), r.issue);
+      else umma_commit_pair(smem_u32(&done_bar), (uint16_t)1, r.issue);
       mbar_wait(smem_u32(&done_bar), 0u, p.wd, nullptr, SITE_GEMM_TEARDOWN);
+      __syncwarp();
     }
   } else {
     // --------------------------------------------------------------- epilogue
@@ -389,13 +427,17 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
     const uint32_t stage_base = base + p.staging_off;     // two 4 KB staging buffers per epilogue warp
     uint32_t sb = 0;
     int it = 0;
-    for (int t = cta; t < n_tiles; t += n_ctas, ++it) {
+    int qh = 0;
+    for (int rd = 0; rd * n_ctas < n_tiles; ++rd) {
+      const int t = round_tile(rd, cta, n_ctas, n_tiles, snake);
+      if (t < 0) continue;
       const int buf = it % p.nbuf;
       const uint32_t use = (uint32_t)(it / p.nbuf);
+      ++it;
       if (!mbar_wait(smem_u32(&accf_bar[buf]), use & 1u, p.wd, abort_p, SITE_GEMM_EPILOGUE)) break;
       tc_fence_after();
       Tile T;
-      decode_tile<CG, L>(t, p, g, rank, T);
+      decode_tile<CG, L>(t, p, g, rank, T, qh);
       // rows and columns this warp's TMEM lane quarter holds
       int lrow, qcol0, qcols;
       bool lvalid;
@@ -729,25 +771,35 @@ static pm_status plan_launch(int dt, int cg, int BK, int stages, int tmem_a, int
   int acc = 0, max_mblk = 1;
   uint32_t stage = 0;
   bool used_m[3] = {false, false, false}, used_n[3] = {false, false, false};
-  int64_t row0 = 0;
-  for (int q = 0; q < G; ++q) {
+  // rows of each problem in the stacked A and C (the caller's order), then
+  // the table's order: largest tile (BM x BN) first, ties in the caller's
+  // order (the schedule round_tile describes)
+  int64_t row_of[kMaxGroups];
+  int order[kMaxGroups];
+  for (int64_t q = 0, r0 = 0; q < G; r0 += M[q], ++q) {
+    row_of[q] = r0;
+    order[q] = (int)q;
+  }
+  if (G > 1)
+    std::stable_sort(order, order + G, [&](int a, int b) { return (int)BMv[a] * BNv[a] > (int)BMv[b] * BNv[b]; });
+  for (int i = 0; i < G; ++i) {
+    const int q = order[i];
     const int bm = BMv[q], bn = BNv[q];
-    g.row0[q] = (int)row0;
-    g.rows[q] = M[q];
-    g.brow0[q] = stacked_b ? q * N : 0;
-    g.tiles_m[q] = (M[q] + cg * bm - 1) / (cg * bm);
-    g.tiles_n[q] = (N + bn - 1) / bn;
-    const int64_t off = (int64_t)g.tile_off[q] + (int64_t)g.tiles_m[q] * g.tiles_n[q];
+    g.row0[i] = (int)row_of[q];
+    g.rows[i] = M[q];
+    g.brow0[i] = stacked_b ? q * N : 0;
+    g.tiles_m[i] = (M[q] + cg * bm - 1) / (cg * bm);
+    g.tiles_n[i] = (N + bn - 1) / bn;
+    const int64_t off = (int64_t)g.tile_off[i] + (int64_t)g.tiles_m[i] * g.tiles_n[i];
     PM_REQUIRE(off < (1ll << 31), PM_EINVAL, "too many tiles");
-    g.tile_off[q + 1] = (int)off;
-    g.bm_idx[q] = (uint8_t)size_index(bm);
-    g.bn_idx[q] = (uint8_t)size_index(bn);
-    used_m[g.bm_idx[q]] = used_n[g.bn_idx[q]] = true;
+    g.tile_off[i + 1] = (int)off;
+    g.bm_idx[i] = (uint8_t)size_index(bm);
+    g.bn_idx[i] = (uint8_t)size_index(bn);
+    used_m[g.bm_idx[i]] = used_n[g.bn_idx[i]] = true;
     const int n_mblk = (bm + 127) / 128;
     acc = std::max(acc, (bm < 128 && cg == 2) ? bn / 2 : n_mblk * bn);
     max_mblk = std::max(max_mblk, n_mblk);
     stage = std::max(stage, (uint32_t)(L * p.n_atoms) * (uint32_t)(bm + bn / cg) * (uint32_t)p.sw);
-    row0 += M[q];
   }
   p.acc_cols = acc;
   // strategy B: one 8-column slot per 128-row x 32-byte A slice, per stage

@@ -235,16 +235,19 @@ __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence:
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
 // tcgen05.mma kinds: 0 = f16 (BF16 operands), 1 = tf32, 2 = f8f6f4 (e4m3).
+// `issue` predicates the instruction: a converged warp can run the issue
+// sequence together (its operands then stay warp-uniform) while one lane
+// (issue != 0) issues.
 template <int CG, int KIND>
 __device__ __forceinline__ void umma(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
-                                     uint32_t accumulate) {
+                                     uint32_t accumulate, uint32_t issue = 1u) {
 // No "memory" clobber: the MMA reads shared memory through the async proxy,
 // ordered after the barrier wait by the volatile asm sequence itself.
 #define PM_UMMA(CGS, KS)                                                                        \
   asm volatile(                                                                                 \
-      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"                                        \
-      "tcgen05.mma.cta_group::" CGS ".kind::" KS " [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem), \
-      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate))
+      "{\n\t.reg .pred p, q;\n\tsetp.ne.b32 p, %4, 0;\n\tsetp.ne.b32 q, %5, 0;\n\t"              \
+      "@q tcgen05.mma.cta_group::" CGS ".kind::" KS " [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem), \
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate), "r"(issue))
   if constexpr (CG == 1) {
     if constexpr (KIND == 0) PM_UMMA("1", "f16");
     else if constexpr (KIND == 1) PM_UMMA("1", "tf32");
@@ -262,12 +265,12 @@ __device__ __forceinline__ void umma(uint32_t d_tmem, uint64_t adesc, uint64_t b
 // One SM (cta_group::1); B still comes from a shared-memory descriptor.
 template <int KIND>
 __device__ __forceinline__ void umma_ta(uint32_t d_tmem, uint32_t a_tmem, uint64_t bdesc, uint32_t idesc,
-                                        uint32_t accumulate) {
+                                        uint32_t accumulate, uint32_t issue = 1u) {
 #define PM_UMMA_TA(KS)                                                                            \
   asm volatile(                                                                                   \
-      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"                                          \
-      "tcgen05.mma.cta_group::1.kind::" KS " [%0], [%1], %2, %3, p;\n\t}" ::"r"(d_tmem),         \
-      "r"(a_tmem), "l"(bdesc), "r"(idesc), "r"(accumulate))
+      "{\n\t.reg .pred p, q;\n\tsetp.ne.b32 p, %4, 0;\n\tsetp.ne.b32 q, %5, 0;\n\t"                \
+      "@q tcgen05.mma.cta_group::1.kind::" KS " [%0], [%1], %2, %3, p;\n\t}" ::"r"(d_tmem),      \
+      "r"(a_tmem), "l"(bdesc), "r"(idesc), "r"(accumulate), "r"(issue))
   if constexpr (KIND == 0) PM_UMMA_TA("f16");
   else if constexpr (KIND == 1) PM_UMMA_TA("tf32");
   else PM_UMMA_TA("f8f6f4");
@@ -278,20 +281,23 @@ __device__ __forceinline__ void umma_ta(uint32_t d_tmem, uint32_t a_tmem, uint64
 // operand) into 128 lanes x 8 columns of tensor memory.  Asynchronous; a
 // later tcgen05.mma of the same thread sees the data, and tcgen05.commit
 // tracks its completion together with the MMAs.
-__device__ __forceinline__ void tmem_cp_128x256b(uint32_t taddr, uint64_t sdesc) {
-  asm volatile("tcgen05.cp.cta_group::1.128x256b [%0], %1;" ::"r"(taddr), "l"(sdesc));
+__device__ __forceinline__ void tmem_cp_128x256b(uint32_t taddr, uint64_t sdesc, uint32_t issue = 1u) {
+  asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %2, 0;\n\t@q tcgen05.cp.cta_group::1.128x256b [%0], %1;\n\t}"
+               ::"r"(taddr), "l"(sdesc), "r"(issue));
 }
 
 // Arrive once on an mbarrier when all prior tcgen05.mma of this thread are done.
-__device__ __forceinline__ void umma_commit(uint32_t bar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
-               : "memory");
+__device__ __forceinline__ void umma_commit(uint32_t bar, uint32_t issue = 1u) {
+  asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %1, 0;\n\t"
+               "@q tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n\t}"
+               ::"r"(bar), "r"(issue) : "memory");
 }
 // CTA-pair form: arrive on the mbarrier at the same offset in every CTA of mask.
-__device__ __forceinline__ void umma_commit_pair(uint32_t bar, uint16_t mask) {
+__device__ __forceinline__ void umma_commit_pair(uint32_t bar, uint16_t mask, uint32_t issue = 1u) {
   asm volatile(
-      "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(bar),
-      "h"(mask)
+      "{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %2, 0;\n\t"
+      "@q tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;\n\t}"
+      ::"r"(bar), "h"(mask), "r"(issue)
       : "memory");
 }
 

@@ -253,8 +253,58 @@ __device__ __forceinline__ void gemm_forward(const pm_cfg& c, const ThetaT<F>& t
   f.T = f.T_stage >= f.T_rl ? f.T_stage : f.T_rl;
 }
 
-// Adjoint of gemm_forward: d[j] += w * dT_hat/dtheta_j.  max() passes the
-// gradient to its first argument on ties; the clamp stops it outside (0,1).
+// Adjoint of one tile's K-steps and writeback, tau = K_tiles T_step + T_store
+// scaled by the weights g_step (of T_step) and g_store (of T_store):
+// d[j] += dtau/dtheta_j; the tensor-rate and S_2SM slopes go to gR and gS
+// (the caller adds them to the right entries).  max() passes the gradient
+// to its first argument on ties; the clamp stops it outside (0,1).
+template <class F>
+__device__ __forceinline__ void step_store_adjoint(const pm_cfg& c, const ThetaT<F>& th, const GemmFwdT<F>& f,
+                                                   F g_step, F g_store, F (&d)[NP], F& gR, F& gS) {
+  const bool measured = th.reading == PM_READING_MEASURED;
+  d[4] += g_store;
+  d[5] -= g_store * (f.store_bytes * th.inv[5]) * th.inv[5];
+  // T_step = max(T_eq8, T_ring); ties to Eq. 8
+  const F g_eq8 = f.ring ? F(0) : g_step;
+  const F g_ring = f.ring ? g_step / (F)c.stages : F(0);   // per term of the ring's cycle
+  F g_sync = g_eq8 + g_ring;
+  F g_c = g_ring, g_io = F(0);
+  if (f.T_c >= f.T_io) g_c += g_eq8; else g_io = g_eq8;
+  // T_io = oma * T_tma + T_sync
+  if (!measured) g_sync += g_io;
+  const F g_tma = g_io * f.oma + g_ring;
+  if (f.oma_free)
+    d[15] += g_io * f.T_tma / (F)(measured ? c.stages - 1 : c.stages);
+  d[4] += g_tma;
+  const F t_bw = f.blend ? f.bstep * th.inv[5] / f.rho : f.bstep * th.inv[5];   // b_step / (B_TMA rho)
+  d[5] -= g_tma * t_bw * th.inv[5];
+  if (f.blend) {
+    // rho = 1 + (rho_L2 - 1) E, E = exp(-W/w0)
+    const F g_rho = -g_tma * t_bw / f.rho;
+    d[16] += g_rho * f.E;
+    d[3] += g_rho * (th.v[16] - F(1)) * f.E * (f.W * th.inv[3]) * th.inv[3];
+  }
+  d[12] += F(2) * g_sync;
+  // T_c = X + (D + D_A,r)/BW_rd + n_instr L_mma + (D + D_A,w)/BW_wr + L_mgmt/K_tiles
+  gR -= g_c * f.X * f.invR;
+  gS -= g_c * f.X * f.invS;
+  d[10] -= g_c * ((f.D + f.DA_r) * th.inv[10]) * th.inv[10];
+  d[9] += g_c * f.n_instr;
+  d[11] -= g_c * ((f.D + f.DA_w) * th.inv[11]) * th.inv[11];
+  if (!measured) d[13] += g_c / f.Kt;
+}
+
+// Adds the tensor-rate and S_2SM slopes to their entries of d; static
+// indices keep d[] in registers.
+template <class F>
+__device__ __forceinline__ void rate_adjoint(const pm_cfg& c, const GemmFwdT<F>& f, F gR, F gS, F (&d)[NP]) {
+  d[6] += f.ri == 6 ? gR : F(0);
+  d[7] += f.ri == 7 ? gR : F(0);
+  d[8] += f.ri == 8 ? gR : F(0);
+  if (c.cta_group == 2) d[14] += gS;
+}
+
+// Adjoint of gemm_forward: d[j] += w * dT_hat/dtheta_j.
 template <class F>
 __device__ __forceinline__ void gemm_adjoint(const pm_cfg& c, const ThetaT<F>& th, const GemmFwdT<F>& f, F w,
                                              F (&d)[NP]) {
@@ -274,45 +324,10 @@ __device__ __forceinline__ void gemm_adjoint(const pm_cfg& c, const ThetaT<F>& t
       d[2] -= g_rl * f.B_rl * th.inv[2];
     }
   }
-  // stage branch
+  // stage branch: launch + waves (K_tiles T_step + T_store)
   d[0] += g_stage;
-  const F g_step = g_stage * f.waves * f.Kt;
-  const F g_store = g_stage * f.waves;
-  d[4] += g_store;
-  d[5] -= g_store * (f.store_bytes * th.inv[5]) * th.inv[5];
-  // T_step = max(T_eq8, T_ring); ties to Eq. 8
-  const F g_eq8 = f.ring ? F(0) : g_step;
-  const F g_ring = f.ring ? g_step / (F)c.stages : F(0);   // per term of the ring's cycle
-  F g_sync = g_eq8 + g_ring;
-  F g_c = g_ring, g_io = F(0);
-  if (f.T_c >= f.T_io) g_c += g_eq8; else g_io = g_eq8;
-  // T_io = oma * T_tma + T_sync
-  if (th.reading != PM_READING_MEASURED) g_sync += g_io;
-  const F g_tma = g_io * f.oma + g_ring;
-  if (f.oma_free)
-    d[15] += g_io * f.T_tma / (F)(th.reading == PM_READING_MEASURED ? c.stages - 1 : c.stages);
-  d[4] += g_tma;
-  const F t_bw = f.blend ? f.bstep * th.inv[5] / f.rho : f.bstep * th.inv[5];   // b_step / (B_TMA rho)
-  d[5] -= g_tma * t_bw * th.inv[5];
-  if (f.blend) {
-    // rho = 1 + (rho_L2 - 1) E, E = exp(-W/w0)
-    const F g_rho = -g_tma * t_bw / f.rho;
-    d[16] += g_rho * f.E;
-    d[3] += g_rho * (th.v[16] - F(1)) * f.E * (f.W * th.inv[3]) * th.inv[3];
-  }
-  d[12] += F(2) * g_sync;
-  // T_c = X + (D + D_A,r)/BW_rd + n_instr L_mma + (D + D_A,w)/BW_wr + L_mgmt/K_tiles
-  gR -= g_c * f.X * f.invR;
-  gS -= g_c * f.X * f.invS;
-  d[10] -= g_c * ((f.D + f.DA_r) * th.inv[10]) * th.inv[10];
-  d[9] += g_c * f.n_instr;
-  d[11] -= g_c * ((f.D + f.DA_w) * th.inv[11]) * th.inv[11];
-  if (!measured) d[13] += g_c / f.Kt;
-  // static indices keep d[] in registers
-  d[6] += f.ri == 6 ? gR : F(0);
-  d[7] += f.ri == 7 ? gR : F(0);
-  d[8] += f.ri == 8 ? gR : F(0);
-  if (c.cta_group == 2) d[14] += gS;
+  step_store_adjoint(c, th, f, g_stage * f.waves * f.Kt, g_stage * f.waves, d, gR, gS);
+  rate_adjoint(c, f, gR, gS, d);
 }
 
 // Memory probes.  Copy/triad through Eq. 16 with W = beta bytes moved;
@@ -659,10 +674,15 @@ __global__ void __launch_bounds__(kTuneThreads) autotune_topk_kernel(const int32
   }
 }
 
-// Grouped autotuner: block b handles launch-level combination b =
-// (BK index, stages, cta_group) in lexicographic order; threads pick each
-// group's (BM, BN), then each worker's busy time under the static schedule
-// (tile t on worker t mod n_conc) is summed group by group.
+// Grouped launches.  The kernel's static schedule (pm_grouped_gemm_run):
+// with several groups the launch lists them largest tile (BM x BN) first,
+// ties in the caller's order, and deals the listed tiles to the n_conc
+// workers round by round, reversing the worker order on odd rounds; one
+// group is dealt plainly round by round.  A group-q tile costs
+//   tau_q = K_tiles T_step_q + T_store_q
+// with that group's (BM, BN) and the launch's (BK, stages, cta_group), and
+// the launch ends with its busiest worker:
+//   T_hat = launch + max_w sum_q n_{w,q} tau_q.
 constexpr int kGroupThreads = 256;
 constexpr int kMaxGroups = 1024;
 
@@ -671,9 +691,20 @@ __device__ __forceinline__ int64_t count_congruent(int64_t X, int64_t w, int64_t
   return X < w ? 0 : (X - w) / n + 1;
 }
 
+// How many of the listed positions [a, b) are dealt to worker w of n.
+// Reversing odd rounds gives position i to worker w exactly when
+// i mod 2n is w or 2n - 1 - w.
+__device__ __forceinline__ int64_t dealt(int64_t a, int64_t b, int64_t w, int64_t n, bool reverse_odd) {
+  if (!reverse_odd) return count_congruent(b - 1, w, n) - count_congruent(a - 1, w, n);
+  const int64_t p = 2 * n, w2 = p - 1 - w;
+  return count_congruent(b - 1, w, p) - count_congruent(a - 1, w, p) + count_congruent(b - 1, w2, p) -
+         count_congruent(a - 1, w2, p);
+}
+
 // Working set of a grouped launch (every group's A rows, its B and its C),
 // for the L2 residency of the TMA loads; called by all threads of a block.
-__device__ float grouped_working_set(const int32_t* Mg, int G, int N, int K, int dt) {
+template <class F>
+__device__ F grouped_working_set(const int32_t* Mg, int G, int N, int K, int dt) {
   __shared__ unsigned long long sum_m;
   if (threadIdx.x == 0) sum_m = 0ull;
   __syncthreads();
@@ -681,40 +712,83 @@ __device__ float grouped_working_set(const int32_t* Mg, int G, int N, int K, int
   for (int q = threadIdx.x; q < G; q += blockDim.x) mine += (unsigned long long)Mg[q];
   atomicAdd(&sum_m, mine);
   __syncthreads();
-  const float sm = (float)sum_m;
+  const F sm = (F)sum_m;
   __syncthreads();
-  return dt_loads(dt) * dt_bytes(dt) * (sm * (float)K + (float)G * (float)N * (float)K) + 4.f * sm * (float)N;
+  return (F)dt_loads(dt) * (F)dt_bytes(dt) * (sm * (F)K + (F)G * (F)N * (F)K) + F(4) * sm * (F)N;
 }
 
-// Makespan of the static schedule: tiles listed group by group, tile t on
-// worker t mod n_conc, each tile of group q taking tau[q]; max over workers.
-// Called by all threads of a block; the result is valid in every thread.
-__device__ float grouped_makespan(const float* tau, const int64_t* tiles, int64_t* off, float* red, int G,
-                                  int64_t n_conc) {
+// The launch's list of groups: list[i] = the group at position i, off[i] =
+// its first tile; tiles[q] = group q's tiles.  Largest tile area first
+// (area / 4096 = 2^class, class 0..4; a group without a valid tile, area 0,
+// last), ties in the caller's order.  Called by all threads.
+__device__ void grouped_list(const int16_t* bm, const int16_t* bn, const int64_t* tiles, int G, int16_t* list,
+                             int64_t* off) {
   if (threadIdx.x == 0) {
+    int k = 0;
+    if (G > 1) {
+      for (int cls = 4; cls >= -1; --cls)
+        for (int q = 0; q < G; ++q)
+          if (__ffs(((int)bm[q] * (int)bn[q]) >> 12) - 1 == cls) list[k++] = (int16_t)q;
+    } else {
+      list[0] = 0;
+    }
     off[0] = 0;
-    for (int q = 0; q < G; ++q) off[q + 1] = off[q] + tiles[q];
+    for (int i = 0; i < G; ++i) off[i + 1] = off[i] + tiles[list[i]];
   }
   __syncthreads();
-  float mx = 0.f;
+}
+
+// Busiest worker's time and (in *w_star) the first worker that has it;
+// busy_w adds n_{w,q} tau_q over the list in order.  Called by all threads;
+// the result is valid in every thread.
+template <class F>
+__device__ F grouped_makespan(const F* tau, const int16_t* list, const int64_t* off, int G, int64_t n_conc,
+                              int* w_star) {
+  __shared__ F red_v[kGroupThreads / 32];
+  __shared__ int red_i[kGroupThreads / 32];
+  const bool rev = G > 1;
+  F mx = F(-1);
+  int mi = 0x7fffffff;
   for (int64_t w = threadIdx.x; w < n_conc; w += blockDim.x) {
-    float busy = 0.f;
-    for (int q = 0; q < G; ++q) {
-      const int64_t cnt = count_congruent(off[q + 1] - 1, w, n_conc) - count_congruent(off[q] - 1, w, n_conc);
-      busy += (float)cnt * tau[q];
+    F busy = F(0);
+    for (int i = 0; i < G; ++i) {
+      const int64_t cnt = dealt(off[i], off[i + 1], w, n_conc, rev);
+      if (cnt) busy += (F)cnt * tau[list[i]];
     }
-    mx = fmaxf(mx, busy);
+    if (busy > mx) { mx = busy; mi = (int)w; }
   }
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+  for (int o = 16; o > 0; o >>= 1) {
+    const F ov = __shfl_xor_sync(0xffffffffu, mx, o);
+    const int oi = __shfl_xor_sync(0xffffffffu, mi, o);
+    if (ov > mx || (ov == mx && oi < mi)) { mx = ov; mi = oi; }
+  }
+  if ((threadIdx.x & 31) == 0) { red_v[threadIdx.x >> 5] = mx; red_i[threadIdx.x >> 5] = mi; }
   __syncthreads();
-  float m = red[0];
-  for (int w = 1; w < (int)(blockDim.x / 32); ++w) m = fmaxf(m, red[w]);
+  F m = red_v[0];
+  int i0 = red_i[0];
+  for (int w = 1; w < (int)(blockDim.x / 32); ++w)
+    if (red_v[w] > m || (red_v[w] == m && red_i[w] < i0)) { m = red_v[w]; i0 = red_i[w]; }
   __syncthreads();
+  if (w_star) *w_star = i0;
   return m;
 }
 
+template <class F>
+__device__ __forceinline__ int64_t launch_tiles(const ThetaT<F>& th, int M, int N, int BM, int BN, int g) {
+  return th.reading == PM_READING_MEASURED ? (int64_t)g * cdiv(M, (int64_t)g * BM) * cdiv(N, BN)
+                                           : cdiv(M, BM) * cdiv(N, BN);
+}
+
+template <class F>
+__device__ __forceinline__ F launch_time(const ThetaT<F>& th) {
+  return th.reading == PM_READING_MEASURED ? th.v[0] + th.v[13] : th.v[0];
+}
+
+// Grouped autotuner: block b handles launch-level combination b =
+// (BK index, stages, cta_group) in lexicographic order; threads pick each
+// group's (BM, BN) minimising tiles x tau, then the makespan of the launch's
+// schedule is evaluated.
 __global__ void __launch_bounds__(kGroupThreads) grouped_tune_kernel(const int32_t* __restrict__ Mg, int G, int N,
                                                                      int K, int dt, Theta th, int n_sm,
                                                                      float* __restrict__ out_t,
@@ -723,12 +797,12 @@ __global__ void __launch_bounds__(kGroupThreads) grouped_tune_kernel(const int32
   __shared__ float tau[kMaxGroups];
   __shared__ int64_t tiles[kMaxGroups];
   __shared__ int64_t off[kMaxGroups + 1];
-  __shared__ float red[kGroupThreads / 32];
+  __shared__ int16_t bm_s[kMaxGroups], bn_s[kMaxGroups], list[kMaxGroups];
   const int combo = blockIdx.x;                 // 0..19
   const int BK = kBK[dt][combo / 10];
   const int s = 2 + (combo / 2) % 5;
   const int g = 1 + combo % 2;
-  const float W = grouped_working_set(Mg, G, N, K, dt);
+  const float W = grouped_working_set<float>(Mg, G, N, K, dt);
   bool any_invalid = false;
   for (int q = threadIdx.x; q < G; q += blockDim.x) {
     float best = INFINITY;
@@ -745,50 +819,91 @@ __global__ void __launch_bounds__(kGroupThreads) grouped_tune_kernel(const int32
         GemmFwd f;
         gemm_forward(c, th, n_sm, f, W);
         const float tq = f.Kt * f.T_step + f.T_store;   // one tile of this group
-        const int64_t nt = th.reading == PM_READING_MEASURED ? (int64_t)g * cdiv(c.M, (int64_t)g * BM) * cdiv(N, BN)
-                                                             : cdiv(c.M, BM) * cdiv(N, BN);
+        const int64_t nt = launch_tiles(th, c.M, N, BM, BN, g);
         const float cost = (float)nt * tq;
         if (cost < best) { best = cost; bm = BM; bn = BN; btau = tq; btiles = nt; }
       }
     if (best == INFINITY) any_invalid = true;
     tau[q] = btau;
     tiles[q] = btiles;
+    bm_s[q] = (int16_t)bm;
+    bn_s[q] = (int16_t)bn;
     out_bm[combo * G + q] = (int16_t)bm;
     out_bn[combo * G + q] = (int16_t)bn;
   }
   any_invalid = __syncthreads_or(any_invalid);
-  const float t = grouped_makespan(tau, tiles, off, red, G, g == 1 ? n_sm : 2 * (n_sm / 2));
-  const float launch = th.reading == PM_READING_MEASURED ? th.v[0] + th.v[13] : th.v[0];
-  if (threadIdx.x == 0) out_t[combo] = (any_invalid || (g != 1 && n_sm < 2)) ? INFINITY : launch + t;
+  grouped_list(bm_s, bn_s, tiles, G, list, off);
+  const float t = grouped_makespan<float>(tau, list, off, G, g == 1 ? n_sm : 2 * (n_sm / 2), nullptr);
+  if (threadIdx.x == 0)
+    out_t[combo] = (any_invalid || (g != 1 && n_sm < 2)) ? INFINITY : launch_time(th) + t;
 }
 
-// Stage-model makespan of one grouped launch with given per-group tiles
-// (the schedule of pm_grouped_gemm_run; same terms as the grouped autotuner).
+// Stage-model makespan of one grouped launch with given per-group tiles (the
+// schedule of pm_grouped_gemm_run; same terms as the grouped autotuner), in
+// F; with grad != nullptr also its gradient in theta (out: T_hat, then NP
+// slopes): the busiest worker's tiles through the tile adjoint.
+template <class F>
 __global__ void __launch_bounds__(kGroupThreads) grouped_predict_kernel(const int32_t* __restrict__ Mg,
                                                                         const int16_t* __restrict__ BMg,
                                                                         const int16_t* __restrict__ BNg, int G, int N,
                                                                         int K, int BK, int s, int g, int dt,
-                                                                        Theta th, int n_sm,
-                                                                        float* __restrict__ out_t) {
-  __shared__ float tau[kMaxGroups];
+                                                                        ThetaT<F> th, int n_sm, bool grad,
+                                                                        F* __restrict__ out) {
+  __shared__ F tau[kMaxGroups];
   __shared__ int64_t tiles[kMaxGroups];
   __shared__ int64_t off[kMaxGroups + 1];
-  __shared__ float red[kGroupThreads / 32];
-  const float W = grouped_working_set(Mg, G, N, K, dt);
+  __shared__ int16_t list[kMaxGroups], pos[kMaxGroups];
+  __shared__ F red_d[kGroupThreads / 32][NP];
+  const F W = grouped_working_set<F>(Mg, G, N, K, dt);
+  const int64_t n_conc = g == 1 ? n_sm : 2 * (n_sm / 2);
   for (int q = threadIdx.x; q < G; q += blockDim.x) {
     pm_cfg c;
     c.M = Mg[q]; c.N = N; c.K = K; c.BM = BMg[q]; c.BN = BNg[q]; c.BK = (int16_t)BK;
     c.stages = (int8_t)s; c.cta_group = (int8_t)g; c.dtype = (int8_t)dt; c.kind = 0; c.tmem_a = 0;
-    GemmFwd f;
+    GemmFwdT<F> f;
     gemm_forward(c, th, n_sm, f, W);
     tau[q] = f.Kt * f.T_step + f.T_store;
-    tiles[q] = th.reading == PM_READING_MEASURED ? (int64_t)g * cdiv(c.M, (int64_t)g * c.BM) * cdiv(N, c.BN)
-                                                 : cdiv(c.M, c.BM) * cdiv(N, c.BN);
+    tiles[q] = launch_tiles(th, c.M, N, c.BM, c.BN, g);
   }
   __syncthreads();
-  const float t = grouped_makespan(tau, tiles, off, red, G, g == 1 ? n_sm : 2 * (n_sm / 2));
-  const float launch = th.reading == PM_READING_MEASURED ? th.v[0] + th.v[13] : th.v[0];
-  if (threadIdx.x == 0) out_t[0] = (g != 1 && n_sm < 2) ? __int_as_float(0x7fc00000) : launch + t;
+  grouped_list(BMg, BNg, tiles, G, list, off);
+  int w_star = 0;
+  const F t = grouped_makespan<F>(tau, list, off, G, n_conc, &w_star);
+  const bool none = g != 1 && n_sm < 2;
+  if (threadIdx.x == 0) out[0] = none ? (F)__int_as_float(0x7fc00000) : launch_time(th) + t;
+  if (!grad) return;
+  for (int i = threadIdx.x; i < G; i += blockDim.x) pos[list[i]] = (int16_t)i;
+  __syncthreads();
+  // d T_hat = d launch + sum_q n_{w*,q} d tau_q
+  F d[NP];
+#pragma unroll
+  for (int j = 0; j < NP; ++j) d[j] = F(0);
+  for (int q = threadIdx.x; q < G; q += blockDim.x) {
+    const int64_t cnt = dealt(off[pos[q]], off[pos[q] + 1], w_star, n_conc, G > 1);
+    if (!cnt) continue;
+    pm_cfg c;
+    c.M = Mg[q]; c.N = N; c.K = K; c.BM = BMg[q]; c.BN = BNg[q]; c.BK = (int16_t)BK;
+    c.stages = (int8_t)s; c.cta_group = (int8_t)g; c.dtype = (int8_t)dt; c.kind = 0; c.tmem_a = 0;
+    GemmFwdT<F> f;
+    gemm_forward(c, th, n_sm, f, W);
+    F gR = F(0), gS = F(0);
+    step_store_adjoint(c, th, f, (F)cnt * f.Kt, (F)cnt, d, gR, gS);
+    rate_adjoint(c, f, gR, gS, d);
+  }
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+  for (int j = 0; j < NP; ++j) {
+    const F v = warp_sum<F>(d[j]);
+    if (lane == 0) red_d[warp][j] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < NP) {
+    F v = F(0);
+    for (int w = 0; w < kGroupThreads / 32; ++w) v += red_d[w][threadIdx.x];
+    if (threadIdx.x == 0) v += F(1);                                           // T_launch
+    if (threadIdx.x == 13 && th.reading == PM_READING_MEASURED) v += F(1);     // L_alloc + L_dealloc
+    out[1 + threadIdx.x] = none ? (F)__int_as_float(0x7fc00000) : v;
+  }
 }
 
 static std::atomic<int> g_reading{PM_READING_MEASURED};
@@ -958,13 +1073,16 @@ static void grouped_launch_of(int i, int dtype, int32_t* launch) {
 
 }  // namespace pm
 
-extern "C" pm_status pm_grouped_predict(int32_t G, const int32_t* M_host, int32_t N, int32_t K,
-                                        const int16_t* BM_host, const int16_t* BN_host, int32_t BK, int32_t stages,
-                                        int32_t cta_group, int32_t dtype, const pm_params* theta_host, int32_t n_sm,
-                                        float* t_pred_host, void* stream) {
+namespace pm {
+
+// One grouped launch's makespan on the GPU (one block), in F; with grad also
+// its gradient.  out_host: 1 value, or 1 + NP with grad.
+template <class F>
+static pm_status grouped_eval(int32_t G, const int32_t* M_host, int32_t N, int32_t K, const int16_t* BM_host,
+                              const int16_t* BN_host, int32_t BK, int32_t stages, int32_t cta_group, int32_t dtype,
+                              const ThetaT<F>& th, int32_t n_sm, bool grad, F* out_host, cudaStream_t s) {
   PM_REQUIRE(G > 0 && G <= kMaxGroups, PM_EINVAL, "G must be in [1, %d]", kMaxGroups);
-  PM_REQUIRE(M_host && BM_host && BN_host && theta_host && t_pred_host && n_sm > 0, PM_EINVAL,
-             "null pointer or n_sm <= 0");
+  PM_REQUIRE(M_host && BM_host && BN_host && out_host && n_sm > 0, PM_EINVAL, "null pointer or n_sm <= 0");
   PM_REQUIRE(N > 0 && K > 0 && dtype >= 0 && dtype <= 2, PM_EINVAL, "bad N, K or dtype");
   for (int q = 0; q < G; ++q) {
     PM_REQUIRE(M_host[q] > 0, PM_EINVAL, "M[%d] <= 0", q);
@@ -972,28 +1090,69 @@ extern "C" pm_status pm_grouped_predict(int32_t G, const int32_t* M_host, int32_
                "group %d: tile %dx%dx%d stages=%d cta_group=%d outside the valid space", q, BM_host[q], BN_host[q],
                BK, stages, cta_group);
   }
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int n_out = grad ? 1 + NP : 1;
   char* buf = nullptr;
-  const size_t bytes = 256 + (size_t)G * 8 + 16;
+  const size_t bytes = 256 + (size_t)G * 8 + 16 + (size_t)n_out * sizeof(F);
   PM_CUDA(cudaMallocAsync((void**)&buf, bytes, s));
   int32_t* dM = (int32_t*)buf;
   int16_t* dbm = (int16_t*)(buf + ((G * 4 + 15) & ~15));
   int16_t* dbn = dbm + ((G + 7) & ~7);
-  float* dt = (float*)(dbn + ((G + 7) & ~7));
+  F* dt = (F*)(dbn + ((G + 7) & ~7));
   pm_status st = PM_OK;
   cudaError_t e = cudaMemcpyAsync(dM, M_host, G * 4, cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = cudaMemcpyAsync(dbm, BM_host, G * 2, cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = cudaMemcpyAsync(dbn, BN_host, G * 2, cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) {
-    grouped_predict_kernel<<<1, kGroupThreads, 0, s>>>(dM, dbm, dbn, G, N, K, BK, stages, cta_group, dtype,
-                                                        to_theta(theta_host, n_sm), n_sm, dt);
+    grouped_predict_kernel<F><<<1, kGroupThreads, 0, s>>>(dM, dbm, dbn, G, N, K, BK, stages, cta_group, dtype, th,
+                                                           n_sm, grad, dt);
     st = launch_status("grouped_predict_kernel");
-    if (st == PM_OK) e = cudaMemcpyAsync(t_pred_host, dt, 4, cudaMemcpyDeviceToHost, s);
+    if (st == PM_OK) e = cudaMemcpyAsync(out_host, dt, n_out * sizeof(F), cudaMemcpyDeviceToHost, s);
   }
   cudaFreeAsync(buf, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (st != PM_OK) return st;
   if (e != cudaSuccess) return cuda_fail(e, "grouped predict copies");
+  return PM_OK;
+}
+
+}  // namespace pm
+
+extern "C" pm_status pm_grouped_predict(int32_t G, const int32_t* M_host, int32_t N, int32_t K,
+                                        const int16_t* BM_host, const int16_t* BN_host, int32_t BK, int32_t stages,
+                                        int32_t cta_group, int32_t dtype, const pm_params* theta_host, int32_t n_sm,
+                                        float* t_pred_host, void* stream) {
+  PM_REQUIRE(theta_host && t_pred_host && n_sm > 0, PM_EINVAL, "null pointer or n_sm <= 0");
+  return grouped_eval<float>(G, M_host, N, K, BM_host, BN_host, BK, stages, cta_group, dtype,
+                             to_theta(theta_host, n_sm), n_sm, false, t_pred_host, static_cast<cudaStream_t>(stream));
+}
+
+extern "C" pm_status pm_grouped_grad(int32_t G, const int32_t* M_host, int32_t N, int32_t K, const int16_t* BM_host,
+                                     const int16_t* BN_host, int32_t BK, int32_t stages, int32_t cta_group,
+                                     int32_t dtype, const double* theta_host, int32_t n_sm, double* out_host,
+                                     void* stream) {
+  PM_REQUIRE(theta_host && out_host && n_sm > 0, PM_EINVAL, "null pointer or n_sm <= 0");
+  ThetaT<double> th;
+  for (int j = 0; j < NP; ++j) {
+    th.v[j] = theta_host[j];
+    th.inv[j] = 1.0 / theta_host[j];
+  }
+  th.reading = g_reading.load();
+  set_concurrency(th, n_sm);
+  return grouped_eval<double>(G, M_host, N, K, BM_host, BN_host, BK, stages, cta_group, dtype, th, n_sm, true,
+                              out_host, static_cast<cudaStream_t>(stream));
+}
+
+extern "C" pm_status pm_grouped_candidates(int32_t G, const int32_t* M_host, int32_t N, int32_t K, int32_t dtype,
+                                           const pm_params* theta_host, int32_t n_sm, float* t_pred_host,
+                                           int16_t* BM_host, int16_t* BN_host, int32_t* launch_host, void* stream) {
+  PM_REQUIRE(t_pred_host && BM_host && BN_host && launch_host, PM_EINVAL, "null output pointer");
+  std::vector<int16_t> hbm, hbn;
+  pm_status st = grouped_candidates(G, M_host, N, K, dtype, theta_host, n_sm, static_cast<cudaStream_t>(stream),
+                                    t_pred_host, hbm, hbn);
+  if (st != PM_OK) return st;
+  std::copy(hbm.begin(), hbm.end(), BM_host);
+  std::copy(hbn.begin(), hbn.end(), BN_host);
+  for (int i = 0; i < 20; ++i) grouped_launch_of(i, dtype, launch_host + 3 * i);
   return PM_OK;
 }
 

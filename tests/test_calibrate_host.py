@@ -168,3 +168,31 @@ def test_pchase_levels_takes_medians_inside_each_level():
     lv = C.pchase_levels([dict(W=w, ns_per_hop=v) for w, v in zip(W, ns)], 256 * 1024, 128 * 2 ** 20)
     assert lv["l1_ns"] == 20.0 and lv["l2_ns"] == 140.0 and lv["dram_ns"] == 400.0
     assert lv["l1_points"] == 4 and lv["dram_points"] == 2
+
+
+def test_stream_interference_fit_recovers_kappas(monkeypatch):
+    # makespans generated by the generic path's own concurrent-stream term
+    # (the oracle standing in for pm_segment_predict): the least-squares fit
+    # returns the generating kappas, and the MMA probe on an eighth of the SMs
+    # is left out (no roofline term describes it)
+    monkeypatch.setattr(C, "_seg_predict", lambda rows, th, psi, n: O.segment_predict(
+        {f: np.array([r.get(f, 1 if f == "execs" else 0) for r in rows]) for f in C.SEG_FIELDS}, th, psi, n))
+    th = O.prior_theta(N_SM)
+    psi = np.array([1.0, 1.4, 2.0, 1.2, 0.05, 1.0, 0.9, 2.1e11, 3.6e-6, 1.9e11, 3.4e-6, 3.7e-6, 0, 0, 0, 0, 0])
+    truth = psi.copy()
+    truth[[12, 13, 14, 15, 16]] = [0.95, 1.1, 1.1, 0.95, 0.18]
+    streams = {}
+    for name in ("triad_2^24_per_stream", "copy_2^16_per_stream", "mma_bf16_%d_ctas_per_stream" % N_SM,
+                 "mma_bf16_%d_ctas_per_stream" % (N_SM // 8)):
+        seg = C.stream_segments(name, N_SM)
+        if seg is None:
+            streams[name] = dict(counts=list(C.STREAM_COUNTS), t_s=[5e-4 * c for c in C.STREAM_COUNTS])
+            continue
+        t = O.segment_predict({k: np.array([v] * 6) for k, v in seg.items()} | {"streams": np.array(C.STREAM_COUNTS)},
+                              th, truth, N_SM)
+        streams[name] = dict(counts=list(C.STREAM_COUNTS), t_s=t.tolist())
+    f = C.fit_stream_interference(streams, th, psi, N_SM)
+    assert f["kappa_launch"] == pytest.approx(0.18, rel=1e-9)
+    assert f["kappa_memory"] == pytest.approx(0.95, rel=1e-9) and f["kappa_compute"] == pytest.approx(1.1, rel=1e-9)
+    assert set(f["classes"]) == {"triad_2^24_per_stream", "copy_2^16_per_stream", "mma_bf16_%d_ctas_per_stream" % N_SM}
+    assert all(v["mae_pct"] < 1e-9 for v in f["classes"].values())

@@ -127,3 +127,22 @@ def test_grouped_exact_integer_split_release(lib, launch):
     for A, B in zip(A_list, B_list):
         assert np.array_equal(C[row0:row0 + A.shape[0]].astype(np.float64), O.gemm_f64(A, B))
         row0 += A.shape[0]
+
+
+def test_grouped_schedule_reorders_groups_exactly(lib):
+    # tiles of four sizes in the caller's order small, large, medium, ...:
+    # the launch lists them largest first and deals them in alternating
+    # round-robin order; every group's product stays exact, on one SM
+    # (cta_group 1) and on CTA pairs, and after graph replay
+    Ms = [40, 700, 130, 2000, 64, 999, 257, 5]
+    N, K = 640, 256
+    A_list, B_list = int_groups(Ms, N, K, seed=81)
+    bm = [64, 256, 128, 256, 64, 128, 128, 64]
+    bn = [64, 256, 128, 128, 256, 256, 64, 128]
+    for launch in ((64, 3, 1), (64, 3, 2)):
+        b_m = [b if O.cfg_valid(b, n, *launch, 1) else 128 for b, n in zip(bm, bn)]
+        C = run_grouped(lib, A_list, B_list, N, K, b_m, bn, launch, graph=True)
+        row0 = 0
+        for A, B in zip(A_list, B_list):
+            assert np.array_equal(C[row0:row0 + A.shape[0]].astype(np.float64), O.gemm_f64(A, B))
+            row0 += A.shape[0]

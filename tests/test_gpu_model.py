@@ -223,6 +223,24 @@ def test_grouped_predict_matches_oracle(lib, reading):
         assert t_g == pytest.approx(t_o, rel=1e-5)
 
 
+@pytest.mark.parametrize("launch", [(64, 4, 1), (128, 3, 2), (64, 2, 1)])
+def test_grouped_grad_matches_oracle(lib, reading, launch):
+    # FP64 makespan and its gradient (the busiest worker's tiles through the
+    # tile adjoint) against the oracle's dual numbers, mixed tiles so the
+    # launch reorders its groups
+    Mg = S.grouped_m(48, 7)
+    th = O.prior_theta(N_SM, reading=reading)
+    G = len(Mg)
+    bm = [(64, 128, 256)[q % 3] for q in range(G)]
+    bn = [(128, 256, 64)[(q // 3) % 3] for q in range(G)]
+    bm = [b if O.cfg_valid(b, n, *launch, 1) else 64 for b, n in zip(bm, bn)]
+    t_g, g_g = lib.pm_grouped_grad(Mg, 2048, 4096, bm, bn, *launch, 1, th, N_SM)
+    t_o, g_o = O.grouped_predict_grad(Mg, 2048, 4096, bm, bn, *launch, 1, th, N_SM)
+    assert t_g == pytest.approx(t_o, rel=1e-12)
+    scale = np.abs(g_o * th).max()
+    assert np.all(np.abs((g_g - g_o) * th) <= 1e-10 * scale), (g_g, g_o)
+
+
 def test_pairs_on_fewer_than_two_sms(lib, reading):
     # one SM: pair records (cta_group 2) are NaN and never picked, as in the
     # oracle; one-SM records match it (every tile its own wave).  Three SMs:

@@ -344,6 +344,14 @@ def test_grouped_single_group_reduces_to_stage_model(reading):
     assert t_grp == pytest.approx(t_gemm, rel=1e-12)
 
 
+def _dealt_worker(k, n, several_groups):
+    """Worker of the k-th tile a grouped launch lists (its schedule, restated
+    here as a plain loop): round-robin, reversed on odd rounds when the launch
+    holds several groups."""
+    rnd, j = divmod(k, n)
+    return n - 1 - j if (several_groups and rnd % 2 == 1) else j
+
+
 def test_grouped_makespan_brute_force(reading):
     # w0 = 0: the single-tile GEMMs below have another working set than the
     # launch, and the schedule, not the L2 factor, is under test here
@@ -352,15 +360,58 @@ def test_grouped_makespan_brute_force(reading):
     Mg = S.grouped_m(6, 3, 16, 600)
     n_sm = 8
     t = O.grouped_predict(Mg, 256, 512, [64] * 6, [128] * 6, 64, 3, 1, 1, th, n_sm)
-    # tau per group from single-tile stage times: T_one - T_launch
+    # tau per group from single-tile stage times: T_one - launch
     busy = [0.0] * n_sm
     k = 0
     for m in Mg:
         tau = one(th, 10 ** 6, M=64, N=128, K=512, BM=64, BN=128, BK=64, stages=3, cta_group=1, dtype=1) - launch_time(th)
         for _ in range(int(np.ceil(m / 64)) * 2):
-            busy[k % n_sm] += tau
+            busy[_dealt_worker(k, n_sm, True)] += tau
             k += 1
     assert t == pytest.approx(launch_time(th) + max(busy), rel=1e-12)
+
+
+def test_grouped_schedule_lists_largest_tiles_first(reading):
+    # mixed tiles: the launch lists the groups by tile area, largest first
+    # (ties in the caller's order), then deals them round by round with the
+    # worker order reversed on odd rounds; brute force over that list
+    th = PRIOR160.copy()
+    th[3] = 0.0
+    Mg = [300, 1000, 64, 2000, 129]
+    BMg = [64, 128, 64, 256, 128]
+    BNg = [128, 128, 256, 256, 64]
+    N, K, n_sm = 512, 1024, 6
+    t = O.grouped_predict(Mg, N, K, BMg, BNg, 64, 4, 1, 1, th, n_sm)
+    order = sorted(range(5), key=lambda q: -BMg[q] * BNg[q])          # stable: ties keep the caller's order
+    assert order == [3, 1, 2, 0, 4]
+    busy = [0.0] * n_sm
+    k = 0
+    for q in order:
+        tau = O.grouped_predict([BMg[q]], N, K, [BMg[q]], [BNg[q]], 64, 4, 1, 1, th, 10 ** 6) - launch_time(th)
+        for _ in range(int(np.ceil(Mg[q] / BMg[q])) * int(np.ceil(N / BNg[q]))):
+            busy[_dealt_worker(k, n_sm, True)] += tau
+            k += 1
+    assert t == pytest.approx(launch_time(th) + max(busy), rel=1e-12)
+
+
+def test_grouped_gradient(reading):
+    # dual-number gradient of the grouped makespan against central differences
+    # in ln theta, and Euler's homogeneity identity (the makespan is a time)
+    th = (PRIOR160 if reading == 0 else PRIOR160_MEASURED).copy()
+    Mg = S.grouped_m(12, 3, 16, 2048)
+    BMg = [64 if m < 200 else (128 if m < 1000 else 256) for m in Mg]
+    BNg = [128 if m < 500 else 256 for m in Mg]
+    args = (Mg, 1024, 2048, BMg, BNg, 64, 4, 1, 1)
+    t, g = O.grouped_predict_grad(*args, th, 152)
+    assert t == O.grouped_predict(*args, th, 152)
+    lat = sum(th[j] * g[j] for j in O.LATENCY_IDX)
+    rate = sum(th[j] * g[j] for j in O.RATE_IDX)
+    assert lat - rate == pytest.approx(t, rel=1e-12)
+    phi, h = np.log(th), 1e-5
+    for j in range(O.N_PARAMS):
+        tp = O.grouped_predict(*args, np.exp(phi + h * np.eye(O.N_PARAMS)[j]), 152)
+        tm = O.grouped_predict(*args, np.exp(phi - h * np.eye(O.N_PARAMS)[j]), 152)
+        assert (tp - tm) / (2 * h) == pytest.approx(g[j] * th[j], rel=1e-5, abs=1e-9 * t)
 
 
 def test_grouped_autotune_brute_force(reading):

@@ -10,7 +10,8 @@ import oracle as O
 
 N_SM = 152
 TH = O.prior_theta(N_SM)
-PSI = np.array([1.2, 1.1, 1.3, 1.5, 0.9, 1.0, 0.8, 2.1e11, 3.6e-6, 1.93e11, 3.4e-6, 1e-5])
+PSI = np.array([1.2, 1.1, 1.3, 1.5, 0.9, 1.0, 0.8, 2.1e11, 3.6e-6, 1.93e11, 3.4e-6, 1e-5,
+                0.9, 1.1, 0.6, 0.7, 0.2])
 
 
 def seg(**kw):
@@ -94,3 +95,24 @@ def test_invalid_records_are_nan():
         rec = dict(flops=1e9, bytes=1e9, kernels=1)
         rec.update(bad)
         assert np.isnan(one(**rec)), bad
+
+
+def test_concurrent_streams_add_tau_c():
+    # Sec. III-A.6: N_c concurrent copies add (N_c - 1) tau_c, tau_c =
+    # kappa_launch x launches + kappa_class x the class-scaled roofline term;
+    # one stream (or 0) adds nothing
+    base = dict(flops=1e9, bytes=4e9, working_set=4e9, kernels=2, cls=0, precision=1)
+    t1 = one(**base)
+    assert one(streams=0, **base) == t1 and one(streams=1, **base) == t1
+    launches = 2 * TH[0]
+    roof = t1 - launches
+    for nc in (2, 3, 8):
+        assert one(streams=nc, **base) == pytest.approx(t1 + (nc - 1) * (PSI[16] * launches + PSI[12] * roof),
+                                                       rel=1e-13)
+    comp = dict(flops=1e15, bytes=1.0, kernels=1, cls=1, precision=1)
+    c1 = one(**comp)
+    assert one(streams=4, **comp) == pytest.approx(c1 + 3 * (PSI[16] * TH[0] + PSI[13] * (c1 - TH[0])), rel=1e-13)
+    # transfers and syncs are not multiplied by the streams (they are the host's)
+    t_h = one(h2d_bytes=1e8, syncs=2, streams=3, **base)
+    assert t_h - one(streams=3, **base) == pytest.approx(1e8 / PSI[7] + PSI[8] + 2 * PSI[11], rel=1e-12)
+    assert np.isnan(one(streams=-1, **base))
