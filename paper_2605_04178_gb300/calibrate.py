@@ -1098,11 +1098,13 @@ def main():
                     help="0: literal equations; 1: readings measured on the kernels (default)")
     ap.add_argument("--sweep", default=SWEEP_PATH)
     ap.add_argument("--out", default=None, help="theta file (default: theta_gb300.json, or _literal for reading 0)")
-    ap.add_argument("--report", default=None)
+    ap.add_argument("--report", default=None, help="report file (default: data/calib_report_gb300.json, or _literal)")
     ap.add_argument("--shapes", default="1024,2048,4096,8192,16384")
     args = ap.parse_args()
     if args.out is None:
         args.out = theta_path(args.reading)
+    if args.report is None:
+        args.report = report_path(args.reading)
     n_sm = pm.sm_count()
     pm.pm_model_set_reading(args.reading)
     if args.measure:
