@@ -52,7 +52,9 @@ __device__ __forceinline__ uint32_t udiv(uint32_t x, const UDiv& u) {
 // inv[j] = 1 / v[j], rounded once on the host: the per-configuration model
 // multiplies where the equations divide by a parameter.  nc[0] / nc[1]
 // divide by the concurrent CTAs of one-SM / paired tiles on nc_nsm SMs
-// (nc_nsm = 0: not prepared, the generic division is used).
+// (nc_nsm = 0: not prepared, the generic division is used).  inv_s[s] =
+// 1/s and inv_s1[s] = 1/(s - 1) for the ring depths 2..7, inv_nsm = 1/nc_nsm:
+// the per-configuration divisions by small integers become multiplications.
 constexpr int NP = PM_NPARAMS;     // model parameters
 constexpr int NREC = NP + 1;        // loss + gradient per partial record
 
@@ -63,11 +65,17 @@ struct ThetaT {
   int reading;       // PM_READING_LITERAL or PM_READING_MEASURED (see pm_model_set_reading)
   int nc_nsm;
   UDiv nc[2];
+  F inv_s[8], inv_s1[8], inv_nsm;
 };
 using Theta = ThetaT<float>;
 
 template <class F>
 inline void set_concurrency(ThetaT<F>& t, int n_sm) {
+  for (int s = 0; s < 8; ++s) {
+    t.inv_s[s] = s >= 1 ? (F)(1.0 / s) : F(0);
+    t.inv_s1[s] = s >= 2 ? (F)(1.0 / (s - 1)) : F(0);
+  }
+  t.inv_nsm = n_sm >= 1 ? (F)(1.0 / n_sm) : F(0);
   t.nc_nsm = 0;
   if (n_sm >= 2) {
     t.nc[0] = make_udiv((uint32_t)n_sm);
@@ -81,6 +89,21 @@ __device__ __forceinline__ double pm_exp(double x) { return exp(x); }
 __device__ __forceinline__ float pm_log(float x) { return logf(x); }
 __device__ __forceinline__ double pm_log(double x) { return log(x); }
 __device__ __forceinline__ float pm_max(float a, float b) { return fmaxf(a, b); }
+// The FP32 throughput paths take the hardware approximations (relative error
+// of a few 1e-7, far inside their 1e-5 tolerance); FP64 stays exact.
+__device__ __forceinline__ float pm_exp_fast(float x) { return __expf(x); }
+__device__ __forceinline__ double pm_exp_fast(double x) { return exp(x); }
+__device__ __forceinline__ float pm_div_fast(float a, float b) { return __fdividef(a, b); }
+__device__ __forceinline__ double pm_div_fast(double a, double b) { return a / b; }
+// x / s and x / (s - 1) for a ring depth s (tabulated reciprocals for 2..7)
+template <class F>
+__device__ __forceinline__ F div_stages(F x, int s, const ThetaT<F>& th) {
+  return (s >= 1 && s < 8) ? x * th.inv_s[s] : x / (F)s;
+}
+template <class F>
+__device__ __forceinline__ F div_stages_m1(F x, int s, const ThetaT<F>& th) {
+  return (s >= 2 && s < 8) ? x * th.inv_s1[s] : x / (F)(s - 1);
+}
 __device__ __forceinline__ double pm_max(double a, double b) { return fmax(a, b); }
 
 // ceil(a / b) for a >= 0, b > 0: a shift when b is a power of two (every tile
@@ -201,11 +224,12 @@ __device__ __forceinline__ void gemm_forward(const pm_cfg& c, const ThetaT<F>& t
   }
   f.Kt = count_to<F>(Kt);
   f.waves = count_to<F>(waves);
-  f.D = F(4) * c.BM * c.BN;
+  // tile products in integers (exact: at most 2^25), one conversion each
+  f.D = (F)(4 * (int)c.BM * (int)c.BN);
   // L_mma once per K-step (literal) or once per tcgen05.mma the K-step
   // issues, BK/k_instr per 128-row block per pass (measured)
   const int kin = dt == PM_FP32 ? 8 : (dt == PM_BF16 ? 16 : 32);
-  f.n_instr = measured ? np * (F)(c.BK / kin) * (F)((c.BM + 127) / 128) : F(1);
+  f.n_instr = measured ? np * (F)((c.BK / kin) * ((c.BM + 127) / 128)) : F(1);
   f.DA_w = c.tmem_a ? l * e * c.BM * c.BK : F(0);
   f.DA_r = c.tmem_a ? np * e * c.BM * c.BK : F(0);
   // measured: strategy B's tcgen05.cp per 128-row x 32-byte A slice, each charged L_mma
@@ -215,39 +239,41 @@ __device__ __forceinline__ void gemm_forward(const pm_cfg& c, const ThetaT<F>& t
   f.S = g == 1 ? F(1) : th.v[14];
   f.invS = g == 1 ? F(1) : th.inv[14];
   const int rows = (measured && g == 1 && c.BM < 128) ? 128 : (int)c.BM;
-  f.X = (np * F(2) * rows * c.BN * c.BK) * (f.invR * f.invS);
+  f.X = (np * (F)(2 * rows * (int)c.BN * (int)c.BK)) * (f.invR * f.invS);
   f.T_c = f.X + T_tmem + T_mgmt;
-  // BN / g: halving is exact, so pairs need no division
+  // BN / g: exact for the one- and two-SM tiles (power-of-two BN)
   const F bn_g = g == 1 ? (F)c.BN : (g == 2 ? F(0.5) * (F)c.BN : (F)c.BN / (F)g);
-  f.bstep = l * e * c.BK * ((F)c.BM + bn_g);
+  f.bstep = g <= 2 ? l * e * (F)((int)c.BK * ((int)c.BM + ((int)c.BN >> (g - 1))))
+                   : l * e * c.BK * ((F)c.BM + bn_g);
   // measured: B_TMA x rho(W), rho = 1 + (rho_L2 - 1) exp(-W/w0) (loads that
   // hit in L2 arrive faster, Sec. III-A.2; Eq. 16's blend shape); w0 <= 0
   // switches the blend off
   f.W = W_launch > F(0) ? W_launch : bytes_min;
   f.blend = measured && th.v[3] > F(0);
-  f.E = f.blend ? pm_exp(-f.W / th.v[3]) : F(0);
+  f.E = f.blend ? pm_exp_fast(-f.W * th.inv[3]) : F(0);
   f.rho = f.blend ? F(1) + (th.v[16] - F(1)) * f.E : F(1);
-  f.T_tma = th.v[4] + (f.blend ? f.bstep * th.inv[5] / f.rho : f.bstep * th.inv[5]);   // rho = 1 unblended
+  f.T_tma = th.v[4] + (f.blend ? pm_div_fast(f.bstep * th.inv[5], f.rho) : f.bstep * th.inv[5]);   // rho = 1 unblended
   const F T_sync = F(2) * th.v[12];
   // 1 - alpha = clamp(c_alpha / s, 0, 1) (literal) or clamp(c_alpha / (s - 1),
   // 0, 1) (measured: s - 1 loads in flight while one stage is consumed; a
   // single stage hides nothing)
-  const F r = measured ? (c.stages > 1 ? th.v[15] / (F)(c.stages - 1) : F(1)) : th.v[15] / (F)c.stages;
+  const F r = measured ? (c.stages > 1 ? div_stages_m1(th.v[15], c.stages, th) : F(1))
+                       : div_stages(th.v[15], c.stages, th);
   f.oma_free = r > F(0) && r < F(1);
   f.oma = r <= F(0) ? F(0) : (r >= F(1) ? F(1) : r);
   f.T_io = measured ? f.oma * f.T_tma : f.oma * f.T_tma + T_sync;
   f.T_eq8 = pm_max(f.T_c, f.T_io) + T_sync;
   // measured: each stage cycles through its load, its MMAs and its full and
   // empty barriers, so s stages finish at most one K-step per cycle / s
-  f.T_ring = measured ? (f.T_tma + f.T_c + T_sync) / (F)c.stages : F(0);
+  f.T_ring = measured ? div_stages(f.T_tma + f.T_c + T_sync, c.stages, th) : F(0);
   f.ring = measured && f.T_ring > f.T_eq8;
   f.T_step = f.ring ? f.T_ring : f.T_eq8;
-  f.store_bytes = F(4) * c.BM * c.BN;
+  f.store_bytes = f.D;
   f.T_store = th.v[4] + f.store_bytes * th.inv[5];
   f.launch = measured ? th.v[0] + th.v[13] : th.v[0];
   f.T_stage = f.launch + f.waves * (f.Kt * f.T_step + f.T_store);
   const F flops = np * F(2) * (F)c.M * (F)c.N * (F)c.K;
-  f.A_rl = flops * (f.invR * f.invS) / (F)n_sm;
+  f.A_rl = th.nc_nsm == n_sm ? flops * (f.invR * f.invS) * th.inv_nsm : flops * (f.invR * f.invS) / (F)n_sm;
   f.B_rl = bytes_min * th.inv[2];
   f.T_rl = f.launch + (f.A_rl >= f.B_rl ? f.A_rl : f.B_rl);
   f.T = f.T_stage >= f.T_rl ? f.T_stage : f.T_rl;
@@ -266,7 +292,7 @@ __device__ __forceinline__ void step_store_adjoint(const pm_cfg& c, const ThetaT
   d[5] -= g_store * (f.store_bytes * th.inv[5]) * th.inv[5];
   // T_step = max(T_eq8, T_ring); ties to Eq. 8
   const F g_eq8 = f.ring ? F(0) : g_step;
-  const F g_ring = f.ring ? g_step / (F)c.stages : F(0);   // per term of the ring's cycle
+  const F g_ring = f.ring ? div_stages(g_step, c.stages, th) : F(0);   // per term of the ring's cycle
   F g_sync = g_eq8 + g_ring;
   F g_c = g_ring, g_io = F(0);
   if (f.T_c >= f.T_io) g_c += g_eq8; else g_io = g_eq8;
@@ -274,13 +300,13 @@ __device__ __forceinline__ void step_store_adjoint(const pm_cfg& c, const ThetaT
   if (!measured) g_sync += g_io;
   const F g_tma = g_io * f.oma + g_ring;
   if (f.oma_free)
-    d[15] += g_io * f.T_tma / (F)(measured ? c.stages - 1 : c.stages);
+    d[15] += measured ? div_stages_m1(g_io * f.T_tma, c.stages, th) : div_stages(g_io * f.T_tma, c.stages, th);
   d[4] += g_tma;
-  const F t_bw = f.blend ? f.bstep * th.inv[5] / f.rho : f.bstep * th.inv[5];   // b_step / (B_TMA rho)
+  const F t_bw = f.blend ? pm_div_fast(f.bstep * th.inv[5], f.rho) : f.bstep * th.inv[5];   // b_step / (B_TMA rho)
   d[5] -= g_tma * t_bw * th.inv[5];
   if (f.blend) {
     // rho = 1 + (rho_L2 - 1) E, E = exp(-W/w0)
-    const F g_rho = -g_tma * t_bw / f.rho;
+    const F g_rho = -pm_div_fast(g_tma * t_bw, f.rho);
     d[16] += g_rho * f.E;
     d[3] += g_rho * (th.v[16] - F(1)) * f.E * (f.W * th.inv[3]) * th.inv[3];
   }
