@@ -502,7 +502,7 @@ def _cpu_per_config() -> dict:
         return min(ts)
 
     out = {}
-    # config 1: FP64 GEMM 512^3 (the definition), all host cores and one thread
+    # FP64 GEMM 512^3 (the definition), all host cores and one thread
     A, B = S.gemm_operands(512, 512, 512, seed=0)
     O.gemm_f64(A, B)
     t_all = best(lambda: O.gemm_f64(A, B))
@@ -517,36 +517,36 @@ def _cpu_per_config() -> dict:
         c1.update(GFLOPps_one_thread=2 * 512 ** 3 / t_one / 1e9, ms_one_thread=t_one * 1e3)
     except OSError:
         pass
-    out["config1_fp64_gemm_512"] = c1
-    # config 2a: triad (one rounding, one thread) and copy over 2^26 FP32
+    out["fp64_gemm_512"] = c1
+    # triad (one rounding, one thread) and copy over 2^26 FP32
     n = 2 ** 26
     b = S.uniform_pm1(1, n)
     c = S.uniform_pm1(1, n, offset=n)
     t_tr = best(lambda: O.triad_f32(b, c, 3.0))
     dst = np.empty_like(b)
     t_cp = best(lambda: np.copyto(dst, b))
-    out["config2a_stream"] = {"n": n, "triad_GBps_one_thread": 12.0 * n / t_tr / 1e9,
+    out["stream_2pow26"] = {"n": n, "triad_GBps_one_thread": 12.0 * n / t_tr / 1e9,
                               "copy_GBps": 8.0 * n / t_cp / 1e9}
-    # config 2c: pointer chase over 256 MB, 2^20 dependent loads
+    # pointer chase over 256 MB, 2^20 dependent loads
     nodes = (256 << 20) // 64
     buf = S.pchase_buffer(nodes, seed=1)
     hops = 2 ** 20
     t_pc = best(lambda: O.pchase(buf, 16, 0, hops), 2)
-    out["config2c_pchase_256MB"] = {"ns_per_hop": t_pc / hops * 1e9}
+    out["pchase_256MB"] = {"ns_per_hop": t_pc / hops * 1e9}
     del b, c, dst, buf
-    # config 4: per-group sampled rows of the grouped GEMM (8 groups x 8 rows, N = K = 4096)
+    # per-group sampled rows of the 64-group grouped GEMM (8 groups x 8 rows, N = K = 4096)
     Bg = S.matrix(3, 4096, 4096, "normal", 0)
     Ag = S.matrix(3, 8, 4096, "normal", 4096 * 4096)
     t_g = best(lambda: [O.gemm_f64(Ag, Bg) for _ in range(8)], 2)
-    out["config4_grouped_rows"] = {"GFLOPps": 8 * 2 * 8 * 4096 * 4096 / t_g / 1e9, "sample": "8 groups x 8 rows"}
-    # config 5: FP64 model with its dual-number gradient over 2e5 configurations
+    out["grouped_rows"] = {"GFLOPps": 8 * 2 * 8 * 4096 * 4096 / t_g / 1e9, "sample": "8 groups x 8 rows"}
+    # FP64 model with its dual-number gradient over 2e5 configurations
     nc = 200000
     cf = S.model_config_batch(nc, seed=4)
     cf["kind"] = np.zeros(nc, dtype=np.int32)
     th = O.prior_theta(152)
     t_m = best(lambda: O.model_batch(cf, th, 152), 2)
     t_mg = best(lambda: O.model_batch(cf, th, 152, grad=True), 2)
-    out["config5_model"] = {"forward_Mcfg_per_s": nc / t_m / 1e6, "forward_grad_Mcfg_per_s": nc / t_mg / 1e6,
+    out["model_2e5"] = {"forward_Mcfg_per_s": nc / t_m / 1e6, "forward_grad_Mcfg_per_s": nc / t_mg / 1e6,
                             "sample": "%d configurations" % nc}
     return out
 
@@ -625,7 +625,7 @@ def secondary(pm, S, theta, n_sm, peaks):
     r_pc = pm.pm_probe_run(pm.probe_args(pm.PM_PROBE_PCHASE, n=nodes, hops=hops, start=0), buf, res, warmup=2, reps=3)
     out["probes"]["pchase_256MB_ns_per_hop"] = 1e9 * r_pc["median_s"] / hops
     del buf
-    # config 1: FP32 (three-pass TF32) GEMM 512^3 in its fixed tile, and the
+    # FP32 (three-pass TF32) GEMM 512^3 in its fixed tile, and the
     # stage model's prediction for that launch (calibrated theta, measured reading)
     A1 = torch.from_numpy(S.matrix(0, 512, 512, "uniform", 0)).cuda()
     B1 = torch.from_numpy(S.matrix(0, 512, 512, "uniform", 512 * 512)).cuda()
@@ -638,7 +638,7 @@ def secondary(pm, S, theta, n_sm, peaks):
     pm.pm_model_predict(pm.cfg_tensor({k: np.array([v]) for k, v in dict(
         M=512, N=512, K=512, BM=128, BN=128, BK=32, stages=2, cta_group=1, dtype=0, kind=0).items()}),
         1, theta, n_sm, p1)
-    out["config1"] = {"workload": "fp32_gemm_512^3_128x128x32_s2_g1", "gpu_us": r1["median_s"] * 1e6,
+    out["fp32_gemm_512"] = {"workload": "fp32_gemm_512^3_128x128x32_s2_g1", "gpu_us": r1["median_s"] * 1e6,
                       "TFLOPps": 2 * 512 ** 3 / r1["median_s"] / 1e12, "model_pred_us": float(p1.item()) * 1e6,
                       "model_ape_pct": abs(float(p1.item()) - r1["median_s"]) / r1["median_s"] * 100}
     # the same launch under the literal equations with their own calibration
@@ -654,8 +654,8 @@ def secondary(pm, S, theta, n_sm, peaks):
             torch.cuda.synchronize()
         finally:
             pm.pm_model_set_reading(pm.PM_READING_MEASURED)
-        out["config1"]["model_pred_us_literal_reading"] = float(p1.item()) * 1e6
-        out["config1"]["model_ape_pct_literal_reading"] = abs(float(p1.item()) - r1["median_s"]) / r1["median_s"] * 100
+        out["fp32_gemm_512"]["model_pred_us_literal_reading"] = float(p1.item()) * 1e6
+        out["fp32_gemm_512"]["model_ape_pct_literal_reading"] = abs(float(p1.item()) - r1["median_s"]) / r1["median_s"] * 100
     del A1, B1, C1, ops1
     # batched model over 1e6 configurations: forward and adjoint
     nc = 10 ** 6
@@ -684,7 +684,7 @@ def secondary(pm, S, theta, n_sm, peaks):
     t_f = timeit(lambda: pm.pm_model_predict(dev, nc, theta, n_sm, t_out))
     t_g = timeit(lambda: pm.pm_model_grad(dev, nc, theta, n_sm, tm, ws, go))
     t_a = timeit(lambda: pm.pm_autotune_pick(MNK, nc // 180, 1, theta, n_sm, picks, tp))
-    # grouped GEMM (config 4): 64 problems, M_g log-uniform in [16, 4096] (seed 3), N = K = 4096, BF16,
+    # grouped GEMM: 64 problems, M_g log-uniform in [16, 4096] (seed 3), N = K = 4096, BF16,
     # tiles and launch from the grouped autotuner (the model's 4 best launches timed, fastest kept), one
     # persistent launch replayed from a CUDA graph
     Mg = S.grouped_m(64, 3)

@@ -4,9 +4,9 @@ measured kernel times with a train/holdout split; Sec. V-B protocol: warm-ups,
 timed runs, median).
 
 Pieces
-  * measure_sweep(): the calibration table -- config 1 (FP32 GEMM 512^3 over
-    the FP32 tile space), config 2 (copy/triad 2^20..2^30, TMA 2D tiles on a
-    1 GiB matrix, pointer chase 16 KB..1 GB) and config 3 (every valid BF16 and
+  * measure_sweep(): the calibration table -- the FP32 GEMM at 512^3 over
+    the FP32 tile space, the memory probes (copy/triad 2^20..2^30, TMA 2D tiles
+    on a 1 GiB matrix, pointer chase 16 KB..1 GB) and the BF16/FP8 sweep (every valid BF16 and
     FP8 tile configuration at M = N = K in {1024..16384}), each timed on the
     device by the library's own harness (pm_gemm_bench / pm_probe_run).
   * measure_tmem_b(): the same GEMM classes under TMEM strategy B (A operand
@@ -96,13 +96,13 @@ def clock_of(r: dict) -> dict:
 
 
 def family_of(r: dict) -> str:
-    if "family" in r:
-        return r["family"]
+    if "launch" in r and "G" in r:
+        return "grouped"
     if r["kind"] == pm.PM_KIND_COPY or r["kind"] == pm.PM_KIND_TRIAD:
-        return "2a_stream"
+        return "stream"
     if r["kind"] == pm.PM_KIND_TMA2D:
-        return "2b_tma"
-    fam = {0: "1_fp32", 1: "3_bf16", 2: "3_fp8"}[int(r["dtype"])]
+        return "tma"
+    fam = {0: "fp32", 1: "bf16", 2: "fp8"}[int(r["dtype"])]
     return fam + "_tmemB" if r.get("tmem_a", 0) else fam
 
 
@@ -133,7 +133,7 @@ def measure_sweep(shapes=(1024, 2048, 4096, 8192, 16384), dtypes=(1, 2), log=pri
     torch.cuda.nvtx.range_push("measure_sweep")
     rows = []
     t0 = time.time()
-    # config 1: FP32 (three-pass TF32) 512^3 over the FP32 tile space
+    # FP32 (three-pass TF32) GEMM at 512^3 over the FP32 tile space
     A, B = S.gemm_operands(512, 512, 512, seed=0)
     ops = pm.GemmOperands(pm.PM_FP32, 512, 512, 512)
     ops.prepare(torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda())
@@ -144,8 +144,8 @@ def measure_sweep(shapes=(1024, 2048, 4096, 8192, 16384), dtypes=(1, 2), log=pri
         r = ops.bench(pm.cfg(512, 512, 512, *t, dtype=0), C, warmup=10, reps=100)
         rows.append(dict(zip(FIELDS, (512, 512, 512, *t, 0, 0, 0)), t=r["median_s"], p25=r["p25_s"],
                          p75=r["p75_s"], **clock_of(r)))
-    log("config 1 done (%d rows, %.0f s)" % (len(rows), time.time() - t0))
-    # config 2: copy / triad over 2^20 .. 2^30 FP32 elements
+    log("FP32 512^3 done (%d rows, %.0f s)" % (len(rows), time.time() - t0))
+    # memory probes: copy / triad over 2^20 .. 2^30 FP32 elements
     nmax = 2 ** 30
     a = torch.from_numpy(S.uniform_pm1(1, nmax)).cuda()
     b = torch.empty_like(a)
@@ -169,7 +169,7 @@ def measure_sweep(shapes=(1024, 2048, 4096, 8192, 16384), dtypes=(1, 2), log=pri
                          kind=pm.PM_KIND_TMA2D, t=r["median_s"], p25=r["p25_s"], p75=r["p75_s"], **clock_of(r)))
     del a, src, dst
     torch.cuda.empty_cache()
-    log("config 2 probes done (%.0f s)" % (time.time() - t0))
+    log("memory probes done (%.0f s)" % (time.time() - t0))
     # pointer chase: 16 KB .. 1 GB working sets, 64-byte node stride
     pchase = []
     for k in range(17):
@@ -193,7 +193,7 @@ def measure_sweep(shapes=(1024, 2048, 4096, 8192, 16384), dtypes=(1, 2), log=pri
     streams = measure_streams()
     settle()
     log("concurrent-stream probes done (%.0f s)" % (time.time() - t0))
-    # config 3: every valid BF16 / FP8 configuration at M = N = K = s
+    # BF16 / FP8 sweep: every valid configuration at M = N = K = s
     for s in shapes:
         A, B = S.gemm_operands(s, s, s, seed=2, dist="normal")
         Ad, Bd = torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()
@@ -212,7 +212,7 @@ def measure_sweep(shapes=(1024, 2048, 4096, 8192, 16384), dtypes=(1, 2), log=pri
             del ops
         del Ad, Bd, C
         torch.cuda.empty_cache()
-        log("config 3 shape %d done (%d rows, %.0f s)" % (s, len(rows), time.time() - t0))
+        log("BF16/FP8 %d^3 done (%d rows, %.0f s)" % (s, len(rows), time.time() - t0))
     settle()
     rows += measure_tmem_b(shapes, dtypes, log)
     settle()
@@ -438,7 +438,7 @@ class GroupedLoss(torch.autograd.Function):
 class GpuObjective:
     """Binds a calibration table to the GPU loss: call with theta (float64
     tensor).  rows: configuration records (pm_cfg fields and the measured t);
-    grouped: measured grouped launches (family 4), each one term of the mean
+    grouped: measured grouped launches (the grouped family), each one term of the mean
     like a configuration."""
 
     def __init__(self, rows, n_sm, grouped=()):
@@ -833,13 +833,13 @@ def measure_segments(table, log=print) -> dict:
     return dict(rows=rows, tau_sync_s=float(np.median(ts)))
 
 
-# Grouped problems of family 4 (config 4's recipe at several sizes): number of
+# Grouped problems of the grouped family (the 64-group recipe at several sizes): number of
 # groups, seed of M_g = round(exp(U[ln 16, ln 4096])), N = K.
 GROUPED_PROBLEMS = ((64, 3, 1024), (64, 3, 2048), (64, 3, 4096), (16, 5, 2048), (16, 5, 4096), (32, 9, 1024))
 
 
 def measure_grouped(theta, n_sm, problems=GROUPED_PROBLEMS, warmup=3, reps=15, log=print) -> list:
-    """Family 4: every launch-level candidate of the grouped autotuner (its
+    """Grouped family: every launch-level candidate of the grouped autotuner (its
     per-group tiles under theta) of each grouped BF16 problem, timed as one
     persistent launch (CUDA events, median of `reps`), operands drawn on the
     device from a seeded generator."""
@@ -857,7 +857,7 @@ def measure_grouped(theta, n_sm, problems=GROUPED_PROBLEMS, warmup=3, reps=15, l
                 continue
             run = lambda: pm.pm_grouped_gemm_run(Mg, NK, NK, bm, bn, *launch, A, B, C)
             ts = _events_times(run, warmup, reps)
-            rows.append(dict(family="4_grouped", G=G, seed=seed, M=Mg, N=NK, K=NK, bm=bm, bn=bn,
+            rows.append(dict(family="grouped", G=G, seed=seed, M=Mg, N=NK, K=NK, bm=bm, bn=bn,
                              launch=list(launch), t=float(np.median(ts)), p25=float(np.percentile(ts, 25)),
                              p75=float(np.percentile(ts, 75))))
         del A, B, C
@@ -906,7 +906,7 @@ def grouped_autotune_report(grouped, theta, n_sm) -> list:
 
 
 def grouped_family(seg_table, theta, n_sm) -> dict:
-    """Family 4 (grouped GEMM): the stage model's makespan (pm_grouped_predict)
+    """Grouped GEMM family: the stage model's makespan (pm_grouped_predict)
     of each measured grouped launch against its time."""
     out = []
     for r in seg_table["rows"]:
@@ -1093,7 +1093,7 @@ def main():
     ap.add_argument("--measure-tmem-b", action="store_true", help="re-measure only the strategy-B GEMM rows")
     ap.add_argument("--measure-streams", action="store_true", help="re-measure only the concurrent-stream probes")
     ap.add_argument("--measure-segments", action="store_true", help="re-measure only the generic-path segments")
-    ap.add_argument("--measure-grouped", action="store_true", help="re-measure only the grouped launches (family 4)")
+    ap.add_argument("--measure-grouped", action="store_true", help="re-measure only the grouped launches")
     ap.add_argument("--reading", type=int, default=pm.PM_READING_MEASURED,
                     help="0: literal equations; 1: readings measured on the kernels (default)")
     ap.add_argument("--sweep", default=SWEEP_PATH)

@@ -15,9 +15,9 @@ FIELDS = C.FIELDS
 
 
 def table(theta):
-    """The calibration table's configurations: config 3 (every valid BF16 and
-    FP8 tile at M = N = K in {1024 .. 16384}, 1,445 rows), config 1 (FP32
-    512^3 over its 55 tiles) and config 2 (copy and triad 2^20 .. 2^30, the
+    """The calibration table's configurations: the BF16/FP8 sweep (every valid BF16 and
+    FP8 tile at M = N = K in {1024 .. 16384}, 1,445 rows), the FP32 GEMM at
+    512^3 over its 55 tiles and the memory probes (copy and triad 2^20 .. 2^30, the
     five TMA tiles), with the oracle's times under theta as the targets."""
     rows = []
     for s in (1024, 2048, 4096, 8192, 16384):
@@ -124,8 +124,8 @@ def test_split_is_seeded_and_disjoint():
 def test_mae_definition():
     rows = [dict(kind=0, dtype=1, t=1.0), dict(kind=0, dtype=1, t=2.0), dict(kind=1, dtype=0, t=4.0)]
     m = C.mae_by_family(rows, np.array([1.1, 1.8, 4.0]))
-    assert m["3_bf16"]["mae_pct"] == pytest.approx(10.0)
-    assert m["2a_stream"]["mae_pct"] == pytest.approx(0.0)
+    assert m["bf16"]["mae_pct"] == pytest.approx(10.0)
+    assert m["stream"]["mae_pct"] == pytest.approx(0.0)
     assert m["all"]["mae_pct"] == pytest.approx(20.0 / 3)
 
 

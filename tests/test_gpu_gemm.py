@@ -164,7 +164,7 @@ def test_tmem_strategy_b_accuracy(lib, dt, tol, t):
 
 
 # ---------------------------------------------------------- real-valued accuracy
-def test_fp32_config1_normwise(lib):
+def test_fp32_512_normwise(lib):
     # 512^3, uniform[-1,1) seed 0, BM=BN=128, BK=32, 2 stages, cta_group 1
     A, B = S.gemm_operands(512, 512, 512, seed=0)
     C, _ = run_gemm(lib, A, B, lib.cfg(512, 512, 512, 128, 128, 32, 2, 1, dtype=0), 0)

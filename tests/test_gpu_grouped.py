@@ -74,7 +74,7 @@ def test_grouped_exact_integer_mixed_tiles(lib, launch):
         row0 += m
 
 
-def test_grouped_config4_shape_reduced_with_graph(lib):
+def test_grouped_64_groups_reduced_with_graph(lib):
     # 64 groups, M log-uniform in [16, 4096] (seed 3), N = K = 1024, tiles
     # and launch from the GPU grouped autotuner; captured in a CUDA graph.
     Mg = S.grouped_m(64, 3)

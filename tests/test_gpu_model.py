@@ -57,7 +57,7 @@ def test_predict_matches_oracle(lib, reading, n):
     assert np.all(np.abs(t_gpu - t_orc) <= 1e-5 * t_orc)
 
 
-def test_predict_probes_and_config1(lib, reading):
+def test_predict_probes_and_fp32_512(lib, reading):
     th = theta32()
     c = probe_cfgs()
     assert np.all(np.abs(predict_gpu(lib, c, th) - O.model_batch(c, th, N_SM)) <= 1e-5 * O.model_batch(c, th, N_SM))

@@ -44,7 +44,7 @@ PRIOR160_MEASURED = O.prior_theta(160, reading=O.READING_MEASURED)
 HAND = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "hand_rows.json")))
 CONFIG_ROWS = HAND["config_rows"]
 # Literal reading (L_mma once per K-step, alpha = 1 - 0.3/s, T_sync in Eqs. 7
-# and 8): the golden values printed with the model's definition (config 1 has
+# and 8): the golden values printed with the model's definition (the FP32 512^3 row has
 # T_c = 4.290643e-07 s and T_io = 3.118298e-07 s per step).
 HAND_LITERAL = [1.438600e-05, 6.278955e-04, 3.385809e-04, 6.608431e-03, 1.268226e-03, 1.899839e-03, 6.067389e-06]
 # Measured reading (L_mma per instruction: 12, 4 and 4 per K-step in the first
