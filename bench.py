@@ -720,6 +720,37 @@ def secondary(pm, S, theta, n_sm, peaks):
                       "roofline_frac": max(gflops / (float(peaks.get("bf16_tflops", 1900.0)) * 1e12),
                                            gbytes / (float(peaks.get("hbm_gbs", 6800.0)) * 1e9)) / t_grp}
     del A_g, B_g, C_g, graph
+    # FP8 e4m3 GEMM 8192^3 (per-tensor scales from the amax pass), in the tile the
+    # library's autotuner picks (the model's 8 best tiles timed), 20 timed launches;
+    # its peak is the measured BF16 burst peak times the nominal FP8/BF16 ratio of 2
+    n8 = 8192
+    gen.manual_seed(2)
+    A8 = torch.randn(n8, n8, device="cuda", generator=gen)
+    B8 = torch.randn(n8, n8, device="cuda", generator=gen)
+    ops8 = pm.GemmOperands(pm.PM_FP8E4M3, n8, n8, n8)
+    ops8.prepare(A8, B8)
+    del A8, B8
+    C8 = torch.empty(n8, n8, dtype=torch.float32, device="cuda")
+    tuned8, _ = pm.pm_gemm_autotune(pm.cfg(n8, n8, n8, dtype=pm.PM_FP8E4M3), 8, theta, n_sm, ops8.A_op, ops8.B_op,
+                                    C8, ops8.scales)
+    tile8 = (tuned8.BM, tuned8.BN, tuned8.BK, tuned8.stages, tuned8.cta_group)
+    r8 = ops8.bench(pm.cfg(n8, n8, n8, *tile8, dtype=pm.PM_FP8E4M3), C8, warmup=5, reps=20)
+    p8 = torch.empty(1, dtype=torch.float32, device="cuda")
+    pm.pm_model_predict(pm.cfg_tensor({k: np.array([v]) for k, v in dict(
+        M=n8, N=n8, K=n8, BM=tile8[0], BN=tile8[1], BK=tile8[2], stages=tile8[3], cta_group=tile8[4],
+        dtype=pm.PM_FP8E4M3, kind=0).items()}), 1, theta, n_sm, p8)
+    fp8_peak = 2.0 * float(peaks.get("bf16_tflops", 1900.0))
+    tf8 = 2.0 * n8 ** 3 / r8["median_s"] / 1e12
+    out["fp8_gemm_8192"] = {"workload": "fp8_e4m3_gemm_8192^3_model_autotuned",
+                            "tile": dict(zip(("BM", "BN", "BK", "stages", "cta_group"), tile8)),
+                            "autotune": "model top-8 tiles (GPU) timed on the device, fastest kept",
+                            "ms": r8["median_s"] * 1e3, "TFLOPps": tf8, "peak_TFLOPps": fp8_peak,
+                            "peak_source": "measured bf16 burst x 2 (nominal FP8/BF16 dense ratio)",
+                            "frac": tf8 / fp8_peak, "model_pred_ms": float(p8.item()) * 1e3,
+                            "model_ape_pct": abs(float(p8.item()) - r8["median_s"]) / r8["median_s"] * 100,
+                            "sm_mhz_begin": r8["sm_mhz_begin"], "sm_mhz_end": r8["sm_mhz_end"],
+                            "clock_reasons": r8["clock_reasons"], "timing": "median of 20 launches after 5 warm-ups"}
+    del C8, ops8
     hbm = float(peaks.get("hbm_gbs", 6800.0))
     out["model"] = {"configs": nc, "forward_Mcfg_per_s": nc / t_f / 1e6, "forward_us": t_f * 1e6,
                     "adjoint_Mcfg_per_s": nc / t_g / 1e6, "adjoint_us": t_g * 1e6,
