@@ -79,9 +79,11 @@ typedef struct {
  * 12 L_mbar    13 L_alloc+L_dealloc      14 S_2SM      15 c_alpha
  * 16 rho_L2 (measured reading only: TMA load speed-up of an L2-resident
  *    working set, Sec. III-A.2)
+ * 17 B_drain/SM (measured reading only: rate at which a tile's accumulator
+ *    is drained when the kernel keeps one accumulator buffer, Sec. III-A.5)
  * with the overlap law alpha(stages) = clamp(1 - c_alpha/stages, 0, 1) (the
  * measured reading: clamp(1 - c_alpha/(stages - 1), 0, 1)). */
-#define PM_NPARAMS 17
+#define PM_NPARAMS 18
 typedef struct { float v[PM_NPARAMS]; } pm_params;
 
 /* Readings of the points the paper leaves open in the stage model:
@@ -100,7 +102,12 @@ typedef struct { float v[PM_NPARAMS]; } pm_params;
  *    persistent CTA allocates tensor memory once: T_launch + L_alloc+L_dealloc
  *    starts every GEMM launch), and a one-SM tile of 64 rows at the tensor
  *    time of 128 rows (an M = 64 tcgen05.mma on one SM takes as long as an
- *    M = 128 one).
+ *    M = 128 one), and T_store + 4 BM BN / B_drain per tile of a launch whose
+ *    accumulator cannot be double-buffered in the 512 TMEM columns (twice
+ *    ceil(BM/128) BN columns, BN/2 for 64 rows per CTA of a pair, plus
+ *    strategy B's A copy per stage, above 512): its next tile waits for the
+ *    drain, which two buffers hide.  A grouped launch is single-buffered when
+ *    any group's tile is.
  * The setting is process-wide and read by every model entry point at launch;
  * fit theta under the reading it will be used with. */
 typedef enum { PM_READING_LITERAL = 0, PM_READING_MEASURED = 1 } pm_reading;

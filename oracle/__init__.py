@@ -40,14 +40,15 @@ _lib = None
 
 KIND_GEMM, KIND_COPY, KIND_TRIAD, KIND_TMA2D = 0, 1, 2, 3
 DT_FP32, DT_BF16, DT_FP8 = 0, 1, 2
-N_PARAMS = 17
+N_PARAMS = 18
 
 PARAM_NAMES = ("T_launch", "B_sus", "B_peak", "w0", "L_TMA", "B_TMA", "R_tf32", "R_bf16", "R_fp8",
-               "L_mma", "BW_tmem_rd", "BW_tmem_wr", "L_mbar", "L_tmem_mgmt", "S_2SM", "c_alpha", "rho_L2")
-# Time-like parameters (seconds) and rate-like parameters (per second); the
-# rest (w0, S_2SM, c_alpha, rho_L2) are dimensionless or sizes.
+               "L_mma", "BW_tmem_rd", "BW_tmem_wr", "L_mbar", "L_tmem_mgmt", "S_2SM", "c_alpha", "rho_L2",
+               "B_drain")
+# Time-like parameters (seconds) and rate-like parameters (bytes or FLOP per
+# second); the rest (w0, S_2SM, c_alpha, rho_L2) are dimensionless or sizes.
 LATENCY_IDX = (0, 4, 9, 12, 13)
-RATE_IDX = (1, 2, 5, 6, 7, 8, 10, 11)
+RATE_IDX = (1, 2, 5, 6, 7, 8, 10, 11, 17)
 
 
 def build(force: bool = False) -> str:
@@ -314,7 +315,9 @@ def set_reading(reading: int) -> None:
     alpha = 1 - c/(s-1), T_sync once, the ring bubble (T_tma + T_c + T_sync)/s as a
     lower bound of T_step, B_TMA scaled by the L2-residency factor
     rho(W) = 1 + (rho_L2 - 1) exp(-W/w0) over the launch's working set W, TMEM
-    management once per launch, 64-row one-SM tiles at the tensor time of 128 rows)."""
+    management once per launch, 64-row one-SM tiles at the tensor time of 128 rows, and
+    each tile of a launch whose accumulator cannot be double-buffered paying its drain,
+    4 BM BN / B_drain, before the next tile starts)."""
     _load().orc_set_reading(int(reading))
 
 
@@ -345,6 +348,7 @@ def prior_theta(n_sm: int, f_hz: float = 1.9e9, reading: int = READING_MEASURED)
     # alpha(2) = 0.85, alpha(6) = 0.95 (reading 0); alpha(2) = 0.85, alpha(3) = 0.925 (reading 1)
     th[15] = 0.3 if reading == READING_LITERAL else 0.15
     th[16] = th[2] / th[1]            # rho_L2: an L2-resident launch loads at the HBM peak/sustained ratio
+    th[17] = th[1] / n_sm             # B_drain per SM (not printed): the SM's share of sustained HBM, like B_TMA
     return th
 
 

@@ -170,10 +170,10 @@ extern "C" uint32_t orc_pchase(const uint32_t* buf, i64 stride_words, uint32_t s
 }
 
 // ---------------------------------------------------------------------------
-// Dual numbers: value plus the 16 partial derivatives with respect to the
+// Dual numbers: value plus the NP partial derivatives with respect to the
 // model parameters theta.  Arithmetic follows the usual differentiation rules.
 // ---------------------------------------------------------------------------
-enum { NP = 17 };
+enum { NP = 18 };
 struct Dual {
   double v;
   double d[NP];
@@ -232,6 +232,10 @@ static inline double value_of(const Dual& a) { return a.v; }
 // 16 rho_L2        TMA load speed-up of an L2-resident working set over a
 //                  streaming one (reading 1; Sec. III-A.2: L2 hit rates
 //                  strongly affect B_TMA); unused by reading 0
+// 17 B_drain       per-SM rate at which a single-buffered accumulator is
+//                  drained before the next tile may start (reading 1;
+//                  Sec. III-A.5: T_store, overlapped only when the kernel
+//                  double-buffers TMEM); unused by reading 0
 // ---------------------------------------------------------------------------
 
 enum { K_GEMM = 0, K_COPY = 1, K_TRIAD = 2, K_TMA2D = 3 };
@@ -300,9 +304,12 @@ static T b_eff(const T* th, double W) {
 //     scaled by an L2-residency factor rho(W) = 1 + (rho_L2 - 1) exp(-W/w0)
 //     over the launch's working set W (Eq. 16's blend shape), the TMEM
 //     management of Sec. III-A.5 paid once per launch (a persistent CTA
-//     allocates its tensor memory once, not once per tile), and a single-SM
+//     allocates its tensor memory once, not once per tile), a single-SM
 //     tile of 64 rows taking the tensor time of 128 rows (an M = 64
-//     tcgen05.mma on one SM runs at half the per-SM rate).
+//     tcgen05.mma on one SM runs at half the per-SM rate), and a launch
+//     whose accumulator cannot be double-buffered in the 512 TMEM columns
+//     paying each tile's drain before the next tile starts (T_store plus
+//     4 BM BN / B_drain; a double-buffered launch overlaps it).
 static int g_reading = 1;   // the measured readings by default
 extern "C" void orc_set_reading(int r) { g_reading = r == 0 ? 0 : 1; }
 extern "C" int orc_reading() { return g_reading; }
@@ -316,12 +323,24 @@ static i64 cta_tiles(i64 M, i64 N, int BM, int BN, int g) {
   return ceil_div(M, (i64)BM) * ceil_div(N, (i64)BN);
 }
 
+// Whether a launch keeps one accumulator buffer only: the kernel holds two
+// when twice the accumulator columns of its largest tile (ceil(BM/128) BN,
+// or BN/2 for a 64-row tile on a CTA pair), plus strategy B's A copy per
+// stage, fit in the 512 TMEM columns.
+static bool single_buffer(int BM, int BN, int BK, int s, int g, int dtype, int tmem_a) {
+  const i64 acc = (BM < 128 && g == 2) ? (i64)BN / 2 : ceil_div(BM, 128) * (i64)BN;
+  const i64 a_ring = tmem_a ? (i64)s * ceil_div(BM, 128) * (i64)(load_mult(dtype) * elem_bytes(dtype)) * BK / 4 : 0;
+  return 2 * acc + a_ring > 512;
+}
+
 // One K-step and one tile of the stage model (Eqs. 2-8).  Returns T_step and
 // T_store through the out-arguments; shared by the GEMM and grouped models.
 // W is the launch's working set in bytes (operands and C), used by the
-// measured reading's L2 residency of the TMA loads.
+// measured reading's L2 residency of the TMA loads; single_buf says whether
+// the launch has one accumulator buffer only (measured reading: its drain is
+// not overlapped).
 template <class T>
-static void stage_terms(const Cfg& c, i64 Kt, const T* th, double W, T& Tstep, T& Tstore) {
+static void stage_terms(const Cfg& c, i64 Kt, const T* th, double W, bool single_buf, T& Tstep, T& Tstore) {
   const bool measured = g_reading == 1;
   const double e = elem_bytes(c.dtype), np = mma_passes(c.dtype), l = load_mult(c.dtype);
   const T& R = th[rate_index(c.dtype)];
@@ -377,7 +396,12 @@ static void stage_terms(const Cfg& c, i64 Kt, const T* th, double W, T& Tstep, T
   Tstep = dmax(T_c, T_io) + T_sync;
   if (measured) Tstep = dmax(Tstep, (T_tma + T_c + T_sync) / lift<T>((double)c.s));
   // Writeback of the FP32 tile: L_store_setup + bytes(C_tile)/B (Sec. III-A.5).
+  // Measured reading: with one accumulator buffer the next tile's MMAs wait
+  // until the epilogue has read the whole accumulator out, so the launch
+  // also pays 4 BM BN / B_drain per tile; two buffers hide that behind the
+  // next tile's main loop.
   Tstore = th[4] + (4.0 * c.BM * c.BN) / th[5];
+  if (measured && single_buf) Tstore = Tstore + (4.0 * c.BM * c.BN) / th[17];
 }
 
 // Stage-centric GEMM time (Sec. III-A; total of Sec. III-C's unified summary):
@@ -401,7 +425,7 @@ static T model_gemm(const Cfg& c, const T* th, int n_sm) {
   // also its working set
   const double bytes_min = l * e * ((double)c.M * c.K + (double)c.N * c.K) + 4.0 * (double)c.M * c.N;
   T Tstep, Tstore;
-  stage_terms<T>(c, Kt, th, bytes_min, Tstep, Tstore);
+  stage_terms<T>(c, Kt, th, bytes_min, single_buffer(c.BM, c.BN, c.BK, c.s, c.g, c.dtype, c.tmem_a), Tstep, Tstore);
   // the launch: T_launch, plus under the measured reading the TMEM
   // management the persistent kernel pays once
   const T launch = g_reading == 1 ? th[0] + th[13] : th[0];
@@ -563,6 +587,9 @@ static T grouped_time(int G, const int32_t* Mg, int32_t N, int32_t K, const int3
   const i64 n_conc = (g == 1) ? n_sm : 2 * (n_sm / 2);
   const double W = grouped_working_set(G, Mg, N, K, dtype);
   const std::vector<int> order = group_order(G, BMg, BNg);
+  // one accumulator buffer for the whole launch if its largest tile needs it
+  bool single = false;
+  for (int q = 0; q < G; ++q) single = single || single_buffer(BMg[q], BNg[q], BK, s, g, dtype, 0);
   std::vector<T> busy(n_conc, lift<T>(0.0));
   std::vector<i64> count(n_conc);
   i64 t = 0;
@@ -572,7 +599,7 @@ static T grouped_time(int G, const int32_t* Mg, int32_t N, int32_t K, const int3
     c.dtype = dtype; c.kind = K_GEMM;
     const i64 Kt = ceil_div(K, BK);
     T Tstep, Tstore;
-    stage_terms<T>(c, Kt, th, W, Tstep, Tstore);
+    stage_terms<T>(c, Kt, th, W, single, Tstep, Tstore);
     const T tau = lift<T>((double)Kt) * Tstep + Tstore;
     // With cta_group 2 a pair of consecutive tiles runs on a worker pair;
     // each CTA of the pair is one worker.
@@ -630,7 +657,9 @@ extern "C" double orc_grouped_autotune(int G, const int32_t* Mg, int32_t N, int3
               c.g = g; c.dtype = dtype; c.kind = K_GEMM;
               const i64 Kt = ceil_div(K, BK);
               double Tstep, Tstore;
-              stage_terms<double>(c, Kt, theta, W, Tstep, Tstore);
+              // the group's tile alone decides its buffering here; the
+              // launch's makespan below applies the launch-wide rule
+              stage_terms<double>(c, Kt, theta, W, single_buffer(c.BM, c.BN, BK, s, g, dtype, 0), Tstep, Tstore);
               const double tiles = (double)cta_tiles(c.M, N, c.BM, c.BN, g);
               const double cost = tiles * ((double)Kt * Tstep + Tstore);
               if (cost < bq) { bq = cost; bm[q] = c.BM; bn[q] = c.BN; }

@@ -22,7 +22,7 @@ PM_OK, PM_EINVAL, PM_EUNSUPPORTED, PM_ECUDA, PM_ETIMEOUT, PM_ENOMEM = 0, -1, -2,
 PM_FP32, PM_BF16, PM_FP8E4M3 = 0, 1, 2
 PM_KIND_GEMM, PM_KIND_COPY, PM_KIND_TRIAD, PM_KIND_TMA2D = 0, 1, 2, 3
 PM_READING_LITERAL, PM_READING_MEASURED = 0, 1
-N_PARAMS = 17                     # PM_NPARAMS: entries of theta (pm_params)
+N_PARAMS = 18                     # PM_NPARAMS: entries of theta (pm_params)
 N_GRAD_OUT = N_PARAMS + 1         # pm_model_grad output: loss, then the gradient
 N_PSI = 17                        # PM_NPSI: entries of the segment parameters (pm_segment_params)
 PM_PROBE_COPY, PM_PROBE_TRIAD, PM_PROBE_TMA2D, PM_PROBE_PCHASE = 1, 2, 3, 4

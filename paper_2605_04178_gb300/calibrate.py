@@ -66,7 +66,8 @@ def prior_theta(n_sm: int, f_hz: float = 1.9e9, reading: int = pm.PM_READING_MEA
     """Parameter priors from the paper's printed values (Table "parameters",
     Sec. II-A sustained figures, Table "arch-params"); cycles at f_hz.  c_alpha
     puts alpha(2) at 0.85 under either overlap law of the reading; rho_L2
-    starts at the peak-to-sustained HBM ratio."""
+    starts at the peak-to-sustained HBM ratio and B_drain, like B_TMA, at the
+    per-SM share of the sustained HBM rate (neither is printed)."""
     th = np.zeros(pm.N_PARAMS)
     th[0] = 5e-6
     th[1] = 6.8e12
@@ -85,6 +86,7 @@ def prior_theta(n_sm: int, f_hz: float = 1.9e9, reading: int = pm.PM_READING_MEA
     th[14] = 1.0
     th[15] = 0.3 if reading == pm.PM_READING_LITERAL else 0.15
     th[16] = th[2] / th[1]
+    th[17] = th[1] / n_sm
     return th
 
 

@@ -157,6 +157,17 @@ __host__ __device__ inline bool tile_valid(int BM, int BN, int BK, int s, int g,
   return true;
 }
 
+// Whether the GEMM kernel keeps one accumulator buffer only: it holds two when
+// twice the accumulator columns of the tile (ceil(BM/128) BN, or BN/2 for a
+// 64-row tile on a CTA pair), plus strategy B's A copy per stage, fit in the
+// 512 TMEM columns.
+__host__ __device__ inline bool single_buffer(int BM, int BN, int BK, int s, int g, int dt, int tmem_a) {
+  const int acc = (BM < 128 && g == 2) ? BN / 2 : ((BM + 127) / 128) * BN;
+  const int le = dt == PM_FP32 ? 8 : (dt == PM_BF16 ? 2 : 1);    // load planes x element bytes
+  const int a_ring = tmem_a ? s * ((BM + 127) / 128) * (le * BK / 4) : 0;
+  return 2 * acc + a_ring > 512;
+}
+
 // Intermediate values of one GEMM evaluation, kept for the adjoint.
 template <class F>
 struct GemmFwdT {
@@ -169,6 +180,7 @@ struct GemmFwdT {
   F T_eq8, T_ring;       // Eq. 8 and the ring bound (measured reading)
   int ri;
   bool oma_free, blend, ring;
+  bool drain;           // measured reading, one accumulator buffer: each tile's drain is paid
 };
 using GemmFwd = GemmFwdT<float>;
 
@@ -196,11 +208,16 @@ using GemmFwd = GemmFwdT<float>;
 //   T_hat = max(T_stage, launch + max(FLOPs/(n_SM R S), bytes_min/B_peak))
 //            launch = T_launch (literal) or T_launch + L_alloc + L_dealloc
 //            (measured: the persistent CTAs allocate TMEM once per launch)
+//   T_store = L_TMA + 4 BM BN / B_TMA, plus 4 BM BN / B_drain (measured
+//            reading) when the kernel keeps one accumulator buffer only, so
+//            the next tile waits for the drain (two buffers overlap it)
 // W_launch > 0 overrides the working set (a grouped launch passes its own);
-// otherwise W = bytes_min of this GEMM (operands once, C once).
+// otherwise W = bytes_min of this GEMM (operands once, C once).  single >= 0
+// overrides the buffering (a grouped launch passes the launch's); otherwise
+// the tile's own.
 template <class F>
 __device__ __forceinline__ void gemm_forward(const pm_cfg& c, const ThetaT<F>& th, int n_sm, GemmFwdT<F>& f,
-                                             F W_launch = F(-1)) {
+                                             F W_launch = F(-1), int single = -1) {
   const bool measured = th.reading == PM_READING_MEASURED;
   const int dt = c.dtype, g = c.cta_group;
   const F e = dt_bytes(dt), np = dt_passes(dt), l = dt_loads(dt);
@@ -269,7 +286,9 @@ __device__ __forceinline__ void gemm_forward(const pm_cfg& c, const ThetaT<F>& t
   f.ring = measured && f.T_ring > f.T_eq8;
   f.T_step = f.ring ? f.T_ring : f.T_eq8;
   f.store_bytes = f.D;
-  f.T_store = th.v[4] + f.store_bytes * th.inv[5];
+  f.drain = measured && (single >= 0 ? single != 0
+                                     : single_buffer(c.BM, c.BN, c.BK, c.stages, c.cta_group, c.dtype, c.tmem_a));
+  f.T_store = th.v[4] + f.store_bytes * th.inv[5] + (f.drain ? f.store_bytes * th.inv[17] : F(0));
   f.launch = measured ? th.v[0] + th.v[13] : th.v[0];
   f.T_stage = f.launch + f.waves * (f.Kt * f.T_step + f.T_store);
   const F flops = np * F(2) * (F)c.M * (F)c.N * (F)c.K;
@@ -290,6 +309,7 @@ __device__ __forceinline__ void step_store_adjoint(const pm_cfg& c, const ThetaT
   const bool measured = th.reading == PM_READING_MEASURED;
   d[4] += g_store;
   d[5] -= g_store * (f.store_bytes * th.inv[5]) * th.inv[5];
+  if (f.drain) d[17] -= g_store * (f.store_bytes * th.inv[17]) * th.inv[17];
   // T_step = max(T_eq8, T_ring); ties to Eq. 8
   const F g_eq8 = f.ring ? F(0) : g_step;
   const F g_ring = f.ring ? div_stages(g_step, c.stages, th) : F(0);   // per term of the ring's cycle
@@ -850,6 +870,8 @@ __global__ void __launch_bounds__(kGroupThreads) grouped_tune_kernel(const int32
         if (cost < best) { best = cost; bm = BM; bn = BN; btau = tq; btiles = nt; }
       }
     if (best == INFINITY) any_invalid = true;
+    // each group's own tile decides its buffering here; the launch's rule is
+    // applied below
     tau[q] = btau;
     tiles[q] = btiles;
     bm_s[q] = (int16_t)bm;
@@ -858,6 +880,17 @@ __global__ void __launch_bounds__(kGroupThreads) grouped_tune_kernel(const int32
     out_bn[combo * G + q] = (int16_t)bn;
   }
   any_invalid = __syncthreads_or(any_invalid);
+  // the launch keeps one accumulator buffer if any group's tile needs it
+  // (measured reading): every other group's tile then pays its drain too
+  bool single = false;
+  for (int q = threadIdx.x; q < G; q += blockDim.x)
+    single = single || (bm_s[q] > 0 && single_buffer(bm_s[q], bn_s[q], BK, s, g, dt, 0));
+  single = __syncthreads_or(single);
+  if (single && th.reading == PM_READING_MEASURED)
+    for (int q = threadIdx.x; q < G; q += blockDim.x)
+      if (bm_s[q] > 0 && !single_buffer(bm_s[q], bn_s[q], BK, s, g, dt, 0))
+        tau[q] += 4.0f * (float)bm_s[q] * (float)bn_s[q] * th.inv[17];
+  __syncthreads();
   grouped_list(bm_s, bn_s, tiles, G, list, off);
   const float t = grouped_makespan<float>(tau, list, off, G, g == 1 ? n_sm : 2 * (n_sm / 2), nullptr);
   if (threadIdx.x == 0)
@@ -882,12 +915,16 @@ __global__ void __launch_bounds__(kGroupThreads) grouped_predict_kernel(const in
   __shared__ F red_d[kGroupThreads / 32][NP];
   const F W = grouped_working_set<F>(Mg, G, N, K, dt);
   const int64_t n_conc = g == 1 ? n_sm : 2 * (n_sm / 2);
+  // one accumulator buffer for the whole launch if any group's tile needs it
+  bool single = false;
+  for (int q = threadIdx.x; q < G; q += blockDim.x) single = single || single_buffer(BMg[q], BNg[q], BK, s, g, dt, 0);
+  const int sb = __syncthreads_or(single) ? 1 : 0;
   for (int q = threadIdx.x; q < G; q += blockDim.x) {
     pm_cfg c;
     c.M = Mg[q]; c.N = N; c.K = K; c.BM = BMg[q]; c.BN = BNg[q]; c.BK = (int16_t)BK;
     c.stages = (int8_t)s; c.cta_group = (int8_t)g; c.dtype = (int8_t)dt; c.kind = 0; c.tmem_a = 0;
     GemmFwdT<F> f;
-    gemm_forward(c, th, n_sm, f, W);
+    gemm_forward(c, th, n_sm, f, W, sb);
     tau[q] = f.Kt * f.T_step + f.T_store;
     tiles[q] = launch_tiles(th, c.M, N, c.BM, c.BN, g);
   }
@@ -911,7 +948,7 @@ __global__ void __launch_bounds__(kGroupThreads) grouped_predict_kernel(const in
     c.M = Mg[q]; c.N = N; c.K = K; c.BM = BMg[q]; c.BN = BNg[q]; c.BK = (int16_t)BK;
     c.stages = (int8_t)s; c.cta_group = (int8_t)g; c.dtype = (int8_t)dt; c.kind = 0; c.tmem_a = 0;
     GemmFwdT<F> f;
-    gemm_forward(c, th, n_sm, f, W);
+    gemm_forward(c, th, n_sm, f, W, sb);
     F gR = F(0), gS = F(0);
     step_store_adjoint(c, th, f, (F)cnt * f.Kt, (F)cnt, d, gR, gS);
     rate_adjoint(c, f, gR, gS, d);

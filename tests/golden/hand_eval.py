@@ -18,7 +18,8 @@ Units: seconds, bytes, bytes/s, FLOP/s.  Parameters theta, by index:
   0 T_launch, 1 B_sus, 2 B_peak, 3 w0, 4 L_TMA, 5 B_TMA per SM,
   6/7/8 R_TC per SM (TF32/BF16/FP8), 9 L_mma, 10/11 TMEM read/write bandwidth
   per SM, 12 L_mbar, 13 L_alloc + L_dealloc, 14 S_2SM, 15 c_alpha,
-  16 rho_L2 (the measured reading's L2-resident TMA speed-up).
+  16 rho_L2 (the measured reading's L2-resident TMA speed-up), 17 B_drain (the
+  measured reading's per-SM drain rate of a single-buffered accumulator).
 """
 import json
 import math
@@ -37,8 +38,8 @@ def printed_prior(n_sm, f_hz=1.9e9, reading=LITERAL):
     (Table "parameters"), TMEM 16/8 TB/s read/write (Table "parameters"),
     BF16 8192 FLOP per cycle per SM (the dense datasheet rate), TF32 half and
     FP8 twice that, TMEM management 100 ns, S_2SM 1, c_alpha for alpha(2) =
-    0.85, rho_L2 the peak-to-sustained HBM ratio.  Cycles are converted at
-    f_hz."""
+    0.85, rho_L2 the peak-to-sustained HBM ratio, B_drain the per-SM share of
+    the sustained HBM rate (like B_TMA).  Cycles are converted at f_hz."""
     bf16 = 8192.0 * f_hz
     return [
         5e-6,                      # 0 T_launch
@@ -58,6 +59,7 @@ def printed_prior(n_sm, f_hz=1.9e9, reading=LITERAL):
         1.0,                       # 14 S_2SM
         0.3 if reading == LITERAL else 0.15,   # 15 c_alpha
         8.0e12 / 6.8e12,           # 16 rho_L2
+        6.8e12 / n_sm,             # 17 B_drain per SM
     ]
 
 
@@ -125,8 +127,14 @@ def gemm_time(th, n_sm, reading, M, N, K, BM, BN, BK, stages, cta_group, dtype):
         T_step = max(T_step, (T_tma + T_c + T_sync) / stages)
 
     # writeback of the FP32 tile, then the kernel total; the measured reading's
-    # launch includes the TMEM allocation and release of the persistent CTAs
+    # launch includes the TMEM allocation and release of the persistent CTAs.
+    # Measured reading: a kernel that cannot hold two accumulators in the 512
+    # TMEM columns (two of ceil(BM/128) BN columns; BN/2 for 64 rows per CTA of
+    # a pair) drains each tile before the next one starts, at B_drain per SM.
     T_store = th[4] + 4.0 * BM * BN / th[5]
+    acc_cols = BN / 2 if (BM < 128 and g == 2) else up(BM, 128) * BN
+    if reading == MEASURED and 2 * acc_cols > 512:
+        T_store += 4.0 * BM * BN / th[17]
     launch = th[0] if reading == LITERAL else th[0] + th[13]
     T_stage = launch + waves * (K_tiles * T_step + T_store)
 
@@ -158,6 +166,11 @@ CONFIG_ROWS = [
 # Load-bound rows (T_io > T_c) that pin the overlap law of Eq. 7: c_alpha = 0.9.
 LOAD_BOUND_ROWS = [dict(M=4096, N=4096, K=4096, BM=128, BN=64, BK=128, stages=s, cta_group=1, dtype=1)
                    for s in (4, 6)]
+# Rows whose 256 x 256 accumulator fills the TMEM columns (one buffer): they
+# pin the measured reading's drain term (one SM and a CTA pair, BF16 and FP8).
+SINGLE_BUFFER_ROWS = [dict(M=8192, N=8192, K=8192, BM=256, BN=256, BK=64, stages=3, cta_group=1, dtype=1),
+                      dict(M=8192, N=8192, K=8192, BM=256, BN=256, BK=128, stages=3, cta_group=1, dtype=2),
+                      dict(M=8192, N=8192, K=8192, BM=256, BN=256, BK=64, stages=4, cta_group=2, dtype=1)]
 
 
 def row_time(th, n_sm, reading, row):
@@ -170,11 +183,13 @@ def row_time(th, n_sm, reading, row):
 def compute():
     n_sm = 160
     out = dict(n_sm=n_sm, f_hz=1.9e9, config_rows=CONFIG_ROWS, load_bound_rows=LOAD_BOUND_ROWS,
-               prior={}, config_times={}, load_bound_times={}, load_bound_times_no_blend={})
+               single_buffer_rows=SINGLE_BUFFER_ROWS, prior={}, config_times={}, load_bound_times={},
+               load_bound_times_no_blend={}, single_buffer_times={})
     for reading, name in ((LITERAL, "literal"), (MEASURED, "measured")):
         th = printed_prior(n_sm, reading=reading)
         out["prior"][name] = th
         out["config_times"][name] = [row_time(th, n_sm, reading, r) for r in CONFIG_ROWS]
+        out["single_buffer_times"][name] = [row_time(th, n_sm, reading, r) for r in SINGLE_BUFFER_ROWS]
         lb = list(th)
         lb[15] = 0.9
         out["load_bound_times"][name] = [row_time(lb, n_sm, reading, r) for r in LOAD_BOUND_ROWS]

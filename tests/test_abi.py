@@ -42,7 +42,7 @@ def test_library_exports_every_declared_symbol(pm):
 
 def test_struct_layouts(pm):
     assert ctypes.sizeof(pm.pm_cfg) == 24 == pm.CFG_DTYPE.itemsize
-    assert ctypes.sizeof(pm.pm_params) == 4 * pm.N_PARAMS == 68
+    assert ctypes.sizeof(pm.pm_params) == 4 * pm.N_PARAMS == 72
     assert pm.SEGMENT_DTYPE.itemsize == 64 and ctypes.sizeof(pm.pm_segment_params) == 8 * pm.N_PSI == 136
     assert pm.pm_version() == 10000
     assert pm._lib.pm_shutdown() == pm.PM_OK                 # nothing created yet: nothing to release

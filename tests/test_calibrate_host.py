@@ -61,10 +61,10 @@ def test_prior_matches_oracle_prior(r):
 # Parameters the table does not determine one by one at the generating
 # point: TMEM read and write bandwidth enter every strategy-A K-step only as
 # D (1/BW_rd + 1/BW_wr) (Eq. 2), so only that sum is fixed; the literal
-# reading does not use rho_L2; under the measured reading the ring bound of
-# Eq. 8 sets every K-step of the table at the printed priors, so alpha's
-# c_alpha (Eq. 7) is not seen at all.
-UNIDENTIFIABLE = {0: {10, 11, 16}, 1: {10, 11, 15}}
+# reading uses neither rho_L2 nor B_drain; under the measured reading the
+# ring bound of Eq. 8 sets every K-step of the table at the printed priors,
+# so alpha's c_alpha (Eq. 7) is not seen at all.
+UNIDENTIFIABLE = {0: {10, 11, 16, 17}, 1: {10, 11, 15}}
 
 
 def identifiable(cols, theta):

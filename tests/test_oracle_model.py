@@ -16,7 +16,7 @@ import pytest
 import oracle as O
 import synthetic as S
 
-FIELDS = ("M", "N", "K", "BM", "BN", "BK", "stages", "cta_group", "dtype", "kind")
+FIELDS = ("M", "N", "K", "BM", "BN", "BK", "stages", "cta_group", "dtype", "kind", "tmem_a")
 
 
 def cfgs(rows):
@@ -82,6 +82,49 @@ def test_hand_evaluated_load_bound_rows(reading, i):
     assert one(th, **LOAD_BOUND_ROWS[i]) == pytest.approx(HAND_LOAD_BOUND[reading][i], rel=1e-12)
     th[3] = 0.0
     assert one(th, **LOAD_BOUND_ROWS[i]) == pytest.approx(HAND_LOAD_BOUND_NO_BLEND[reading][i], rel=1e-12)
+
+
+SINGLE_BUFFER_ROWS = HAND["single_buffer_rows"]
+
+
+@pytest.mark.parametrize("i", range(3))
+def test_hand_evaluated_single_buffer_rows(reading, i):
+    # 256 x 256 accumulators fill the 512 TMEM columns: under the measured
+    # reading each tile's drain is paid before the next tile (hand script)
+    th = PRIOR160 if reading == 0 else PRIOR160_MEASURED
+    expect = HAND["single_buffer_times"]["literal" if reading == 0 else "measured"][i]
+    assert one(th, **SINGLE_BUFFER_ROWS[i]) == pytest.approx(expect, rel=1e-12)
+
+
+def test_single_buffer_drain_closed_form(reading):
+    # Measured reading: a launch that keeps one accumulator buffer pays
+    # 4 BM BN / B_drain per tile, so with the stage branch binding its time
+    # exceeds the same launch at an unbounded drain rate by exactly
+    # waves * 4 BM BN / B_drain; a double-buffered launch and the literal
+    # reading do not depend on B_drain at all.
+    th = PRIOR160_MEASURED.copy() if reading == 1 else PRIOR160.copy()
+    fast = th.copy()
+    fast[17] = 1e30
+    single = dict(M=4096, N=4096, K=2048, BM=256, BN=256, BK=64, stages=3, cta_group=1, dtype=1)
+    double = dict(M=4096, N=4096, K=2048, BM=128, BN=256, BK=64, stages=3, cta_group=1, dtype=1)
+    tiles = 16 * 16
+    waves = -(-tiles // 160)
+    d_single = one(th, **single) - one(fast, **single)
+    d_double = one(th, **double) - one(fast, **double)
+    if reading == 1:
+        assert d_single == pytest.approx(waves * 4.0 * 256 * 256 / th[17], rel=1e-9)
+    else:
+        assert d_single == 0.0
+    assert d_double == 0.0
+    # the buffering rule of the kernel: two accumulators of ceil(BM/128) BN
+    # columns (BN/2 for 64 rows per CTA of a pair) in 512 columns, plus a
+    # strategy-B ring of A copies; a pair of 256-row CTAs is single-buffered
+    pair = dict(single, cta_group=2)
+    b_ring = dict(M=4096, N=4096, K=2048, BM=128, BN=256, BK=64, stages=4, cta_group=1, dtype=1, tmem_a=1)
+    b_small = dict(b_ring, BN=64)
+    for row, is_single in ((pair, True), (b_ring, True), (b_small, False)):
+        d = one(th, **row) - one(fast, **row)
+        assert (d > 0) == (is_single and reading == 1), row
 
 
 def test_l2_residency_of_tma_loads_closed_form(reading):
@@ -386,8 +429,16 @@ def test_grouped_schedule_lists_largest_tiles_first(reading):
     assert order == [3, 1, 2, 0, 4]
     busy = [0.0] * n_sm
     k = 0
+    # the 256 x 256 group fills the TMEM columns, so the whole launch keeps one
+    # accumulator buffer: under the measured reading every group's tile then
+    # pays its drain, which its own one-group launch (two buffers) does not
+    launch_single = any(2 * (-(-a // 128)) * b > 512 for a, b in zip(BMg, BNg))
+    assert launch_single
     for q in order:
         tau = O.grouped_predict([BMg[q]], N, K, [BMg[q]], [BNg[q]], 64, 4, 1, 1, th, 10 ** 6) - launch_time(th)
+        own_single = 2 * (-(-BMg[q] // 128)) * BNg[q] > 512
+        if O.reading() == O.READING_MEASURED and not own_single:
+            tau += 4.0 * BMg[q] * BNg[q] / th[17]
         for _ in range(int(np.ceil(Mg[q] / BMg[q])) * int(np.ceil(N / BNg[q]))):
             busy[_dealt_worker(k, n_sm, True)] += tau
             k += 1

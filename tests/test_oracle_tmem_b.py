@@ -93,6 +93,7 @@ def test_strategy_b_equals_a_at_unbounded_tmem_bandwidth(reading):
     th = PRIOR160.copy()
     th[10] = th[11] = 1e30
     th[9] = 0.0                                        # and free tensor-pipe instructions
+    th[17] = 1e30                                      # and a free drain: B's A ring can leave one buffer
     rows = []
     for dt in (0, 1, 2):
         for t in S.tile_space(dt):
