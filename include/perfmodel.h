@@ -344,7 +344,7 @@ pm_status pm_gemm_autotune(const pm_cfg* shape, int32_t k, const pm_params* thet
  * fixed device-memory budget).  The paper has no counterpart: this is an
  * interface convenience of this library.  Same inputs and output as
  * pm_model_grad, minus the workspace: the per-block partial sums go to a
- * fixed 589,824-byte array inside the library, present on every GPU that
+ * fixed 622,592-byte array inside the library, present on every GPU that
  * loads it until the process exits.  At most 1,048,576 configurations per
  * call; larger n returns PM_ENOMEM with a message and launches nothing.
  * It launches the same grid as pm_model_grad, so its output is bit-identical

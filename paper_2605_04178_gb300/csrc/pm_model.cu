@@ -1333,7 +1333,7 @@ extern "C" pm_status pm_grouped_gemm_autotune(int32_t G, const int32_t* M_host, 
 // Capacity: the call launches the same grid as pm_model_grad (grad_blocks(n):
 // at most four blocks per SM, one partial record of NREC doubles each), so its
 // partial sums are added in the same order and its output is bit-identical to
-// pm_model_grad's.  The array holds kGradStaticRecords records (589,824
+// pm_model_grad's.  The array holds kGradStaticRecords records (622,592
 // bytes), enough for GPUs of up to 1024 SMs; batches are limited to
 // kGradStaticRecords * kGradThreads = 1,048,576 configurations per call.
 // Every record a call reads is first written by that call, so nothing has to
