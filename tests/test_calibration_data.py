@@ -29,10 +29,11 @@ def _load(name):
         return json.load(f)
 
 
-def _theta():
-    with open(os.path.join(ROOT, "paper_2605_04178_gb300", "theta_gb300.json")) as f:
+def _theta(reading=O.READING_MEASURED):
+    name = "theta_gb300.json" if reading == O.READING_MEASURED else "theta_gb300_literal.json"
+    with open(os.path.join(ROOT, "paper_2605_04178_gb300", name)) as f:
         meta = json.load(f)
-    assert meta["reading"] == O.READING_MEASURED
+    assert meta["reading"] == reading
     th = np.array(meta["theta"], dtype=np.float64)
     assert th.size == O.N_PARAMS
     return th
@@ -77,6 +78,7 @@ def measured_reading():
 def test_theta_reproduces_its_report(measured_reading):
     th = _theta()
     report = _load("calib_report_gb300.json")
+    assert report["reading"] == O.READING_MEASURED
     assert np.allclose(report["theta"], th, rtol=1e-12, atol=0)
     got = _mae_by_family(_load("sweep_gb300.json"), th)
     for fam, v in report["mae_all"].items():
@@ -90,3 +92,18 @@ def test_theta_predicts_the_second_box(measured_reading):
     assert other["all"] <= 6.5
     for fam in own:
         assert abs(other[fam] - own[fam]) <= 1.0, (fam, own[fam], other[fam])
+
+
+def test_literal_theta_reproduces_its_report():
+    prev = O.reading()
+    O.set_reading(O.READING_LITERAL)
+    try:
+        th = _theta(O.READING_LITERAL)
+        report = _load("calib_report_gb300_literal.json")
+        assert report["reading"] == O.READING_LITERAL
+        assert np.allclose(report["theta"], th, rtol=1e-12, atol=0)
+        got = _mae_by_family(_load("sweep_gb300.json"), th)
+        for fam, v in report["mae_all"].items():
+            assert got[fam] == pytest.approx(v["mae_pct"], abs=0.05), fam
+    finally:
+        O.set_reading(prev)
